@@ -1,0 +1,228 @@
+/*
+ * mala.h -- C ABI of the GB300 (sm_103a) MALA inference hot path.
+ *
+ * The library computes, for every point of a real-space grid, the SNAP-style
+ * bispectrum descriptors of the atoms within a cutoff (paper Sec. "Bispectrum
+ * descriptors", Eqs. ionicdensity, SNAPExpansion, snap_dim), feeds them through
+ * a per-point feed-forward network (Sec. "Machine learning with neural
+ * networks", Eq. ffnn) to the local density of states (LDOS) on N_E energies,
+ * and integrates the LDOS into the density of states D(e) (Eq. DOS.from.ldos),
+ * the Fermi level (root of the electron-count equation, Sec. "Observable
+ * calculation"), the band energy (Eq. band.energy) and the electronic density
+ * n(r) (Eq. density.from.ldos), with the energy integrals evaluated as weighted
+ * sums (Eqs. ldosintegralgeneral, ldosintegralsummation, fermidiracspecial).
+ *
+ * Conventions shared by every entry point
+ *   - Status: every call returns MALA_OK (0), MALA_PENDING (1) or a negative
+ *     MALA_ERR_* code and never aborts; mala_last_error() gives a message for
+ *     the calling thread's last non-OK status.  Nothing throws across the ABI.
+ *   - Units: Angstrom for lengths, eV for energies.
+ *   - Grid: point (ix, iy, iz) of an orthorhombic cell with side lengths
+ *     L = diag(cell) sits at ((ix/Nx) Lx, (iy/Ny) Ly, (iz/Nz) Lz); its flat
+ *     index is p = ix + Nx (iy + Ny iz); P = Nx Ny Nz.  Only orthorhombic
+ *     cells are accepted (MALA_ERR_UNSUPPORTED otherwise).
+ *   - Host vs device: pointers documented as "host" are read during the call
+ *     and may be freed on return; "device" pointers must be device memory of
+ *     the context's GPU, written in stream order on `stream`.
+ *   - stream: a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Calls that return host results (fermi, band energy, D(e)) synchronise
+ *     that stream before returning.
+ *   - Precision: MALA_MIXED computes descriptors in FP32 (compensated sum over
+ *     neighbours), the network in BF16 on the tensor cores with FP32
+ *     accumulation, and the Fermi level, weights and energy reductions in FP64;
+ *     MALA_FP64_PLAIN computes every step in FP64 on the GPU.
+ */
+#ifndef MALA_H
+#define MALA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MALA_OK 0
+#define MALA_PENDING 1
+#define MALA_ERR_INVALID_ARG (-1)
+#define MALA_ERR_OOM (-2)          /* allocation failed or the context's HBM budget is exceeded */
+#define MALA_ERR_UNSUPPORTED (-3)  /* valid input outside what this build handles */
+#define MALA_ERR_FERMI_BRACKET (-4)/* N(mu) - N_e has no sign change on the bracket */
+#define MALA_ERR_TIMEOUT (-5)      /* a bounded device or host wait ran out */
+#define MALA_ERR_CUDA (-6)         /* a CUDA runtime/driver call failed */
+#define MALA_ERR_NOT_FOUND (-7)    /* unknown ticket */
+
+typedef enum { MALA_FP64_PLAIN = 0, MALA_MIXED = 1 } mala_precision;
+
+typedef struct mala_ctx mala_ctx;
+typedef struct mala_model mala_model;
+
+/* One atomic configuration (host memory).  species may be NULL (all 0). */
+typedef struct {
+    int32_t n_atoms;
+    const double* pos;       /* host [n_atoms][3], Cartesian */
+    const int32_t* species;  /* host [n_atoms], values 0..n_species-1, or NULL */
+    double cell[3][3];       /* rows are the lattice vectors; must be diagonal */
+    int32_t grid[3];         /* Nx, Ny, Nz >= 1 */
+    int32_t periodic[3];     /* 1 = periodic along that axis, 0 = open */
+} mala_snapshot;
+
+/* Descriptor hyperparameters.  f_c(r) = (cos(pi (r-rmin0)/(rcut-rmin0)) + 1)/2,
+ * omega = rfac0 pi (r-rmin0)/(rcut-rmin0); wself is the weight of the delta(0)
+ * self term of Eq. (ionicdensity); weights[s] is the element weight w_eta of
+ * species s (NULL: 1 for every species).  twojmax must be even and <= 10. */
+typedef struct {
+    int32_t twojmax;
+    double rcut, rfac0, rmin0, wself;
+    int32_t n_species;
+    const double* weights;   /* host [n_species] or NULL */
+} mala_bispectrum_params;
+
+/* Feed-forward network x_{l+1} = act(W_l x_l + b_l), Eq. (ffnn); act is
+ * LeakyReLU(leaky_slope) on hidden layers and the identity on the output layer
+ * (activate_output = 1 applies it there too).  Optional input standardisation
+ * x0 = (B - in_shift) * in_scale.  All arrays are host FP64. */
+typedef struct {
+    int32_t n_layers;             /* >= 1 */
+    const int32_t* dims;          /* host [n_layers + 1]; dims[0] = n_B, dims[n_layers] = N_E */
+    const double* const* W;       /* host, W[l] is [dims[l+1]][dims[l]] row-major */
+    const double* const* b;       /* host, b[l] is [dims[l+1]] */
+    double leaky_slope;
+    int32_t activate_output;
+    const double* in_shift;       /* host [dims[0]] or NULL */
+    const double* in_scale;       /* host [dims[0]] or NULL */
+} mala_mlp_desc;
+
+/* Energy grid e_xi = e0 + xi de (xi = 0..n_E-1), electronic temperature kT and
+ * electron count N_e for the Fermi level. */
+typedef struct {
+    int32_t n_E;
+    double e0_eV, de_eV, kT_eV, n_electrons;
+} mala_energy_grid;
+
+/* Results of a whole prediction (mala_predict, mala_poll). */
+typedef struct {
+    int32_t status;              /* MALA_OK or an error of that request */
+    int32_t n_B, n_E;
+    int64_t n_points;
+    double fermi_eV;             /* Fermi level */
+    double band_energy_eV;       /* E_b = sum_xi w1_xi(eF) D_xi */
+    double electron_count;       /* dV sum_r n(r), FP64 */
+    const double* dos;           /* host [n_E]: D(e_xi), owned by the library */
+    const void* B_dev;           /* device [P][n_B] (float for MIXED, double for FP64_PLAIN) */
+    const void* ldos_dev;        /* device [P][n_E] (bf16 for MIXED, double for FP64_PLAIN) */
+    const void* density_dev;     /* device [P] (float for MIXED, double for FP64_PLAIN) */
+    double submit_to_done_s;     /* serving latency (mala_poll only) */
+} mala_result;
+
+/* ---- context ------------------------------------------------------------ */
+
+/* Create a context on CUDA device `device`.  hbm_budget_bytes caps the device
+ * memory the context allocates for its own workspaces (0 = no cap); requests
+ * that would exceed it fail with MALA_ERR_OOM.  The context owns its streams,
+ * the Clebsch-Gordan tables and its workspaces. */
+int mala_create(mala_ctx** out, int device, size_t hbm_budget_bytes);
+void mala_destroy(mala_ctx* ctx);
+const char* mala_last_error(void);
+int mala_version(void);
+/* Bytes of device memory the context currently holds. */
+size_t mala_device_bytes(const mala_ctx* ctx);
+
+/* Per-kernel timing.  mala_profile(ctx, 1) clears the totals and makes the
+ * library bracket each of its kernel launches with CUDA events recorded on the
+ * stream the kernel is launched on; mala_profile(ctx, 0) stops recording.
+ * mala_profile_get waits for the recorded events and returns the summed
+ * duration (ms) and the number of launches of the named kernel ("k_neighbors",
+ * "k_ui", "k_zb", "k_mlp", "k_dos_reduce", "k_fermi", "k_density"). */
+int mala_profile(mala_ctx* ctx, int enable);
+int mala_profile_get(mala_ctx* ctx, const char* kernel, double* total_ms, int64_t* launches);
+
+/* ---- network ---------------------------------------------------------- */
+
+/* Upload a network once (BF16 copies for MALA_MIXED, FP64 for MALA_FP64_PLAIN);
+ * the descriptor arrays may be freed on return. */
+int mala_model_create(mala_ctx* ctx, const mala_mlp_desc* desc, mala_model** out);
+void mala_model_destroy(mala_model* model);
+
+/* ---- the hot path, one step at a time ----------------------------------- */
+
+/* Neighbour lists of every grid point (Eq. ionicdensity: |R_a + s L - r| < rcut,
+ * strict, over all periodic images s).  Membership is decided in FP64 exactly
+ * as (x_a + s L) - r rounded without fused multiply-add where FP32 cannot
+ * decide it.  Outputs (device, point-major): counts[P]; atoms[P][cap] and
+ * shifts[P][cap][3] (image shift s) for the first min(count, cap) neighbours in
+ * an unspecified order.  *max_count (host) receives the largest count. */
+int mala_neighbor_lists(mala_ctx* ctx, const mala_snapshot* snap, double rcut, int32_t cap,
+                        int32_t* counts_dev, int32_t* atoms_dev, int32_t* shifts_dev,
+                        int32_t* max_count, void* stream);
+
+/* Bispectrum descriptors B[P][n_B] (device; float for MALA_MIXED, double for
+ * MALA_FP64_PLAIN) with n_B = (twojmax+2)(twojmax+3)(twojmax+4)/24, component
+ * order lexicographic in (J1, J2, J) over 0 <= J2 <= J1 <= J <= twojmax,
+ * J1+J2+J even, |J1-J2| <= J <= J1+J2 (Eq. snap_dim). */
+int mala_descriptors(mala_ctx* ctx, const mala_snapshot* snap, const mala_bispectrum_params* bp,
+                     void* B_dev, mala_precision precision, void* stream);
+
+/* Expansion coefficients u^J of Eq. (SNAPExpansion) for every grid point,
+ * J = 0..twojmax, device complex output u_dev[P][sum_J (J+1)^2][2] (row-major
+ * [ma][mb] blocks in increasing J; float for MIXED, double for FP64_PLAIN). */
+int mala_expansion_coefficients(mala_ctx* ctx, const mala_snapshot* snap,
+                                const mala_bispectrum_params* bp, void* u_dev,
+                                mala_precision precision, void* stream);
+
+/* LDOS[P][N_E] = network(B) (device; bf16 for MALA_MIXED, double for
+ * MALA_FP64_PLAIN).  B_dev as written by mala_descriptors with the same
+ * precision.  dos_sum_dev (device double [N_E], may be NULL) receives the
+ * column sums sum_r LDOS(r, xi) of the values written to ldos_dev. */
+int mala_ldos_forward(mala_ctx* ctx, const mala_model* model, const void* B_dev, int64_t P,
+                      void* ldos_dev, double* dos_sum_dev, mala_precision precision, void* stream);
+
+/* Energy integrals of an LDOS[P][N_E] (device, bf16 for MIXED, double for
+ * FP64_PLAIN) on a cell of volume cell_volume: D_xi = dV sum_r LDOS(r, xi)
+ * with dV = cell_volume / P; the Fermi level by FP64 bisection of
+ * N(mu) = sum_xi w0_xi(mu) D_xi - N_e on [e_0 - 20 kT, e_max + 20 kT] down to a
+ * width of 1e-12 eV (at most 200 halvings); the band energy sum_xi w1_xi D_xi;
+ * the density n(r) = sum_xi w0_xi(eF) LDOS(r, xi) into density_dev (device
+ * [P], float for MIXED, double for FP64_PLAIN).  w0/w1 are the exact integrals
+ * of the piecewise-linear interpolant times e^0 / e^1 times the Fermi function,
+ * in closed form through Li2/Li3.  dos_sum_dev (device [N_E], may be NULL)
+ * supplies precomputed column sums (mala_ldos_forward's); otherwise they are
+ * computed from ldos_dev.  Host outputs (any may be NULL): dos_host[N_E],
+ * fermi_eV, band_energy_eV, electron_count (dV sum_r n(r) in FP64). */
+int mala_integrate(mala_ctx* ctx, const void* ldos_dev, int64_t P, double cell_volume,
+                   const mala_energy_grid* eg, const double* dos_sum_dev, void* density_dev,
+                   double* dos_host, double* fermi_eV, double* band_energy_eV,
+                   double* electron_count, mala_precision precision, void* stream);
+
+/* ---- the whole path ----------------------------------------------------- */
+
+/* Descriptors -> LDOS -> integrals for one snapshot.  Intermediate B and LDOS
+ * live in the context's workspace; result->B_dev / ldos_dev / density_dev point
+ * into it and stay valid until the next call on this context.
+ * density_host (host [P], float for MIXED, double for FP64_PLAIN; may be NULL)
+ * receives a copy of n(r).  Synchronises `stream`. */
+int mala_predict(mala_ctx* ctx, const mala_snapshot* snap, const mala_bispectrum_params* bp,
+                 const mala_model* model, const mala_energy_grid* eg, mala_precision precision,
+                 void* density_host, mala_result* result, void* stream);
+
+/* ---- serving ------------------------------------------------------------ */
+
+/* Queue a prediction.  The library copies every input (the caller may free
+ * them on return), admits the request when its device memory fits in the
+ * budget, and runs it on the GPU concurrently with other admitted requests.
+ * Non-blocking; *ticket identifies the request. */
+int mala_submit(mala_ctx* ctx, const mala_snapshot* snap, const mala_bispectrum_params* bp,
+                const mala_model* model, const mala_energy_grid* eg, mala_precision precision,
+                uint64_t* ticket);
+/* MALA_PENDING while the request runs, MALA_OK when *out is filled (device
+ * pointers stay valid until mala_release), or the request's error. */
+int mala_poll(mala_ctx* ctx, uint64_t ticket, mala_result* out);
+/* Block until the ticket completes or timeout_s passes (MALA_ERR_TIMEOUT). */
+int mala_wait(mala_ctx* ctx, uint64_t ticket, double timeout_s, mala_result* out);
+/* Free the device outputs of a completed request. */
+int mala_release(mala_ctx* ctx, uint64_t ticket);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MALA_H */

@@ -1,0 +1,335 @@
+// mala_abi.cu -- the C ABI declared in include/mala.h: context, error
+// reporting, workspaces and the descriptor step (neighbour lists, u, B).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+
+#include "mala_internal.h"
+#include "snap_common.cuh"
+
+namespace mala {
+
+static thread_local char g_err[1024] = "";
+
+void set_error(const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+int fail(int code, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+DevBuf::~DevBuf() { release(); }
+
+void DevBuf::release() {
+    if (ptr) {
+        cudaFree(ptr);
+        if (owner) owner->used -= bytes;
+    }
+    ptr = nullptr;
+    bytes = 0;
+}
+
+int DevBuf::reserve(Ctx* ctx, size_t n) {
+    if (n <= bytes && ptr) return MALA_OK;
+    release();
+    owner = ctx;
+    if (n == 0) return MALA_OK;
+    if (ctx->budget && ctx->used + n > ctx->budget)
+        return fail(MALA_ERR_OOM, "workspace of %zu bytes exceeds the HBM budget (%zu of %zu in use)", n,
+                    (size_t)ctx->used, ctx->budget);
+    cudaError_t e = cudaMalloc(&ptr, n);
+    if (e != cudaSuccess) {
+        ptr = nullptr;
+        cudaGetLastError();
+        return fail(MALA_ERR_OOM, "cudaMalloc(%zu) failed: %s", n, cudaGetErrorString(e));
+    }
+    bytes = n;
+    ctx->used += n;
+    return MALA_OK;
+}
+
+// ---- validation ---------------------------------------------------------
+
+int check_snapshot(const mala_snapshot* s) {
+    if (!s) return fail(MALA_ERR_INVALID_ARG, "snapshot is NULL");
+    if (s->n_atoms < 0) return fail(MALA_ERR_INVALID_ARG, "n_atoms < 0");
+    if (s->n_atoms > 0 && !s->pos) return fail(MALA_ERR_INVALID_ARG, "positions are NULL");
+    for (int d = 0; d < 3; ++d) {
+        if (s->grid[d] < 1) return fail(MALA_ERR_INVALID_ARG, "grid[%d] = %d < 1", d, s->grid[d]);
+        if (!(s->cell[d][d] > 0.0) || !std::isfinite(s->cell[d][d]))
+            return fail(MALA_ERR_INVALID_ARG, "cell[%d][%d] must be positive and finite", d, d);
+        for (int e = 0; e < 3; ++e)
+            if (e != d && s->cell[d][e] != 0.0)
+                return fail(MALA_ERR_UNSUPPORTED, "only orthorhombic (diagonal) cells are supported");
+    }
+    for (int64_t i = 0; i < 3 * (int64_t)s->n_atoms; ++i)
+        if (!std::isfinite(s->pos[i])) return fail(MALA_ERR_INVALID_ARG, "position %lld is not finite", (long long)i / 3);
+    const double P = (double)s->grid[0] * s->grid[1] * s->grid[2];
+    if (P > 4.0e9) return fail(MALA_ERR_UNSUPPORTED, "grid of %.3g points is too large", P);
+    return MALA_OK;
+}
+
+int check_bparams(const mala_bispectrum_params* bp) {
+    if (!bp) return fail(MALA_ERR_INVALID_ARG, "bispectrum params are NULL");
+    if (bp->twojmax < 0 || (bp->twojmax & 1) || bp->twojmax > kTJMax)
+        return fail(MALA_ERR_UNSUPPORTED, "twojmax = %d: this build supports even values 0..%d", bp->twojmax, kTJMax);
+    if (!(bp->rcut > 0.0) || !std::isfinite(bp->rcut)) return fail(MALA_ERR_INVALID_ARG, "rcut must be > 0");
+    if (!(bp->rmin0 >= 0.0) || !(bp->rmin0 < bp->rcut)) return fail(MALA_ERR_INVALID_ARG, "need 0 <= rmin0 < rcut");
+    if (!std::isfinite(bp->rfac0) || !std::isfinite(bp->wself)) return fail(MALA_ERR_INVALID_ARG, "rfac0/wself not finite");
+    if (bp->weights && bp->n_species < 1) return fail(MALA_ERR_INVALID_ARG, "weights given with n_species < 1");
+    return MALA_OK;
+}
+
+static cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// ---- descriptor step ------------------------------------------------------
+
+// Run neighbour search + compute_ui + compute_zi/bi over the snapshot in
+// chunks of tiles.  B (device, [P][nB]) and/or u_full (device,
+// [P][n_full][2]) may be NULL.  dbg: optional neighbour-list output.
+template <class T>
+static int run_descriptors(Ctx* c, const mala_snapshot* snap, const mala_bispectrum_params* bp, T* B, T* u_full,
+                           NbrOut* dbg, cudaStream_t st) {
+    SnapDev sd;
+    MALA_TRY(stage_snapshot(c, snap, bp, bp->rcut, &sd, st));
+    const SnapGeom& g = sd.g;
+    const int tj = bp->twojmax;
+    const int nh = n_half(tj);
+    int kmax = c->kmax_hint;
+    for (int attempt = 0; attempt < 3; ++attempt) {
+        const size_t per_tile = (size_t)nh * 32 * 2 * sizeof(T) + (size_t)kmax * 32 * (5 * sizeof(T)) + 32 * sizeof(int);
+        const size_t chunk_budget = (size_t)4 << 30;
+        int64_t chunk = (int64_t)(chunk_budget / per_tile);
+        if (chunk < 1) chunk = 1;
+        if (chunk > g.n_tiles) chunk = g.n_tiles;
+        MALA_TRY(c->ws_u.reserve(c, (size_t)chunk * nh * 32 * 2 * sizeof(T)));
+        MALA_TRY(c->ws_nbr_ab.reserve(c, (size_t)chunk * kmax * 32 * 4 * sizeof(T)));
+        MALA_TRY(c->ws_nbr_c.reserve(c, (size_t)chunk * kmax * 32 * sizeof(T)));
+        MALA_TRY(c->ws_nbr_cnt.reserve(c, (size_t)chunk * 32 * sizeof(int)));
+        NbrOut nb;
+        nb.ab = c->ws_nbr_ab.ptr;
+        nb.cw = c->ws_nbr_c.ptr;
+        nb.cnt = c->ws_nbr_cnt.as<int>();
+        nb.kmax = kmax;
+        if (dbg) {
+            nb.dbg_atoms = dbg->dbg_atoms;
+            nb.dbg_shifts = dbg->dbg_shifts;
+            nb.dbg_counts = dbg->dbg_counts;
+            nb.dbg_cap = dbg->dbg_cap;
+        }
+        MALA_CUDA_TRY(cudaMemsetAsync(sd.maxcnt, 0, sizeof(int), st));
+        for (int64_t t0 = 0; t0 < g.n_tiles; t0 += chunk) {
+            const int64_t nt = (g.n_tiles - t0) < chunk ? (g.n_tiles - t0) : chunk;
+            if (sizeof(T) == 4)
+                MALA_PROF(c, "k_neighbors", st, launch_neighbors(sd, bp->rcut, bp->rfac0, bp->rmin0, t0, nt, nb, st));
+            else
+                MALA_PROF(c, "k_neighbors", st, launch_neighbors_f64(sd, bp->rcut, bp->rfac0, bp->rmin0, t0, nt, nb, st));
+            if (B || u_full) {
+                T* uh = c->ws_u.as<T>();
+                MALA_PROF(c, "k_ui", st, launch_ui<T>(tj, nb, bp->wself, nt, uh, st));
+                if (B) MALA_PROF(c, "k_zb", st, launch_zb<T>(c, tj, uh, g, t0, nt, B, st));
+                if (u_full) launch_u_expand<T>(tj, uh, g, t0, nt, u_full, st);
+            }
+        }
+        MALA_CUDA_TRY(cudaGetLastError());
+        MALA_CUDA_TRY(cudaMemcpyAsync(c->host_ints, sd.maxcnt, sizeof(int) * 2, cudaMemcpyDeviceToHost, st));
+        MALA_CUDA_TRY(cudaMemcpyAsync(c->host_ints + 2, c->tables.err_d, sizeof(int), cudaMemcpyDeviceToHost, st));
+        MALA_CUDA_TRY(cudaStreamSynchronize(st));
+        if (c->host_ints[1]) return fail(MALA_ERR_INVALID_ARG, "species index outside 0..n_species-1");
+        if (c->host_ints[2]) {
+            cudaMemsetAsync(c->tables.err_d, 0, sizeof(int), st);
+            return fail(MALA_ERR_UNSUPPORTED, "a bispectrum partial sum exceeded 1e9 (outside the fixed-point range)");
+        }
+        const int maxcnt = c->host_ints[0];
+        if (dbg) dbg->kmax = maxcnt;
+        if (maxcnt <= kmax) {
+            if (maxcnt > c->kmax_hint) c->kmax_hint = maxcnt;
+            return MALA_OK;
+        }
+        kmax = (maxcnt + 7) & ~7;
+        c->kmax_hint = kmax;
+    }
+    return fail(MALA_ERR_UNSUPPORTED, "neighbour capacity could not be established");
+}
+
+int snap_descriptors(Ctx* c, const mala_snapshot* snap, const mala_bispectrum_params* bp, void* B, void* u_full,
+                     mala_precision prec, cudaStream_t st) {
+    if (prec == MALA_MIXED) return run_descriptors<float>(c, snap, bp, (float*)B, (float*)u_full, nullptr, st);
+    return run_descriptors<double>(c, snap, bp, (double*)B, (double*)u_full, nullptr, st);
+}
+
+// ---- per-kernel event timing ---------------------------------------------
+
+int prof_begin(Ctx* c, const char* name, cudaStream_t st) {
+    if (!c->prof.on) return -1;
+    std::lock_guard<std::mutex> lk(c->prof_mu);
+    Prof::Rec r;
+    r.name = name;
+    for (cudaEvent_t* e : {&r.a, &r.b}) {
+        if (!c->prof.pool.empty()) {
+            *e = c->prof.pool.back();
+            c->prof.pool.pop_back();
+        } else if (cudaEventCreate(e) != cudaSuccess) {
+            return -1;
+        }
+    }
+    cudaEventRecord(r.a, st);
+    c->prof.pending.push_back(r);
+    return (int)c->prof.pending.size() - 1;
+}
+
+void prof_end(Ctx* c, int idx, cudaStream_t st) {
+    if (idx < 0) return;
+    std::lock_guard<std::mutex> lk(c->prof_mu);
+    if (idx < (int)c->prof.pending.size()) cudaEventRecord(c->prof.pending[idx].b, st);
+}
+
+static void prof_collect(Ctx* c) {
+    std::lock_guard<std::mutex> lk(c->prof_mu);
+    for (auto& r : c->prof.pending) {
+        cudaEventSynchronize(r.b);
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+            auto& t = c->prof.total[r.name];
+            t.first += ms;
+            t.second += 1;
+        }
+        c->prof.pool.push_back(r.a);
+        c->prof.pool.push_back(r.b);
+    }
+    c->prof.pending.clear();
+}
+
+}  // namespace mala
+
+using namespace mala;
+
+struct mala_ctx : public mala::Ctx {};
+struct mala_model : public mala::Model {};
+
+extern "C" {
+
+int mala_version(void) { return 1; }
+
+const char* mala_last_error(void) { return mala::g_err; }
+
+int mala_create(mala_ctx** out, int device, size_t hbm_budget_bytes) {
+    if (!out) return fail(MALA_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return fail(MALA_ERR_CUDA, "no CUDA device available: %s", cudaGetErrorString(e));
+    }
+    if (device < 0 || device >= ndev) return fail(MALA_ERR_INVALID_ARG, "device %d out of range", device);
+    MALA_CUDA_TRY(cudaSetDevice(device));
+    cudaDeviceProp prop;
+    MALA_CUDA_TRY(cudaGetDeviceProperties(&prop, device));
+    if (prop.major < 10) return fail(MALA_ERR_UNSUPPORTED, "device %s (sm_%d%d) is not a Blackwell GPU", prop.name, prop.major, prop.minor);
+    auto* c = new mala_ctx();
+    c->device = device;
+    c->budget = hbm_budget_bytes;
+    c->num_sms = prop.multiProcessorCount;
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaMallocHost(&c->host_ints, 64 * sizeof(int)) != cudaSuccess ||
+        cudaMallocHost(&c->host_scalars, 64 * sizeof(double)) != cudaSuccess) {
+        delete c;
+        return fail(MALA_ERR_CUDA, "stream / pinned buffer creation failed");
+    }
+    int rc = upload_cg_tables(c);
+    if (rc != MALA_OK) {
+        mala_destroy(c);
+        return rc;
+    }
+    *out = c;
+    return MALA_OK;
+}
+
+void mala_destroy(mala_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    prof_collect(c);
+    for (cudaEvent_t e : c->prof.pool) cudaEventDestroy(e);
+    if (c->stream) cudaStreamDestroy(c->stream);
+    if (c->host_ints) cudaFreeHost(c->host_ints);
+    if (c->host_scalars) cudaFreeHost(c->host_scalars);
+    if (c->host_dos) cudaFreeHost(c->host_dos);
+    delete c;
+}
+
+size_t mala_device_bytes(const mala_ctx* c) { return c ? (size_t)c->used : 0; }
+
+int mala_profile(mala_ctx* c, int enable) {
+    if (!c) return fail(MALA_ERR_INVALID_ARG, "context is NULL");
+    prof_collect(c);
+    if (enable) c->prof.total.clear();
+    c->prof.on = enable != 0;
+    return MALA_OK;
+}
+
+int mala_profile_get(mala_ctx* c, const char* kernel, double* total_ms, int64_t* launches) {
+    if (!c || !kernel) return fail(MALA_ERR_INVALID_ARG, "bad arguments");
+    prof_collect(c);
+    auto it = c->prof.total.find(kernel);
+    if (total_ms) *total_ms = it == c->prof.total.end() ? 0.0 : it->second.first;
+    if (launches) *launches = it == c->prof.total.end() ? 0 : it->second.second;
+    return MALA_OK;
+}
+
+int mala_neighbor_lists(mala_ctx* c, const mala_snapshot* snap, double rcut, int32_t cap, int32_t* counts_dev,
+                        int32_t* atoms_dev, int32_t* shifts_dev, int32_t* max_count, void* stream) {
+    if (!c) return fail(MALA_ERR_INVALID_ARG, "context is NULL");
+    MALA_TRY(check_snapshot(snap));
+    if (!(rcut > 0.0)) return fail(MALA_ERR_INVALID_ARG, "rcut must be > 0");
+    if (cap < 0 || (cap > 0 && (!atoms_dev || !shifts_dev)) || !counts_dev)
+        return fail(MALA_ERR_INVALID_ARG, "bad neighbour-list output arguments");
+    std::lock_guard<std::mutex> lk(c->mu);
+    MALA_CUDA_TRY(cudaSetDevice(c->device));
+    mala_bispectrum_params bp = {0, rcut, 0.99363, 0.0, 1.0, 0, nullptr};
+    NbrOut dbg;
+    dbg.dbg_atoms = atoms_dev;
+    dbg.dbg_shifts = shifts_dev;
+    dbg.dbg_counts = counts_dev;
+    dbg.dbg_cap = cap;
+    int rc = run_descriptors<float>(c, snap, &bp, nullptr, nullptr, &dbg, as_stream(stream));
+    if (rc == MALA_OK && max_count) *max_count = dbg.kmax;
+    return rc;
+}
+
+int mala_descriptors(mala_ctx* c, const mala_snapshot* snap, const mala_bispectrum_params* bp, void* B_dev,
+                     mala_precision precision, void* stream) {
+    if (!c) return fail(MALA_ERR_INVALID_ARG, "context is NULL");
+    MALA_TRY(check_snapshot(snap));
+    MALA_TRY(check_bparams(bp));
+    if (!B_dev) return fail(MALA_ERR_INVALID_ARG, "B output is NULL");
+    if (precision != MALA_MIXED && precision != MALA_FP64_PLAIN) return fail(MALA_ERR_INVALID_ARG, "bad precision");
+    std::lock_guard<std::mutex> lk(c->mu);
+    MALA_CUDA_TRY(cudaSetDevice(c->device));
+    return snap_descriptors(c, snap, bp, B_dev, nullptr, precision, as_stream(stream));
+}
+
+int mala_expansion_coefficients(mala_ctx* c, const mala_snapshot* snap, const mala_bispectrum_params* bp,
+                                void* u_dev, mala_precision precision, void* stream) {
+    if (!c) return fail(MALA_ERR_INVALID_ARG, "context is NULL");
+    MALA_TRY(check_snapshot(snap));
+    MALA_TRY(check_bparams(bp));
+    if (!u_dev) return fail(MALA_ERR_INVALID_ARG, "u output is NULL");
+    std::lock_guard<std::mutex> lk(c->mu);
+    MALA_CUDA_TRY(cudaSetDevice(c->device));
+    return snap_descriptors(c, snap, bp, nullptr, u_dev, precision, as_stream(stream));
+}
+
+}  // extern "C"

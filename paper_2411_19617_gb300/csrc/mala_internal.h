@@ -1,0 +1,226 @@
+// mala_internal.h -- host-side internals shared by the library's translation
+// units: the context, workspace buffers, error reporting and kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <condition_variable>
+#include <cstdint>
+#include <cstdio>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/mala.h"
+
+namespace mala {
+
+// ---- error reporting ------------------------------------------------------
+
+void set_error(const char* fmt, ...);
+int fail(int code, const char* fmt, ...);
+
+#define MALA_CUDA_TRY(expr)                                                                 \
+    do {                                                                                    \
+        cudaError_t e_ = (expr);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            return ::mala::fail(MALA_ERR_CUDA, "%s failed: %s (%s:%d)", #expr,              \
+                                cudaGetErrorString(e_), __FILE__, __LINE__);                \
+    } while (0)
+
+#define MALA_TRY(expr)              \
+    do {                            \
+        int s_ = (expr);            \
+        if (s_ != MALA_OK) return s_; \
+    } while (0)
+
+// ---- device buffers ---------------------------------------------------------
+
+struct Ctx;
+
+// A growable device buffer accounted against the context's HBM budget.
+struct DevBuf {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+    Ctx* owner = nullptr;
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    ~DevBuf();
+    int reserve(Ctx* ctx, size_t n);  // ensures capacity >= n bytes (contents not kept)
+    void release();
+    template <class T> T* as() const { return static_cast<T*>(ptr); }
+};
+
+// ---- descriptor tables (host-built, uploaded once) -------------------------
+
+struct SnapTables {
+    // global Clebsch-Gordan table (kTJMax numbering), float and double copies
+    std::vector<double> cg;                 // host
+    double* cg_d = nullptr;                 // device double copy
+    // per twojmax: triple ids assigned to each zb warp
+    int zb_warps = 8;
+    std::map<int, std::vector<int16_t>> warp_lists;  // [warps][max_len] with -1 padding
+    std::map<int, int> warp_list_len;
+    // FP32 zb work units (triple, row, m1 row) per supported twojmax (index tj/2)
+    int4* tri_d = nullptr;              // per triple: (global id, first unit, unit count, column)
+    unsigned short* units_d = nullptr;  // ma | m1a << 4
+    int tri_off[8] = {0};
+    int tri_n[8] = {0};
+    int unit_off[8] = {0};
+    int* err_d = nullptr;  // device error flags [8]
+};
+
+// Per-kernel CUDA-event timing on the launching stream (mala_profile).
+struct Prof {
+    bool on = false;
+    struct Rec {
+        const char* name;
+        cudaEvent_t a, b;
+    };
+    std::vector<Rec> pending;
+    std::vector<cudaEvent_t> pool;
+    std::map<std::string, std::pair<double, int64_t>> total;  // name -> (ms, launches)
+};
+int prof_begin(struct Ctx* c, const char* name, cudaStream_t st);
+void prof_end(struct Ctx* c, int idx, cudaStream_t st);
+#define MALA_PROF(c, name, st, stmt)                        \
+    do {                                                    \
+        int pi_ = ::mala::prof_begin((c), (name), (st));    \
+        stmt;                                               \
+        ::mala::prof_end((c), pi_, (st));                   \
+    } while (0)
+
+// Network uploaded for one precision.
+struct Model {
+    Ctx* ctx = nullptr;
+    int n_layers = 0;
+    std::vector<int> dims;
+    float leaky_slope = 0.01f;
+    int activate_output = 0;
+    // MIXED: bf16 weights padded to K multiple of 16 / N multiple of 16, fp32 bias
+    std::vector<void*> Wbf;      // device bf16 [Npad][Kpad] per layer
+    std::vector<float*> bias;    // device fp32 [Npad]
+    std::vector<int> Kpad, Npad;
+    float* in_shift = nullptr;   // device fp32 [dims[0]] (0 if absent)
+    float* in_scale = nullptr;   // device fp32 [dims[0]] (1 if absent)
+    // FP64_PLAIN
+    std::vector<double*> Wd, bd;
+    double* in_shift_d = nullptr;
+    double* in_scale_d = nullptr;
+    size_t bytes = 0;
+};
+
+struct SnapStage;  // per-call staging of one snapshot (atoms, bins, neighbours)
+
+// One queued or running request of the serving loop.
+struct Request;
+
+struct Ctx {
+    int device = 0;
+    size_t budget = 0;  // 0 = unlimited
+    std::atomic<size_t> used{0};
+    cudaStream_t stream = nullptr;  // internal work stream for synchronous helpers
+    SnapTables tables;
+    int num_sms = 0;
+    // workspaces of the synchronous path
+    DevBuf ws_atoms, ws_bins, ws_nbr_ab, ws_nbr_c, ws_nbr_cnt, ws_u, ws_misc, ws_B, ws_ldos,
+        ws_dens, ws_dos, ws_tile_dos, ws_units;
+    double* host_dos = nullptr;     // pinned [max N_E]
+    size_t host_dos_len = 0;
+    double* host_scalars = nullptr; // pinned small buffer
+    int* host_ints = nullptr;       // pinned small buffer
+    std::mutex mu;                  // serialises synchronous calls on this context
+    std::mutex prof_mu;
+    Prof prof;
+    int kmax_hint = 64;             // neighbour capacity that sufficed last time
+    // serving
+    struct Server* server = nullptr;
+};
+
+// ---- kernel launchers (descriptor path) ------------------------------------
+
+struct SnapGeom {
+    int n_atoms;
+    double L[3];
+    int periodic[3];
+    int grid[3];
+    int64_t P;
+    int tiles[3];
+    int64_t n_tiles;
+    int nb[3];        // bins per axis
+    double bs[3];     // bin size per axis
+    int n_bins;
+};
+
+struct SnapDev {
+    SnapGeom g;
+    double* wpos = nullptr;   // [3][n] wrapped positions (SoA)
+    float* wsp = nullptr;     // [n] element weight
+    int* bin_of = nullptr;    // [n]
+    int* bin_start = nullptr; // [n_bins + 1]
+    int* bin_atoms = nullptr; // [n]
+    int* bin_fill = nullptr;  // [n_bins]
+    int* maxcnt = nullptr;    // [4] device counters (max count, overflow flags)
+};
+
+int stage_snapshot(Ctx* c, const mala_snapshot* snap, const mala_bispectrum_params* bp,
+                   double rcut, SnapDev* sd, cudaStream_t st);
+
+// neighbour records of every tile: ab[tile][k][32] float4 (Cayley-Klein a, b),
+// cw[tile][k][32] float (w * f_c), cnt[tile][32]; optional debug output of the
+// atom index / image shift in point-major order.
+struct NbrOut {
+    void* ab = nullptr;   // float4 (MIXED) or double4 (FP64_PLAIN) records
+    void* cw = nullptr;   // float or double
+    int* cnt = nullptr;
+    int kmax = 0;
+    // debug
+    int* dbg_atoms = nullptr;  // [P][dbg_cap]
+    int* dbg_shifts = nullptr; // [P][dbg_cap][3]
+    int* dbg_counts = nullptr; // [P]
+    int dbg_cap = 0;
+};
+
+void launch_neighbors(const SnapDev& sd, double rcut, double rfac0, double rmin0, int64_t tile0,
+                      int64_t ntiles, const NbrOut& out, cudaStream_t st);
+void launch_neighbors_f64(const SnapDev& sd, double rcut, double rfac0, double rmin0, int64_t tile0,
+                          int64_t ntiles, const NbrOut& out, cudaStream_t st);
+
+// u half storage [tile][n_half][32] complex
+template <class T>
+void launch_ui(int twojmax, const NbrOut& nb, double wself, int64_t ntiles, T* u_half, cudaStream_t st);
+
+template <class T>
+void launch_zb(Ctx* c, int twojmax, const T* u_half, const SnapGeom& g, int64_t tile0, int64_t ntiles,
+               T* B, cudaStream_t st);
+template <>
+void launch_zb<float>(Ctx* c, int twojmax, const float* u_half, const SnapGeom& g, int64_t tile0,
+                      int64_t ntiles, float* B, cudaStream_t st);
+template <>
+void launch_zb<double>(Ctx* c, int twojmax, const double* u_half, const SnapGeom& g, int64_t tile0,
+                       int64_t ntiles, double* B, cudaStream_t st);
+
+template <class T>
+void launch_u_expand(int twojmax, const T* u_half, const SnapGeom& g, int64_t tile0, int64_t ntiles,
+                     T* u_full, cudaStream_t st);
+
+int upload_cg_tables(Ctx* c);
+int upload_zb_lists_f64(const int* lists, int bytes);
+int snap_descriptors(Ctx* c, const mala_snapshot* snap, const mala_bispectrum_params* bp, void* B,
+                     void* u_full, mala_precision prec, cudaStream_t st);
+
+// ---- network and integrals ---------------------------------------------------
+
+int mlp_forward(Ctx* c, const Model* m, const void* B, int64_t P, void* ldos, double* dos_sum,
+                mala_precision prec, cudaStream_t st);
+int integrate(Ctx* c, const void* ldos, int64_t P, double volume, const mala_energy_grid* eg,
+              const double* dos_sum, void* density, double* dos_host, double* fermi, double* eb,
+              double* ne, mala_precision prec, cudaStream_t st);
+
+}  // namespace mala

@@ -1,0 +1,312 @@
+// snap_ui.cu -- compute_ui: expansion coefficients u_j of the ionic density
+// (paper Eq. ionicdensity expanded in the hyperspherical harmonics of
+// Eq. SNAPExpansion):
+//     u^J = wself I + sum_k c_k U^J(a_k, b_k),   c_k = w_eta f_c(r_k).
+//
+// U^J of the SU(2) element [[conj a, -conj b], [b, a]] has columns
+//     U^J[.][mb] = N(J, ., mb) * coeffs of (conj(a) xi - conj(b) eta)^(J-mb) (b xi + a eta)^mb
+// (coefficient of xi^(J-ma) eta^ma in row ma, N the normalisation
+// sqrt((J-ma)! ma! / ((J-mb)! mb!))).  A column therefore grows level by level
+// by multiplying a coefficient vector with one linear form:
+//     column mb of level J   = (conj a xi - conj b eta) * column mb of level J-1,
+//     column mb of level 2mb = (b xi + a eta)(conj a xi - conj b eta) * column mb-1 of level 2mb-2.
+// Only columns mb <= J/2 are generated; the others follow from
+// U[J-ma][J-mb] = (-1)^(ma-mb) conj(U[ma][mb]).
+//
+// Mapping: one warp per tile of 32 grid points, lane = point.  The elements
+// are split into "segments" (one column chain over a range of levels) small
+// enough that their sums and Kahan compensations stay in registers; each
+// segment loops over the lane's neighbours, rebuilding its column from the
+// seed, and accumulates c_k * coefficient with compensated (Kahan) summation.
+// The normalisation N and the self term are applied once at the end.  Output:
+// the half set of u (rows ma < J/2, plus the middle row's columns <= J/2 for
+// even J) in [tile][element][lane] layout.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "mala_internal.h"
+#include "snap_common.cuh"
+
+namespace mala {
+
+namespace {
+
+constexpr int kSegElemsF32 = 24;  // sums + compensations of 24 complex numbers: 96 registers
+constexpr int kSegElemsF64 = 10;
+
+struct Seg {
+    int mb, l0, l1;
+};
+struct SegPlan {
+    Seg s[64];
+    int n;
+};
+
+__host__ __device__ constexpr int seg_level_elems(int mb, int J) { return (2 * mb == J) ? mb + 1 : J + 1; }
+__host__ __device__ constexpr int seg_offset(int mb, int l0, int J) {
+    int o = 0;
+    for (int k = l0; k < J; ++k) o += seg_level_elems(mb, k);
+    return o;
+}
+
+__host__ __device__ constexpr SegPlan make_plan(int tj, int emax) {
+    SegPlan p{};
+    p.n = 0;
+    for (int mb = 0; 2 * mb <= tj; ++mb) {
+        int l0 = 2 * mb, acc = 0;
+        for (int J = 2 * mb; J <= tj; ++J) {
+            const int e = seg_level_elems(mb, J);
+            if (acc > 0 && acc + e > emax) {
+                p.s[p.n] = Seg{mb, l0, J - 1};
+                ++p.n;
+                l0 = J;
+                acc = 0;
+            }
+            acc += e;
+        }
+        p.s[p.n] = Seg{mb, l0, tj};
+        ++p.n;
+    }
+    return p;
+}
+
+template <class T, int TJ> struct Plan {
+    static constexpr SegPlan value = make_plan(TJ, sizeof(T) == 4 ? kSegElemsF32 : kSegElemsF64);
+};
+
+template <class T> struct C2;
+template <> struct C2<float> { using type = float2; };
+template <> struct C2<double> { using type = double2; };
+template <class T> struct AB4;
+template <> struct AB4<float> { using type = float4; };
+template <> struct AB4<double> { using type = double4; };
+
+// v <- (alpha xi + beta eta) v for a coefficient vector of length n
+// (-> n + 1); alpha = (alr, ali), beta = (ber, bei).  n must be a
+// compile-time constant after unrolling so that v stays in registers.
+template <class T>
+__device__ __forceinline__ void mul_linear(T (&vr)[kTJMax + 1], T (&vi)[kTJMax + 1], int n, T alr, T ali,
+                                           T ber, T bei) {
+#pragma unroll
+    for (int i = kTJMax; i >= 0; --i) {
+        if (i <= n) {
+            T nr = T(0), ni = T(0);
+            if (i < n) {
+                nr = alr * vr[i] - ali * vi[i];
+                ni = alr * vi[i] + ali * vr[i];
+            }
+            if (i > 0) {
+                nr += ber * vr[i - 1] - bei * vi[i - 1];
+                ni += ber * vi[i - 1] + bei * vr[i - 1];
+            }
+            vr[i] = nr;
+            vi[i] = ni;
+        }
+    }
+}
+
+template <class T>
+__device__ __forceinline__ void kahan_add(T& s, T& c, T x) {
+    const T y = x - c;
+    const T t = s + y;
+    c = (t - s) - y;
+    s = t;
+}
+
+template <class T>
+__device__ __forceinline__ void load_nbr(const typename AB4<T>::type* __restrict__ ab_t, const T* __restrict__ cw_t,
+                                         int k, int cnt, int lane, typename AB4<T>::type& ab, T& c) {
+    if (k < cnt) {
+        ab = ab_t[(size_t)k * 32 + lane];
+        c = cw_t[(size_t)k * 32 + lane];
+    } else {
+        ab.x = T(1);
+        ab.y = ab.z = ab.w = T(0);
+        c = T(0);
+    }
+}
+
+template <class T, int TJ, int MB, int L0, int L1>
+__device__ __forceinline__ void ui_segment(const typename AB4<T>::type* __restrict__ ab_t,
+                                           const T* __restrict__ cw_t, int cnt, int kwarp, int lane, T wself,
+                                           bool store, typename C2<T>::type* __restrict__ uo) {
+    constexpr int NE = seg_offset(MB, L0, L1 + 1);
+    T sr[NE], si[NE], cr[NE], ci[NE];
+#pragma unroll
+    for (int e = 0; e < NE; ++e) sr[e] = si[e] = cr[e] = ci[e] = T(0);
+
+    typename AB4<T>::type abn;
+    T cn;
+    load_nbr<T>(ab_t, cw_t, 0, cnt, lane, abn, cn);
+    for (int k = 0; k < kwarp; ++k) {
+        const typename AB4<T>::type ab = abn;
+        const T c = cn;
+        load_nbr<T>(ab_t, cw_t, k + 1, cnt, lane, abn, cn);  // prefetch the next record
+        // linear forms: L1 = conj(a) xi - conj(b) eta, L2 = b xi + a eta
+        const T l1ar = ab.x, l1ai = -ab.y, l1br = -ab.z, l1bi = ab.w;
+        const T l2ar = ab.z, l2ai = ab.w, l2br = ab.x, l2bi = ab.y;
+        T vr[kTJMax + 1], vi[kTJMax + 1];
+        vr[0] = T(1);
+        vi[0] = T(0);
+        // seed: (L1 L2)^MB at level 2 MB
+#pragma unroll
+        for (int st = 0; st < MB; ++st) {
+            mul_linear<T>(vr, vi, 2 * st + 1, l1ar, l1ai, l1br, l1bi);
+            mul_linear<T>(vr, vi, 2 * st + 2, l2ar, l2ai, l2br, l2bi);
+        }
+#pragma unroll
+        for (int J = 2 * MB; J <= L1; ++J) {
+            if (J > 2 * MB) mul_linear<T>(vr, vi, J, l1ar, l1ai, l1br, l1bi);  // length J -> J+1
+            if (J >= L0) {
+                const int off = seg_offset(MB, L0, J);
+                const int ne = seg_level_elems(MB, J);
+#pragma unroll
+                for (int i = 0; i < kTJMax + 1; ++i) {
+                    if (i < ne) {
+                        kahan_add(sr[off + i], cr[off + i], c * vr[i]);
+                        kahan_add(si[off + i], ci[off + i], c * vi[i]);
+                    }
+                }
+            }
+        }
+    }
+    if (!store) return;
+    // normalise, map to the half set, add the self term, store
+#pragma unroll
+    for (int J = L0; J <= L1; ++J) {
+        const int off = seg_offset(MB, L0, J);
+        const int ne = seg_level_elems(MB, J);
+#pragma unroll
+        for (int i = 0; i < kTJMax + 1; ++i) {
+            if (i < ne) {
+                const T nrm = T(unorm(J, i, MB));
+                T vr_ = (sr[off + i] - cr[off + i]) * nrm;
+                T vi_ = (si[off + i] - ci[off + i]) * nrm;
+                typename C2<T>::type o;
+                int slot;
+                if (2 * i <= J) {
+                    slot = hoff(J) + i * (J + 1) + MB;
+                    if (i == MB) vr_ += wself;
+                    o.x = vr_;
+                    o.y = vi_;
+                } else {
+                    slot = hoff(J) + (J - i) * (J + 1) + (J - MB);
+                    const T sg = ((i - MB) & 1) ? T(-1) : T(1);
+                    o.x = sg * vr_;
+                    o.y = -sg * vi_;
+                }
+                uo[(size_t)slot * 32 + lane] = o;
+            }
+        }
+    }
+}
+
+// All warps of the block run the same segment between barriers, so the SM
+// fetches one segment's code at a time.
+template <class T, int TJ, int I>
+__device__ __forceinline__ void run_segments(const typename AB4<T>::type* ab_t, const T* cw_t, int cnt, int kwarp,
+                                             int lane, T wself, bool store, typename C2<T>::type* uo) {
+    if constexpr (I < Plan<T, TJ>::value.n) {
+        constexpr Seg sg = Plan<T, TJ>::value.s[I];
+        ui_segment<T, TJ, sg.mb, sg.l0, sg.l1>(ab_t, cw_t, cnt, kwarp, lane, wself, store, uo);
+        __syncthreads();
+        run_segments<T, TJ, I + 1>(ab_t, cw_t, cnt, kwarp, lane, wself, store, uo);
+    }
+}
+
+template <class T> struct UiWarps { static constexpr int value = 12; };
+template <> struct UiWarps<double> { static constexpr int value = 6; };
+
+template <class T, int TJ>
+__global__ void __launch_bounds__(UiWarps<T>::value * 32, 1)
+    k_ui(const typename AB4<T>::type* __restrict__ ab, const T* __restrict__ cw, const int* __restrict__ cnt,
+         int kmax, T wself, int64_t ntiles, typename C2<T>::type* __restrict__ u) {
+    constexpr int W = UiWarps<T>::value;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t tl = (int64_t)blockIdx.x * W + warp;
+    const bool live = tl < ntiles;
+    const int64_t tls = live ? tl : 0;
+    const int n = live ? cnt[tls * 32 + lane] : 0;
+    const int kw = __reduce_max_sync(0xffffffffu, n);
+    const auto* ab_t = ab + (size_t)tls * kmax * 32;
+    const T* cw_t = cw + (size_t)tls * kmax * 32;
+    auto* uo = u + (size_t)tls * n_half(TJ) * 32;
+    run_segments<T, TJ, 0>(ab_t, cw_t, n, kw, lane, wself, live, uo);
+}
+
+// half set -> full (J+1)^2 blocks per point, point-major (for tests / the ABI)
+template <class T>
+__global__ void k_u_expand(int tj, const typename C2<T>::type* __restrict__ uh, SnapGeom g, int64_t tile0,
+                           int64_t ntiles, T* __restrict__ uf) {
+    const int64_t tl = blockIdx.x;
+    if (tl >= ntiles) return;
+    const int64_t tile = tile0 + tl;
+    const int tx = (int)(tile % g.tiles[0]);
+    const int ty = (int)((tile / g.tiles[0]) % g.tiles[1]);
+    const int tz = (int)(tile / ((int64_t)g.tiles[0] * g.tiles[1]));
+    const int nh = n_half(tj), nf = n_full(tj);
+    for (int idx = threadIdx.x; idx < 32 * nf; idx += blockDim.x) {
+        const int lane = idx / nf, e = idx % nf;
+        const int ix = tx * kTileX + (lane % kTileX);
+        const int iy = ty * kTileY + ((lane / kTileX) % kTileY);
+        const int iz = tz * kTileZ + lane / (kTileX * kTileY);
+        if (ix >= g.grid[0] || iy >= g.grid[1] || iz >= g.grid[2]) continue;
+        const int64_t p = ix + (int64_t)g.grid[0] * (iy + (int64_t)g.grid[1] * iz);
+        int J = 0;
+        while (full_off(J + 1) <= e) ++J;
+        const int r = e - full_off(J);
+        const int ma = r / (J + 1), mb = r % (J + 1);
+        bool direct = (2 * ma < J) || (2 * ma == J && 2 * mb <= J);
+        int sma = direct ? ma : J - ma, smb = direct ? mb : J - mb;
+        const auto v = uh[((size_t)tl * nh + hoff(J) + sma * (J + 1) + smb) * 32 + lane];
+        T re = v.x, im = v.y;
+        if (!direct) {
+            const T sg = ((sma - smb) & 1) ? T(-1) : T(1);
+            re = sg * re;
+            im = -sg * im;
+        }
+        uf[((size_t)p * nf + e) * 2] = re;
+        uf[((size_t)p * nf + e) * 2 + 1] = im;
+    }
+}
+
+template <class T, int TJ>
+void launch_ui_tj(const NbrOut& nb, double wself, int64_t ntiles, T* u_half, cudaStream_t st) {
+    constexpr int W = UiWarps<T>::value;
+    const unsigned blocks = (unsigned)((ntiles + W - 1) / W);
+    k_ui<T, TJ><<<blocks, W * 32, 0, st>>>(reinterpret_cast<const typename AB4<T>::type*>(nb.ab),
+                                                  reinterpret_cast<const T*>(nb.cw), nb.cnt, nb.kmax, (T)wself,
+                                                  ntiles, reinterpret_cast<typename C2<T>::type*>(u_half));
+}
+
+}  // namespace
+
+template <class T>
+void launch_ui(int twojmax, const NbrOut& nb, double wself, int64_t ntiles, T* u_half, cudaStream_t st) {
+    if (ntiles <= 0) return;
+    switch (twojmax) {
+        case 0: launch_ui_tj<T, 0>(nb, wself, ntiles, u_half, st); break;
+        case 2: launch_ui_tj<T, 2>(nb, wself, ntiles, u_half, st); break;
+        case 4: launch_ui_tj<T, 4>(nb, wself, ntiles, u_half, st); break;
+        case 6: launch_ui_tj<T, 6>(nb, wself, ntiles, u_half, st); break;
+        case 8: launch_ui_tj<T, 8>(nb, wself, ntiles, u_half, st); break;
+        case 10: launch_ui_tj<T, 10>(nb, wself, ntiles, u_half, st); break;
+        default: break;
+    }
+}
+
+template <class T>
+void launch_u_expand(int twojmax, const T* u_half, const SnapGeom& g, int64_t tile0, int64_t ntiles, T* u_full,
+                     cudaStream_t st) {
+    if (ntiles <= 0) return;
+    k_u_expand<T><<<(unsigned)ntiles, 256, 0, st>>>(twojmax, reinterpret_cast<const typename C2<T>::type*>(u_half),
+                                                    g, tile0, ntiles, u_full);
+}
+
+template void launch_ui<float>(int, const NbrOut&, double, int64_t, float*, cudaStream_t);
+template void launch_ui<double>(int, const NbrOut&, double, int64_t, double*, cudaStream_t);
+template void launch_u_expand<float>(int, const float*, const SnapGeom&, int64_t, int64_t, float*, cudaStream_t);
+template void launch_u_expand<double>(int, const double*, const SnapGeom&, int64_t, int64_t, double*, cudaStream_t);
+
+}  // namespace mala
