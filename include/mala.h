@@ -194,6 +194,13 @@ int mala_integrate(mala_ctx* ctx, const void* ldos_dev, int64_t P, double cell_v
                    double* dos_host, double* fermi_eV, double* band_energy_eV,
                    double* electron_count, mala_precision precision, void* stream);
 
+/* Electron count N(mu) = sum_xi w0_xi(mu) D_xi of a density of states D (host
+ * [n_E], the values mala_integrate returns in dos_host) at chemical potential
+ * mu, with the same FP64 closed-form weights the Fermi-level search uses.
+ * eg->n_electrons is ignored.  Synchronous. */
+int mala_electron_count(mala_ctx* ctx, const double* dos_host, const mala_energy_grid* eg, double mu,
+                        double* count);
+
 /* ---- the whole path ----------------------------------------------------- */
 
 /* Descriptors -> LDOS -> integrals for one snapshot.  Intermediate B and LDOS

@@ -76,6 +76,78 @@ class _EnergyGridArgs:
         self.c = e
 
 
+class _DevView:
+    """Zero-copy view of library-owned device memory for torch.as_tensor."""
+
+    def __init__(self, ptr: int, shape, typestr: str):
+        self.__cuda_array_interface__ = {"shape": tuple(int(x) for x in shape), "typestr": typestr,
+                                         "data": (int(ptr), False), "version": 3, "strides": None}
+
+
+def device_view(ptr: int, shape, dtype):
+    """torch tensor aliasing device memory the library owns (no copy)."""
+    torch = _torch()
+    if dtype == torch.bfloat16:
+        t = torch.as_tensor(_DevView(ptr, shape, "<i2"), device="cuda")
+        return t.view(torch.bfloat16)
+    typestr = {torch.float32: "<f4", torch.float64: "<f8", torch.int32: "<i4"}[dtype]
+    return torch.as_tensor(_DevView(ptr, shape, typestr), device="cuda")
+
+
+class Model:
+    """A network uploaded to the library (BF16 + tensor maps, and FP64)."""
+
+    def __init__(self, ctx: "Context", mlp):
+        self.ctx = ctx
+        self.dims = tuple(int(d) for d in mlp.dims)
+        nl = len(self.dims) - 1
+        self._dims = np.ascontiguousarray(self.dims, dtype=np.int32)
+        self._W = [np.ascontiguousarray(w, dtype=np.float64) for w in mlp.W]
+        self._b = [np.ascontiguousarray(b, dtype=np.float64) for b in mlp.b]
+        self._shift = None if mlp.in_shift is None else np.ascontiguousarray(mlp.in_shift, dtype=np.float64)
+        self._scale = None if mlp.in_scale is None else np.ascontiguousarray(mlp.in_scale, dtype=np.float64)
+        Wp = (C.POINTER(C.c_double) * nl)(*[w.ctypes.data_as(C.POINTER(C.c_double)) for w in self._W])
+        bp = (C.POINTER(C.c_double) * nl)(*[b.ctypes.data_as(C.POINTER(C.c_double)) for b in self._b])
+        d = _lib.MLPDesc()
+        d.n_layers = nl
+        d.dims = self._dims.ctypes.data_as(C.POINTER(C.c_int32))
+        d.W = C.cast(Wp, C.POINTER(C.POINTER(C.c_double)))
+        d.b = C.cast(bp, C.POINTER(C.POINTER(C.c_double)))
+        d.leaky_slope = float(mlp.leaky_slope)
+        d.activate_output = 0
+        d.in_shift = None if self._shift is None else self._shift.ctypes.data_as(C.POINTER(C.c_double))
+        d.in_scale = None if self._scale is None else self._scale.ctypes.data_as(C.POINTER(C.c_double))
+        h = C.c_void_p()
+        check(lib().mala_model_create(ctx.h, C.byref(d), C.byref(h)), "mala_model_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            lib().mala_model_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _result_dict(r: "_lib.Result", precision: int):
+    torch = _torch()
+    out = {"status": int(r.status), "fermi": float(r.fermi_eV), "band_energy": float(r.band_energy_eV),
+           "electron_count": float(r.electron_count), "n_points": int(r.n_points), "n_B": int(r.n_B),
+           "n_E": int(r.n_E), "latency_s": float(r.submit_to_done_s)}
+    out["dos"] = np.ctypeslib.as_array(r.dos, shape=(r.n_E,)).copy() if r.dos else None
+    fdt = torch.float32 if precision == MIXED else torch.float64
+    ldt = torch.bfloat16 if precision == MIXED else torch.float64
+    if r.B_dev:
+        out["B"] = device_view(r.B_dev, (r.n_points, r.n_B), fdt)
+        out["ldos"] = device_view(r.ldos_dev, (r.n_points, r.n_E), ldt)
+        out["density"] = device_view(r.density_dev, (r.n_points,), fdt)
+    return out
+
+
 class Context:
     """A library context on one CUDA device (owns streams, tables, workspaces)."""
 
@@ -151,3 +223,92 @@ class Context:
         check(lib().mala_expansion_coefficients(self.h, C.byref(a.c), C.byref(b.c), C.c_void_p(out.data_ptr()),
                                                 int(precision), _stream_ptr(stream)), "mala_expansion_coefficients")
         return out
+
+    # ---- network and integrals --------------------------------------------
+
+    def ldos_forward(self, model: Model, B, precision: int = MIXED, dos_sum: bool = True, stream=None):
+        """(LDOS[P][N_E] bf16/f64, column sums [N_E] f64 or None) on the GPU."""
+        torch = _torch()
+        P = int(B.shape[0])
+        nE = model.dims[-1]
+        dev = torch.device("cuda", self.device)
+        ldos = torch.empty((P, nE), dtype=torch.bfloat16 if precision == MIXED else torch.float64, device=dev)
+        ds = torch.zeros(nE, dtype=torch.float64, device=dev) if dos_sum else None
+        check(lib().mala_ldos_forward(self.h, model.h, C.c_void_p(B.data_ptr()), P, C.c_void_p(ldos.data_ptr()),
+                                      C.c_void_p(ds.data_ptr()) if ds is not None else None, int(precision),
+                                      _stream_ptr(stream)), "mala_ldos_forward")
+        return ldos, ds
+
+    def integrate(self, ldos, volume: float, eg, precision: int = MIXED, dos_sum=None, n_electrons=None,
+                  density: bool = True, stream=None, raise_on_bracket: bool = True):
+        """D(e), Fermi level, band energy, electron count and n(r) of an LDOS."""
+        torch = _torch()
+        P = int(ldos.shape[0])
+        dev = torch.device("cuda", self.device)
+        dens = None
+        if density:
+            dens = torch.empty(P, dtype=torch.float32 if precision == MIXED else torch.float64, device=dev)
+        e = _EnergyGridArgs(eg, n_electrons)
+        D = np.zeros(int(eg.n_E))
+        eF, Eb, Ne = C.c_double(0), C.c_double(0), C.c_double(0)
+        rc = lib().mala_integrate(self.h, C.c_void_p(ldos.data_ptr()), P, float(volume), C.byref(e.c),
+                                  C.c_void_p(dos_sum.data_ptr()) if dos_sum is not None else None,
+                                  C.c_void_p(dens.data_ptr()) if dens is not None else None,
+                                  D.ctypes.data_as(C.c_void_p), C.byref(eF), C.byref(Eb), C.byref(Ne),
+                                  int(precision), _stream_ptr(stream))
+        if rc != _lib.MALA_ERR_FERMI_BRACKET or raise_on_bracket:
+            check(rc, "mala_integrate")
+        return {"status": rc, "dos": D, "fermi": eF.value, "band_energy": Eb.value, "electron_count": Ne.value,
+                "density": dens}
+
+    def electron_count(self, D, eg, mu: float) -> float:
+        """N(mu) = sum_xi w0_xi(mu) D_xi on the GPU."""
+        D = np.ascontiguousarray(D, dtype=np.float64)
+        e = _EnergyGridArgs(eg)
+        out = C.c_double(0.0)
+        check(lib().mala_electron_count(self.h, D.ctypes.data_as(C.POINTER(C.c_double)), C.byref(e.c), float(mu),
+                                        C.byref(out)), "mala_electron_count")
+        return float(out.value)
+
+    # ---- the whole path ------------------------------------------------------
+
+    def predict(self, snap, bp, model: Model, eg, precision: int = MIXED, n_electrons=None, density_host=None,
+                stream=None, raise_on_bracket: bool = True):
+        """Descriptors -> LDOS -> integrals.  Device outputs alias the context's
+        workspace (valid until the next call); density_host (numpy) receives n(r)."""
+        a, b, e = _SnapshotArgs(snap), _BParamsArgs(bp), _EnergyGridArgs(eg, n_electrons)
+        r = _lib.Result()
+        rc = lib().mala_predict(self.h, C.byref(a.c), C.byref(b.c), model.h, C.byref(e.c), int(precision),
+                                density_host.ctypes.data_as(C.c_void_p) if density_host is not None else None,
+                                C.byref(r), _stream_ptr(stream))
+        if rc != _lib.MALA_ERR_FERMI_BRACKET or raise_on_bracket:
+            check(rc, "mala_predict")
+        out = _result_dict(r, precision)
+        out["status"] = rc
+        return out
+
+    # ---- serving ----------------------------------------------------------------
+
+    def submit(self, snap, bp, model: Model, eg, precision: int = MIXED, n_electrons=None) -> int:
+        a, b, e = _SnapshotArgs(snap), _BParamsArgs(bp), _EnergyGridArgs(eg, n_electrons)
+        t = C.c_uint64(0)
+        check(lib().mala_submit(self.h, C.byref(a.c), C.byref(b.c), model.h, C.byref(e.c), int(precision),
+                                C.byref(t)), "mala_submit")
+        return int(t.value)
+
+    def poll(self, ticket: int, precision: int = MIXED):
+        """None while pending, else the result dict (raises on a failed request)."""
+        r = _lib.Result()
+        rc = lib().mala_poll(self.h, C.c_uint64(ticket), C.byref(r))
+        if rc == _lib.MALA_PENDING:
+            return None
+        check(rc, "mala_poll")
+        return _result_dict(r, precision)
+
+    def wait(self, ticket: int, timeout_s: float = 60.0, precision: int = MIXED):
+        r = _lib.Result()
+        check(lib().mala_wait(self.h, C.c_uint64(ticket), float(timeout_s), C.byref(r)), "mala_wait")
+        return _result_dict(r, precision)
+
+    def release(self, ticket: int):
+        check(lib().mala_release(self.h, C.c_uint64(ticket)), "mala_release")

@@ -1,0 +1,469 @@
+// integrate.cu -- the LDOS integrals of paper Sec. "Observable calculation":
+//   D(e_xi)  = dV sum_r LDOS(r, xi)                       (Eq. DOS.from.ldos)
+//   N(mu)    = sum_xi w0_xi(mu) D_xi                      (Eq. NumberElectrons_from_DOS)
+//   e_F      : root of N(mu) - N_e by FP64 bisection
+//   E_b      = sum_xi w1_xi(e_F) D_xi                      (Eq. band.energy)
+//   n(r)     = sum_xi w0_xi(e_F) LDOS(r, xi)              (Eq. density.from.ldos)
+// with w_n,xi(mu) = int hat_xi(e) e^n f((e - mu)/kT) de the exact weights of
+// the piecewise-linear interpolant between energy-grid points
+// (Eqs. ldosintegralgeneral / ldosintegralsummation).
+//
+// Closed forms.  With f(y) = 1/(1+e^y) and, for y >= 0, L = ln(1 + e^-y),
+// z = -e^-y:
+//   H0(y) = -L,  H1(y) = -y L + Li2(z),  H2(y) = -y^2 L + 2 y Li2(z) + 2 Li3(z)
+// are antiderivatives of f, y f, y^2 f (the polylogarithm form of f,
+// Eq. fermidiracspecial).  Below the Fermi level (x < 0) f(x) = 1 - f(-x) turns
+// every piece into an exact polynomial integral minus an integral over y >= 0,
+// so no large terms cancel.  Li2 and Li3 on z in [-1, 0) are summed from their
+// Bernoulli-number expansions in u = -ln(1 - z), |u| <= ln 2:
+//   Li2 = sum_k B_k u^(k+1)/(k+1)!,
+//   Li3 = sum_{n,k} B_n B_k u^(n+k+1) / ((n+1)! k! (n+k+1))
+// (term-by-term integrals of dLi2/du = u/(e^u - 1), dLi3/du = Li2/(e^u - 1)).
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <vector>
+
+#include "mala_internal.h"
+
+namespace mala {
+
+namespace {
+
+constexpr int kPolyTerms = 26;
+__constant__ double c_li2[kPolyTerms + 1];  // coefficient of u^m, m = 0..kPolyTerms
+__constant__ double c_li3[kPolyTerms + 1];
+
+constexpr int kFermiThreads = 256;
+
+__device__ __forceinline__ double horner(const double* c, double u) {
+    double s = 0.0;
+#pragma unroll
+    for (int m = kPolyTerms; m >= 1; --m) s = s * u + c[m];
+    return s * u;
+}
+
+// antiderivatives of y^j f(y), j = 0, 1, 2, valid for y >= 0
+__device__ __forceinline__ void hfun(double y, double& h0, double& h1, double& h2) {
+    const double L = log1p(exp(-y));
+    const double u = -L;
+    const double li2 = horner(c_li2, u), li3 = horner(c_li3, u);
+    h0 = -L;
+    h1 = -y * L + li2;
+    h2 = -y * y * L + 2.0 * y * li2 + 2.0 * li3;
+}
+
+// M_k = int_a^b (e - a)^k f((e - mu)/kT) de, k = 0, 1, 2
+__device__ void interval_moments(double a, double b, double mu, double kT, double& M0, double& M1, double& M2) {
+    const double xa = (a - mu) / kT, xb = (b - mu) / kT;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;  // int (x - xa)^k f(x) dx over [xa, xb]
+    // part with x >= 0: direct antiderivatives, (x - xa)^k expanded in x
+    const double p0 = fmax(xa, 0.0);
+    if (xb > p0) {
+        double a0, a1, a2, b0, b1, b2;
+        hfun(p0, a0, a1, a2);
+        hfun(xb, b0, b1, b2);
+        const double d0 = b0 - a0, d1 = b1 - a1, d2 = b2 - a2;
+        s0 += d0;
+        s1 += d1 - xa * d0;
+        s2 += d2 - 2.0 * xa * d1 + xa * xa * d0;
+    }
+    // part with x < 0: f(x) = 1 - f(-x); y = -x in [-x1, -xa]
+    const double x1 = fmin(xb, 0.0);
+    if (x1 > xa) {
+        const double t = x1 - xa;
+        s0 += t;
+        s1 += t * t / 2.0;
+        s2 += t * t * t / 3.0;
+        double a0, a1, a2, b0, b1, b2;
+        hfun(-x1, a0, a1, a2);
+        hfun(-xa, b0, b1, b2);
+        const double d0 = b0 - a0, d1 = b1 - a1, d2 = b2 - a2;
+        // int (x - xa)^k f(-x) dx = int (-(y + xa))^k f(y) dy over [-x1, -xa]
+        s0 -= d0;
+        s1 -= -(d1 + xa * d0);
+        s2 -= d2 + 2.0 * xa * d1 + xa * xa * d0;
+    }
+    M0 = kT * s0;
+    M1 = kT * kT * s1;
+    M2 = kT * kT * kT * s2;
+}
+
+__device__ double block_sum(double v, double* sred) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if (lane == 0) sred[warp] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sred[w];
+    __syncthreads();
+    if (threadIdx.x == 0) sred[32] = t;
+    __syncthreads();
+    return sred[32];
+}
+
+// N(mu) with D held in shared memory
+__device__ double electron_count(const double* sD, int nE, double e0, double de, double mu, double kT, double* sred) {
+    double part = 0.0;
+    for (int i = threadIdx.x; i < nE - 1; i += blockDim.x) {
+        const double a = e0 + i * de, b = e0 + (i + 1) * de;
+        double M0, M1, M2;
+        interval_moments(a, b, mu, kT, M0, M1, M2);
+        part += (M0 - M1 / de) * sD[i] + (M1 / de) * sD[i + 1];
+    }
+    return block_sum(part, sred);
+}
+
+// scal: [0] e_F, [1] E_b, [2] status (0 ok, 1 no bracket), [3] N(e_F), [4] iterations
+__global__ void __launch_bounds__(kFermiThreads) k_fermi(const double* __restrict__ dos_sum, int nE, double dV, double e0,
+                                                         double de, double kT, double Ne, double tol, int max_iter,
+                                                         double* __restrict__ D, double* __restrict__ w0d,
+                                                         float* __restrict__ w0f, double* __restrict__ scal) {
+    extern __shared__ double sD[];
+    __shared__ double sred[33];
+    __shared__ double sb[3];  // lo, hi, flo
+    __shared__ int sflag;
+    for (int i = threadIdx.x; i < nE; i += blockDim.x) {
+        sD[i] = dV * dos_sum[i];
+        D[i] = sD[i];
+    }
+    __syncthreads();
+    double lo = e0 - 20.0 * kT, hi = e0 + (nE - 1) * de + 20.0 * kT;
+    const double flo = electron_count(sD, nE, e0, de, lo, kT, sred) - Ne;
+    const double fhi = electron_count(sD, nE, e0, de, hi, kT, sred) - Ne;
+    int status = 0, it = 0;
+    double eF;
+    if (flo == 0.0) {
+        eF = lo;
+    } else if (fhi == 0.0) {
+        eF = hi;
+    } else if ((flo > 0.0) == (fhi > 0.0)) {
+        status = 1;
+        eF = 0.5 * (lo + hi);
+    } else {
+        if (threadIdx.x == 0) {
+            sb[0] = lo;
+            sb[1] = hi;
+            sb[2] = flo;
+        }
+        __syncthreads();
+        bool exact = false;
+        for (it = 0; it < max_iter; ++it) {
+            lo = sb[0];
+            hi = sb[1];
+            if (hi - lo < tol) break;
+            const double mid = 0.5 * (lo + hi);
+            const double fm = electron_count(sD, nE, e0, de, mid, kT, sred) - Ne;
+            if (threadIdx.x == 0) {
+                sflag = 0;
+                if (fm == 0.0) {
+                    sb[0] = sb[1] = mid;
+                    sflag = 1;
+                } else if ((fm > 0.0) == (sb[2] > 0.0)) {
+                    sb[0] = mid;
+                    sb[2] = fm;
+                } else {
+                    sb[1] = mid;
+                }
+            }
+            __syncthreads();
+            if (sflag) {
+                exact = true;
+                break;
+            }
+        }
+        eF = exact ? sb[0] : 0.5 * (sb[0] + sb[1]);
+    }
+    // weights at e_F, the band energy and the electron count
+    double pn = 0.0, pe = 0.0;
+    for (int x = threadIdx.x; x < nE; x += blockDim.x) {
+        double w0 = 0.0, w1 = 0.0;
+        const double ex = e0 + x * de;
+        if (x > 0) {  // right half of hat_x on [e_{x-1}, e_x]
+            const double a = e0 + (x - 1) * de;
+            double M0, M1, M2;
+            interval_moments(a, ex, eF, kT, M0, M1, M2);
+            w0 += M1 / de;
+            w1 += (a * M1 + M2) / de;
+        }
+        if (x < nE - 1) {  // left half of hat_x on [e_x, e_{x+1}]
+            double M0, M1, M2;
+            interval_moments(ex, ex + de, eF, kT, M0, M1, M2);
+            w0 += M0 - M1 / de;
+            w1 += ex * M0 + M1 - (ex * M1 + M2) / de;
+        }
+        w0d[x] = w0;
+        w0f[x] = (float)w0;
+        pn += w0 * sD[x];
+        pe += w1 * sD[x];
+    }
+    const double Nf = block_sum(pn, sred);
+    const double Eb = block_sum(pe, sred);
+    if (threadIdx.x == 0) {
+        scal[0] = eF;
+        scal[1] = Eb;
+        scal[2] = (double)status;
+        scal[3] = Nf;
+        scal[4] = (double)it;
+    }
+}
+
+// column sums over blocks of 128 rows (FP32 in row order, as the network
+// epilogue forms them) -> FP64 partial rows
+template <class TL>
+__global__ void k_colsum(const TL* __restrict__ L, int64_t P, int nE, double* __restrict__ part) {
+    const int64_t r0 = (int64_t)blockIdx.x * 128;
+    const int64_t r1 = min(P, r0 + 128);
+    for (int c = threadIdx.x; c < nE; c += blockDim.x) {
+        if constexpr (sizeof(TL) == 2) {
+            float s = 0.f;
+            for (int64_t r = r0; r < r1; ++r) s += __bfloat162float(L[r * nE + c]);
+            part[(int64_t)blockIdx.x * nE + c] = (double)s;
+        } else {
+            double s = 0.0;
+            for (int64_t r = r0; r < r1; ++r) s += (double)L[r * nE + c];
+            part[(int64_t)blockIdx.x * nE + c] = s;
+        }
+    }
+}
+
+__global__ void k_sum_rows(const double* __restrict__ part, int64_t nt, int nE, double* __restrict__ out) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nE) return;
+    double s = 0.0;
+    for (int64_t t = 0; t < nt; ++t) s += part[t * nE + c];
+    out[c] = s;
+}
+
+// n(r) = sum_xi w0_xi LDOS(r, xi): one warp per row, lanes over energies;
+// per-block FP64 partial sums of n for the electron-count check.
+constexpr int kDensWarps = 8;
+
+__global__ void __launch_bounds__(kDensWarps * 32) k_density_bf16(const __nv_bfloat16* __restrict__ L, int64_t P, int nE,
+                                                                  const float* __restrict__ w0, float* __restrict__ n,
+                                                                  double* __restrict__ part) {
+    __shared__ double sp[kDensWarps];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double acc = 0.0;
+    const int64_t stride = (int64_t)gridDim.x * kDensWarps;
+    if ((nE & 1) == 0) {
+        const int np = nE >> 1;
+        for (int64_t r = (int64_t)blockIdx.x * kDensWarps + warp; r < P; r += stride) {
+            const __nv_bfloat162* row = reinterpret_cast<const __nv_bfloat162*>(L + r * nE);
+            float s = 0.f;
+            for (int q = lane; q < np; q += 32) {
+                const float2 v = __bfloat1622float2(row[q]);
+                s = fmaf(v.x, __ldg(w0 + 2 * q), s);
+                s = fmaf(v.y, __ldg(w0 + 2 * q + 1), s);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0) {
+                n[r] = s;
+                acc += (double)s;
+            }
+        }
+    } else {
+        for (int64_t r = (int64_t)blockIdx.x * kDensWarps + warp; r < P; r += stride) {
+            const __nv_bfloat16* row = L + r * nE;
+            float s = 0.f;
+            for (int q = lane; q < nE; q += 32) s = fmaf(__bfloat162float(row[q]), __ldg(w0 + q), s);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0) {
+                n[r] = s;
+                acc += (double)s;
+            }
+        }
+    }
+    if (lane == 0) sp[warp] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < kDensWarps; ++w) t += sp[w];
+        part[blockIdx.x] = t;
+    }
+}
+
+__global__ void __launch_bounds__(kDensWarps * 32) k_density_f64(const double* __restrict__ L, int64_t P, int nE,
+                                                                 const double* __restrict__ w0, double* __restrict__ n,
+                                                                 double* __restrict__ part) {
+    __shared__ double sp[kDensWarps];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double acc = 0.0;
+    const int64_t stride = (int64_t)gridDim.x * kDensWarps;
+    for (int64_t r = (int64_t)blockIdx.x * kDensWarps + warp; r < P; r += stride) {
+        const double* row = L + r * nE;
+        double s = 0.0;
+        for (int q = lane; q < nE; q += 32) s += row[q] * w0[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) {
+            n[r] = s;
+            acc += s;
+        }
+    }
+    if (lane == 0) sp[warp] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < kDensWarps; ++w) t += sp[w];
+        part[blockIdx.x] = t;
+    }
+}
+
+// N(mu) for one mu (single block)
+__global__ void __launch_bounds__(kFermiThreads) k_count(const double* __restrict__ D, int nE, double e0, double de,
+                                                         double kT, double mu, double* __restrict__ out) {
+    extern __shared__ double sD[];
+    __shared__ double sred[33];
+    for (int i = threadIdx.x; i < nE; i += blockDim.x) sD[i] = D[i];
+    __syncthreads();
+    const double n = electron_count(sD, nE, e0, de, mu, kT, sred);
+    if (threadIdx.x == 0) *out = n;
+}
+
+__global__ void k_sum_vec(const double* __restrict__ part, int n, double* __restrict__ out) {
+    __shared__ double s[256];
+    double t = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) t += part[i];
+    s[threadIdx.x] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0;
+        for (int i = 0; i < (int)blockDim.x; ++i) a += s[i];
+        *out = a;
+    }
+}
+
+// Bernoulli numbers B_0..B_n (B_1 = -1/2) from sum_{k=0}^{m} C(m+1, k) B_k = 0
+std::vector<double> bernoulli(int n) {
+    std::vector<double> B(n + 1, 0.0);
+    B[0] = 1.0;
+    for (int m = 1; m <= n; ++m) {
+        double s = 0.0, c = 1.0;  // c = C(m+1, k)
+        for (int k = 0; k < m; ++k) {
+            s += c * B[k];
+            c = c * (double)(m + 1 - k) / (double)(k + 1);
+        }
+        B[m] = -s / (double)(m + 1);
+        if (m >= 3 && (m & 1)) B[m] = 0.0;  // odd Bernoulli numbers beyond B_1 vanish
+    }
+    return B;
+}
+
+}  // namespace
+
+int upload_polylog_tables() {
+    const std::vector<double> B = bernoulli(kPolyTerms + 1);
+    std::vector<double> fact(kPolyTerms + 3, 1.0);
+    for (int i = 1; i < (int)fact.size(); ++i) fact[i] = fact[i - 1] * i;
+    double c2[kPolyTerms + 1] = {0}, c3[kPolyTerms + 1] = {0};
+    for (int m = 1; m <= kPolyTerms; ++m) {
+        c2[m] = B[m - 1] / fact[m];  // u^m: k = m - 1
+        double s = 0.0;
+        for (int n = 0; n <= m - 1; ++n) {
+            const int k = m - 1 - n;
+            s += B[n] * B[k] / (fact[n + 1] * fact[k] * (double)m);
+        }
+        c3[m] = s;
+    }
+    MALA_CUDA_TRY(cudaMemcpyToSymbol(c_li2, c2, sizeof(c2)));
+    MALA_CUDA_TRY(cudaMemcpyToSymbol(c_li3, c3, sizeof(c3)));
+    return MALA_OK;
+}
+
+int electron_count_at(Ctx* c, const double* D_host, const mala_energy_grid* eg, double mu, double* out,
+                      cudaStream_t st) {
+    const int nE = eg->n_E;
+    MALA_TRY(c->ws_w.reserve(c, sizeof(double) * (nE + 1)));
+    double* d = c->ws_w.as<double>();
+    MALA_CUDA_TRY(cudaMemcpyAsync(d, D_host, sizeof(double) * nE, cudaMemcpyHostToDevice, st));
+    k_count<<<1, kFermiThreads, sizeof(double) * nE, st>>>(d, nE, eg->e0_eV, eg->de_eV, eg->kT_eV, mu, d + nE);
+    MALA_CUDA_TRY(cudaGetLastError());
+    MALA_CUDA_TRY(cudaMemcpyAsync(c->host_scalars + 16, d + nE, sizeof(double), cudaMemcpyDeviceToHost, st));
+    MALA_CUDA_TRY(cudaStreamSynchronize(st));
+    *out = c->host_scalars[16];
+    return MALA_OK;
+}
+
+int integrate(Ctx* c, const void* ldos, int64_t P, double volume, const mala_energy_grid* eg, const double* dos_sum,
+              void* density, double* dos_host, double* fermi, double* eb, double* ne, mala_precision prec,
+              cudaStream_t st) {
+    const int nE = eg->n_E;
+    // workspace: dsum[nE] | D[nE] | w0d[nE] | w0f[nE] (float) | scal[8] | nsum[1] | partial rows
+    const int64_t ntile = (P + 127) / 128;
+    const int dens_blocks = (int)std::min<int64_t>(std::max<int64_t>(1, (P + kDensWarps - 1) / kDensWarps),
+                                                   (int64_t)c->num_sms * 16);
+    const size_t n_part = std::max<size_t>((size_t)ntile * nE, (size_t)dens_blocks);
+    const size_t doubles = 3 * (size_t)nE + (nE + 1) / 2 + 16 + n_part;
+    MALA_TRY(c->ws_red.reserve(c, sizeof(double) * doubles));
+    double* dsum = c->ws_red.as<double>();
+    double* D = dsum + nE;
+    double* w0d = D + nE;
+    float* w0f = reinterpret_cast<float*>(w0d + nE);
+    double* scal = w0d + nE + (nE + 1) / 2;
+    double* nsum = scal + 8;
+    double* part = scal + 16;
+    const bool mixed = prec == MALA_MIXED;
+    if (!dos_sum) {
+        if (P > 0) {
+            if (mixed)
+                MALA_PROF(c, "k_dos_reduce", st,
+                          (k_colsum<__nv_bfloat16><<<(unsigned)ntile, 256, 0, st>>>(
+                              static_cast<const __nv_bfloat16*>(ldos), P, nE, part)));
+            else
+                MALA_PROF(c, "k_dos_reduce", st,
+                          (k_colsum<double><<<(unsigned)ntile, 256, 0, st>>>(static_cast<const double*>(ldos), P, nE,
+                                                                            part)));
+            k_sum_rows<<<(nE + 127) / 128, 128, 0, st>>>(part, ntile, nE, dsum);
+        } else {
+            MALA_CUDA_TRY(cudaMemsetAsync(dsum, 0, sizeof(double) * nE, st));
+        }
+        dos_sum = dsum;
+    }
+    const double dV = volume / (double)(P > 0 ? P : 1);
+    MALA_PROF(c, "k_fermi", st,
+              (k_fermi<<<1, kFermiThreads, sizeof(double) * nE, st>>>(dos_sum, nE, dV, eg->e0_eV, eg->de_eV, eg->kT_eV,
+                                                                      eg->n_electrons, 1e-12, 200, D, w0d, w0f, scal)));
+    if (P > 0 && density) {
+        if (mixed)
+            MALA_PROF(c, "k_density", st,
+                      (k_density_bf16<<<dens_blocks, kDensWarps * 32, 0, st>>>(static_cast<const __nv_bfloat16*>(ldos), P,
+                                                                              nE, w0f, static_cast<float*>(density),
+                                                                              part)));
+        else
+            MALA_PROF(c, "k_density", st,
+                      (k_density_f64<<<dens_blocks, kDensWarps * 32, 0, st>>>(static_cast<const double*>(ldos), P, nE,
+                                                                             w0d, static_cast<double*>(density), part)));
+        k_sum_vec<<<1, 256, 0, st>>>(part, dens_blocks, nsum);
+    } else {
+        MALA_CUDA_TRY(cudaMemsetAsync(nsum, 0, sizeof(double), st));
+    }
+    MALA_CUDA_TRY(cudaGetLastError());
+    if (c->host_dos_len < (size_t)nE) {
+        if (c->host_dos) cudaFreeHost(c->host_dos);
+        c->host_dos = nullptr;
+        c->host_dos_len = 0;
+        MALA_CUDA_TRY(cudaMallocHost(&c->host_dos, sizeof(double) * nE));
+        c->host_dos_len = nE;
+    }
+    MALA_CUDA_TRY(cudaMemcpyAsync(c->host_scalars, scal, sizeof(double) * 9, cudaMemcpyDeviceToHost, st));
+    MALA_CUDA_TRY(cudaMemcpyAsync(c->host_dos, D, sizeof(double) * nE, cudaMemcpyDeviceToHost, st));
+    MALA_CUDA_TRY(cudaStreamSynchronize(st));
+    if (dos_host) memcpy(dos_host, c->host_dos, sizeof(double) * nE);
+    const double* hs = c->host_scalars;
+    if (fermi) *fermi = hs[0];
+    if (eb) *eb = hs[1];
+    if (ne) *ne = dV * hs[8];
+    if (hs[2] != 0.0)
+        return fail(MALA_ERR_FERMI_BRACKET, "N(mu) - N_e has no sign change on [e0 - 20 kT, e_max + 20 kT]");
+    return MALA_OK;
+}
+
+}  // namespace mala

@@ -34,7 +34,7 @@ DevBuf::~DevBuf() { release(); }
 void DevBuf::release() {
     if (ptr) {
         cudaFree(ptr);
-        if (owner) owner->used -= bytes;
+        if (owner) owner->root()->used -= bytes;
     }
     ptr = nullptr;
     bytes = 0;
@@ -45,9 +45,10 @@ int DevBuf::reserve(Ctx* ctx, size_t n) {
     release();
     owner = ctx;
     if (n == 0) return MALA_OK;
-    if (ctx->budget && ctx->used + n > ctx->budget)
+    Ctx* r = ctx->root();
+    if (r->budget && r->used + n > r->budget)
         return fail(MALA_ERR_OOM, "workspace of %zu bytes exceeds the HBM budget (%zu of %zu in use)", n,
-                    (size_t)ctx->used, ctx->budget);
+                    (size_t)r->used, r->budget);
     cudaError_t e = cudaMalloc(&ptr, n);
     if (e != cudaSuccess) {
         ptr = nullptr;
@@ -55,7 +56,7 @@ int DevBuf::reserve(Ctx* ctx, size_t n) {
         return fail(MALA_ERR_OOM, "cudaMalloc(%zu) failed: %s", n, cudaGetErrorString(e));
     }
     bytes = n;
-    ctx->used += n;
+    r->used += n;
     return MALA_OK;
 }
 
@@ -249,6 +250,7 @@ int mala_create(mala_ctx** out, int device, size_t hbm_budget_bytes) {
         return fail(MALA_ERR_CUDA, "stream / pinned buffer creation failed");
     }
     int rc = upload_cg_tables(c);
+    if (rc == MALA_OK) rc = upload_polylog_tables();
     if (rc != MALA_OK) {
         mala_destroy(c);
         return rc;
@@ -260,6 +262,7 @@ int mala_create(mala_ctx** out, int device, size_t hbm_budget_bytes) {
 void mala_destroy(mala_ctx* c) {
     if (!c) return;
     cudaSetDevice(c->device);
+    server_stop(c);
     cudaDeviceSynchronize();
     prof_collect(c);
     for (cudaEvent_t e : c->prof.pool) cudaEventDestroy(e);

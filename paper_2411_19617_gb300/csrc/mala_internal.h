@@ -2,8 +2,10 @@
 // units: the context, workspace buffers, error reporting and kernel launchers.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <condition_variable>
 #include <cstdint>
@@ -96,13 +98,19 @@ void prof_end(struct Ctx* c, int idx, cudaStream_t st);
         ::mala::prof_end((c), pi_, (st));                   \
     } while (0)
 
-// Network uploaded for one precision.
+// Network uploaded once: BF16 padded copies + tensor maps for the
+// tensor-core path, FP64 copies for the plain path.
 struct Model {
     Ctx* ctx = nullptr;
     int n_layers = 0;
     std::vector<int> dims;
     float leaky_slope = 0.01f;
+    double slope_d = 0.01;
     int activate_output = 0;
+    bool mixed_ok = false;           // shape fits the tensor-core kernel
+    std::vector<int> boxN;           // TMA box rows per layer
+    std::vector<CUtensorMap> maps;   // BF16 weights [Npad][Kpad], 128-byte swizzle
+    std::vector<void*> allocs;
     // MIXED: bf16 weights padded to K multiple of 16 / N multiple of 16, fp32 bias
     std::vector<void*> Wbf;      // device bf16 [Npad][Kpad] per layer
     std::vector<float*> bias;    // device fp32 [Npad]
@@ -122,15 +130,17 @@ struct SnapStage;  // per-call staging of one snapshot (atoms, bins, neighbours)
 struct Request;
 
 struct Ctx {
+    Ctx* parent = nullptr;  // serving slots are child contexts of the user's context
     int device = 0;
     size_t budget = 0;  // 0 = unlimited
     std::atomic<size_t> used{0};
+    Ctx* root() { return parent ? parent : this; }
     cudaStream_t stream = nullptr;  // internal work stream for synchronous helpers
     SnapTables tables;
     int num_sms = 0;
     // workspaces of the synchronous path
     DevBuf ws_atoms, ws_bins, ws_nbr_ab, ws_nbr_c, ws_nbr_cnt, ws_u, ws_misc, ws_B, ws_ldos,
-        ws_dens, ws_dos, ws_tile_dos, ws_units;
+        ws_dens, ws_dos, ws_tile_dos, ws_units, ws_mlp64, ws_red, ws_w;
     double* host_dos = nullptr;     // pinned [max N_E]
     size_t host_dos_len = 0;
     double* host_scalars = nullptr; // pinned small buffer
@@ -211,12 +221,18 @@ void launch_u_expand(int twojmax, const T* u_half, const SnapGeom& g, int64_t ti
                      T* u_full, cudaStream_t st);
 
 int upload_cg_tables(Ctx* c);
+int upload_polylog_tables();
 int upload_zb_lists_f64(const int* lists, int bytes);
 int snap_descriptors(Ctx* c, const mala_snapshot* snap, const mala_bispectrum_params* bp, void* B,
                      void* u_full, mala_precision prec, cudaStream_t st);
 
 // ---- network and integrals ---------------------------------------------------
 
+int model_upload(Ctx* c, const mala_mlp_desc* d, Model* m);
+void server_stop(Ctx* c);
+int electron_count_at(Ctx* c, const double* D_host, const mala_energy_grid* eg, double mu, double* out,
+                      cudaStream_t st);
+void model_free(Model* m);
 int mlp_forward(Ctx* c, const Model* m, const void* B, int64_t P, void* ldos, double* dos_sum,
                 mala_precision prec, cudaStream_t st);
 int integrate(Ctx* c, const void* ldos, int64_t P, double volume, const mala_energy_grid* eg,

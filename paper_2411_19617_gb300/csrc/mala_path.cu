@@ -1,0 +1,431 @@
+// mala_path.cu -- C ABI of the network and integral steps, the whole path
+// (mala_predict) and the serving loop (mala_submit / mala_poll / mala_wait /
+// mala_release).
+//
+// Serving.  A server owns a FIFO of requests (each a deep copy of its inputs)
+// and a few worker slots.  A slot is a child context: its own CUDA stream,
+// workspaces and pinned buffers, sharing the parent's tables and HBM budget
+// accounting.  A worker takes the oldest queued request whose device memory
+// (its outputs plus any workspace growth) fits in what the budget has left,
+// allocates the request's outputs, runs descriptors -> network -> integrals on
+// its stream and marks the request done; requests on different slots run
+// concurrently on the GPU.  Outputs stay on the device until mala_release.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstring>
+
+#include "mala_internal.h"
+#include "snap_common.cuh"
+
+namespace mala {
+
+int check_snapshot(const mala_snapshot* s);
+int check_bparams(const mala_bispectrum_params* bp);
+
+static cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+static int check_model_desc(const mala_mlp_desc* d) {
+    if (!d) return fail(MALA_ERR_INVALID_ARG, "network descriptor is NULL");
+    if (d->n_layers < 1 || d->n_layers > 16 || !d->dims || !d->W || !d->b)
+        return fail(MALA_ERR_INVALID_ARG, "bad network descriptor");
+    for (int l = 0; l <= d->n_layers; ++l)
+        if (d->dims[l] < 1 || d->dims[l] > 65536) return fail(MALA_ERR_INVALID_ARG, "bad layer width %d", d->dims[l]);
+    for (int l = 0; l < d->n_layers; ++l)
+        if (!d->W[l] || !d->b[l]) return fail(MALA_ERR_INVALID_ARG, "layer %d weights are NULL", l);
+    if (!std::isfinite(d->leaky_slope)) return fail(MALA_ERR_INVALID_ARG, "leaky slope is not finite");
+    return MALA_OK;
+}
+
+static int check_egrid(const mala_energy_grid* eg) {
+    if (!eg) return fail(MALA_ERR_INVALID_ARG, "energy grid is NULL");
+    if (eg->n_E < 2 || eg->n_E > 4096) return fail(MALA_ERR_INVALID_ARG, "n_E = %d outside 2..4096", eg->n_E);
+    if (!(eg->de_eV > 0.0) || !(eg->kT_eV > 0.0) || !std::isfinite(eg->e0_eV) || !std::isfinite(eg->n_electrons))
+        return fail(MALA_ERR_INVALID_ARG, "energy grid needs de > 0, kT > 0 and finite e0, N_e");
+    return MALA_OK;
+}
+
+static double cell_volume(const mala_snapshot* s) { return s->cell[0][0] * s->cell[1][1] * s->cell[2][2]; }
+
+// descriptors -> LDOS -> integrals into the given device buffers
+static int run_path(Ctx* c, const mala_snapshot* snap, const mala_bispectrum_params* bp, const Model* m,
+                    const mala_energy_grid* eg, mala_precision prec, void* B, void* ldos, void* dens, double* dos_sum,
+                    mala_result* res, double* dos_host, cudaStream_t st) {
+    const int64_t P = (int64_t)snap->grid[0] * snap->grid[1] * snap->grid[2];
+    MALA_TRY(snap_descriptors(c, snap, bp, B, nullptr, prec, st));
+    MALA_TRY(mlp_forward(c, m, B, P, ldos, dos_sum, prec, st));
+    double eF = 0.0, Eb = 0.0, Ne = 0.0;
+    int rc = integrate(c, ldos, P, cell_volume(snap), eg, dos_sum, dens, dos_host, &eF, &Eb, &Ne, prec, st);
+    res->status = rc;
+    res->n_B = n_triples(bp->twojmax);
+    res->n_E = eg->n_E;
+    res->n_points = P;
+    res->fermi_eV = eF;
+    res->band_energy_eV = Eb;
+    res->electron_count = Ne;
+    res->B_dev = B;
+    res->ldos_dev = ldos;
+    res->density_dev = dens;
+    return rc;
+}
+
+static int check_path_args(const mala_snapshot* snap, const mala_bispectrum_params* bp, const Model* m,
+                           const mala_energy_grid* eg, mala_precision prec) {
+    MALA_TRY(check_snapshot(snap));
+    MALA_TRY(check_bparams(bp));
+    MALA_TRY(check_egrid(eg));
+    if (!m) return fail(MALA_ERR_INVALID_ARG, "model is NULL");
+    if (prec != MALA_MIXED && prec != MALA_FP64_PLAIN) return fail(MALA_ERR_INVALID_ARG, "bad precision");
+    if (m->dims[0] != n_triples(bp->twojmax))
+        return fail(MALA_ERR_INVALID_ARG, "network input width %d != %d descriptors", m->dims[0], n_triples(bp->twojmax));
+    if (m->dims[m->n_layers] != eg->n_E)
+        return fail(MALA_ERR_INVALID_ARG, "network output width %d != n_E %d", m->dims[m->n_layers], eg->n_E);
+    return MALA_OK;
+}
+
+static size_t path_output_bytes(int64_t P, int nB, int nE, mala_precision prec) {
+    const size_t e = prec == MALA_MIXED ? 4 : 8, l = prec == MALA_MIXED ? 2 : 8;
+    return (size_t)P * nB * e + (size_t)P * nE * l + (size_t)P * e + (size_t)nE * 8 + 4 * 256;
+}
+
+// ---- serving ---------------------------------------------------------------
+
+struct Request {
+    uint64_t ticket = 0;
+    std::vector<double> pos;
+    std::vector<int32_t> species;
+    std::vector<double> weights;
+    mala_snapshot snap{};
+    mala_bispectrum_params bp{};
+    mala_energy_grid eg{};
+    const Model* model = nullptr;
+    mala_precision prec = MALA_MIXED;
+    int64_t P = 0;
+    size_t out_bytes = 0;
+    // results
+    int state = 0;  // 0 queued, 1 running, 2 done
+    int status = MALA_PENDING;
+    std::string error;
+    void* buf = nullptr;  // outputs: B | LDOS | density | dos_sum
+    size_t buf_bytes = 0;
+    std::vector<double> dos;
+    mala_result res{};
+    std::chrono::steady_clock::time_point t_submit, t_done;
+};
+
+struct Server {
+    Ctx* root = nullptr;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<uint64_t> queue;
+    std::map<uint64_t, std::unique_ptr<Request>> reqs;
+    std::vector<std::unique_ptr<Ctx>> slots;
+    std::vector<std::thread> workers;
+    uint64_t next_ticket = 1;
+    bool stop = false;
+    int running = 0;
+};
+
+static void carve(Request* r, void* base, void** B, void** L, void** D, double** S) {
+    const size_t e = r->prec == MALA_MIXED ? 4 : 8, l = r->prec == MALA_MIXED ? 2 : 8;
+    const int nB = n_triples(r->bp.twojmax), nE = r->eg.n_E;
+    auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+    char* p = static_cast<char*>(base);
+    *B = p;
+    p += al((size_t)r->P * nB * e);
+    *L = p;
+    p += al((size_t)r->P * nE * l);
+    *D = p;
+    p += al((size_t)r->P * e);
+    *S = reinterpret_cast<double*>(p);
+}
+
+static void worker_loop(Server* sv, Ctx* slot) {
+    cudaSetDevice(slot->device);
+    for (;;) {
+        Request* r = nullptr;
+        {
+            std::unique_lock<std::mutex> lk(sv->mu);
+            for (;;) {
+                if (sv->stop) return;
+                // oldest queued request whose outputs fit in the budget
+                Ctx* root = sv->root;
+                for (auto it = sv->queue.begin(); it != sv->queue.end(); ++it) {
+                    Request* q = sv->reqs[*it].get();
+                    const bool fits = !root->budget || root->used + q->out_bytes <= root->budget || sv->running == 0;
+                    if (fits) {
+                        r = q;
+                        sv->queue.erase(it);
+                        break;
+                    }
+                }
+                if (r) break;
+                sv->cv_work.wait(lk);
+            }
+            r->state = 1;
+            ++sv->running;
+        }
+        int rc = MALA_OK;
+        Ctx* root = sv->root;
+        if (root->budget && root->used + r->out_bytes > root->budget) {
+            rc = fail(MALA_ERR_OOM, "request of %zu bytes does not fit in the HBM budget", r->out_bytes);
+        } else if (cudaMalloc(&r->buf, r->out_bytes) != cudaSuccess) {
+            cudaGetLastError();
+            r->buf = nullptr;
+            rc = fail(MALA_ERR_OOM, "cudaMalloc(%zu) for request outputs failed", r->out_bytes);
+        } else {
+            root->used += r->out_bytes;
+            r->buf_bytes = r->out_bytes;
+            void *B, *L, *D;
+            double* S;
+            carve(r, r->buf, &B, &L, &D, &S);
+            r->dos.assign(r->eg.n_E, 0.0);
+            std::lock_guard<std::mutex> lk(slot->mu);
+            rc = run_path(slot, &r->snap, &r->bp, r->model, &r->eg, r->prec, B, L, D, S, &r->res, r->dos.data(),
+                          slot->stream);
+        }
+        {
+            std::lock_guard<std::mutex> lk(sv->mu);
+            r->status = rc;
+            if (rc != MALA_OK) r->error = mala_last_error();
+            r->t_done = std::chrono::steady_clock::now();
+            r->res.status = rc;
+            r->res.dos = r->dos.empty() ? nullptr : r->dos.data();
+            r->res.submit_to_done_s = std::chrono::duration<double>(r->t_done - r->t_submit).count();
+            r->state = 2;
+            --sv->running;
+        }
+        sv->cv_done.notify_all();
+        sv->cv_work.notify_all();
+    }
+}
+
+static int server_start(Ctx* c) {
+    if (c->server) return MALA_OK;
+    auto* sv = new Server();
+    sv->root = c;
+    int nslots = 4;
+    if (const char* e = getenv("MALA_SERVE_SLOTS")) nslots = std::max(1, std::min(16, atoi(e)));
+    for (int i = 0; i < nslots; ++i) {
+        auto s = std::make_unique<Ctx>();
+        s->parent = c;
+        s->device = c->device;
+        s->num_sms = c->num_sms;
+        s->tables = c->tables;
+        s->kmax_hint = c->kmax_hint;
+        if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaMallocHost(&s->host_ints, 64 * sizeof(int)) != cudaSuccess ||
+            cudaMallocHost(&s->host_scalars, 64 * sizeof(double)) != cudaSuccess) {
+            delete sv;
+            return fail(MALA_ERR_CUDA, "could not create a serving slot");
+        }
+        sv->slots.push_back(std::move(s));
+    }
+    for (auto& s : sv->slots) sv->workers.emplace_back(worker_loop, sv, s.get());
+    c->server = sv;
+    return MALA_OK;
+}
+
+void server_stop(Ctx* c) {
+    Server* sv = c->server;
+    if (!sv) return;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sv->stop = true;
+    }
+    sv->cv_work.notify_all();
+    for (auto& t : sv->workers) t.join();
+    for (auto& kv : sv->reqs)
+        if (kv.second->buf) {
+            cudaFree(kv.second->buf);
+            c->used -= kv.second->buf_bytes;
+        }
+    for (auto& s : sv->slots) {
+        cudaStreamSynchronize(s->stream);
+        cudaStreamDestroy(s->stream);
+        cudaFreeHost(s->host_ints);
+        cudaFreeHost(s->host_scalars);
+        if (s->host_dos) cudaFreeHost(s->host_dos);
+    }
+    delete sv;
+    c->server = nullptr;
+}
+
+}  // namespace mala
+
+using namespace mala;
+
+struct mala_ctx : public mala::Ctx {};
+struct mala_model : public mala::Model {};
+
+extern "C" {
+
+int mala_model_create(mala_ctx* c, const mala_mlp_desc* desc, mala_model** out) {
+    if (!c || !out) return fail(MALA_ERR_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    MALA_TRY(check_model_desc(desc));
+    MALA_CUDA_TRY(cudaSetDevice(c->device));
+    auto* m = new mala_model();
+    int rc = model_upload(c, desc, m);
+    if (rc != MALA_OK) {
+        model_free(m);
+        delete m;
+        return rc;
+    }
+    *out = m;
+    return MALA_OK;
+}
+
+void mala_model_destroy(mala_model* m) {
+    if (!m) return;
+    model_free(m);
+    delete m;
+}
+
+int mala_ldos_forward(mala_ctx* c, const mala_model* m, const void* B_dev, int64_t P, void* ldos_dev,
+                      double* dos_sum_dev, mala_precision precision, void* stream) {
+    if (!c || !m || (!B_dev && P > 0) || (!ldos_dev && P > 0) || P < 0) return fail(MALA_ERR_INVALID_ARG, "bad arguments");
+    if (precision != MALA_MIXED && precision != MALA_FP64_PLAIN) return fail(MALA_ERR_INVALID_ARG, "bad precision");
+    std::lock_guard<std::mutex> lk(c->mu);
+    MALA_CUDA_TRY(cudaSetDevice(c->device));
+    return mlp_forward(c, m, B_dev, P, ldos_dev, dos_sum_dev, precision, as_stream(stream));
+}
+
+int mala_integrate(mala_ctx* c, const void* ldos_dev, int64_t P, double cell_volume_, const mala_energy_grid* eg,
+                   const double* dos_sum_dev, void* density_dev, double* dos_host, double* fermi_eV,
+                   double* band_energy_eV, double* electron_count, mala_precision precision, void* stream) {
+    if (!c || P < 0 || (P > 0 && !ldos_dev && !dos_sum_dev)) return fail(MALA_ERR_INVALID_ARG, "bad arguments");
+    MALA_TRY(check_egrid(eg));
+    if (!(cell_volume_ > 0.0)) return fail(MALA_ERR_INVALID_ARG, "cell volume must be > 0");
+    if (precision != MALA_MIXED && precision != MALA_FP64_PLAIN) return fail(MALA_ERR_INVALID_ARG, "bad precision");
+    if (density_dev && !ldos_dev) return fail(MALA_ERR_INVALID_ARG, "density needs the LDOS");
+    std::lock_guard<std::mutex> lk(c->mu);
+    MALA_CUDA_TRY(cudaSetDevice(c->device));
+    return integrate(c, ldos_dev, P, cell_volume_, eg, dos_sum_dev, density_dev, dos_host, fermi_eV, band_energy_eV,
+                     electron_count, precision, as_stream(stream));
+}
+
+int mala_electron_count(mala_ctx* c, const double* dos_host, const mala_energy_grid* eg, double mu, double* count) {
+    if (!c || !dos_host || !count || !std::isfinite(mu)) return fail(MALA_ERR_INVALID_ARG, "bad arguments");
+    MALA_TRY(check_egrid(eg));
+    std::lock_guard<std::mutex> lk(c->mu);
+    MALA_CUDA_TRY(cudaSetDevice(c->device));
+    return electron_count_at(c, dos_host, eg, mu, count, c->stream);
+}
+
+int mala_predict(mala_ctx* c, const mala_snapshot* snap, const mala_bispectrum_params* bp, const mala_model* m,
+                 const mala_energy_grid* eg, mala_precision prec, void* density_host, mala_result* res, void* stream) {
+    if (!c || !res) return fail(MALA_ERR_INVALID_ARG, "NULL argument");
+    memset(res, 0, sizeof(*res));
+    MALA_TRY(check_path_args(snap, bp, m, eg, prec));
+    std::lock_guard<std::mutex> lk(c->mu);
+    MALA_CUDA_TRY(cudaSetDevice(c->device));
+    const int64_t P = (int64_t)snap->grid[0] * snap->grid[1] * snap->grid[2];
+    const int nB = n_triples(bp->twojmax), nE = eg->n_E;
+    const size_t e = prec == MALA_MIXED ? 4 : 8, l = prec == MALA_MIXED ? 2 : 8;
+    MALA_TRY(c->ws_B.reserve(c, (size_t)P * nB * e + 256));
+    MALA_TRY(c->ws_ldos.reserve(c, (size_t)P * nE * l + 256));
+    MALA_TRY(c->ws_dens.reserve(c, (size_t)P * e + 256));
+    MALA_TRY(c->ws_dos.reserve(c, (size_t)nE * 8 + 256));
+    cudaStream_t st = as_stream(stream);
+    int rc = run_path(c, snap, bp, m, eg, prec, c->ws_B.ptr, c->ws_ldos.ptr, c->ws_dens.ptr, c->ws_dos.as<double>(), res,
+                      nullptr, st);
+    res->dos = c->host_dos;
+    if (rc != MALA_OK && rc != MALA_ERR_FERMI_BRACKET) return rc;
+    if (density_host) {
+        MALA_CUDA_TRY(cudaMemcpyAsync(density_host, c->ws_dens.ptr, (size_t)P * e, cudaMemcpyDeviceToHost, st));
+        MALA_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    return rc;
+}
+
+int mala_submit(mala_ctx* c, const mala_snapshot* snap, const mala_bispectrum_params* bp, const mala_model* m,
+                const mala_energy_grid* eg, mala_precision prec, uint64_t* ticket) {
+    if (!c || !ticket) return fail(MALA_ERR_INVALID_ARG, "NULL argument");
+    MALA_TRY(check_path_args(snap, bp, m, eg, prec));
+    if (!c->server) {
+        std::lock_guard<std::mutex> lk(c->mu);
+        MALA_TRY(server_start(c));
+    }
+    auto r = std::make_unique<Request>();
+    r->pos.assign(snap->pos, snap->pos + 3 * (size_t)snap->n_atoms);
+    if (snap->species) r->species.assign(snap->species, snap->species + snap->n_atoms);
+    r->snap = *snap;
+    r->snap.pos = r->pos.data();
+    r->snap.species = snap->species ? r->species.data() : nullptr;
+    r->bp = *bp;
+    if (bp->weights) {
+        r->weights.assign(bp->weights, bp->weights + bp->n_species);
+        r->bp.weights = r->weights.data();
+    }
+    r->eg = *eg;
+    r->model = m;
+    r->prec = prec;
+    r->P = (int64_t)snap->grid[0] * snap->grid[1] * snap->grid[2];
+    r->out_bytes = path_output_bytes(r->P, n_triples(bp->twojmax), eg->n_E, prec);
+    r->t_submit = std::chrono::steady_clock::now();
+    Server* sv = c->server;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        r->ticket = sv->next_ticket++;
+        *ticket = r->ticket;
+        sv->queue.push_back(r->ticket);
+        sv->reqs[r->ticket] = std::move(r);
+    }
+    sv->cv_work.notify_one();
+    return MALA_OK;
+}
+
+static int fill_result(Request* r, mala_result* out) {
+    if (r->state != 2) return MALA_PENDING;
+    if (out) *out = r->res;
+    if (r->status != MALA_OK) return fail(r->status, "%s", r->error.c_str());
+    return MALA_OK;
+}
+
+int mala_poll(mala_ctx* c, uint64_t ticket, mala_result* out) {
+    if (!c || !c->server) return fail(MALA_ERR_NOT_FOUND, "no such ticket");
+    Server* sv = c->server;
+    std::lock_guard<std::mutex> lk(sv->mu);
+    auto it = sv->reqs.find(ticket);
+    if (it == sv->reqs.end()) return fail(MALA_ERR_NOT_FOUND, "no such ticket");
+    return fill_result(it->second.get(), out);
+}
+
+int mala_wait(mala_ctx* c, uint64_t ticket, double timeout_s, mala_result* out) {
+    if (!c || !c->server) return fail(MALA_ERR_NOT_FOUND, "no such ticket");
+    Server* sv = c->server;
+    std::unique_lock<std::mutex> lk(sv->mu);
+    auto it = sv->reqs.find(ticket);
+    if (it == sv->reqs.end()) return fail(MALA_ERR_NOT_FOUND, "no such ticket");
+    Request* r = it->second.get();
+    const auto deadline = std::chrono::steady_clock::now() + std::chrono::duration<double>(timeout_s);
+    while (r->state != 2) {
+        if (sv->cv_done.wait_until(lk, deadline) == std::cv_status::timeout && r->state != 2)
+            return fail(MALA_ERR_TIMEOUT, "request %llu not done after %.3f s", (unsigned long long)ticket, timeout_s);
+    }
+    return fill_result(r, out);
+}
+
+int mala_release(mala_ctx* c, uint64_t ticket) {
+    if (!c || !c->server) return fail(MALA_ERR_NOT_FOUND, "no such ticket");
+    Server* sv = c->server;
+    std::unique_ptr<Request> r;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        auto it = sv->reqs.find(ticket);
+        if (it == sv->reqs.end()) return fail(MALA_ERR_NOT_FOUND, "no such ticket");
+        if (it->second->state != 2) return fail(MALA_ERR_INVALID_ARG, "request %llu is still running", (unsigned long long)ticket);
+        r = std::move(it->second);
+        sv->reqs.erase(it);
+    }
+    if (r->buf) {
+        cudaFree(r->buf);
+        c->used -= r->buf_bytes;
+    }
+    sv->cv_work.notify_all();
+    return MALA_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,635 @@
+// mlp_tc.cu -- the per-point feed-forward network (paper Eq. ffnn,
+// x_{l+1} = act(W_l x_l + b_l)) on the 5th-generation tensor cores, plus the
+// FP64 path.
+//
+// MIXED path, one CTA of 4 warps per tile of 128 grid points (M = 128):
+//   * the descriptors B[P][n_B] (FP32) are standardised ((B - shift) * scale),
+//     rounded to BF16 and written to shared memory in the UMMA K-major layout
+//     with the 128-byte swizzle (the layout TMA produces with SWIZZLE_128B);
+//   * every layer is a chain of tcgen05.mma (kind::f16, BF16 x BF16 -> FP32)
+//     issued by one thread into a tensor-memory accumulator D[128][N] (one TMEM
+//     lane per point); the layer's weights W_l[N][K] stream through a
+//     double-buffered shared-memory stage in K-blocks of 64 by TMA;
+//   * the epilogue reads D with tcgen05.ld (thread = point), adds the bias,
+//     applies LeakyReLU on hidden layers and writes the BF16 activations back
+//     to shared memory as the next layer's A operand (same swizzled layout);
+//   * the last epilogue writes the LDOS in BF16 and, from the same rounded
+//     values, the tile's column sums sum_r LDOS(r, xi) (the DOS partials, FP64).
+// Every wait on an mbarrier is bounded (about one second of clock cycles); on
+// expiry the kernel records an error code, frees its tensor memory and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+#include "mala_internal.h"
+
+namespace mala {
+
+namespace {
+
+constexpr int kMlpThreads = 128;
+constexpr int kMaxLayers = 4;
+constexpr int kKBlk = 64;             // K elements per swizzle block (128 bytes of BF16)
+constexpr int kMaxHiddenPad = 448;    // widest K of a hidden activation (7 blocks)
+constexpr int kMaxNPad = 400;         // widest layer output held in one W stage
+constexpr int kHBytes = 128 * kMaxHiddenPad * 2;  // 114688
+constexpr int kStageBytes = kMaxNPad * 128;        // 51200: [N rows][64 K] BF16
+constexpr int kSmemBytes = kHBytes + 2 * kStageBytes + 1024 /* barriers, tmem slot */ + 1024 /* alignment */;
+constexpr long long kWaitCycles = 2000000000LL;
+
+struct LayerDev {
+    int K, Kpad, N, Npad, nkb;  // nkb = Kpad / 64
+    int boxN;                   // TMA box rows (Npad split in <= 256-row boxes)
+    int act;                    // apply LeakyReLU
+    const float* bias;          // [Npad]
+};
+
+struct MlpParams {
+    int n_layers;
+    LayerDev L[kMaxLayers];
+    float slope;
+    int nB;                 // descriptor count (K of layer 0)
+    const float* B;         // [P][nB]
+    const float* shift;     // [nB]
+    const float* scale;     // [nB]
+    __nv_bfloat16* ldos;    // [P][N_E]
+    double* tile_dos;       // [n_tiles][N_E] or nullptr
+    int64_t P;
+    int* err;
+};
+
+struct TMaps {
+    CUtensorMap m[kMaxLayers];
+};
+
+// ---- PTX wrappers ---------------------------------------------------------
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t phase) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait; false (and *err set) if the phase did not complete in time.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase, int* err, int code) {
+    const long long t0 = clock64();
+    while (!mbar_try(bar, phase)) {
+        if (clock64() - t0 > kWaitCycles) {
+            atomicCAS(err, 0, code);
+            return false;
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row
+// groups 1024 bytes apart (SBO), version 1.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+    d |= (uint64_t)1 << 16;                   // LBO (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;         // SBO
+    d |= (uint64_t)1 << 46;                   // descriptor version
+    d |= (uint64_t)2 << 61;                   // SWIZZLE_128B
+    return d;
+}
+
+// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major.
+__device__ __forceinline__ uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// byte offset of element (row r, k) in a [128][64] BF16 K-block with the
+// 128-byte swizzle (16-byte chunk index XOR row % 8)
+__device__ __forceinline__ uint32_t swz(int r, int k) {
+    return (uint32_t)(r * 128 + ((((k >> 3) ^ (r & 7)) & 7) << 4) + ((k & 7) << 1));
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t*>(&h);
+}
+
+__global__ void __launch_bounds__(kMlpThreads, 1) k_mlp_tc(const __grid_constant__ TMaps maps, MlpParams prm) {
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    unsigned char* sH = sm;                          // activations, K-blocks of [128][64] BF16
+    unsigned char* sW = sm + kHBytes;                // two weight stages
+    // barriers: full[2] (TMA -> stage), done (end of a layer's MMAs, waited by
+    // every thread), free (a stage's MMAs finished, waited by the issuing thread)
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sm + kHBytes + 2 * kStageBytes);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 4);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int64_t row0 = (int64_t)blockIdx.x * 128;
+    const uint32_t bar_full0 = smem_u32(&bars[0]), bar_full1 = smem_u32(&bars[1]), bar_done = smem_u32(&bars[2]);
+    const uint32_t bar_free = smem_u32(&bars[3]);
+
+    if (tid == 0) {
+        mbar_init(bar_full0, 1);
+        mbar_init(bar_full1, 1);
+        mbar_init(bar_done, 1);
+        mbar_init(bar_free, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        for (int l = 0; l < prm.n_layers; ++l)
+            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&maps.m[l])) : "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(tslot)));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    // ---- input tile: (B - shift) * scale -> BF16, swizzled, zero-padded ----
+    {
+        const int K0pad = prm.L[0].Kpad;
+        for (int idx = tid; idx < 128 * K0pad; idx += kMlpThreads) {
+            const int r = idx / K0pad, k = idx % K0pad;
+            float v = 0.f;
+            if (k < prm.nB && row0 + r < prm.P) v = (prm.B[(row0 + r) * prm.nB + k] - prm.shift[k]) * prm.scale[k];
+            const __nv_bfloat16 h = __float2bfloat16_rn(v);
+            *reinterpret_cast<__nv_bfloat16*>(sH + (k / kKBlk) * (128 * 128) + swz(r, k % kKBlk)) = h;
+        }
+    }
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+    uint32_t ph_full[2] = {0, 0}, ph_done = 0, ph_free = 0;
+    bool ok = true;
+
+    for (int l = 0; l < prm.n_layers && ok; ++l) {
+        const LayerDev& L = prm.L[l];
+        // ---- MMA chain of layer l (one thread issues, the rest wait) ----
+        if (tid == 0) {
+            const uint32_t stage_bytes = (uint32_t)L.Npad * 128u;
+            auto load_stage = [&](int kb, int s) {
+                const uint32_t bar = s ? bar_full1 : bar_full0;
+                mbar_expect_tx(bar, stage_bytes);
+                for (int n0 = 0; n0 < L.Npad; n0 += L.boxN)
+                    tma_load_2d(smem_u32(sW + s * kStageBytes + n0 * 128), &maps.m[l], kb * kKBlk, n0, bar);
+            };
+            load_stage(0, 0);
+            if (L.nkb > 1) load_stage(1, 1);
+            for (int kb = 0; kb < L.nkb && ok; ++kb) {
+                const int s = kb & 1;
+                ok = mbar_wait(s ? bar_full1 : bar_full0, ph_full[s], prm.err, 2);
+                ph_full[s] ^= 1;
+                if (!ok) break;
+                tc_fence_after();
+                const uint32_t a_base = smem_u32(sH + kb * (128 * 128));
+                const uint32_t b_base = smem_u32(sW + s * kStageBytes);
+                for (int k = 0; k < kKBlk / 16; ++k) {
+                    for (int n0 = 0; n0 < L.Npad; n0 += 256) {
+                        const int nn = min(256, L.Npad - n0);
+                        mma_bf16(tmem + (uint32_t)n0, sdesc(a_base + k * 32), sdesc(b_base + n0 * 128 + k * 32),
+                                 idesc_bf16(128, nn), (kb > 0 || k > 0) ? 1u : 0u);
+                    }
+                }
+                if (kb + 2 < L.nkb) {
+                    // the stage is refilled once the MMAs reading it have completed
+                    mma_commit(bar_free);
+                    ok = mbar_wait(bar_free, ph_free, prm.err, 3);
+                    ph_free ^= 1;
+                    if (ok) load_stage(kb + 2, s);
+                }
+            }
+            mma_commit(bar_done);
+        }
+        __syncthreads();
+        if (!ok) break;
+        ok = mbar_wait(bar_done, ph_done, prm.err, 4);
+        ph_done ^= 1;
+        if (!__syncthreads_and(ok)) {
+            ok = false;
+            break;
+        }
+        tc_fence_after();
+        // ---- epilogue: TMEM -> registers (thread = point) -> bias/activation ----
+        const int r = tid;
+        const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+        const bool last = (l == prm.n_layers - 1);
+        if (!last) {
+            const int Knext = prm.L[l + 1].Kpad;
+            for (int c0 = 0; c0 < Knext; c0 += 16) {
+                float v[16];
+                if (c0 < L.Npad) {
+                    tmem_ld16(trow + (uint32_t)c0, v);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) v[i] = 0.f;
+                }
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const int c = c0 + i;
+                    float x = (c < L.N) ? v[i] + L.bias[c] : 0.f;
+                    if (L.act) x = x > 0.f ? x : prm.slope * x;
+                    v[i] = x;
+                }
+                uint4 q0, q1;
+                q0.x = pack_bf16(v[0], v[1]);
+                q0.y = pack_bf16(v[2], v[3]);
+                q0.z = pack_bf16(v[4], v[5]);
+                q0.w = pack_bf16(v[6], v[7]);
+                q1.x = pack_bf16(v[8], v[9]);
+                q1.y = pack_bf16(v[10], v[11]);
+                q1.z = pack_bf16(v[12], v[13]);
+                q1.w = pack_bf16(v[14], v[15]);
+                unsigned char* blk = sH + (c0 / kKBlk) * (128 * 128);
+                *reinterpret_cast<uint4*>(blk + swz(r, c0 % kKBlk)) = q0;
+                *reinterpret_cast<uint4*>(blk + swz(r, c0 % kKBlk + 8)) = q1;
+            }
+            fence_proxy_async();
+            tc_fence_before();
+            __syncthreads();
+            tc_fence_after();
+        } else {
+            // output: BF16 rows staged in the (now idle) weight stages, then
+            // coalesced stores and per-column sums of the stored values
+            const int NE = L.N;
+            __nv_bfloat16* so = reinterpret_cast<__nv_bfloat16*>(sW);  // [128][NEpad16]
+            const int ldo = (NE + 15) & ~15;
+            for (int c0 = 0; c0 < ldo; c0 += 16) {
+                float v[16];
+                tmem_ld16(trow + (uint32_t)c0, v);
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const int c = c0 + i;
+                    float x = (c < NE) ? v[i] + L.bias[c] : 0.f;
+                    if (L.act) x = x > 0.f ? x : prm.slope * x;
+                    so[r * ldo + c] = __float2bfloat16_rn(x);
+                }
+            }
+            tc_fence_before();
+            __syncthreads();
+            const int64_t nrows = min((int64_t)128, prm.P - row0);
+            for (int idx = tid; idx < nrows * NE; idx += kMlpThreads) {
+                const int rr = idx / NE, c = idx % NE;
+                prm.ldos[(row0 + rr) * NE + c] = so[rr * ldo + c];
+            }
+            if (prm.tile_dos) {
+                for (int c = tid; c < NE; c += kMlpThreads) {
+                    float s = 0.f;
+                    for (int rr = 0; rr < nrows; ++rr) s += __bfloat162float(so[rr * ldo + c]);
+                    prm.tile_dos[(int64_t)blockIdx.x * NE + c] = (double)s;
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
+    }
+}
+
+// ---- FP64 path: plain tiled GEMM + bias + activation per layer -------------
+
+constexpr int kT64 = 32;
+
+__global__ void k_mlp_f64_layer(const double* __restrict__ X, int ldx, int K, const double* __restrict__ W,
+                                const double* __restrict__ bias, int N, int64_t P, double slope, int act,
+                                const double* __restrict__ shift, const double* __restrict__ scale,
+                                double* __restrict__ Y) {
+    __shared__ double sx[kT64][kT64 + 1];
+    __shared__ double sw[kT64][kT64 + 1];
+    const int tx = threadIdx.x % kT64, ty = threadIdx.x / kT64;  // 32 x 8 threads
+    const int64_t r0 = (int64_t)blockIdx.x * kT64;
+    const int n0 = blockIdx.y * kT64;
+    double acc[4] = {0, 0, 0, 0};
+    for (int k0 = 0; k0 < K; k0 += kT64) {
+        for (int i = ty; i < kT64; i += 8) {
+            const int64_t r = r0 + i;
+            const int k = k0 + tx;
+            double v = 0.0;
+            if (r < P && k < K) {
+                v = X[r * ldx + k];
+                if (shift) v = (v - shift[k]) * scale[k];
+            }
+            sx[i][tx] = v;
+            const int n = n0 + i;
+            sw[i][tx] = (n < N && k < K) ? W[(int64_t)n * K + k] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int kk = 0; kk < kT64; ++kk) {
+            const double wv = sw[tx][kk];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[j] += sx[ty + 8 * j][kk] * wv;
+        }
+        __syncthreads();
+    }
+    const int n = n0 + tx;
+    if (n >= N) return;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int64_t r = r0 + ty + 8 * j;
+        if (r >= P) continue;
+        double v = acc[j] + bias[n];
+        if (act) v = v > 0.0 ? v : slope * v;
+        Y[r * N + n] = v;
+    }
+}
+
+// column sums of the FP64 LDOS per block of rows
+__global__ void k_colsum_f64(const double* __restrict__ L, int64_t P, int NE, int64_t rows_per_block,
+                             double* __restrict__ part) {
+    const int64_t r0 = (int64_t)blockIdx.x * rows_per_block;
+    const int64_t r1 = min(P, r0 + rows_per_block);
+    for (int c = threadIdx.x; c < NE; c += blockDim.x) {
+        double s = 0.0;
+        for (int64_t r = r0; r < r1; ++r) s += L[r * NE + c];
+        part[(int64_t)blockIdx.x * NE + c] = s;
+    }
+}
+
+// deterministic sum of partial rows: out[c] = sum_t part[t][c] in order of t
+__global__ void k_dos_reduce(const double* __restrict__ part, int64_t nt, int NE, double* __restrict__ out) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= NE) return;
+    double s = 0.0;
+    for (int64_t t = 0; t < nt; ++t) s += part[t * NE + c];
+    out[c] = s;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+int pad_to(int v, int m) { return (v + m - 1) / m * m; }
+
+}  // namespace
+
+// ---- model upload -----------------------------------------------------------
+
+int model_upload(Ctx* c, const mala_mlp_desc* d, Model* m) {
+    m->ctx = c;
+    m->n_layers = d->n_layers;
+    m->dims.assign(d->dims, d->dims + d->n_layers + 1);
+    m->leaky_slope = (float)d->leaky_slope;
+    m->slope_d = d->leaky_slope;
+    m->activate_output = d->activate_output;
+    const int nl = d->n_layers;
+    // MIXED layout: K padded to 64 (128-byte swizzle blocks), N padded to 16
+    m->Kpad.resize(nl);
+    m->Npad.resize(nl);
+    m->mixed_ok = true;
+    for (int l = 0; l < nl; ++l) {
+        m->Kpad[l] = pad_to(m->dims[l], kKBlk);
+        m->Npad[l] = pad_to(m->dims[l + 1], 16);
+        if (l > 0 && m->Kpad[l] > kMaxHiddenPad) m->mixed_ok = false;
+        if (m->Kpad[l] > kMaxHiddenPad || m->Npad[l] > kMaxNPad) m->mixed_ok = false;
+        if (l + 1 < nl && pad_to(m->dims[l + 1], kKBlk) > kMaxHiddenPad) m->mixed_ok = false;
+    }
+    if (nl > kMaxLayers) m->mixed_ok = false;
+    if (m->dims[nl] > 256) m->mixed_ok = false;
+    auto dalloc = [&](size_t bytes, void** p) -> int {
+        Ctx* r = c->root();
+        if (r->budget && r->used + bytes > r->budget) return fail(MALA_ERR_OOM, "model exceeds the HBM budget");
+        if (cudaMalloc(p, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(MALA_ERR_OOM, "cudaMalloc for the model failed");
+        }
+        r->used += bytes;
+        m->bytes += bytes;
+        m->allocs.push_back(*p);
+        return MALA_OK;
+    };
+    for (int l = 0; l < nl; ++l) {
+        const int K = m->dims[l], N = m->dims[l + 1];
+        // FP64 copies
+        void* pw = nullptr;
+        void* pb = nullptr;
+        MALA_TRY(dalloc(sizeof(double) * (size_t)K * N, &pw));
+        MALA_TRY(dalloc(sizeof(double) * (size_t)N, &pb));
+        MALA_CUDA_TRY(cudaMemcpy(pw, d->W[l], sizeof(double) * (size_t)K * N, cudaMemcpyHostToDevice));
+        MALA_CUDA_TRY(cudaMemcpy(pb, d->b[l], sizeof(double) * (size_t)N, cudaMemcpyHostToDevice));
+        m->Wd.push_back((double*)pw);
+        m->bd.push_back((double*)pb);
+        if (!m->mixed_ok) continue;
+        // BF16 [Npad][Kpad], FP32 bias [Npad]
+        const int Kp = m->Kpad[l], Np = m->Npad[l];
+        std::vector<__nv_bfloat16> w((size_t)Np * Kp, __float2bfloat16(0.f));
+        std::vector<float> bb(Np, 0.f);
+        for (int n = 0; n < N; ++n) {
+            for (int k = 0; k < K; ++k) w[(size_t)n * Kp + k] = __float2bfloat16((float)d->W[l][(size_t)n * K + k]);
+            bb[n] = (float)d->b[l][n];
+        }
+        void* pwb = nullptr;
+        void* pbb = nullptr;
+        MALA_TRY(dalloc(sizeof(__nv_bfloat16) * w.size(), &pwb));
+        MALA_TRY(dalloc(sizeof(float) * bb.size(), &pbb));
+        MALA_CUDA_TRY(cudaMemcpy(pwb, w.data(), sizeof(__nv_bfloat16) * w.size(), cudaMemcpyHostToDevice));
+        MALA_CUDA_TRY(cudaMemcpy(pbb, bb.data(), sizeof(float) * bb.size(), cudaMemcpyHostToDevice));
+        m->Wbf.push_back(pwb);
+        m->bias.push_back((float*)pbb);
+    }
+    // input standardisation (identity when absent)
+    const int n0 = m->dims[0];
+    std::vector<double> sh(n0, 0.0), sc(n0, 1.0);
+    if (d->in_shift) for (int k = 0; k < n0; ++k) sh[k] = d->in_shift[k];
+    if (d->in_scale) for (int k = 0; k < n0; ++k) sc[k] = d->in_scale[k];
+    std::vector<float> shf(sh.begin(), sh.end()), scf(sc.begin(), sc.end());
+    void* p1 = nullptr;
+    void* p2 = nullptr;
+    void* p3 = nullptr;
+    void* p4 = nullptr;
+    MALA_TRY(dalloc(sizeof(float) * n0, &p1));
+    MALA_TRY(dalloc(sizeof(float) * n0, &p2));
+    MALA_TRY(dalloc(sizeof(double) * n0, &p3));
+    MALA_TRY(dalloc(sizeof(double) * n0, &p4));
+    MALA_CUDA_TRY(cudaMemcpy(p1, shf.data(), sizeof(float) * n0, cudaMemcpyHostToDevice));
+    MALA_CUDA_TRY(cudaMemcpy(p2, scf.data(), sizeof(float) * n0, cudaMemcpyHostToDevice));
+    MALA_CUDA_TRY(cudaMemcpy(p3, sh.data(), sizeof(double) * n0, cudaMemcpyHostToDevice));
+    MALA_CUDA_TRY(cudaMemcpy(p4, sc.data(), sizeof(double) * n0, cudaMemcpyHostToDevice));
+    m->in_shift = (float*)p1;
+    m->in_scale = (float*)p2;
+    m->in_shift_d = (double*)p3;
+    m->in_scale_d = (double*)p4;
+    // tensor maps of the BF16 weights
+    if (m->mixed_ok) {
+        auto enc = get_encode();
+        if (!enc) return fail(MALA_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+        for (int l = 0; l < nl; ++l) {
+            const int Kp = m->Kpad[l], Np = m->Npad[l];
+            int boxN = Np;
+            while (boxN > 256) boxN /= 2;  // 400 -> 200
+            boxN = pad_to(boxN, 8);
+            while (Np % boxN) boxN -= 8;
+            m->boxN.push_back(boxN);
+            CUtensorMap map;
+            cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)Np};
+            cuuint64_t strides[1] = {(cuuint64_t)Kp * 2};
+            cuuint32_t box[2] = {(cuuint32_t)kKBlk, (cuuint32_t)boxN};
+            cuuint32_t es[2] = {1, 1};
+            CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, m->Wbf[l], dims, strides, box, es,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS) return fail(MALA_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d) for layer %d", (int)r, l);
+            m->maps.push_back(map);
+        }
+    }
+    return MALA_OK;
+}
+
+void model_free(Model* m) {
+    for (void* p : m->allocs) cudaFree(p);
+    if (m->ctx) m->ctx->root()->used -= m->bytes;
+    m->allocs.clear();
+    m->bytes = 0;
+}
+
+// ---- forward ------------------------------------------------------------------
+
+int mlp_forward(Ctx* c, const Model* m, const void* B, int64_t P, void* ldos, double* dos_sum, mala_precision prec,
+                cudaStream_t st) {
+    const int nl = m->n_layers;
+    const int NE = m->dims[nl];
+    if (P <= 0) {
+        if (dos_sum) MALA_CUDA_TRY(cudaMemsetAsync(dos_sum, 0, sizeof(double) * NE, st));
+        return MALA_OK;
+    }
+    if (prec == MALA_MIXED) {
+        if (!m->mixed_ok)
+            return fail(MALA_ERR_UNSUPPORTED, "network shape outside the tensor-core kernel's limits "
+                                              "(<= %d layers, hidden width <= %d, output <= 256)", kMaxLayers, kMaxHiddenPad);
+        const int64_t ntiles = (P + 127) / 128;
+        double* tile_dos = nullptr;
+        if (dos_sum) {
+            MALA_TRY(c->ws_tile_dos.reserve(c, sizeof(double) * (size_t)ntiles * NE));
+            tile_dos = c->ws_tile_dos.as<double>();
+        }
+        TMaps maps;
+        memset(&maps, 0, sizeof(maps));
+        MlpParams prm;
+        memset(&prm, 0, sizeof(prm));
+        prm.n_layers = nl;
+        for (int l = 0; l < nl; ++l) {
+            maps.m[l] = m->maps[l];
+            LayerDev& L = prm.L[l];
+            L.K = m->dims[l];
+            L.Kpad = m->Kpad[l];
+            L.N = m->dims[l + 1];
+            L.Npad = m->Npad[l];
+            L.nkb = L.Kpad / kKBlk;
+            L.boxN = m->boxN[l];
+            L.act = (l < nl - 1) || m->activate_output;
+            L.bias = m->bias[l];
+        }
+        // hidden layers feed the next layer with K = Npad rounded to 64
+        for (int l = 0; l + 1 < nl; ++l) prm.L[l + 1].Kpad = pad_to(m->dims[l + 1], kKBlk), prm.L[l + 1].nkb = prm.L[l + 1].Kpad / kKBlk;
+        prm.slope = m->leaky_slope;
+        prm.nB = m->dims[0];
+        prm.B = static_cast<const float*>(B);
+        prm.shift = m->in_shift;
+        prm.scale = m->in_scale;
+        prm.ldos = static_cast<__nv_bfloat16*>(ldos);
+        prm.tile_dos = tile_dos;
+        prm.P = P;
+        prm.err = c->tables.err_d + 1;
+        cudaFuncSetAttribute(k_mlp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+        MALA_PROF(c, "k_mlp", st, (k_mlp_tc<<<(unsigned)ntiles, kMlpThreads, kSmemBytes, st>>>(maps, prm)));
+        MALA_CUDA_TRY(cudaGetLastError());
+        if (dos_sum)
+            MALA_PROF(c, "k_dos_reduce", st,
+                      (k_dos_reduce<<<(NE + 127) / 128, 128, 0, st>>>(tile_dos, ntiles, NE, dos_sum)));
+        MALA_CUDA_TRY(cudaGetLastError());
+        return MALA_OK;
+    }
+    // FP64: layer by layer through a ping-pong workspace
+    int wmax = 0;
+    for (int l = 1; l < nl; ++l) wmax = std::max(wmax, m->dims[l]);
+    MALA_TRY(c->ws_mlp64.reserve(c, sizeof(double) * (size_t)P * (size_t)std::max(1, wmax) * 2));
+    double* buf[2] = {c->ws_mlp64.as<double>(), c->ws_mlp64.as<double>() + (size_t)P * std::max(1, wmax)};
+    const double* x = static_cast<const double*>(B);
+    int ldx = m->dims[0];
+    for (int l = 0; l < nl; ++l) {
+        const int K = m->dims[l], N = m->dims[l + 1];
+        double* y = (l == nl - 1) ? static_cast<double*>(ldos) : buf[l & 1];
+        dim3 grid((unsigned)((P + kT64 - 1) / kT64), (unsigned)((N + kT64 - 1) / kT64));
+        const int act = (l < nl - 1) || m->activate_output;
+        MALA_PROF(c, "k_mlp", st,
+                  (k_mlp_f64_layer<<<grid, kT64 * 8, 0, st>>>(x, ldx, K, m->Wd[l], m->bd[l], N, P, m->slope_d, act,
+                                                            l == 0 ? m->in_shift_d : nullptr,
+                                                            l == 0 ? m->in_scale_d : nullptr, y)));
+        x = y;
+        ldx = N;
+    }
+    MALA_CUDA_TRY(cudaGetLastError());
+    if (dos_sum) {
+        const int64_t rpb = 1024;
+        const int64_t nb = (P + rpb - 1) / rpb;
+        MALA_TRY(c->ws_tile_dos.reserve(c, sizeof(double) * (size_t)nb * NE));
+        k_colsum_f64<<<(unsigned)nb, 128, 0, st>>>(static_cast<const double*>(ldos), P, NE, rpb, c->ws_tile_dos.as<double>());
+        MALA_PROF(c, "k_dos_reduce", st,
+                  (k_dos_reduce<<<(NE + 127) / 128, 128, 0, st>>>(c->ws_tile_dos.as<double>(), nb, NE, dos_sum)));
+        MALA_CUDA_TRY(cudaGetLastError());
+    }
+    return MALA_OK;
+}
+
+}  // namespace mala

@@ -208,14 +208,24 @@ def serving_trace(n_req: int = 2000, rate_per_s: float = 200.0, seed: int = 5,
 # network parameters
 # --------------------------------------------------------------------------
 
-def random_mlp(dims: Sequence[int], seed: int, leaky_slope: float = 0.01) -> MLP:
+def random_mlp(dims: Sequence[int], seed: int, leaky_slope: float = 0.01, out_bias: float = 0.0) -> MLP:
+    """Random network; `out_bias` is added to the output layer's bias so that a
+    random network on standardised inputs yields a mostly positive LDOS (a
+    physical LDOS is non-negative, which makes the Fermi level unique)."""
     rng = np.random.default_rng(seed)
     W, b = [], []
     for l in range(len(dims) - 1):
         bound = 1.0 / math.sqrt(dims[l])
         W.append(rng.uniform(-bound, bound, size=(dims[l + 1], dims[l])))
         b.append(rng.uniform(-bound, bound, size=(dims[l + 1],)))
+    b[-1] = b[-1] + out_bias
     return MLP(dims=tuple(int(d) for d in dims), W=W, b=b, leaky_slope=leaky_slope)
+
+
+def with_input_scaling(mlp: MLP, shift: np.ndarray, scale: np.ndarray) -> MLP:
+    """Copy of `mlp` with the input standardisation (x - shift) * scale."""
+    return MLP(dims=mlp.dims, W=mlp.W, b=mlp.b, leaky_slope=mlp.leaky_slope,
+               in_shift=np.asarray(shift, np.float64), in_scale=np.asarray(scale, np.float64))
 
 
 # --------------------------------------------------------------------------
@@ -229,31 +239,31 @@ def config(idx: int):
     if idx == 1:
         snap = al_fcc(2, 0.1, 18, seed=1)
         bp = BispectrumParams(twojmax=6, rcut=4.676)
-        mlp = random_mlp((30, 100, 100, 11), seed=11)
+        mlp = random_mlp((30, 100, 100, 11), seed=11, out_bias=1.0)
         eg = EnergyGrid(n_E=11, e0_eV=-5.0, de_eV=1.0)
         return [snap], bp, mlp, eg, "fp64"
     if idx == 2:
         snap = al_fcc(4, 0.3, 90, seed=2)
         bp = BispectrumParams(twojmax=10, rcut=4.676)
-        mlp = random_mlp((91, 400, 400, 250), seed=12)
+        mlp = random_mlp((91, 400, 400, 250), seed=12, out_bias=1.0)
         eg = EnergyGrid(n_E=250, e0_eV=-8.0, de_eV=0.1)
         return [snap], bp, mlp, eg, "mixed"
     if idx == 3:
         snaps = boron_clusters(64, seed=3)
         bp = BispectrumParams(twojmax=10, rcut=4.676)
-        mlp = random_mlp((91, 400, 400, 11), seed=13)
+        mlp = random_mlp((91, 400, 400, 11), seed=13, out_bias=1.0)
         eg = EnergyGrid(n_E=11, e0_eV=-5.0, de_eV=1.0)
         return snaps, bp, mlp, eg, "mixed"
     if idx == 4:
         snap = be_slab()
         bp = BispectrumParams(twojmax=10, rcut=4.5)
-        mlp = random_mlp((91, 400, 400, 11), seed=14)
+        mlp = random_mlp((91, 400, 400, 11), seed=14, out_bias=1.0)
         eg = EnergyGrid(n_E=11, e0_eV=-5.0, de_eV=1.0)
         return [snap], bp, mlp, eg, "mixed"
     if idx == 5:
         reqs = serving_trace()
         bp = BispectrumParams(twojmax=10, rcut=4.676)
-        mlp = random_mlp((91, 400, 400, 250), seed=15)
+        mlp = random_mlp((91, 400, 400, 250), seed=15, out_bias=1.0)
         eg = EnergyGrid(n_E=250, e0_eV=-8.0, de_eV=0.1)
         return reqs, bp, mlp, eg, "mixed"
     raise ValueError(f"unknown workload {idx}")

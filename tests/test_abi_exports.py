@@ -1,0 +1,45 @@
+"""The C ABI library builds for sm_103a, loads on a machine without a GPU and
+exports every function include/mala.h declares; the ctypes prototypes cover
+the same set.  No compute call is made here."""
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    src = open(os.path.join(ROOT, "include", "mala.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*(mala_[a-z_0-9]+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_hot_path_calls():
+    names = _declared_functions()
+    for required in ("mala_descriptors", "mala_ldos_forward", "mala_integrate", "mala_submit", "mala_poll",
+                     "mala_create", "mala_destroy", "mala_last_error", "mala_predict"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2411_19617_gb300 import _lib, build
+    path = build.build()
+    assert os.path.exists(path)
+    L = _lib.lib(path)
+    missing = [n for n in _declared_functions() if not hasattr(L, n)]
+    assert not missing, missing
+    assert set(_declared_functions()) == set(_lib.PROTOTYPES), "ctypes prototypes out of sync with mala.h"
+    assert L.mala_version() == 1
+
+
+def test_binding_raises_without_the_library(tmp_path):
+    from paper_2411_19617_gb300 import _lib
+    saved = _lib._lib
+    _lib._lib = None
+    try:
+        with pytest.raises(RuntimeError):
+            _lib.lib(str(tmp_path / "missing.so"))
+    finally:
+        _lib._lib = saved
