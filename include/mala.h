@@ -133,7 +133,8 @@ size_t mala_device_bytes(const mala_ctx* ctx);
  * stream the kernel is launched on; mala_profile(ctx, 0) stops recording.
  * mala_profile_get waits for the recorded events and returns the summed
  * duration (ms) and the number of launches of the named kernel ("k_neighbors",
- * "k_ui", "k_zb", "k_mlp", "k_dos_reduce", "k_fermi", "k_density"). */
+ * "k_ui", "k_zb", "k_mlp", "k_dos_reduce", "k_fermi", "k_density", ...), or
+ * of every kernel of the library for the name "all". */
 int mala_profile(mala_ctx* ctx, int enable);
 int mala_profile_get(mala_ctx* ctx, const char* kernel, double* total_ms, int64_t* launches);
 

@@ -384,7 +384,8 @@ int electron_count_at(Ctx* c, const double* D_host, const mala_energy_grid* eg, 
     MALA_TRY(c->ws_w.reserve(c, sizeof(double) * (nE + 1)));
     double* d = c->ws_w.as<double>();
     MALA_CUDA_TRY(cudaMemcpyAsync(d, D_host, sizeof(double) * nE, cudaMemcpyHostToDevice, st));
-    k_count<<<1, kFermiThreads, sizeof(double) * nE, st>>>(d, nE, eg->e0_eV, eg->de_eV, eg->kT_eV, mu, d + nE);
+    MALA_PROF(c, "k_count", st,
+              (k_count<<<1, kFermiThreads, sizeof(double) * nE, st>>>(d, nE, eg->e0_eV, eg->de_eV, eg->kT_eV, mu, d + nE)));
     MALA_CUDA_TRY(cudaGetLastError());
     MALA_CUDA_TRY(cudaMemcpyAsync(c->host_scalars + 16, d + nE, sizeof(double), cudaMemcpyDeviceToHost, st));
     MALA_CUDA_TRY(cudaStreamSynchronize(st));
@@ -421,7 +422,7 @@ int integrate(Ctx* c, const void* ldos, int64_t P, double volume, const mala_ene
                 MALA_PROF(c, "k_dos_reduce", st,
                           (k_colsum<double><<<(unsigned)ntile, 256, 0, st>>>(static_cast<const double*>(ldos), P, nE,
                                                                             part)));
-            k_sum_rows<<<(nE + 127) / 128, 128, 0, st>>>(part, ntile, nE, dsum);
+            MALA_PROF(c, "k_sum_rows", st, (k_sum_rows<<<(nE + 127) / 128, 128, 0, st>>>(part, ntile, nE, dsum)));
         } else {
             MALA_CUDA_TRY(cudaMemsetAsync(dsum, 0, sizeof(double) * nE, st));
         }
@@ -441,7 +442,7 @@ int integrate(Ctx* c, const void* ldos, int64_t P, double volume, const mala_ene
             MALA_PROF(c, "k_density", st,
                       (k_density_f64<<<dens_blocks, kDensWarps * 32, 0, st>>>(static_cast<const double*>(ldos), P, nE,
                                                                              w0d, static_cast<double*>(density), part)));
-        k_sum_vec<<<1, 256, 0, st>>>(part, dens_blocks, nsum);
+        MALA_PROF(c, "k_sum_vec", st, (k_sum_vec<<<1, 256, 0, st>>>(part, dens_blocks, nsum)));
     } else {
         MALA_CUDA_TRY(cudaMemsetAsync(nsum, 0, sizeof(double), st));
     }

@@ -140,7 +140,7 @@ static int run_descriptors(Ctx* c, const mala_snapshot* snap, const mala_bispect
                 T* uh = c->ws_u.as<T>();
                 MALA_PROF(c, "k_ui", st, launch_ui<T>(tj, nb, bp->wself, nt, uh, st));
                 if (B) MALA_PROF(c, "k_zb", st, launch_zb<T>(c, tj, uh, g, t0, nt, B, st));
-                if (u_full) launch_u_expand<T>(tj, uh, g, t0, nt, u_full, st);
+                if (u_full) MALA_PROF(c, "k_u_expand", st, launch_u_expand<T>(tj, uh, g, t0, nt, u_full, st));
             }
         }
         MALA_CUDA_TRY(cudaGetLastError());
@@ -286,6 +286,17 @@ int mala_profile(mala_ctx* c, int enable) {
 int mala_profile_get(mala_ctx* c, const char* kernel, double* total_ms, int64_t* launches) {
     if (!c || !kernel) return fail(MALA_ERR_INVALID_ARG, "bad arguments");
     prof_collect(c);
+    if (strcmp(kernel, "all") == 0) {
+        double ms = 0.0;
+        int64_t n = 0;
+        for (auto& kv : c->prof.total) {
+            ms += kv.second.first;
+            n += kv.second.second;
+        }
+        if (total_ms) *total_ms = ms;
+        if (launches) *launches = n;
+        return MALA_OK;
+    }
     auto it = c->prof.total.find(kernel);
     if (total_ms) *total_ms = it == c->prof.total.end() ? 0.0 : it->second.first;
     if (launches) *launches = it == c->prof.total.end() ? 0 : it->second.second;

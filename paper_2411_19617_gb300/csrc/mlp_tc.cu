@@ -624,7 +624,9 @@ int mlp_forward(Ctx* c, const Model* m, const void* B, int64_t P, void* ldos, do
         const int64_t rpb = 1024;
         const int64_t nb = (P + rpb - 1) / rpb;
         MALA_TRY(c->ws_tile_dos.reserve(c, sizeof(double) * (size_t)nb * NE));
-        k_colsum_f64<<<(unsigned)nb, 128, 0, st>>>(static_cast<const double*>(ldos), P, NE, rpb, c->ws_tile_dos.as<double>());
+        MALA_PROF(c, "k_colsum", st,
+                  (k_colsum_f64<<<(unsigned)nb, 128, 0, st>>>(static_cast<const double*>(ldos), P, NE, rpb,
+                                                               c->ws_tile_dos.as<double>())));
         MALA_PROF(c, "k_dos_reduce", st,
                   (k_dos_reduce<<<(NE + 127) / 128, 128, 0, st>>>(c->ws_tile_dos.as<double>(), nb, NE, dos_sum)));
         MALA_CUDA_TRY(cudaGetLastError());

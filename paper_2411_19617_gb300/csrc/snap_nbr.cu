@@ -404,14 +404,18 @@ int stage_snapshot(Ctx* c, const mala_snapshot* snap, const mala_bispectrum_para
     MALA_CUDA_TRY(cudaMemsetAsync(sd->bin_fill, 0, sizeof(int) * nbins, st));
     MALA_CUDA_TRY(cudaMemsetAsync(sd->maxcnt, 0, sizeof(int) * 4, st));
     if (n > 0) {
-        k_stage_atoms<<<(n + 127) / 128, 128, 0, st>>>(n, pos_d, snap->species ? sp_d : nullptr,
-                                                       (bp && bp->weights) ? wtab : nullptr, ns, g,
-                                                       sd->wpos, sd->wsp, sd->bin_of, bcount, sd->maxcnt + 1);
+        MALA_PROF(c, "k_stage_atoms", st,
+                  (k_stage_atoms<<<(n + 127) / 128, 128, 0, st>>>(n, pos_d, snap->species ? sp_d : nullptr,
+                                                                  (bp && bp->weights) ? wtab : nullptr, ns, g, sd->wpos,
+                                                                  sd->wsp, sd->bin_of, bcount, sd->maxcnt + 1)));
     }
-    k_scan_bins<<<1, 1024, 0, st>>>(nbins, bcount, sd->bin_start);
+    MALA_PROF(c, "k_scan_bins", st, (k_scan_bins<<<1, 1024, 0, st>>>(nbins, bcount, sd->bin_start)));
     if (n > 0) {
-        k_fill_bins<<<(n + 127) / 128, 128, 0, st>>>(n, sd->bin_of, sd->bin_start, sd->bin_fill, sd->bin_atoms);
-        k_sort_bins<<<(nbins + 127) / 128, 128, 0, st>>>(nbins, sd->bin_start, sd->bin_atoms);
+        MALA_PROF(c, "k_fill_bins", st,
+                  (k_fill_bins<<<(n + 127) / 128, 128, 0, st>>>(n, sd->bin_of, sd->bin_start, sd->bin_fill,
+                                                                sd->bin_atoms)));
+        MALA_PROF(c, "k_sort_bins", st,
+                  (k_sort_bins<<<(nbins + 127) / 128, 128, 0, st>>>(nbins, sd->bin_start, sd->bin_atoms)));
     }
     MALA_CUDA_TRY(cudaGetLastError());
     return MALA_OK;
