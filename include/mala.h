@@ -141,7 +141,9 @@ int mala_profile_get(mala_ctx* ctx, const char* kernel, double* total_ms, int64_
 /* ---- network ---------------------------------------------------------- */
 
 /* Upload a network once (BF16 copies for MALA_MIXED, FP64 for MALA_FP64_PLAIN);
- * the descriptor arrays may be freed on return. */
+ * the descriptor arrays may be freed on return.  mala_destroy frees the device
+ * memory of the context's remaining networks; mala_model_destroy is still
+ * needed afterwards to free the handle itself. */
 int mala_model_create(mala_ctx* ctx, const mala_mlp_desc* desc, mala_model** out);
 void mala_model_destroy(mala_model* model);
 

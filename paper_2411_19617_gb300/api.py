@@ -98,7 +98,7 @@ class Model:
     """A network uploaded to the library (BF16 + tensor maps, and FP64)."""
 
     def __init__(self, ctx: "Context", mlp):
-        self.ctx = ctx
+        self.ctx = ctx  # keeps the context alive at least as long as the network
         self.dims = tuple(int(d) for d in mlp.dims)
         nl = len(self.dims) - 1
         self._dims = np.ascontiguousarray(self.dims, dtype=np.int32)

@@ -468,3 +468,4 @@ int integrate(Ctx* c, const void* ldos, int64_t P, double volume, const mala_ene
 }
 
 }  // namespace mala
+

@@ -264,6 +264,15 @@ void mala_destroy(mala_ctx* c) {
     cudaSetDevice(c->device);
     server_stop(c);
     cudaDeviceSynchronize();
+    {
+        // networks outliving their context keep only their host object
+        std::lock_guard<std::mutex> lk(c->models_mu);
+        for (Model* m : c->models) {
+            model_free(m);
+            m->ctx = nullptr;
+        }
+        c->models.clear();
+    }
     prof_collect(c);
     for (cudaEvent_t e : c->prof.pool) cudaEventDestroy(e);
     if (c->stream) cudaStreamDestroy(c->stream);

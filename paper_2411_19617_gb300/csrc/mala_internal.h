@@ -12,6 +12,7 @@
 #include <cstdio>
 #include <deque>
 #include <map>
+#include <set>
 #include <memory>
 #include <mutex>
 #include <string>
@@ -151,6 +152,9 @@ struct Ctx {
     int kmax_hint = 64;             // neighbour capacity that sufficed last time
     // serving
     struct Server* server = nullptr;
+    // networks created on this context; mala_destroy frees their device memory
+    std::mutex models_mu;
+    std::set<Model*> models;
 };
 
 // ---- kernel launchers (descriptor path) ------------------------------------

@@ -273,13 +273,23 @@ int mala_model_create(mala_ctx* c, const mala_mlp_desc* desc, mala_model** out) 
         delete m;
         return rc;
     }
+    {
+        std::lock_guard<std::mutex> lk(c->models_mu);
+        c->models.insert(m);
+    }
     *out = m;
     return MALA_OK;
 }
 
 void mala_model_destroy(mala_model* m) {
     if (!m) return;
-    model_free(m);
+    if (Ctx* c = m->ctx) {
+        {
+            std::lock_guard<std::mutex> lk(c->models_mu);
+            c->models.erase(m);
+        }
+        model_free(m);
+    }
     delete m;
 }
 

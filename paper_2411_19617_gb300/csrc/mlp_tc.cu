@@ -537,8 +537,9 @@ int model_upload(Ctx* c, const mala_mlp_desc* d, Model* m) {
 }
 
 void model_free(Model* m) {
+    if (!m->ctx) return;
     for (void* p : m->allocs) cudaFree(p);
-    if (m->ctx) m->ctx->root()->used -= m->bytes;
+    m->ctx->root()->used -= m->bytes;
     m->allocs.clear();
     m->bytes = 0;
 }
