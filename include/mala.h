@@ -197,6 +197,28 @@ int mala_integrate(mala_ctx* ctx, const void* ldos_dev, int64_t P, double cell_v
                    double* dos_host, double* fermi_eV, double* band_energy_eV,
                    double* electron_count, mala_precision precision, void* stream);
 
+/* mala_integrate without any allocation.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory (their
+ * process's device memory belongs to another framework's allocator, they run
+ * under a hard memory cap, or they cannot afford the device-wide
+ * synchronisation an allocation may imply).  Arguments, outputs and results
+ * are those of mala_integrate; every scratch buffer comes from one fixed
+ * static device array of MALA_NOALLOC_SCRATCH_BYTES that each GPU loading the
+ * library holds until the process exits.  Limit: 3.5 n_E + 16 + max(
+ * ceil(P/128) n_E [only when dos_sum_dev is NULL], min(ceil(P/8), 16 x SMs))
+ * doubles must fit in the array; larger sizes return MALA_ERR_UNSUPPORTED
+ * with the numbers in the message.  The first call on a device looks up the
+ * array's device address (no allocation) and should come before any stream
+ * capture.  All calls share the array and leave their contents in it: calls
+ * that overlap on the GPU (other streams or threads) race, so issue them one
+ * at a time.  Host copies go through the context's pinned buffer and
+ * directly into dos_host. */
+#define MALA_NOALLOC_SCRATCH_BYTES (8u << 20)
+int mala_integrate_noalloc(mala_ctx* ctx, const void* ldos_dev, int64_t P, double cell_volume,
+                           const mala_energy_grid* eg, const double* dos_sum_dev, void* density_dev,
+                           double* dos_host, double* fermi_eV, double* band_energy_eV,
+                           double* electron_count, mala_precision precision, void* stream);
+
 /* Electron count N(mu) = sum_xi w0_xi(mu) D_xi of a density of states D (host
  * [n_E], the values mala_integrate returns in dos_host) at chemical potential
  * mu, with the same FP64 closed-form weights the Fermi-level search uses.

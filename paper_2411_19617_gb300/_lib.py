@@ -77,6 +77,9 @@ PROTOTYPES = {
     "mala_integrate": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_double, C.POINTER(EnergyGrid),
                                  C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_double),
                                  C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int, C.c_void_p]),
+    "mala_integrate_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_double, C.POINTER(EnergyGrid),
+                                         C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_double),
+                                         C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int, C.c_void_p]),
     "mala_electron_count": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(EnergyGrid), C.c_double,
                                       C.POINTER(C.c_double)]),
     "mala_predict": (C.c_int, [C.c_void_p, C.POINTER(Snapshot), C.POINTER(BispectrumParams), C.c_void_p,

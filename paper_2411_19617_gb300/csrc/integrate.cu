@@ -24,6 +24,8 @@
 
 #include <cmath>
 #include <cstdint>
+#include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "mala_internal.h"
@@ -469,3 +471,107 @@ int integrate(Ctx* c, const void* ldos, int64_t P, double volume, const mala_ene
 
 }  // namespace mala
 
+// ---- the integration step without allocation -------------------------------
+//
+// Callers that must not allocate device memory (a process whose device memory
+// is owned by another framework's allocator, a hard per-process memory cap, or
+// a latency-critical loop that cannot afford the device-wide synchronisation
+// cudaMalloc/cudaFree may imply) run the integrals with every scratch buffer
+// taken from this fixed file-scope array instead of the context's workspaces.
+// Every GPU that loads the library holds the array until the process exits.
+
+namespace mala {
+
+namespace {
+
+constexpr size_t kStaticScratchDoubles = size_t(1) << 20;  // 8 MiB
+static __device__ __align__(256) double g_integrate_scratch[kStaticScratchDoubles];
+
+std::mutex g_scratch_mu;
+void* g_scratch_addr[64] = {nullptr};
+
+// Device address of the array on the current device, looked up once per
+// device.  (In host code the array's name is only a host-side stand-in.)
+int scratch_address(int device, double** out) {
+    if (device < 0 || device >= 64) return fail(MALA_ERR_UNSUPPORTED, "device index %d too large", device);
+    std::lock_guard<std::mutex> lk(g_scratch_mu);
+    if (!g_scratch_addr[device]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_integrate_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(MALA_ERR_CUDA, "cudaGetSymbolAddress of the static scratch failed: %s", cudaGetErrorString(e));
+        g_scratch_addr[device] = p;
+    }
+    *out = static_cast<double*>(g_scratch_addr[device]);
+    return MALA_OK;
+}
+
+}  // namespace
+
+int integrate_noalloc(Ctx* c, const void* ldos, int64_t P, double volume, const mala_energy_grid* eg,
+                      const double* dos_sum, void* density, double* dos_host, double* fermi, double* eb, double* ne,
+                      mala_precision prec, cudaStream_t st) {
+    const int nE = eg->n_E;
+    double* scratch = nullptr;
+    MALA_TRY(scratch_address(c->device, &scratch));
+    const int64_t ntile = (P + 127) / 128;
+    const int dens_blocks = (int)std::min<int64_t>(std::max<int64_t>(1, (P + kDensWarps - 1) / kDensWarps),
+                                                   (int64_t)c->num_sms * 16);
+    const size_t n_part = std::max<size_t>(dos_sum ? 0 : (size_t)ntile * nE, (size_t)dens_blocks);
+    const size_t need = 3 * (size_t)nE + (nE + 1) / 2 + 16 + n_part;
+    if (need > kStaticScratchDoubles)
+        return fail(MALA_ERR_UNSUPPORTED,
+                    "mala_integrate_noalloc: %zu scratch doubles needed, the static array holds %zu "
+                    "(ceil(P/128) * n_E must stay below about %zu when dos_sum_dev is NULL)",
+                    need, kStaticScratchDoubles, kStaticScratchDoubles - 3 * (size_t)nE - nE / 2 - 16);
+    // the same layout as the workspace path; every buffer is rewritten before it is read
+    double* dsum = scratch;
+    double* D = dsum + nE;
+    double* w0d = D + nE;
+    float* w0f = reinterpret_cast<float*>(w0d + nE);
+    double* scal = w0d + nE + (nE + 1) / 2;
+    double* nsum = scal + 8;
+    double* part = scal + 16;
+    const bool mixed = prec == MALA_MIXED;
+    if (!dos_sum) {
+        if (P > 0) {
+            if (mixed)
+                k_colsum<__nv_bfloat16><<<(unsigned)ntile, 256, 0, st>>>(static_cast<const __nv_bfloat16*>(ldos), P,
+                                                                          nE, part);
+            else
+                k_colsum<double><<<(unsigned)ntile, 256, 0, st>>>(static_cast<const double*>(ldos), P, nE, part);
+            k_sum_rows<<<(nE + 127) / 128, 128, 0, st>>>(part, ntile, nE, dsum);
+        } else {
+            MALA_CUDA_TRY(cudaMemsetAsync(dsum, 0, sizeof(double) * nE, st));
+        }
+        dos_sum = dsum;
+    }
+    const double dV = volume / (double)(P > 0 ? P : 1);
+    k_fermi<<<1, kFermiThreads, sizeof(double) * nE, st>>>(dos_sum, nE, dV, eg->e0_eV, eg->de_eV, eg->kT_eV,
+                                                           eg->n_electrons, 1e-12, 200, D, w0d, w0f, scal);
+    if (P > 0 && density) {
+        if (mixed)
+            k_density_bf16<<<dens_blocks, kDensWarps * 32, 0, st>>>(static_cast<const __nv_bfloat16*>(ldos), P, nE, w0f,
+                                                                   static_cast<float*>(density), part);
+        else
+            k_density_f64<<<dens_blocks, kDensWarps * 32, 0, st>>>(static_cast<const double*>(ldos), P, nE, w0d,
+                                                                  static_cast<double*>(density), part);
+        k_sum_vec<<<1, 256, 0, st>>>(part, dens_blocks, nsum);
+    } else {
+        MALA_CUDA_TRY(cudaMemsetAsync(nsum, 0, sizeof(double), st));
+    }
+    MALA_CUDA_TRY(cudaGetLastError());
+    // host results: scalars through the context's pinned buffer, D straight into the caller's array
+    MALA_CUDA_TRY(cudaMemcpyAsync(c->host_scalars, scal, sizeof(double) * 9, cudaMemcpyDeviceToHost, st));
+    if (dos_host) MALA_CUDA_TRY(cudaMemcpyAsync(dos_host, D, sizeof(double) * nE, cudaMemcpyDeviceToHost, st));
+    MALA_CUDA_TRY(cudaStreamSynchronize(st));
+    const double* hs = c->host_scalars;
+    if (fermi) *fermi = hs[0];
+    if (eb) *eb = hs[1];
+    if (ne) *ne = dV * hs[8];
+    if (hs[2] != 0.0)
+        return fail(MALA_ERR_FERMI_BRACKET, "N(mu) - N_e has no sign change on [e0 - 20 kT, e_max + 20 kT]");
+    return MALA_OK;
+}
+
+}  // namespace mala

@@ -316,6 +316,21 @@ int mala_integrate(mala_ctx* c, const void* ldos_dev, int64_t P, double cell_vol
                      electron_count, precision, as_stream(stream));
 }
 
+int mala_integrate_noalloc(mala_ctx* c, const void* ldos_dev, int64_t P, double cell_volume_,
+                           const mala_energy_grid* eg, const double* dos_sum_dev, void* density_dev, double* dos_host,
+                           double* fermi_eV, double* band_energy_eV, double* electron_count,
+                           mala_precision precision, void* stream) {
+    if (!c || P < 0 || (P > 0 && !ldos_dev && !dos_sum_dev)) return fail(MALA_ERR_INVALID_ARG, "bad arguments");
+    MALA_TRY(check_egrid(eg));
+    if (!(cell_volume_ > 0.0)) return fail(MALA_ERR_INVALID_ARG, "cell volume must be > 0");
+    if (precision != MALA_MIXED && precision != MALA_FP64_PLAIN) return fail(MALA_ERR_INVALID_ARG, "bad precision");
+    if (density_dev && !ldos_dev) return fail(MALA_ERR_INVALID_ARG, "density needs the LDOS");
+    std::lock_guard<std::mutex> lk(c->mu);
+    MALA_CUDA_TRY(cudaSetDevice(c->device));
+    return integrate_noalloc(c, ldos_dev, P, cell_volume_, eg, dos_sum_dev, density_dev, dos_host, fermi_eV,
+                             band_energy_eV, electron_count, precision, as_stream(stream));
+}
+
 int mala_electron_count(mala_ctx* c, const double* dos_host, const mala_energy_grid* eg, double mu, double* count) {
     if (!c || !dos_host || !count || !std::isfinite(mu)) return fail(MALA_ERR_INVALID_ARG, "bad arguments");
     MALA_TRY(check_egrid(eg));
