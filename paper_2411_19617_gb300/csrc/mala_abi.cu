@@ -251,6 +251,7 @@ int mala_create(mala_ctx** out, int device, size_t hbm_budget_bytes) {
     }
     int rc = upload_cg_tables(c);
     if (rc == MALA_OK) rc = upload_polylog_tables();
+    if (rc == MALA_OK) rc = upload_ui_tables();
     if (rc != MALA_OK) {
         mala_destroy(c);
         return rc;

@@ -226,6 +226,7 @@ void launch_u_expand(int twojmax, const T* u_half, const SnapGeom& g, int64_t ti
 
 int upload_cg_tables(Ctx* c);
 int upload_polylog_tables();
+int upload_ui_tables();
 int upload_zb_lists_f64(const int* lists, int bytes);
 int snap_descriptors(Ctx* c, const mala_snapshot* snap, const mala_bispectrum_params* bp, void* B,
                      void* u_full, mala_precision prec, cudaStream_t st);

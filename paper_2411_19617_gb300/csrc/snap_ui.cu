@@ -23,6 +23,7 @@
 // even J) in [tile][element][lane] layout.
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstdint>
 
 #include "mala_internal.h"
@@ -31,6 +32,14 @@
 namespace mala {
 
 namespace {
+
+// normalisation sqrt((J-ma)! ma! / ((J-mb)! mb!)) of U^J, [J][ma][mb], filled by the host
+__constant__ double c_unorm_d[(kTJMax + 1) * (kTJMax + 1) * (kTJMax + 1)];
+__constant__ float c_unorm_f[(kTJMax + 1) * (kTJMax + 1) * (kTJMax + 1)];
+
+template <class T> __device__ __forceinline__ T unorm_at(int idx);
+template <> __device__ __forceinline__ float unorm_at<float>(int idx) { return c_unorm_f[idx]; }
+template <> __device__ __forceinline__ double unorm_at<double>(int idx) { return c_unorm_d[idx]; }
 
 constexpr int kSegElemsF32 = 24;  // sums + compensations of 24 complex numbers: 96 registers
 constexpr int kSegElemsF64 = 10;
@@ -180,7 +189,7 @@ __device__ __forceinline__ void ui_segment(const typename AB4<T>::type* __restri
 #pragma unroll
         for (int i = 0; i < kTJMax + 1; ++i) {
             if (i < ne) {
-                const T nrm = T(unorm(J, i, MB));
+                const T nrm = unorm_at<T>((J * (kTJMax + 1) + i) * (kTJMax + 1) + MB);
                 T vr_ = (sr[off + i] - cr[off + i]) * nrm;
                 T vi_ = (si[off + i] - ci[off + i]) * nrm;
                 typename C2<T>::type o;
@@ -281,6 +290,23 @@ void launch_ui_tj(const NbrOut& nb, double wself, int64_t ntiles, T* u_half, cud
 }
 
 }  // namespace
+
+int upload_ui_tables() {
+    constexpr int n = (kTJMax + 1) * (kTJMax + 1) * (kTJMax + 1);
+    double d[n];
+    float f[n];
+    for (int J = 0; J <= kTJMax; ++J)
+        for (int a = 0; a <= kTJMax; ++a)
+            for (int b = 0; b <= kTJMax; ++b) {
+                double v = 0.0;
+                if (a <= J && b <= J) v = std::sqrt(fact_d(J - a) * fact_d(a) / (fact_d(J - b) * fact_d(b)));
+                d[(J * (kTJMax + 1) + a) * (kTJMax + 1) + b] = v;
+                f[(J * (kTJMax + 1) + a) * (kTJMax + 1) + b] = (float)v;
+            }
+    MALA_CUDA_TRY(cudaMemcpyToSymbol(c_unorm_d, d, sizeof(d)));
+    MALA_CUDA_TRY(cudaMemcpyToSymbol(c_unorm_f, f, sizeof(f)));
+    return MALA_OK;
+}
 
 template <class T>
 void launch_ui(int twojmax, const NbrOut& nb, double wself, int64_t ntiles, T* u_half, cudaStream_t st) {

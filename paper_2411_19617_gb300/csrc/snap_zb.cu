@@ -83,7 +83,7 @@ double triple_cost(int j1, int j2, int j) {
 
 int upload_cg_tables(Ctx* c) {
     std::vector<double> tab(kCgSize, 0.0);
-    std::vector<float> tabf(kCgSize, 0.0f);
+    std::vector<float2> tabf(kCgSize, make_float2(0.f, 0.f));
     int n = 0;
     for (int j1 = 0; j1 <= kTJMax; ++j1)
         for (int j2 = 0; j2 <= j1; ++j2)
@@ -95,12 +95,25 @@ int upload_cg_tables(Ctx* c) {
                         const int m = 2 * ma - j, m1 = 2 * m1a - j1;
                         const double v = cg_racah(j1, m1, j2, m - m1, j, m);
                         tab[off + ma * (j1 + 1) + m1a] = v;
-                        tabf[off + ma * (j1 + 1) + m1a] = (float)v;
+                        tabf[off + ma * (j1 + 1) + m1a] = make_float2((float)v, (float)v);
                     }
                 ++n;
             }
     c->tables.cg = tab;
-    MALA_CUDA_TRY(cudaMemcpyToSymbol(c_cg, tabf.data(), sizeof(float) * kCgSize));
+    MALA_CUDA_TRY(cudaMemcpyToSymbol(c_cg2, tabf.data(), sizeof(float2) * kCgSize));
+    {
+        std::vector<int> fm(kNFull);
+        for (int J = 0; J <= kTJMax; ++J)
+            for (int ma = 0; ma <= J; ++ma)
+                for (int mb = 0; mb <= J; ++mb) {
+                    const bool direct = (2 * ma < J) || (2 * ma == J && 2 * mb <= J);
+                    const int sma = direct ? ma : J - ma, smb = direct ? mb : J - mb;
+                    const int h = hoff(J) + sma * (J + 1) + smb;
+                    const int neg = ((sma - smb) & 1) ? 1 : 0;
+                    fm[full_off(J) + ma * (J + 1) + mb] = h | (direct ? 0 : (1 << 16) | (neg << 17));
+                }
+        MALA_CUDA_TRY(cudaMemcpyToSymbol(c_fullmap, fm.data(), sizeof(int) * kNFull));
+    }
     MALA_TRY(c->ws_misc.reserve(c, sizeof(double) * kCgSize));
     c->tables.cg_d = c->ws_misc.as<double>();
     MALA_CUDA_TRY(cudaMemcpy(c->tables.cg_d, tab.data(), sizeof(double) * kCgSize, cudaMemcpyHostToDevice));

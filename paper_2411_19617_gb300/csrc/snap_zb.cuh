@@ -15,7 +15,11 @@ constexpr int kZbWarps = 8;
 constexpr int kZbMaxList = 32;
 constexpr int kCgSize = cg_table_size();
 
-static __constant__ float c_cg[kCgSize];
+// Clebsch-Gordan table as (c, c) pairs: one operand of a packed FP32x2 FMA
+static __constant__ float2 c_cg2[kCgSize];
+// full (J+1)^2 element -> half-set element: index | mirrored << 16 | negate << 17
+constexpr int kNFull = n_full(kTJMax);
+static __constant__ int c_fullmap[kNFull];
 // per supported twojmax (index tj/2): [warp][slot] = global triple id | (local index << 8), -1 = end
 static __constant__ int c_zb_list[kTJMax / 2 + 1][kZbWarps][kZbMaxList];
 
@@ -26,7 +30,7 @@ template <> struct C2<float> { using type = float2; };
 template <> struct C2<double> { using type = double2; };
 
 template <class T> __device__ __forceinline__ T cg_at(const T* gtab, int idx);
-template <> __device__ __forceinline__ float cg_at<float>(const float*, int idx) { return c_cg[idx]; }
+template <> __device__ __forceinline__ float cg_at<float>(const float*, int idx) { return c_cg2[idx].x; }
 template <> __device__ __forceinline__ double cg_at<double>(const double* gtab, int idx) { return __ldg(gtab + idx); }
 
 // Row `row` of u^JJ from the half set, scaled by `scale`.
@@ -216,50 +220,130 @@ constexpr int kZbUWarps = 16;
 constexpr double kFixScale = 4294967296.0;  // 2^32
 constexpr float kFixLimit = 1.0e9f;          // |partial| bound that keeps 16 partials inside int64
 
+template <int IMM>
+__device__ __forceinline__ float2 lds2(uint32_t addr) {
+    float2 v;
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2+%3];" : "=f"(v.x), "=f"(v.y) : "r"(addr), "n"(IMM));
+    return v;
+}
+
+template <int N, int I = 0>
+__device__ __forceinline__ void lds_row(float2 (&v)[N], uint32_t addr) {
+    if constexpr (I < N) {
+        v[I] = lds2<I * 256>(addr);
+        lds_row<N, I + 1>(v, addr);
+    }
+}
+
+// The contraction of one unit, fully expanded at compile time (template
+// recursion: no index of a register array is ever a run-time value), in
+// outer-product order: for each x element, the terms of all columns follow
+// one another, so consecutive instructions update independent accumulators.
+//   ACC = 0: z = (c2, c2) * t + z as one packed FMA (pair table in constant memory)
+//   ACC = 1: z.re += c2 t.re, z.im += c2 t.im as scalar FMAs with a constant operand
+#ifndef MALA_ZB_ACC
+#define MALA_ZB_ACC 0
+#endif
+
+template <int J1, int J2, int OFF, int D, int NCOL, int M1B, int MB>
+__device__ __forceinline__ void conv_row(const float2 (&xx)[J1 + 1], const float2 (&xs)[J1 + 1],
+                                         const float2 (&y)[J2 + 1], const float2 (&ys)[J2 + 1], float2 (&z)[NCOL]) {
+    if constexpr (MB < NCOL) {
+        constexpr int M2B = MB - M1B + D;
+        if constexpr (M2B >= 0 && M2B <= J2) {
+            float2 t = __fmul2_rn(xx[M1B], y[M2B]);
+            t = __ffma2_rn(xs[M1B], ys[M2B], t);
+#if MALA_ZB_ACC == 0
+            z[MB] = __ffma2_rn(c_cg2[OFF + MB * (J1 + 1) + M1B], t, z[MB]);
+#else
+            const float c = c_cg2[OFF + MB * (J1 + 1) + M1B].x;
+            z[MB].x = fmaf(c, t.x, z[MB].x);
+            z[MB].y = fmaf(c, t.y, z[MB].y);
+#endif
+        }
+        conv_row<J1, J2, OFF, D, NCOL, M1B, MB + 1>(xx, xs, y, ys, z);
+    }
+}
+
+template <int J1, int J2, int OFF, int D, int NCOL, int M1B>
+__device__ __forceinline__ void conv_all(const float2 (&xx)[J1 + 1], const float2 (&xs)[J1 + 1],
+                                         const float2 (&y)[J2 + 1], const float2 (&ys)[J2 + 1], float2 (&z)[NCOL]) {
+    if constexpr (M1B <= J1) {
+        conv_row<J1, J2, OFF, D, NCOL, M1B, 0>(xx, xs, y, ys, z);
+        conv_all<J1, J2, OFF, D, NCOL, M1B + 1>(xx, xs, y, ys, z);
+    }
+}
+
+template <int J, int NCOL, bool MID, int MB>
+__device__ __forceinline__ void dot_cols(const float2 (&wv)[NCOL], const float2 (&z)[NCOL], float2& acc,
+                                         float2& accm) {
+    if constexpr (MB < NCOL) {
+        if constexpr (MID && 2 * MB == J)
+            accm = __ffma2_rn(wv[MB], z[MB], accm);
+        else
+            acc = __ffma2_rn(wv[MB], z[MB], acc);
+        dot_cols<J, NCOL, MID, MB + 1>(wv, z, acc, accm);
+    }
+}
+
+template <int N, int I = 0>
+__device__ __forceinline__ void zero2(float2 (&z)[N]) {
+    if constexpr (I < N) {
+        z[I] = make_float2(0.f, 0.f);
+        zero2<N, I + 1>(z);
+    }
+}
+
+template <int N, int I = 0>
+__device__ __forceinline__ void prep_x(const float2 (&v)[N], float2 (&xx)[N], float2 (&xs)[N]) {
+    if constexpr (I < N) {
+        xx[I] = make_float2(v[I].x, v[I].x);
+        xs[I] = make_float2(-v[I].y, v[I].y);
+        prep_x<N, I + 1>(v, xx, xs);
+    }
+}
+
+template <int N, int I = 0>
+__device__ __forceinline__ void prep_y(const float2 (&v)[N], float2 (&ys)[N]) {
+    if constexpr (I < N) {
+        ys[I] = make_float2(v[I].y, v[I].x);
+        prep_y<N, I + 1>(v, ys);
+    }
+}
+
+// One unit: conv[mb] = sum_m1b c2(mb, m1b) x[m1b] y[mb - m1b + d] (complex),
+// returned as c1 * sum_mb weight(mb) Re(conj(w[mb]) conv[mb]).  The complex
+// products run on packed FP32x2 instructions: with xx = (x.re, x.re),
+// xs = (-x.im, x.im) and ys = (y.im, y.re),
+//   t = xx * y;  t = xs * ys + t  (= x y);  z = (c2, c2) * t + z.
+// Shared-memory addresses are 32-bit; each row is one base plus immediates.
 template <int J1, int J2, int J, int NCOL, bool MID>
-__device__ __forceinline__ float unit_full(const float2* __restrict__ su, int ma, int m1a) {
+__device__ __forceinline__ float unit_full(uint32_t sbase, int ma, int m1a) {
     constexpr int d = (J1 + J2 - J) / 2;
     constexpr int OFF = cg_offset(J1, J2, J);
     const int m2a = ma - m1a + d;
-    const float2* xr = su + (size_t)(full_off(J1) + m1a * (J1 + 1)) * 32;
-    const float2* yr = su + (size_t)(full_off(J2) + m2a * (J2 + 1)) * 32;
-    float2 x[J1 + 1], y[J2 + 1];
-#pragma unroll
-    for (int k = 0; k <= J1; ++k) x[k] = xr[k * 32];
-#pragma unroll
-    for (int k = 0; k <= J2; ++k) y[k] = yr[k * 32];
-    float zr[NCOL], zi[NCOL];
-#pragma unroll
-    for (int mb = 0; mb < NCOL; ++mb) {
-        zr[mb] = 0.f;
-        zi[mb] = 0.f;
-#pragma unroll
-        for (int m1b = 0; m1b <= J1; ++m1b) {
-            const int m2b = mb - m1b + d;
-            if (m2b >= 0 && m2b <= J2) {
-                const float c2 = c_cg[OFF + mb * (J1 + 1) + m1b];
-                const float tr = x[m1b].x * y[m2b].x - x[m1b].y * y[m2b].y;
-                const float ti = x[m1b].x * y[m2b].y + x[m1b].y * y[m2b].x;
-                zr[mb] += c2 * tr;
-                zi[mb] += c2 * ti;
-            }
-        }
-    }
-    const float2* w = su + (size_t)(full_off(J) + ma * (J + 1)) * 32;
-    float r = 0.f;
-#pragma unroll
-    for (int mb = 0; mb < NCOL; ++mb) {
-        const float2 v = w[mb * 32];
-        const float t = v.x * zr[mb] + v.y * zi[mb];
-        r += (MID && 2 * mb == J) ? t : 2.f * t;
-    }
-    return c_cg[OFF + ma * (J1 + 1) + m1a] * r;
+    constexpr uint32_t F1 = full_off(J1) * 256u, F2 = full_off(J2) * 256u, FJ = full_off(J) * 256u;
+    const uint32_t xa = sbase + F1 + (uint32_t)m1a * ((J1 + 1) * 256u);
+    const uint32_t ya = sbase + F2 + (uint32_t)m2a * ((J2 + 1) * 256u);
+    const uint32_t wa = sbase + FJ + (uint32_t)ma * ((J + 1) * 256u);
+    float2 xv[J1 + 1], xx[J1 + 1], xs[J1 + 1], y[J2 + 1], ys[J2 + 1], wv[NCOL];
+    lds_row<J1 + 1>(xv, xa);
+    lds_row<J2 + 1>(y, ya);
+    lds_row<NCOL>(wv, wa);
+    prep_x<J1 + 1>(xv, xx, xs);
+    prep_y<J2 + 1>(y, ys);
+    float2 z[NCOL];
+    zero2<NCOL>(z);
+    conv_all<J1, J2, OFF, d, NCOL, 0>(xx, xs, y, ys, z);
+    float2 acc = make_float2(0.f, 0.f), accm = make_float2(0.f, 0.f);
+    dot_cols<J, NCOL, MID, 0>(wv, z, acc, accm);
+    const float r = 2.f * (acc.x + acc.y) + (accm.x + accm.y);
+    return c_cg2[OFF + ma * (J1 + 1) + m1a].x * r;
 }
 
 // this warp's units (ma | m1a << 4) of one triple, starting at `first`
 template <int J1, int J2, int J>
-__device__ __forceinline__ float triple_units(const float2* __restrict__ su, const unsigned short* __restrict__ ul,
-                                              int n, int first) {
+__device__ __forceinline__ float triple_units(uint32_t su, const unsigned short* __restrict__ ul, int n, int first) {
     float acc = 0.f;
     for (int i = first; i < n; i += kZbUWarps) {
         const int e = ul[i];
@@ -276,7 +360,7 @@ __device__ __forceinline__ float triple_units(const float2* __restrict__ su, con
 }
 
 template <int LO, int HI>
-__device__ __forceinline__ float triple_dispatch(int id, const float2* su, const unsigned short* ul, int n, int first) {
+__device__ __forceinline__ float triple_dispatch(int id, uint32_t su, const unsigned short* ul, int n, int first) {
     if constexpr (HI - LO == 1) {
         return triple_units<triple_field(LO, 0), triple_field(LO, 1), triple_field(LO, 2)>(su, ul, n, first);
     } else {
@@ -303,15 +387,10 @@ __global__ void __launch_bounds__(kZbUWarps * 32, 1)
         const float2* src = u + (size_t)tl * nh * 32;
         for (int idx = threadIdx.x; idx < nf * 32; idx += blockDim.x) {
             const int e = idx >> 5, l = idx & 31;
-            int J = 0;
-            while (full_off(J + 1) <= e) ++J;
-            const int r = e - full_off(J);
-            const int ma = r / (J + 1), mb = r % (J + 1);
-            const bool direct = (2 * ma < J) || (2 * ma == J && 2 * mb <= J);
-            const int sma = direct ? ma : J - ma, smb = direct ? mb : J - mb;
-            float2 v = src[(size_t)(hoff(J) + sma * (J + 1) + smb) * 32 + l];
-            if (!direct) {
-                const float sg = ((sma - smb) & 1) ? -1.f : 1.f;
+            const int m = c_fullmap[e];
+            float2 v = src[(size_t)(m & 0xffff) * 32 + l];
+            if (m & 0x10000) {  // mirrored element: (-1)^(ma-mb) conj
+                const float sg = (m & 0x20000) ? -1.f : 1.f;
                 v.x = sg * v.x;
                 v.y = -sg * v.y;
             }
@@ -321,7 +400,7 @@ __global__ void __launch_bounds__(kZbUWarps * 32, 1)
     }
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const float2* su = su_all + lane;
+    const uint32_t su = (uint32_t)__cvta_generic_to_shared(su_all) + (uint32_t)lane * 8u;
     bool bad = false;
     for (int t = 0; t < ntri; ++t) {
         const int4 d = __ldg(tri + t);  // (gid, start, count, column)
