@@ -101,19 +101,7 @@ int upload_cg_tables(Ctx* c) {
             }
     c->tables.cg = tab;
     MALA_CUDA_TRY(cudaMemcpyToSymbol(c_cg2, tabf.data(), sizeof(float2) * kCgSize));
-    {
-        std::vector<int> fm(kNFull);
-        for (int J = 0; J <= kTJMax; ++J)
-            for (int ma = 0; ma <= J; ++ma)
-                for (int mb = 0; mb <= J; ++mb) {
-                    const bool direct = (2 * ma < J) || (2 * ma == J && 2 * mb <= J);
-                    const int sma = direct ? ma : J - ma, smb = direct ? mb : J - mb;
-                    const int h = hoff(J) + sma * (J + 1) + smb;
-                    const int neg = ((sma - smb) & 1) ? 1 : 0;
-                    fm[full_off(J) + ma * (J + 1) + mb] = h | (direct ? 0 : (1 << 16) | (neg << 17));
-                }
-        MALA_CUDA_TRY(cudaMemcpyToSymbol(c_fullmap, fm.data(), sizeof(int) * kNFull));
-    }
+
     MALA_TRY(c->ws_misc.reserve(c, sizeof(double) * kCgSize));
     c->tables.cg_d = c->ws_misc.as<double>();
     MALA_CUDA_TRY(cudaMemcpy(c->tables.cg_d, tab.data(), sizeof(double) * kCgSize, cudaMemcpyHostToDevice));
@@ -193,10 +181,10 @@ template <>
 void launch_zb<float>(Ctx* c, int twojmax, const float* u_half, const SnapGeom& g, int64_t tile0, int64_t ntiles,
                       float* B, cudaStream_t st) {
     if (ntiles <= 0) return;
-    const size_t smem = sizeof(float2) * (size_t)n_full(twojmax) * 32 + sizeof(long long) * (size_t)n_triples(twojmax) * 32;
+    const size_t smem = sizeof(float4) * (size_t)n_half(twojmax) * 32 + sizeof(long long) * (size_t)n_triples(twojmax) * 64;
     cudaFuncSetAttribute(k_zb_units, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const int k = twojmax / 2;
-    k_zb_units<<<(unsigned)ntiles, kZbUWarps * 32, smem, st>>>(
+    k_zb_units<<<(unsigned)((ntiles + 1) / 2), kZbUWarps * 32, smem, st>>>(
         twojmax, reinterpret_cast<const float2*>(u_half), g, tile0, ntiles, c->tables.tri_d + c->tables.tri_off[k],
         c->tables.tri_n[k], c->tables.units_d + c->tables.unit_off[k], B, c->tables.err_d);
 }

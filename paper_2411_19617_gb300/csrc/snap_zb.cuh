@@ -17,9 +17,7 @@ constexpr int kCgSize = cg_table_size();
 
 // Clebsch-Gordan table as (c, c) pairs: one operand of a packed FP32x2 FMA
 static __constant__ float2 c_cg2[kCgSize];
-// full (J+1)^2 element -> half-set element: index | mirrored << 16 | negate << 17
-constexpr int kNFull = n_full(kTJMax);
-static __constant__ int c_fullmap[kNFull];
+
 // per supported twojmax (index tj/2): [warp][slot] = global triple id | (local index << 8), -1 = end
 static __constant__ int c_zb_list[kTJMax / 2 + 1][kZbWarps][kZbMaxList];
 
@@ -202,165 +200,190 @@ __global__ void __launch_bounds__(kZbWarps * 32)
 }
 
 
-// ---- FP32 kernel: all warps of an SM sweep the same triple -------------------
+// ---- FP32 kernel: two grid points per lane, packed FP32x2 arithmetic --------
 //
 // B is linear in each (row ma, u^J1 row m1a) contribution:
 //   B = sum_{ma, m1a} c1(ma, m1a) * sum_mb w(ma, mb) Re(conj(u^J[ma][mb]) conv_{ma,m1a}[mb]),
-// so a "unit" (triple, ma, m1a) yields a scalar per point.  One CTA of 16
-// warps owns an SM (the full u of its tile, 130 KB at twojmax = 10, fills the
-// shared memory); the warps walk the triples in the same order and deal each
-// triple's units round-robin, so the whole SM executes one triple's unrolled
-// code at a time and the instruction cache holds it.  The u half set is
-// expanded to full (J+1)^2 blocks while staging, so rows load without any
-// mirror arithmetic.  Per-warp partial sums are added in 64-bit fixed point
-// (2^-32 resolution) with shared-memory atomics: integer addition is
-// associative, so B does not depend on the order of the warps.
+// conv[mb] = sum_m1b c2(mb, m1b) x[m1b] y[mb - m1b + d],  x = u^J1[m1a], y = u^J2[ma - m1a + d],
+// so a "unit" (triple, ma, m1a) yields a scalar per point.
+//
+// One CTA handles 64 grid points (two tiles); lane l holds point l of both
+// tiles, and every value is a pair (point A, point B), so each packed FP32x2
+// instruction (FMUL2 / FFMA2) does the same scalar step for two points and the
+// operands need no shuffling.  The u half set of the 64 points sits in shared
+// memory as float4 (A.re, B.re, A.im, B.im) per element and lane (128 KB at
+// twojmax = 10); rows above the middle are read through the mirror
+// u[J-ma][J-mb] = (-1)^(ma-mb) conj(u[ma][mb]) with compile-time column signs,
+// the run-time row parities folding into the unit's scalar.  The units of all
+// triples are dealt round-robin to the warps, which therefore execute the same
+// triple's code at nearly the same time (instruction-cache locality).  Partial
+// sums meet in 64-bit fixed point (2^-32) through shared-memory atomics:
+// integer addition is associative, so B does not depend on the warp order.
 
 constexpr int kZbUWarps = 16;
 constexpr double kFixScale = 4294967296.0;  // 2^32
 constexpr float kFixLimit = 1.0e9f;          // |partial| bound that keeps 16 partials inside int64
 
-template <int IMM>
-__device__ __forceinline__ float2 lds2(uint32_t addr) {
-    float2 v;
-    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2+%3];" : "=f"(v.x), "=f"(v.y) : "r"(addr), "n"(IMM));
+__device__ __forceinline__ float4 lds4(uint32_t addr) {
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(addr));
     return v;
 }
 
-template <int N, int I = 0>
-__device__ __forceinline__ void lds_row(float2 (&v)[N], uint32_t addr) {
-    if constexpr (I < N) {
-        v[I] = lds2<I * 256>(addr);
-        lds_row<N, I + 1>(v, addr);
+template <int IMM>
+__device__ __forceinline__ float4 lds4i(uint32_t addr) {
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4+%5];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "r"(addr), "n"(IMM));
+    return v;
+}
+
+// element e of the half set: float4 per lane, 512 bytes per element
+constexpr uint32_t kElemBytes = 512u;
+
+enum RowCase { kDirect = 0, kMiddle = 1, kMirror = 2 };
+
+// Row `row` of u^JJ as pairs re[k] = (A.re, B.re), im[k] = (A.im, B.im), up to
+// the sign (-1)^row of mirrored rows (returned separately by the caller).
+template <int JJ, int CASE, int K>
+__device__ __forceinline__ void load_row_pairs(uint32_t sbase, int row, float2 (&re)[JJ + 1], float2 (&im)[JJ + 1]) {
+    if constexpr (K <= JJ) {
+        constexpr uint32_t H = (uint32_t)hoff(JJ);
+        float4 v;
+        bool mirror;
+        if constexpr (CASE == kDirect) {
+            v = lds4i<K * 512>(sbase + (H + (uint32_t)row * (JJ + 1)) * kElemBytes);
+            mirror = false;
+        } else if constexpr (CASE == kMiddle) {
+            // row JJ/2: columns <= JJ/2 stored, the others mirrored within the row
+            constexpr int col = (2 * K <= JJ) ? K : JJ - K;
+            v = lds4i<(H + (JJ / 2) * (JJ + 1) + col) * 512>(sbase);
+            mirror = 2 * K > JJ;
+        } else {
+            v = lds4i<(JJ - K) * 512>(sbase + (H + (uint32_t)(JJ - row) * (JJ + 1)) * kElemBytes);
+            mirror = true;
+        }
+        if (mirror) {
+            // (-1)^(K - row) conj(v); the (-1)^row part is applied by the caller
+            constexpr bool neg = CASE == kMiddle ? (((K - JJ / 2) & 1) != 0) : ((K & 1) != 0);
+            if (neg) {
+                re[K] = make_float2(-v.x, -v.y);
+                im[K] = make_float2(v.z, v.w);
+            } else {
+                re[K] = make_float2(v.x, v.y);
+                im[K] = make_float2(-v.z, -v.w);
+            }
+        } else {
+            re[K] = make_float2(v.x, v.y);
+            im[K] = make_float2(v.z, v.w);
+        }
+        load_row_pairs<JJ, CASE, K + 1>(sbase, row, re, im);
     }
 }
 
-// The contraction of one unit, fully expanded at compile time (template
-// recursion: no index of a register array is ever a run-time value), in
-// outer-product order: for each x element, the terms of all columns follow
-// one another, so consecutive instructions update independent accumulators.
-//   ACC = 0: z = (c2, c2) * t + z as one packed FMA (pair table in constant memory)
-//   ACC = 1: z.re += c2 t.re, z.im += c2 t.im as scalar FMAs with a constant operand
-#ifndef MALA_ZB_ACC
-#define MALA_ZB_ACC 0
-#endif
+// returns (-1)^row for mirrored rows, 1 otherwise (middle rows carry their signs inside)
+template <int JJ>
+__device__ __forceinline__ float load_row_any(uint32_t sbase, int row, float2 (&re)[JJ + 1], float2 (&im)[JJ + 1]) {
+    if (2 * row < JJ) {
+        load_row_pairs<JJ, kDirect, 0>(sbase, row, re, im);
+        return 1.f;
+    }
+    if (2 * row == JJ) {
+        load_row_pairs<JJ, kMiddle, 0>(sbase, row, re, im);
+        return 1.f;
+    }
+    load_row_pairs<JJ, kMirror, 0>(sbase, row, re, im);
+    return (row & 1) ? -1.f : 1.f;
+}
 
-template <int J1, int J2, int OFF, int D, int NCOL, int M1B, int MB>
-__device__ __forceinline__ void conv_row(const float2 (&xx)[J1 + 1], const float2 (&xs)[J1 + 1],
-                                         const float2 (&y)[J2 + 1], const float2 (&ys)[J2 + 1], float2 (&z)[NCOL]) {
-    if constexpr (MB < NCOL) {
+template <int N, int I = 0>
+__device__ __forceinline__ void negate_pairs(const float2 (&a)[N], float2 (&b)[N]) {
+    if constexpr (I < N) {
+        b[I] = make_float2(-a[I].x, -a[I].y);
+        negate_pairs<N, I + 1>(a, b);
+    }
+}
+
+// terms of column MB: zr += c2 (xr yr - xi yi), zi += c2 (xr yi + xi yr)
+template <int J1, int J2, int OFF, int D, int MB, int M1B>
+__device__ __forceinline__ void col_terms(const float2 (&xr)[J1 + 1], const float2 (&xi)[J1 + 1],
+                                          const float2 (&yr)[J2 + 1], const float2 (&yi)[J2 + 1],
+                                          const float2 (&yn)[J2 + 1], float2& zr, float2& zi) {
+    if constexpr (M1B <= J1) {
         constexpr int M2B = MB - M1B + D;
         if constexpr (M2B >= 0 && M2B <= J2) {
-            float2 t = __fmul2_rn(xx[M1B], y[M2B]);
-            t = __ffma2_rn(xs[M1B], ys[M2B], t);
-#if MALA_ZB_ACC == 0
-            z[MB] = __ffma2_rn(c_cg2[OFF + MB * (J1 + 1) + M1B], t, z[MB]);
-#else
-            const float c = c_cg2[OFF + MB * (J1 + 1) + M1B].x;
-            z[MB].x = fmaf(c, t.x, z[MB].x);
-            z[MB].y = fmaf(c, t.y, z[MB].y);
-#endif
+            const float2 c = c_cg2[OFF + MB * (J1 + 1) + M1B];
+            float2 tr = __fmul2_rn(xr[M1B], yr[M2B]);
+            tr = __ffma2_rn(xi[M1B], yn[M2B], tr);
+            float2 ti = __fmul2_rn(xr[M1B], yi[M2B]);
+            ti = __ffma2_rn(xi[M1B], yr[M2B], ti);
+            zr = __ffma2_rn(c, tr, zr);
+            zi = __ffma2_rn(c, ti, zi);
         }
-        conv_row<J1, J2, OFF, D, NCOL, M1B, MB + 1>(xx, xs, y, ys, z);
+        col_terms<J1, J2, OFF, D, MB, M1B + 1>(xr, xi, yr, yi, yn, zr, zi);
     }
 }
 
-template <int J1, int J2, int OFF, int D, int NCOL, int M1B>
-__device__ __forceinline__ void conv_all(const float2 (&xx)[J1 + 1], const float2 (&xs)[J1 + 1],
-                                         const float2 (&y)[J2 + 1], const float2 (&ys)[J2 + 1], float2 (&z)[NCOL]) {
-    if constexpr (M1B <= J1) {
-        conv_row<J1, J2, OFF, D, NCOL, M1B, 0>(xx, xs, y, ys, z);
-        conv_all<J1, J2, OFF, D, NCOL, M1B + 1>(xx, xs, y, ys, z);
-    }
-}
-
-template <int J, int NCOL, bool MID, int MB>
-__device__ __forceinline__ void dot_cols(const float2 (&wv)[NCOL], const float2 (&z)[NCOL], float2& acc,
-                                         float2& accm) {
+template <int J1, int J2, int J, int NCOL, bool MID, int OFF, int MB>
+__device__ __forceinline__ void cols(uint32_t wa, const float2 (&xr)[J1 + 1], const float2 (&xi)[J1 + 1],
+                                     const float2 (&yr)[J2 + 1], const float2 (&yi)[J2 + 1],
+                                     const float2 (&yn)[J2 + 1], float2& acc, float2& accm) {
     if constexpr (MB < NCOL) {
-        if constexpr (MID && 2 * MB == J)
-            accm = __ffma2_rn(wv[MB], z[MB], accm);
-        else
-            acc = __ffma2_rn(wv[MB], z[MB], acc);
-        dot_cols<J, NCOL, MID, MB + 1>(wv, z, acc, accm);
+        constexpr int D = (J1 + J2 - J) / 2;
+        float2 zr = make_float2(0.f, 0.f), zi = make_float2(0.f, 0.f);
+        col_terms<J1, J2, OFF, D, MB, 0>(xr, xi, yr, yi, yn, zr, zi);
+        const float4 w = lds4i<MB * 512>(wa);
+        if constexpr (MID && 2 * MB == J) {
+            accm = __ffma2_rn(make_float2(w.x, w.y), zr, accm);
+            accm = __ffma2_rn(make_float2(w.z, w.w), zi, accm);
+        } else {
+            acc = __ffma2_rn(make_float2(w.x, w.y), zr, acc);
+            acc = __ffma2_rn(make_float2(w.z, w.w), zi, acc);
+        }
+        cols<J1, J2, J, NCOL, MID, OFF, MB + 1>(wa, xr, xi, yr, yi, yn, acc, accm);
     }
 }
 
-template <int N, int I = 0>
-__device__ __forceinline__ void zero2(float2 (&z)[N]) {
-    if constexpr (I < N) {
-        z[I] = make_float2(0.f, 0.f);
-        zero2<N, I + 1>(z);
-    }
-}
-
-template <int N, int I = 0>
-__device__ __forceinline__ void prep_x(const float2 (&v)[N], float2 (&xx)[N], float2 (&xs)[N]) {
-    if constexpr (I < N) {
-        xx[I] = make_float2(v[I].x, v[I].x);
-        xs[I] = make_float2(-v[I].y, v[I].y);
-        prep_x<N, I + 1>(v, xx, xs);
-    }
-}
-
-template <int N, int I = 0>
-__device__ __forceinline__ void prep_y(const float2 (&v)[N], float2 (&ys)[N]) {
-    if constexpr (I < N) {
-        ys[I] = make_float2(v[I].y, v[I].x);
-        prep_y<N, I + 1>(v, ys);
-    }
-}
-
-// One unit: conv[mb] = sum_m1b c2(mb, m1b) x[m1b] y[mb - m1b + d] (complex),
-// returned as c1 * sum_mb weight(mb) Re(conj(w[mb]) conv[mb]).  The complex
-// products run on packed FP32x2 instructions: with xx = (x.re, x.re),
-// xs = (-x.im, x.im) and ys = (y.im, y.re),
-//   t = xx * y;  t = xs * ys + t  (= x y);  z = (c2, c2) * t + z.
-// Shared-memory addresses are 32-bit; each row is one base plus immediates.
-template <int J1, int J2, int J, int NCOL, bool MID>
-__device__ __forceinline__ float unit_full(uint32_t sbase, int ma, int m1a) {
+template <int J1, int J2, int J>
+__device__ __forceinline__ float2 unit_pairs(uint32_t sbase, int ma, int m1a) {
     constexpr int d = (J1 + J2 - J) / 2;
     constexpr int OFF = cg_offset(J1, J2, J);
     const int m2a = ma - m1a + d;
-    constexpr uint32_t F1 = full_off(J1) * 256u, F2 = full_off(J2) * 256u, FJ = full_off(J) * 256u;
-    const uint32_t xa = sbase + F1 + (uint32_t)m1a * ((J1 + 1) * 256u);
-    const uint32_t ya = sbase + F2 + (uint32_t)m2a * ((J2 + 1) * 256u);
-    const uint32_t wa = sbase + FJ + (uint32_t)ma * ((J + 1) * 256u);
-    float2 xv[J1 + 1], xx[J1 + 1], xs[J1 + 1], y[J2 + 1], ys[J2 + 1], wv[NCOL];
-    lds_row<J1 + 1>(xv, xa);
-    lds_row<J2 + 1>(y, ya);
-    lds_row<NCOL>(wv, wa);
-    prep_x<J1 + 1>(xv, xx, xs);
-    prep_y<J2 + 1>(y, ys);
-    float2 z[NCOL];
-    zero2<NCOL>(z);
-    conv_all<J1, J2, OFF, d, NCOL, 0>(xx, xs, y, ys, z);
+    float2 xr[J1 + 1], xi[J1 + 1], yr[J2 + 1], yi[J2 + 1], yn[J2 + 1];
+    const float sx = load_row_any<J1>(sbase, m1a, xr, xi);
+    const float sy = load_row_any<J2>(sbase, m2a, yr, yi);
+    negate_pairs<J2 + 1>(yi, yn);
+    const uint32_t wa = sbase + ((uint32_t)hoff(J) + (uint32_t)ma * (J + 1)) * kElemBytes;
     float2 acc = make_float2(0.f, 0.f), accm = make_float2(0.f, 0.f);
-    dot_cols<J, NCOL, MID, 0>(wv, z, acc, accm);
-    const float r = 2.f * (acc.x + acc.y) + (accm.x + accm.y);
-    return c_cg2[OFF + ma * (J1 + 1) + m1a].x * r;
+    if constexpr ((J & 1) == 0) {
+        if (2 * ma == J) {
+            cols<J1, J2, J, J / 2 + 1, true, OFF, 0>(wa, xr, xi, yr, yi, yn, acc, accm);
+        } else {
+            cols<J1, J2, J, J + 1, false, OFF, 0>(wa, xr, xi, yr, yi, yn, acc, accm);
+        }
+    } else {
+        cols<J1, J2, J, J + 1, false, OFF, 0>(wa, xr, xi, yr, yi, yn, acc, accm);
+    }
+    const float s = c_cg2[OFF + ma * (J1 + 1) + m1a].x * sx * sy;
+    return make_float2(s * (2.f * acc.x + accm.x), s * (2.f * acc.y + accm.y));
 }
 
 // this warp's units (ma | m1a << 4) of one triple, starting at `first`
 template <int J1, int J2, int J>
-__device__ __forceinline__ float triple_units(uint32_t su, const unsigned short* __restrict__ ul, int n, int first) {
-    float acc = 0.f;
+__device__ __forceinline__ float2 triple_units(uint32_t su, const unsigned short* __restrict__ ul, int n, int first) {
+    float2 acc = make_float2(0.f, 0.f);
     for (int i = first; i < n; i += kZbUWarps) {
         const int e = ul[i];
-        const int ma = e & 0xf, m1a = e >> 4;
-        if constexpr ((J & 1) == 0) {
-            if (2 * ma == J) {
-                acc += unit_full<J1, J2, J, J / 2 + 1, true>(su, ma, m1a);
-                continue;
-            }
-        }
-        acc += unit_full<J1, J2, J, J + 1, false>(su, ma, m1a);
+        const float2 r = unit_pairs<J1, J2, J>(su, e & 0xf, e >> 4);
+        acc.x += r.x;
+        acc.y += r.y;
     }
     return acc;
 }
 
 template <int LO, int HI>
-__device__ __forceinline__ float triple_dispatch(int id, uint32_t su, const unsigned short* ul, int n, int first) {
+__device__ __forceinline__ float2 triple_dispatch(int id, uint32_t su, const unsigned short* ul, int n, int first) {
     if constexpr (HI - LO == 1) {
         return triple_units<triple_field(LO, 0), triple_field(LO, 1), triple_field(LO, 2)>(su, ul, n, first);
     } else {
@@ -376,54 +399,52 @@ __global__ void __launch_bounds__(kZbUWarps * 32, 1)
                const int4* __restrict__ tri, int ntri, const unsigned short* __restrict__ units,
                float* __restrict__ B, int* __restrict__ err) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int nh = n_half(tj), nf = n_full(tj);
+    const int nh = n_half(tj);
     const int nB = n_triples(tj);
-    float2* su_all = reinterpret_cast<float2*>(smem_raw);
-    unsigned long long* sacc = reinterpret_cast<unsigned long long*>(smem_raw + sizeof(float2) * (size_t)nf * 32);
-    const int64_t tl = blockIdx.x;
-    if (tl >= ntiles) return;
-    // stage: expand the half set into full (J+1)^2 blocks
+    float4* su4 = reinterpret_cast<float4*>(smem_raw);
+    unsigned long long* sacc = reinterpret_cast<unsigned long long*>(smem_raw + sizeof(float4) * (size_t)nh * 32);
+    const int64_t tA = 2 * (int64_t)blockIdx.x;  // local tiles tA (points A) and tA + 1 (points B)
+    if (tA >= ntiles) return;
+    const bool hasB = tA + 1 < ntiles;
     {
-        const float2* src = u + (size_t)tl * nh * 32;
-        for (int idx = threadIdx.x; idx < nf * 32; idx += blockDim.x) {
-            const int e = idx >> 5, l = idx & 31;
-            const int m = c_fullmap[e];
-            float2 v = src[(size_t)(m & 0xffff) * 32 + l];
-            if (m & 0x10000) {  // mirrored element: (-1)^(ma-mb) conj
-                const float sg = (m & 0x20000) ? -1.f : 1.f;
-                v.x = sg * v.x;
-                v.y = -sg * v.y;
-            }
-            su_all[idx] = v;
+        const float2* srcA = u + (size_t)tA * nh * 32;
+        const float2* srcB = u + (size_t)(tA + 1) * nh * 32;
+        for (int idx = threadIdx.x; idx < nh * 32; idx += blockDim.x) {
+            const float2 a = __ldg(srcA + idx);
+            const float2 b = hasB ? __ldg(srcB + idx) : make_float2(0.f, 0.f);
+            su4[idx] = make_float4(a.x, b.x, a.y, b.y);
         }
-        for (int i = threadIdx.x; i < nB * 32; i += blockDim.x) sacc[i] = 0ull;
+        for (int i = threadIdx.x; i < nB * 64; i += blockDim.x) sacc[i] = 0ull;
     }
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t su = (uint32_t)__cvta_generic_to_shared(su_all) + (uint32_t)lane * 8u;
+    const uint32_t su = (uint32_t)__cvta_generic_to_shared(su4) + (uint32_t)lane * 16u;
     bool bad = false;
     for (int t = 0; t < ntri; ++t) {
         const int4 d = __ldg(tri + t);  // (gid, start, count, column)
         const int first = ((warp - d.y) % kZbUWarps + kZbUWarps) % kZbUWarps;
         if (first >= d.z) continue;
-        const float acc = triple_dispatch<0, n_triples(kTJMax)>(d.x, su, units + d.y, d.z, first);
-        bad |= !(fabsf(acc) < kFixLimit);
-        atomicAdd(&sacc[d.w * 32 + lane], (unsigned long long)__double2ll_rn((double)acc * kFixScale));
+        const float2 acc = triple_dispatch<0, n_triples(kTJMax)>(d.x, su, units + d.y, d.z, first);
+        bad |= !(fabsf(acc.x) < kFixLimit) || !(fabsf(acc.y) < kFixLimit);
+        atomicAdd(&sacc[d.w * 64 + lane], (unsigned long long)__double2ll_rn((double)acc.x * kFixScale));
+        atomicAdd(&sacc[d.w * 64 + 32 + lane], (unsigned long long)__double2ll_rn((double)acc.y * kFixScale));
     }
     if (__any_sync(0xffffffffu, bad) && lane == 0) atomicExch(err, 1);
     __syncthreads();
-    const int64_t tile = tile0 + tl;
-    const int tx = (int)(tile % g.tiles[0]);
-    const int ty = (int)((tile / g.tiles[0]) % g.tiles[1]);
-    const int tz = (int)(tile / ((int64_t)g.tiles[0] * g.tiles[1]));
-    for (int idx = threadIdx.x; idx < 32 * nB; idx += blockDim.x) {
-        const int l = idx / nB, t = idx % nB;
+    for (int idx = threadIdx.x; idx < 64 * nB; idx += blockDim.x) {
+        const int pl = idx / nB, t = idx % nB;  // pl: 0..31 tile A, 32..63 tile B
+        const int l = pl & 31;
+        const int64_t tile = tile0 + tA + (pl >> 5);
+        if ((pl >> 5) && !hasB) continue;
+        const int tx = (int)(tile % g.tiles[0]);
+        const int ty = (int)((tile / g.tiles[0]) % g.tiles[1]);
+        const int tz = (int)(tile / ((int64_t)g.tiles[0] * g.tiles[1]));
         const int ix = tx * kTileX + (l % kTileX);
         const int iy = ty * kTileY + ((l / kTileX) % kTileY);
         const int iz = tz * kTileZ + l / (kTileX * kTileY);
         if (ix >= g.grid[0] || iy >= g.grid[1] || iz >= g.grid[2]) continue;
         const int64_t p = ix + (int64_t)g.grid[0] * (iy + (int64_t)g.grid[1] * iz);
-        B[(size_t)p * nB + t] = (float)((double)(long long)sacc[t * 32 + l] * (1.0 / kFixScale));
+        B[(size_t)p * nB + t] = (float)((double)(long long)sacc[t * 64 + pl] * (1.0 / kFixScale));
     }
 }
 
