@@ -72,7 +72,7 @@ struct SnapTables {
     std::map<int, int> warp_list_len;
     // FP32 zb work units (triple, row, m1 row) per supported twojmax (index tj/2)
     int4* tri_d = nullptr;              // per triple: (global id, first unit, unit count, column)
-    unsigned short* units_d = nullptr;  // ma | m1a << 4
+    unsigned short* units_d = nullptr;  // ma | m1a << 4 | twice << 8
     int tri_off[8] = {0};
     int tri_n[8] = {0};
     int unit_off[8] = {0};

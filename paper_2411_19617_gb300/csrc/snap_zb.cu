@@ -136,7 +136,7 @@ int upload_cg_tables(Ctx* c) {
     MALA_CUDA_TRY(cudaMemcpyToSymbol(c_zb_list, lists, sizeof(lists)));
     MALA_TRY(upload_zb_lists_f64(&lists[0][0][0], (int)sizeof(lists)));
     // FP32 work units: per twojmax, for every triple (in index-set order) the
-    // (ma, m1a) row pairs with a non-empty coupling, packed ma | m1a << 4.
+    // (ma, m1a) row pairs with a non-empty coupling, packed ma | m1a << 4 | twice << 8.
     std::vector<int> tri;               // int4 records (gid, first unit, count, column)
     std::vector<unsigned short> units;  // all units
     for (int tj = 0; tj <= kTJMax; tj += 2) {
@@ -154,7 +154,13 @@ int upload_cg_tables(Ctx* c) {
                             for (int m1a = 0; m1a <= j1; ++m1a) {
                                 const int m2a = ma - m1a + d;
                                 if (m2a < 0 || m2a > j2) continue;
-                                units.push_back((unsigned short)(ma | (m1a << 4)));
+                                // j1 == j2: the unit (ma, m1a) equals the unit (ma, m2a), since
+                                // C(j1 m1 j1 m2|j m) = (-1)^(2 j1 - j) C(j1 m2 j1 m1|j m) and both
+                                // coefficients of a term flip together; keep m1a <= m2a, count
+                                // m1a < m2a twice (bit 8)
+                                if (j1 == j2 && m1a > m2a) continue;
+                                const int twice = (j1 == j2 && m1a < m2a) ? 1 : 0;
+                                units.push_back((unsigned short)(ma | (m1a << 4) | (twice << 8)));
                             }
                         tri.insert(tri.end(), {gid, first, (int)units.size() - ubase - first, lid});
                         ++lid;

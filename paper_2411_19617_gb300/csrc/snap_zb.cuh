@@ -346,7 +346,7 @@ __device__ __forceinline__ void cols(uint32_t wa, const float2 (&xr)[J1 + 1], co
 }
 
 template <int J1, int J2, int J>
-__device__ __forceinline__ float2 unit_pairs(uint32_t sbase, int ma, int m1a) {
+__device__ __forceinline__ float2 unit_pairs(uint32_t sbase, int ma, int m1a, float mult) {
     constexpr int d = (J1 + J2 - J) / 2;
     constexpr int OFF = cg_offset(J1, J2, J);
     const int m2a = ma - m1a + d;
@@ -365,17 +365,17 @@ __device__ __forceinline__ float2 unit_pairs(uint32_t sbase, int ma, int m1a) {
     } else {
         cols<J1, J2, J, J + 1, false, OFF, 0>(wa, xr, xi, yr, yi, yn, acc, accm);
     }
-    const float s = c_cg2[OFF + ma * (J1 + 1) + m1a].x * sx * sy;
+    const float s = c_cg2[OFF + ma * (J1 + 1) + m1a].x * sx * sy * mult;
     return make_float2(s * (2.f * acc.x + accm.x), s * (2.f * acc.y + accm.y));
 }
 
-// this warp's units (ma | m1a << 4) of one triple, starting at `first`
+// this warp's units (ma | m1a << 4 | twice << 8) of one triple, starting at `first`
 template <int J1, int J2, int J>
 __device__ __forceinline__ float2 triple_units(uint32_t su, const unsigned short* __restrict__ ul, int n, int first) {
     float2 acc = make_float2(0.f, 0.f);
     for (int i = first; i < n; i += kZbUWarps) {
         const int e = ul[i];
-        const float2 r = unit_pairs<J1, J2, J>(su, e & 0xf, e >> 4);
+        const float2 r = unit_pairs<J1, J2, J>(su, e & 0xf, (e >> 4) & 0xf, (e & 0x100) ? 2.f : 1.f);
         acc.x += r.x;
         acc.y += r.y;
     }

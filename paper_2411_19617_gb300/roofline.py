@@ -2,7 +2,7 @@
 
 Counts follow the definitions, not the kernels' instruction streams:
   * compute_zi on the half set of Z (rows m < j/2, plus the middle row's
-    columns m' <= j/2 for even 2j): every coupling term
+    columns m' <= j/2 for even 2j), j1 = j2 row pairs counted once: every coupling term
     C C u^{j1} u^{j2} costs a complex product (6 flop), a real scale (2 flop)
     and a complex accumulate (2 flop) = 10 flop;
   * compute_bi: Re(conj(u^j) Z) per half-set element = 4 flop;
@@ -22,17 +22,21 @@ def triples(twojmax: int):
 
 @lru_cache(maxsize=None)
 def zi_terms_half(twojmax: int) -> int:
+    """Coupling terms of the half set of Z.  For j1 == j2 the row pairs
+    (m1a, m2a) and (m2a, m1a) give the same product (the two Clebsch-Gordan
+    factors change sign together under the exchange), so only m1a <= m2a
+    is counted."""
     total = 0
     for (j1, j2, j) in triples(twojmax):
         d = (j1 + j2 - j) // 2
 
-        def nvalid(mb):
-            return sum(1 for m1 in range(j1 + 1) if 0 <= mb - m1 + d <= j2)
+        def nvalid(mb, sym=False):
+            return sum(1 for m1 in range(j1 + 1) if 0 <= mb - m1 + d <= j2 and (not sym or m1 <= mb - m1 + d))
 
         for ma in range(j + 1):
             for mb in range(j + 1):
                 if (2 * ma < j) or (2 * ma == j and 2 * mb <= j):
-                    total += nvalid(ma) * nvalid(mb)
+                    total += nvalid(ma, sym=(j1 == j2)) * nvalid(mb)
     return total
 
 
