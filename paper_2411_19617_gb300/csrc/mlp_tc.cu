@@ -2,19 +2,27 @@
 // x_{l+1} = act(W_l x_l + b_l)) on the 5th-generation tensor cores, plus the
 // FP64 path.
 //
-// MIXED path, one CTA of 4 warps per tile of 128 grid points (M = 128):
-//   * the descriptors B[P][n_B] (FP32) are standardised ((B - shift) * scale),
-//     rounded to BF16 and written to shared memory in the UMMA K-major layout
-//     with the 128-byte swizzle (the layout TMA produces with SWIZZLE_128B);
+// MIXED path: a persistent kernel, one CTA of 8 warps per SM, walking tiles of
+// 128 grid points (M = 128):
+//   * the descriptors B[P][n_B] (FP32) of a tile are read row by row
+//     (coalesced), standardised ((B - shift) * scale), rounded to BF16 and
+//     written to shared memory in the UMMA K-major layout with the 128-byte
+//     swizzle (the layout TMA produces with SWIZZLE_128B);
 //   * every layer is a chain of tcgen05.mma (kind::f16, BF16 x BF16 -> FP32)
 //     issued by one thread into a tensor-memory accumulator D[128][N] (one TMEM
-//     lane per point); the layer's weights W_l[N][K] stream through a
-//     double-buffered shared-memory stage in K-blocks of 64 by TMA;
-//   * the epilogue reads D with tcgen05.ld (thread = point), adds the bias,
-//     applies LeakyReLU on hidden layers and writes the BF16 activations back
-//     to shared memory as the next layer's A operand (same swizzled layout);
+//     lane per point); the layer's weights W_l[N][K] stream through two
+//     shared-memory stages in K-blocks of 64 by TMA: block kb+1 is fetched
+//     while the MMAs of block kb run, and the first two blocks of the next
+//     layer (or of the next tile's first layer) are fetched while the
+//     epilogue runs;
+//   * the epilogue reads D with tcgen05.ld (thread = point, the two warps that
+//     share a TMEM lane quarter take alternate 32-column chunks), adds the
+//     bias, applies LeakyReLU on hidden layers and writes the BF16 activations
+//     back to shared memory as the next layer's A operand;
 //   * the last epilogue writes the LDOS in BF16 and, from the same rounded
-//     values, the tile's column sums sum_r LDOS(r, xi) (the DOS partials, FP64).
+//     values, adds the tile's column sums sum_r LDOS(r, xi) to the CTA's FP64
+//     DOS partial; the partials of all CTAs are summed in CTA order afterwards,
+//     so the DOS does not depend on timing.
 // Every wait on an mbarrier is bounded (about one second of clock cycles); on
 // expiry the kernel records an error code, frees its tensor memory and returns.
 #include <cuda.h>
@@ -33,14 +41,16 @@ namespace mala {
 
 namespace {
 
-constexpr int kMlpThreads = 128;
+constexpr int kMlpThreads = 256;
 constexpr int kMaxLayers = 4;
 constexpr int kKBlk = 64;             // K elements per swizzle block (128 bytes of BF16)
 constexpr int kMaxHiddenPad = 448;    // widest K of a hidden activation (7 blocks)
 constexpr int kMaxNPad = 400;         // widest layer output held in one W stage
 constexpr int kHBytes = 128 * kMaxHiddenPad * 2;  // 114688
 constexpr int kStageBytes = kMaxNPad * 128;        // 51200: [N rows][64 K] BF16
-constexpr int kSmemBytes = kHBytes + 2 * kStageBytes + 1024 /* barriers, tmem slot */ + 1024 /* alignment */;
+constexpr int kMaxNE = 256;                        // widest output layer
+constexpr int kSmemBytes = kHBytes + 2 * kStageBytes + 1024 /* barriers, tmem slot */ + kMaxNE * 8 /* DOS partial */ +
+                           1024 /* alignment */;
 constexpr long long kWaitCycles = 2000000000LL;
 
 struct LayerDev {
@@ -59,7 +69,7 @@ struct MlpParams {
     const float* shift;     // [nB]
     const float* scale;     // [nB]
     __nv_bfloat16* ldos;    // [P][N_E]
-    double* tile_dos;       // [n_tiles][N_E] or nullptr
+    double* cta_dos;        // [gridDim.x][N_E] or nullptr
     int64_t P;
     int* err;
 };
@@ -144,18 +154,6 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-    uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
 // byte offset of element (row r, k) in a [128][64] BF16 K-block with the
 // 128-byte swizzle (16-byte chunk index XOR row % 8)
 __device__ __forceinline__ uint32_t swz(int r, int k) {
@@ -167,25 +165,78 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
     return *reinterpret_cast<uint32_t*>(&h);
 }
 
+// tcgen05.ld of 32 consecutive columns of the warp's TMEM lane quarter
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr + 16u));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Weight pipeline state of the issuing thread.  Stage s holds K-block kb with
+// kb % 2 == s.  full[s] completes when a stage's TMA bytes have landed,
+// free[s] when the MMAs that read it have finished; every completion of either
+// is waited exactly once, in order, before the barrier can complete again.
+struct WPipe {
+    uint32_t full[2], free_[2];
+    uint32_t ph_full[2] = {0, 0}, ph_free[2] = {0, 0};
+    bool pend[2] = {false, false};      // a free[s] completion not yet waited for
+    bool inflight[2] = {false, false};  // a full[s] completion not yet waited for
+};
+
+__device__ __forceinline__ bool wait_full(WPipe& wp, int s, int* err) {
+    const bool ok = mbar_wait(wp.full[s], wp.ph_full[s], err, 2);
+    wp.ph_full[s] ^= 1;
+    wp.inflight[s] = false;
+    return ok;
+}
+
+__device__ __forceinline__ bool load_stage(WPipe& wp, const CUtensorMap* map, const LayerDev& L, int kb,
+                                           unsigned char* sW, int* err) {
+    const int s = kb & 1;
+    if (wp.pend[s]) {
+        if (!mbar_wait(wp.free_[s], wp.ph_free[s], err, 3)) return false;
+        wp.ph_free[s] ^= 1;
+        wp.pend[s] = false;
+    }
+    mbar_expect_tx(wp.full[s], (uint32_t)L.Npad * 128u);
+    wp.inflight[s] = true;
+    for (int n0 = 0; n0 < L.Npad; n0 += L.boxN)
+        tma_load_2d(smem_u32(sW + s * kStageBytes + n0 * 128), map, kb * kKBlk, n0, wp.full[s]);
+    return true;
+}
+
 __global__ void __launch_bounds__(kMlpThreads, 1) k_mlp_tc(const __grid_constant__ TMaps maps, MlpParams prm) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     unsigned char* sH = sm;                          // activations, K-blocks of [128][64] BF16
     unsigned char* sW = sm + kHBytes;                // two weight stages
-    // barriers: full[2] (TMA -> stage), done (end of a layer's MMAs, waited by
-    // every thread), free (a stage's MMAs finished, waited by the issuing thread)
     uint64_t* bars = reinterpret_cast<uint64_t*>(sm + kHBytes + 2 * kStageBytes);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 4);
-    const int tid = threadIdx.x, warp = tid >> 5;
-    const int64_t row0 = (int64_t)blockIdx.x * 128;
-    const uint32_t bar_full0 = smem_u32(&bars[0]), bar_full1 = smem_u32(&bars[1]), bar_done = smem_u32(&bars[2]);
-    const uint32_t bar_free = smem_u32(&bars[3]);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 8);
+    double* sDos = reinterpret_cast<double*>(sm + kHBytes + 2 * kStageBytes + 1024);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int quarter = warp & 3, half = warp >> 2;  // TMEM lane quarter, column-chunk parity
+    const int64_t ntiles = (prm.P + 127) / 128;
+    const int NE = prm.L[prm.n_layers - 1].N;
+    WPipe wp;
+    wp.full[0] = smem_u32(&bars[0]);
+    wp.full[1] = smem_u32(&bars[1]);
+    wp.free_[0] = smem_u32(&bars[2]);
+    wp.free_[1] = smem_u32(&bars[3]);
+    const uint32_t bar_done = smem_u32(&bars[4]);
 
     if (tid == 0) {
-        mbar_init(bar_full0, 1);
-        mbar_init(bar_full1, 1);
-        mbar_init(bar_done, 1);
-        mbar_init(bar_free, 1);
+        for (int i = 0; i < 5; ++i) mbar_init(smem_u32(&bars[i]), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         for (int l = 0; l < prm.n_layers; ++l)
             asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&maps.m[l])) : "memory");
@@ -194,143 +245,176 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_mlp_tc(const __grid_constant
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(tslot)));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
-    // ---- input tile: (B - shift) * scale -> BF16, swizzled, zero-padded ----
-    {
-        const int K0pad = prm.L[0].Kpad;
-        for (int idx = tid; idx < 128 * K0pad; idx += kMlpThreads) {
-            const int r = idx / K0pad, k = idx % K0pad;
-            float v = 0.f;
-            if (k < prm.nB && row0 + r < prm.P) v = (prm.B[(row0 + r) * prm.nB + k] - prm.shift[k]) * prm.scale[k];
-            const __nv_bfloat16 h = __float2bfloat16_rn(v);
-            *reinterpret_cast<__nv_bfloat16*>(sH + (k / kKBlk) * (128 * 128) + swz(r, k % kKBlk)) = h;
-        }
-    }
-    fence_proxy_async();
+    for (int c = tid; c < NE; c += kMlpThreads) sDos[c] = 0.0;
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tslot;
-    uint32_t ph_full[2] = {0, 0}, ph_done = 0, ph_free = 0;
+    const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16);
+    uint32_t ph_done = 0;
     bool ok = true;
+    if (tid == 0 && (int64_t)blockIdx.x < ntiles) {
+        for (int kb = 0; kb < min(2, prm.L[0].nkb) && ok; ++kb) ok = load_stage(wp, &maps.m[0], prm.L[0], kb, sW, prm.err);
+    }
 
-    for (int l = 0; l < prm.n_layers && ok; ++l) {
-        const LayerDev& L = prm.L[l];
-        // ---- MMA chain of layer l (one thread issues, the rest wait) ----
-        if (tid == 0) {
-            const uint32_t stage_bytes = (uint32_t)L.Npad * 128u;
-            auto load_stage = [&](int kb, int s) {
-                const uint32_t bar = s ? bar_full1 : bar_full0;
-                mbar_expect_tx(bar, stage_bytes);
-                for (int n0 = 0; n0 < L.Npad; n0 += L.boxN)
-                    tma_load_2d(smem_u32(sW + s * kStageBytes + n0 * 128), &maps.m[l], kb * kKBlk, n0, bar);
-            };
-            load_stage(0, 0);
-            if (L.nkb > 1) load_stage(1, 1);
-            for (int kb = 0; kb < L.nkb && ok; ++kb) {
-                const int s = kb & 1;
-                ok = mbar_wait(s ? bar_full1 : bar_full0, ph_full[s], prm.err, 2);
-                ph_full[s] ^= 1;
-                if (!ok) break;
-                tc_fence_after();
-                const uint32_t a_base = smem_u32(sH + kb * (128 * 128));
-                const uint32_t b_base = smem_u32(sW + s * kStageBytes);
-                for (int k = 0; k < kKBlk / 16; ++k) {
-                    for (int n0 = 0; n0 < L.Npad; n0 += 256) {
-                        const int nn = min(256, L.Npad - n0);
-                        mma_bf16(tmem + (uint32_t)n0, sdesc(a_base + k * 32), sdesc(b_base + n0 * 128 + k * 32),
-                                 idesc_bf16(128, nn), (kb > 0 || k > 0) ? 1u : 0u);
-                    }
-                }
-                if (kb + 2 < L.nkb) {
-                    // the stage is refilled once the MMAs reading it have completed
-                    mma_commit(bar_free);
-                    ok = mbar_wait(bar_free, ph_free, prm.err, 3);
-                    ph_free ^= 1;
-                    if (ok) load_stage(kb + 2, s);
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t row0 = tile * 128;
+        const int nrows = (int)min((int64_t)128, prm.P - row0);
+        // ---- input tile: (B - shift) * scale -> BF16, swizzled, zero-padded ----
+        {
+            const int K0pad = prm.L[0].Kpad;
+            const float* src = prm.B + row0 * prm.nB;
+            for (int r = warp; r < 128; r += kMlpThreads / 32) {
+                for (int k = lane; k < K0pad; k += 32) {
+                    float v = 0.f;
+                    if (k < prm.nB && r < nrows) v = (__ldg(src + (int64_t)r * prm.nB + k) - __ldg(prm.shift + k)) * __ldg(prm.scale + k);
+                    *reinterpret_cast<__nv_bfloat16*>(sH + (k / kKBlk) * (128 * 128) + swz(r, k % kKBlk)) =
+                        __float2bfloat16_rn(v);
                 }
             }
-            mma_commit(bar_done);
         }
-        __syncthreads();
-        if (!ok) break;
-        ok = mbar_wait(bar_done, ph_done, prm.err, 4);
-        ph_done ^= 1;
+        fence_proxy_async();
+        tc_fence_before();
         if (!__syncthreads_and(ok)) {
             ok = false;
             break;
         }
         tc_fence_after();
-        // ---- epilogue: TMEM -> registers (thread = point) -> bias/activation ----
-        const int r = tid;
-        const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
-        const bool last = (l == prm.n_layers - 1);
-        if (!last) {
-            const int Knext = prm.L[l + 1].Kpad;
-            for (int c0 = 0; c0 < Knext; c0 += 16) {
-                float v[16];
-                if (c0 < L.Npad) {
-                    tmem_ld16(trow + (uint32_t)c0, v);
-                } else {
+
+        for (int l = 0; l < prm.n_layers; ++l) {
+            const LayerDev& L = prm.L[l];
+            // ---- MMA chain of layer l (one thread issues, the rest wait) ----
+            if (tid == 0) {
+                for (int kb = 0; kb < L.nkb && ok; ++kb) {
+                    const int s = kb & 1;
+                    ok = wait_full(wp, s, prm.err);
+                    if (!ok) break;
+                    tc_fence_after();
+                    const uint32_t a_base = smem_u32(sH + kb * (128 * 128));
+                    const uint32_t b_base = smem_u32(sW + s * kStageBytes);
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) v[i] = 0.f;
+                    for (int k = 0; k < kKBlk / 16; ++k) {
+                        for (int n0 = 0; n0 < L.Npad; n0 += 256) {
+                            const int nn = min(256, L.Npad - n0);
+                            mma_bf16(tmem + (uint32_t)n0, sdesc(a_base + k * 32), sdesc(b_base + n0 * 128 + k * 32),
+                                     idesc_bf16(128, nn), (kb > 0 || k > 0) ? 1u : 0u);
+                        }
+                    }
+                    mma_commit(wp.free_[s]);
+                    wp.pend[s] = true;
+                    // block kb+1 goes to the other stage once the MMAs of kb-1 are done
+                    if (kb >= 1 && kb + 1 < L.nkb) {
+                        ok = load_stage(wp, &maps.m[l], L, kb + 1, sW, prm.err);
+                        if (!ok) break;
+                    }
                 }
-#pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    const int c = c0 + i;
-                    float x = (c < L.N) ? v[i] + L.bias[c] : 0.f;
-                    if (L.act) x = x > 0.f ? x : prm.slope * x;
-                    v[i] = x;
-                }
-                uint4 q0, q1;
-                q0.x = pack_bf16(v[0], v[1]);
-                q0.y = pack_bf16(v[2], v[3]);
-                q0.z = pack_bf16(v[4], v[5]);
-                q0.w = pack_bf16(v[6], v[7]);
-                q1.x = pack_bf16(v[8], v[9]);
-                q1.y = pack_bf16(v[10], v[11]);
-                q1.z = pack_bf16(v[12], v[13]);
-                q1.w = pack_bf16(v[14], v[15]);
-                unsigned char* blk = sH + (c0 / kKBlk) * (128 * 128);
-                *reinterpret_cast<uint4*>(blk + swz(r, c0 % kKBlk)) = q0;
-                *reinterpret_cast<uint4*>(blk + swz(r, c0 % kKBlk + 8)) = q1;
+                mma_commit(bar_done);
             }
-            fence_proxy_async();
-            tc_fence_before();
-            __syncthreads();
+            const bool mine = mbar_wait(bar_done, ph_done, prm.err, 4);
+            ph_done ^= 1;
+            if (!__syncthreads_and(ok && mine)) {
+                ok = false;
+                break;
+            }
             tc_fence_after();
-        } else {
-            // output: BF16 rows staged in the (now idle) weight stages, then
-            // coalesced stores and per-column sums of the stored values
-            const int NE = L.N;
-            __nv_bfloat16* so = reinterpret_cast<__nv_bfloat16*>(sW);  // [128][NEpad16]
-            const int ldo = (NE + 15) & ~15;
-            for (int c0 = 0; c0 < ldo; c0 += 16) {
-                float v[16];
-                tmem_ld16(trow + (uint32_t)c0, v);
+            const bool last = (l == prm.n_layers - 1);
+            // the stages are idle now: fetch the next layer's first blocks during the epilogue
+            if (tid == 0) {
+                const int nl = last ? 0 : l + 1;
+                const bool more = !last || tile + gridDim.x < ntiles;
+                if (more)
+                    for (int kb = 0; kb < min(2, prm.L[nl].nkb) && ok; ++kb)
+                        ok = load_stage(wp, &maps.m[nl], prm.L[nl], kb, sW, prm.err);
+            }
+            // ---- epilogue: TMEM -> registers (thread = point) -> bias/activation ----
+            const int r = quarter * 32 + lane;
+            if (!last) {
+                const int Knext = prm.L[l + 1].Kpad;
+                for (int c0 = half * 32; c0 < Knext; c0 += 64) {
+                    float v[32];
+                    tmem_ld32(trow + (uint32_t)c0, v);
 #pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    const int c = c0 + i;
-                    float x = (c < NE) ? v[i] + L.bias[c] : 0.f;
-                    if (L.act) x = x > 0.f ? x : prm.slope * x;
-                    so[r * ldo + c] = __float2bfloat16_rn(x);
+                    for (int i = 0; i < 32; ++i) {
+                        const int c = c0 + i;
+                        float x = (c < L.N) ? v[i] + __ldg(L.bias + c) : 0.f;
+                        if (L.act) x = x > 0.f ? x : prm.slope * x;
+                        v[i] = x;
+                    }
+                    unsigned char* blk = sH + (c0 / kKBlk) * (128 * 128);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        uint4 w4;
+                        w4.x = pack_bf16(v[8 * q + 0], v[8 * q + 1]);
+                        w4.y = pack_bf16(v[8 * q + 2], v[8 * q + 3]);
+                        w4.z = pack_bf16(v[8 * q + 4], v[8 * q + 5]);
+                        w4.w = pack_bf16(v[8 * q + 6], v[8 * q + 7]);
+                        *reinterpret_cast<uint4*>(blk + swz(r, c0 % kKBlk + 8 * q)) = w4;
+                    }
                 }
-            }
-            tc_fence_before();
-            __syncthreads();
-            const int64_t nrows = min((int64_t)128, prm.P - row0);
-            for (int idx = tid; idx < nrows * NE; idx += kMlpThreads) {
-                const int rr = idx / NE, c = idx % NE;
-                prm.ldos[(row0 + rr) * NE + c] = so[rr * ldo + c];
-            }
-            if (prm.tile_dos) {
-                for (int c = tid; c < NE; c += kMlpThreads) {
-                    float s = 0.f;
-                    for (int rr = 0; rr < nrows; ++rr) s += __bfloat162float(so[rr * ldo + c]);
-                    prm.tile_dos[(int64_t)blockIdx.x * NE + c] = (double)s;
+                fence_proxy_async();
+                tc_fence_before();
+                __syncthreads();
+                tc_fence_after();
+            } else {
+                // output: BF16 rows staged in the activation buffer (its MMAs are
+                // done), row stride padded by 16 bytes against bank conflicts
+                __nv_bfloat16* so = reinterpret_cast<__nv_bfloat16*>(sH);
+                const int ldc = (NE + 31) & ~31;
+                const int ldo = ldc + 8;
+                for (int c0 = half * 32; c0 < ldc; c0 += 64) {
+                    float v[32];
+                    tmem_ld32(trow + (uint32_t)c0, v);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        float x[8];
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            const int c = c0 + 8 * q + i;
+                            float t = (c < NE) ? v[8 * q + i] + __ldg(L.bias + c) : 0.f;
+                            if (L.act) t = t > 0.f ? t : prm.slope * t;
+                            x[i] = t;
+                        }
+                        uint4 w4;
+                        w4.x = pack_bf16(x[0], x[1]);
+                        w4.y = pack_bf16(x[2], x[3]);
+                        w4.z = pack_bf16(x[4], x[5]);
+                        w4.w = pack_bf16(x[6], x[7]);
+                        *reinterpret_cast<uint4*>(so + r * ldo + c0 + 8 * q) = w4;
+                    }
                 }
+                tc_fence_before();
+                __syncthreads();
+                __nv_bfloat16* dst = prm.ldos + row0 * NE;
+                if ((NE & 1) == 0) {
+                    const int hw = NE / 2;
+                    for (int idx = tid; idx < nrows * hw; idx += kMlpThreads) {
+                        const int rr = idx / hw, c2 = idx - rr * hw;
+                        reinterpret_cast<uint32_t*>(dst)[idx] = *reinterpret_cast<const uint32_t*>(so + rr * ldo + 2 * c2);
+                    }
+                } else {
+                    for (int idx = tid; idx < nrows * NE; idx += kMlpThreads) {
+                        const int rr = idx / NE, c = idx - rr * NE;
+                        dst[idx] = so[rr * ldo + c];
+                    }
+                }
+                if (prm.cta_dos) {
+                    for (int c = tid; c < NE; c += kMlpThreads) {
+                        float sum = 0.f;
+                        for (int rr = 0; rr < nrows; ++rr) sum += __bfloat162float(so[rr * ldo + c]);
+                        sDos[c] += (double)sum;
+                    }
+                }
+                __syncthreads();  // the staging buffer is the next tile's input buffer
             }
         }
+        if (!ok) break;
     }
+    if (prm.cta_dos)
+        for (int c = tid; c < NE; c += kMlpThreads) prm.cta_dos[(int64_t)blockIdx.x * NE + c] = sDos[c];
+    // after an error: let copies still in flight land before the CTA exits
+    if (tid == 0)
+        for (int s2 = 0; s2 < 2; ++s2)
+            if (wp.inflight[s2]) wait_full(wp, s2, prm.err);
     tc_fence_before();
     __syncthreads();
     if (warp == 0) {
@@ -559,10 +643,14 @@ int mlp_forward(Ctx* c, const Model* m, const void* B, int64_t P, void* ldos, do
             return fail(MALA_ERR_UNSUPPORTED, "network shape outside the tensor-core kernel's limits "
                                               "(<= %d layers, hidden width <= %d, output <= 256)", kMaxLayers, kMaxHiddenPad);
         const int64_t ntiles = (P + 127) / 128;
-        double* tile_dos = nullptr;
+        int dev = 0, nsm = 0;
+        MALA_CUDA_TRY(cudaGetDevice(&dev));
+        MALA_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        const int grid = (int)std::min<int64_t>(ntiles, std::max(1, nsm));
+        double* cta_dos = nullptr;
         if (dos_sum) {
-            MALA_TRY(c->ws_tile_dos.reserve(c, sizeof(double) * (size_t)ntiles * NE));
-            tile_dos = c->ws_tile_dos.as<double>();
+            MALA_TRY(c->ws_tile_dos.reserve(c, sizeof(double) * (size_t)grid * NE));
+            cta_dos = c->ws_tile_dos.as<double>();
         }
         TMaps maps;
         memset(&maps, 0, sizeof(maps));
@@ -589,15 +677,15 @@ int mlp_forward(Ctx* c, const Model* m, const void* B, int64_t P, void* ldos, do
         prm.shift = m->in_shift;
         prm.scale = m->in_scale;
         prm.ldos = static_cast<__nv_bfloat16*>(ldos);
-        prm.tile_dos = tile_dos;
+        prm.cta_dos = cta_dos;
         prm.P = P;
         prm.err = c->tables.err_d + 1;
         cudaFuncSetAttribute(k_mlp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
-        MALA_PROF(c, "k_mlp", st, (k_mlp_tc<<<(unsigned)ntiles, kMlpThreads, kSmemBytes, st>>>(maps, prm)));
+        MALA_PROF(c, "k_mlp", st, (k_mlp_tc<<<(unsigned)grid, kMlpThreads, kSmemBytes, st>>>(maps, prm)));
         MALA_CUDA_TRY(cudaGetLastError());
         if (dos_sum)
             MALA_PROF(c, "k_dos_reduce", st,
-                      (k_dos_reduce<<<(NE + 127) / 128, 128, 0, st>>>(tile_dos, ntiles, NE, dos_sum)));
+                      (k_dos_reduce<<<(NE + 127) / 128, 128, 0, st>>>(cta_dos, grid, NE, dos_sum)));
         MALA_CUDA_TRY(cudaGetLastError());
         return MALA_OK;
     }
