@@ -165,9 +165,10 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
     return *reinterpret_cast<uint32_t*>(&h);
 }
 
-// tcgen05.ld of 32 consecutive columns of the warp's TMEM lane quarter
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-    uint32_t r[32];
+// tcgen05.ld of 32 consecutive columns of the warp's TMEM lane quarter.  The
+// registers are valid only after tmem_wait(), which names them as operands so
+// that no use can be scheduled ahead of the wait.
+__device__ __forceinline__ void tmem_issue32(uint32_t taddr, uint32_t (&r)[32]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
@@ -178,9 +179,35 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
         : "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
           "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
         : "r"(taddr + 16u));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_wait(uint32_t (&r)[32]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]),
+                   "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]),
+                   "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]),
+                   "+r"(r[30]), "+r"(r[31])
+                 :
+                 : "memory");
+}
+
+// bias + activation of 32 accumulator columns c0.. (zero beyond the layer's N)
+__device__ __forceinline__ void bias_act32(const uint32_t (&r)[32], float (&x)[32], int c0, const LayerDev& L,
+                                           float slope) {
 #pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+    for (int q = 0; q < 8; ++q) {
+        float4 b = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (c0 + 4 * q < L.Npad) b = __ldg(reinterpret_cast<const float4*>(L.bias) + (c0 / 4 + q));
+        const float bb[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int c = c0 + 4 * q + i;
+            float t = (c < L.N) ? __uint_as_float(r[4 * q + i]) + bb[i] : 0.f;
+            if (L.act) t = t > 0.f ? t : slope * t;
+            x[4 * q + i] = t;
+        }
+    }
 }
 
 // Weight pipeline state of the issuing thread.  Stage s holds K-block kb with
@@ -261,15 +288,45 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_mlp_tc(const __grid_constant
         const int64_t row0 = tile * 128;
         const int nrows = (int)min((int64_t)128, prm.P - row0);
         // ---- input tile: (B - shift) * scale -> BF16, swizzled, zero-padded ----
+        // warp w takes rows 4w..4w+3 (+32 per pass), lane k = lane + 32 j;
+        // up to 16 loads per thread are in flight before the first store
         {
             const int K0pad = prm.L[0].Kpad;
-            const float* src = prm.B + row0 * prm.nB;
-            for (int r = warp; r < 128; r += kMlpThreads / 32) {
-                for (int k = lane; k < K0pad; k += 32) {
-                    float v = 0.f;
-                    if (k < prm.nB && r < nrows) v = (__ldg(src + (int64_t)r * prm.nB + k) - __ldg(prm.shift + k)) * __ldg(prm.scale + k);
-                    *reinterpret_cast<__nv_bfloat16*>(sH + (k / kKBlk) * (128 * 128) + swz(r, k % kKBlk)) =
-                        __float2bfloat16_rn(v);
+            const int nch = K0pad / 32;
+            const float* __restrict__ src = prm.B + row0 * prm.nB;
+            for (int rb = warp * 4; rb < 128; rb += 4 * (kMlpThreads / 32)) {
+                for (int j0 = 0; j0 < nch; j0 += 4) {
+                    float v[4][4];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            const int k = lane + 32 * (j0 + j);
+                            v[i][j] = (k < prm.nB && rb + i < nrows) ? __ldg(src + (int64_t)(rb + i) * prm.nB + k) : 0.f;
+                        }
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        if (j0 + j >= nch) break;
+                        const int k = lane + 32 * (j0 + j);
+                        const bool in = k < prm.nB;
+                        const float sh = in ? __ldg(prm.shift + k) : 0.f;
+                        const float sc = in ? __ldg(prm.scale + k) : 0.f;
+#pragma unroll
+                        for (int i = 0; i < 4; ++i)
+                            *reinterpret_cast<__nv_bfloat16*>(sH + (k / kKBlk) * (128 * 128) + swz(rb + i, k % kKBlk)) =
+                                __float2bfloat16_rn((v[i][j] - sh) * sc);
+                    }
+                }
+            }
+            // warm L2 with the next tile's descriptors (a hint; skipped when unaligned)
+            if (tid == 32) {
+                const int64_t nt = tile + gridDim.x;
+                if (nt < ntiles) {
+                    const int64_t nr = min((int64_t)128, prm.P - nt * 128);
+                    const float* nsrc = prm.B + nt * 128 * prm.nB;
+                    const uint32_t bytes = (uint32_t)(nr * prm.nB * 4) & ~15u;
+                    if ((reinterpret_cast<uintptr_t>(nsrc) & 15) == 0 && bytes > 0)
+                        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(nsrc), "r"(bytes) : "memory");
                 }
             }
         }
@@ -330,25 +387,37 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_mlp_tc(const __grid_constant
             const int r = quarter * 32 + lane;
             if (!last) {
                 const int Knext = prm.L[l + 1].Kpad;
-                for (int c0 = half * 32; c0 < Knext; c0 += 64) {
-                    float v[32];
-                    tmem_ld32(trow + (uint32_t)c0, v);
-#pragma unroll
-                    for (int i = 0; i < 32; ++i) {
-                        const int c = c0 + i;
-                        float x = (c < L.N) ? v[i] + __ldg(L.bias + c) : 0.f;
-                        if (L.act) x = x > 0.f ? x : prm.slope * x;
-                        v[i] = x;
-                    }
+                // this warp's 32-column chunks c0 = half*32 + 64 j; the TMEM read of
+                // chunk j+1 is in flight while chunk j is converted
+                auto store_chunk = [&](const uint32_t (&rr)[32], int c0) {
+                    float x[32];
+                    bias_act32(rr, x, c0, L, prm.slope);
                     unsigned char* blk = sH + (c0 / kKBlk) * (128 * 128);
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
                         uint4 w4;
-                        w4.x = pack_bf16(v[8 * q + 0], v[8 * q + 1]);
-                        w4.y = pack_bf16(v[8 * q + 2], v[8 * q + 3]);
-                        w4.z = pack_bf16(v[8 * q + 4], v[8 * q + 5]);
-                        w4.w = pack_bf16(v[8 * q + 6], v[8 * q + 7]);
+                        w4.x = pack_bf16(x[8 * q + 0], x[8 * q + 1]);
+                        w4.y = pack_bf16(x[8 * q + 2], x[8 * q + 3]);
+                        w4.z = pack_bf16(x[8 * q + 4], x[8 * q + 5]);
+                        w4.w = pack_bf16(x[8 * q + 6], x[8 * q + 7]);
                         *reinterpret_cast<uint4*>(blk + swz(r, c0 % kKBlk + 8 * q)) = w4;
+                    }
+                };
+                const int nch = (Knext - half * 32 + 63) / 64;
+                uint32_t ra[32], rb[32];
+                if (nch > 0) {
+                    tmem_issue32(trow + (uint32_t)(half * 32), ra);
+                    tmem_wait(ra);
+                }
+                for (int j = 0; j < nch; j += 2) {
+                    const int c0 = half * 32 + 64 * j;
+                    if (j + 1 < nch) tmem_issue32(trow + (uint32_t)(c0 + 64), rb);
+                    store_chunk(ra, c0);
+                    if (j + 1 < nch) {
+                        tmem_wait(rb);
+                        if (j + 2 < nch) tmem_issue32(trow + (uint32_t)(c0 + 128), ra);
+                        store_chunk(rb, c0 + 64);
+                        if (j + 2 < nch) tmem_wait(ra);
                     }
                 }
                 fence_proxy_async();
@@ -362,23 +431,18 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_mlp_tc(const __grid_constant
                 const int ldc = (NE + 31) & ~31;
                 const int ldo = ldc + 8;
                 for (int c0 = half * 32; c0 < ldc; c0 += 64) {
-                    float v[32];
-                    tmem_ld32(trow + (uint32_t)c0, v);
+                    uint32_t rr[32];
+                    tmem_issue32(trow + (uint32_t)c0, rr);
+                    tmem_wait(rr);
+                    float x[32];
+                    bias_act32(rr, x, c0, L, prm.slope);
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
-                        float x[8];
-#pragma unroll
-                        for (int i = 0; i < 8; ++i) {
-                            const int c = c0 + 8 * q + i;
-                            float t = (c < NE) ? v[8 * q + i] + __ldg(L.bias + c) : 0.f;
-                            if (L.act) t = t > 0.f ? t : prm.slope * t;
-                            x[i] = t;
-                        }
                         uint4 w4;
-                        w4.x = pack_bf16(x[0], x[1]);
-                        w4.y = pack_bf16(x[2], x[3]);
-                        w4.z = pack_bf16(x[4], x[5]);
-                        w4.w = pack_bf16(x[6], x[7]);
+                        w4.x = pack_bf16(x[8 * q + 0], x[8 * q + 1]);
+                        w4.y = pack_bf16(x[8 * q + 2], x[8 * q + 3]);
+                        w4.z = pack_bf16(x[8 * q + 4], x[8 * q + 5]);
+                        w4.w = pack_bf16(x[8 * q + 6], x[8 * q + 7]);
                         *reinterpret_cast<uint4*>(so + r * ldo + c0 + 8 * q) = w4;
                     }
                 }
