@@ -1,7 +1,10 @@
 // integrate.cu -- the LDOS integrals of paper Sec. "Observable calculation":
 //   D(e_xi)  = dV sum_r LDOS(r, xi)                       (Eq. DOS.from.ldos)
 //   N(mu)    = sum_xi w0_xi(mu) D_xi                      (Eq. NumberElectrons_from_DOS)
-//   e_F      : root of N(mu) - N_e by FP64 bisection
+//   e_F      : root of N(mu) - N_e by FP64 bisection, run "wide": each round
+//              evaluates, on one SM each, the 127 midpoints that the next 7
+//              bisection steps could visit, then every block replays the 7
+//              decisions, so the iterates are those of plain bisection
 //   E_b      = sum_xi w1_xi(e_F) D_xi                      (Eq. band.energy)
 //   n(r)     = sum_xi w0_xi(e_F) LDOS(r, xi)              (Eq. density.from.ldos)
 // with w_n,xi(mu) = int hat_xi(e) e^n f((e - mu)/kT) de the exact weights of
@@ -22,6 +25,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -47,8 +51,17 @@ __device__ __forceinline__ double horner(const double* c, double u) {
     return s * u;
 }
 
-// antiderivatives of y^j f(y), j = 0, 1, 2, valid for y >= 0
+// antiderivatives of y^j f(y), j = 0, 1, 2, valid for y >= 0.  Beyond y = 40
+// the leading terms of L = e^-y - e^-2y/2 + ..., Li_s(-e^-y) = -e^-y + ... are
+// exact to a relative e^-40 (below FP64 rounding), so the series are skipped.
 __device__ __forceinline__ void hfun(double y, double& h0, double& h1, double& h2) {
+    if (y > 40.0) {
+        const double e = exp(-y);
+        h0 = -e;
+        h1 = -(y + 1.0) * e;
+        h2 = -((y + 2.0) * y + 2.0) * e;
+        return;
+    }
     const double L = log1p(exp(-y));
     const double u = -L;
     const double li2 = horner(c_li2, u), li3 = horner(c_li3, u);
@@ -59,7 +72,8 @@ __device__ __forceinline__ void hfun(double y, double& h0, double& h1, double& h
 
 // M_k = int_a^b (e - a)^k f((e - mu)/kT) de, k = 0, 1, 2
 __device__ void interval_moments(double a, double b, double mu, double kT, double& M0, double& M1, double& M2) {
-    const double xa = (a - mu) / kT, xb = (b - mu) / kT;
+    const double ikT = 1.0 / kT;
+    const double xa = (a - mu) * ikT, xb = (b - mu) * ikT;
     double s0 = 0.0, s1 = 0.0, s2 = 0.0;  // int (x - xa)^k f(x) dx over [xa, xb]
     // part with x >= 0: direct antiderivatives, (x - xa)^k expanded in x
     const double p0 = fmax(xa, 0.0);
@@ -78,7 +92,7 @@ __device__ void interval_moments(double a, double b, double mu, double kT, doubl
         const double t = x1 - xa;
         s0 += t;
         s1 += t * t / 2.0;
-        s2 += t * t * t / 3.0;
+        s2 += t * t * t * (1.0 / 3.0);
         double a0, a1, a2, b0, b1, b2;
         hfun(-x1, a0, a1, a2);
         hfun(-xa, b0, b1, b2);
@@ -111,76 +125,179 @@ __device__ double block_sum(double v, double* sred) {
 
 // N(mu) with D held in shared memory
 __device__ double electron_count(const double* sD, int nE, double e0, double de, double mu, double kT, double* sred) {
+    const double ide = 1.0 / de;
     double part = 0.0;
     for (int i = threadIdx.x; i < nE - 1; i += blockDim.x) {
         const double a = e0 + i * de, b = e0 + (i + 1) * de;
         double M0, M1, M2;
         interval_moments(a, b, mu, kT, M0, M1, M2);
-        part += (M0 - M1 / de) * sD[i] + (M1 / de) * sD[i + 1];
+        const double m1 = M1 * ide;
+        part += (M0 - m1) * sD[i] + m1 * sD[i + 1];
     }
     return block_sum(part, sred);
 }
 
-// scal: [0] e_F, [1] E_b, [2] status (0 ok, 1 no bracket), [3] N(e_F), [4] iterations
-__global__ void __launch_bounds__(kFermiThreads) k_fermi(const double* __restrict__ dos_sum, int nE, double dV, double e0,
-                                                         double de, double kT, double Ne, double tol, int max_iter,
-                                                         double* __restrict__ D, double* __restrict__ w0d,
-                                                         float* __restrict__ w0f, double* __restrict__ scal) {
+// ---- e_F by wide bisection --------------------------------------------------
+//
+// Bisection on [lo, hi] visits, in its next 7 steps, 7 of the 127 midpoints of
+// the complete binary tree of halvings below [lo, hi] (node k in heap order,
+// children 2k+1 = left half, 2k+2 = right half).  A round evaluates
+// N(mu) - N_e at all 127 nodes, one block each, with the same block size and
+// reduction order as a single evaluation, and the next kernel replays the 7
+// decisions: the brackets, midpoints and iteration count are bit for bit those
+// of the one-step-at-a-time loop.  fstate holds two slots of the bracket state
+// (lo, hi, f(lo), iterations, status, done, exact) and two rows of node values,
+// each written by one round and read by the next.
+constexpr int kWideDepth = 7;
+constexpr int kWideNodes = (1 << kWideDepth) - 1;
+constexpr int kFsSlot = 8;
+constexpr int kFsInit = 2 * kFsSlot;        // f(lo0), f(hi0)
+constexpr int kFsNodes = kFsInit + 8;       // 2 rows of 128 node values
+constexpr int kFermiStateDoubles = kFsNodes + 2 * 128;
+
+struct Bracket {
+    double lo, hi, flo;
+    int it, status;
+    bool done, exact;
+};
+
+__device__ __forceinline__ void load_bracket(const double* p, Bracket& b) {
+    b.lo = p[0];
+    b.hi = p[1];
+    b.flo = p[2];
+    b.it = (int)p[3];
+    b.status = (int)p[4];
+    b.done = p[5] != 0.0;
+    b.exact = p[6] != 0.0;
+}
+
+__device__ __forceinline__ void store_bracket(double* p, const Bracket& b) {
+    p[0] = b.lo;
+    p[1] = b.hi;
+    p[2] = b.flo;
+    p[3] = (double)b.it;
+    p[4] = (double)b.status;
+    p[5] = b.done ? 1.0 : 0.0;
+    p[6] = b.exact ? 1.0 : 0.0;
+}
+
+// bracket at the start of the bisection, from f at both ends
+__device__ Bracket initial_bracket(double lo, double hi, double flo, double fhi) {
+    Bracket b{lo, hi, flo, 0, 0, false, false};
+    if (flo == 0.0) {
+        b.hi = lo;
+        b.exact = b.done = true;
+    } else if (fhi == 0.0) {
+        b.lo = hi;
+        b.exact = b.done = true;
+    } else if ((flo > 0.0) == (fhi > 0.0)) {
+        b.status = 1;
+        b.done = true;
+    }
+    return b;
+}
+
+// up to kWideDepth bisection steps with the node values fm of the tree below b
+__device__ void replay(Bracket& b, const double* fm, double tol, int max_iter) {
+    int k = 0;
+    for (int step = 0; step < kWideDepth && !b.done; ++step) {
+        if (b.it >= max_iter || b.hi - b.lo < tol) {
+            b.done = true;
+            break;
+        }
+        const double mid = 0.5 * (b.lo + b.hi);
+        const double f = fm[k];
+        if (f == 0.0) {
+            b.lo = b.hi = mid;
+            b.exact = b.done = true;
+            break;
+        }
+        if ((f > 0.0) == (b.flo > 0.0)) {
+            b.lo = mid;
+            b.flo = f;
+            k = 2 * k + 2;
+        } else {
+            b.hi = mid;
+            k = 2 * k + 1;
+        }
+        ++b.it;
+    }
+}
+
+// midpoint of tree node k below [lo, hi], halving along its path from the root
+__device__ double node_mid(double lo, double hi, int k) {
+    int path[kWideDepth];
+    int d = 0;
+    while (k > 0) {
+        path[d++] = k;
+        k = (k - 1) / 2;
+    }
+    for (int i = d - 1; i >= 0; --i) {
+        const double mid = 0.5 * (lo + hi);
+        if ((path[i] & 1) == 0) lo = mid;  // right child
+        else hi = mid;                     // left child
+    }
+    return 0.5 * (lo + hi);
+}
+
+__device__ __forceinline__ void stage_D(const double* __restrict__ D, int nE, double* sD) {
+    for (int i = threadIdx.x; i < nE; i += blockDim.x) sD[i] = D[i];
+    __syncthreads();
+}
+
+// D = dV * dos_sum; f at the initial bracket ends (block 0: lo, block 1: hi)
+__global__ void __launch_bounds__(kFermiThreads) k_fermi_init(const double* __restrict__ dos_sum, int nE, double dV,
+                                                              double e0, double de, double kT, double Ne,
+                                                              double* __restrict__ D, double* __restrict__ fs) {
     extern __shared__ double sD[];
     __shared__ double sred[33];
-    __shared__ double sb[3];  // lo, hi, flo
-    __shared__ int sflag;
     for (int i = threadIdx.x; i < nE; i += blockDim.x) {
         sD[i] = dV * dos_sum[i];
-        D[i] = sD[i];
+        if (blockIdx.x == 0) D[i] = sD[i];
     }
     __syncthreads();
-    double lo = e0 - 20.0 * kT, hi = e0 + (nE - 1) * de + 20.0 * kT;
-    const double flo = electron_count(sD, nE, e0, de, lo, kT, sred) - Ne;
-    const double fhi = electron_count(sD, nE, e0, de, hi, kT, sred) - Ne;
-    int status = 0, it = 0;
-    double eF;
-    if (flo == 0.0) {
-        eF = lo;
-    } else if (fhi == 0.0) {
-        eF = hi;
-    } else if ((flo > 0.0) == (fhi > 0.0)) {
-        status = 1;
-        eF = 0.5 * (lo + hi);
-    } else {
-        if (threadIdx.x == 0) {
-            sb[0] = lo;
-            sb[1] = hi;
-            sb[2] = flo;
-        }
-        __syncthreads();
-        bool exact = false;
-        for (it = 0; it < max_iter; ++it) {
-            lo = sb[0];
-            hi = sb[1];
-            if (hi - lo < tol) break;
-            const double mid = 0.5 * (lo + hi);
-            const double fm = electron_count(sD, nE, e0, de, mid, kT, sred) - Ne;
-            if (threadIdx.x == 0) {
-                sflag = 0;
-                if (fm == 0.0) {
-                    sb[0] = sb[1] = mid;
-                    sflag = 1;
-                } else if ((fm > 0.0) == (sb[2] > 0.0)) {
-                    sb[0] = mid;
-                    sb[2] = fm;
-                } else {
-                    sb[1] = mid;
-                }
-            }
-            __syncthreads();
-            if (sflag) {
-                exact = true;
-                break;
-            }
-        }
-        eF = exact ? sb[0] : 0.5 * (sb[0] + sb[1]);
-    }
+    const double mu = blockIdx.x == 0 ? e0 - 20.0 * kT : e0 + (nE - 1) * de + 20.0 * kT;
+    const double f = electron_count(sD, nE, e0, de, mu, kT, sred) - Ne;
+    if (threadIdx.x == 0) fs[kFsInit + blockIdx.x] = f;
+}
+
+// bracket at the start of round r (r = 0: from the initial ends)
+__device__ Bracket round_start(const double* fs, int r, double e0, double de, double kT, int nE, double tol,
+                               int max_iter) {
+    if (r == 0)
+        return initial_bracket(e0 - 20.0 * kT, e0 + (nE - 1) * de + 20.0 * kT, fs[kFsInit], fs[kFsInit + 1]);
+    Bracket b;
+    load_bracket(fs + ((r - 1) & 1) * kFsSlot, b);
+    replay(b, fs + kFsNodes + ((r - 1) & 1) * 128, tol, max_iter);
+    return b;
+}
+
+__global__ void __launch_bounds__(kFermiThreads) k_fermi_round(const double* __restrict__ D, int nE, double e0, double de,
+                                                               double kT, double Ne, double tol, int max_iter,
+                                                               double* __restrict__ fs, int r) {
+    extern __shared__ double sD[];
+    __shared__ double sred[33];
+    const Bracket b = round_start(fs, r, e0, de, kT, nE, tol, max_iter);
+    if (blockIdx.x == 0 && threadIdx.x == 0) store_bracket(fs + (r & 1) * kFsSlot, b);
+    if (b.done) return;
+    stage_D(D, nE, sD);
+    const double mu = node_mid(b.lo, b.hi, blockIdx.x);
+    const double f = electron_count(sD, nE, e0, de, mu, kT, sred) - Ne;
+    if (threadIdx.x == 0) fs[kFsNodes + (r & 1) * 128 + blockIdx.x] = f;
+}
+
+// scal: [0] e_F, [1] E_b, [2] status (0 ok, 1 no bracket), [3] N(e_F), [4] iterations
+__global__ void __launch_bounds__(kFermiThreads) k_fermi_final(const double* __restrict__ Dg, int nE, double e0,
+                                                               double de, double kT, double tol, int max_iter,
+                                                               const double* __restrict__ fs, int rounds,
+                                                               double* __restrict__ w0d, float* __restrict__ w0f,
+                                                               double* __restrict__ scal) {
+    extern __shared__ double sD[];
+    __shared__ double sred[33];
+    const Bracket b = round_start(fs, rounds, e0, de, kT, nE, tol, max_iter);
+    stage_D(Dg, nE, sD);
+    const double eF = b.exact ? b.lo : 0.5 * (b.lo + b.hi);
+    const int status = b.status, it = b.it;
     // weights at e_F, the band energy and the electron count
     double pn = 0.0, pe = 0.0;
     for (int x = threadIdx.x; x < nE; x += blockDim.x) {
@@ -343,6 +460,26 @@ __global__ void k_sum_vec(const double* __restrict__ part, int n, double* __rest
     }
 }
 
+constexpr double kFermiTol = 1e-12;
+constexpr int kFermiMaxIter = 200;
+
+// init, enough rounds of 7 steps to shrink the bracket below the tolerance, final
+void launch_fermi(const double* dos_sum, int nE, double dV, const mala_energy_grid* eg, double* D, double* w0d,
+                  float* w0f, double* scal, double* fstate, cudaStream_t st) {
+    const size_t sm = sizeof(double) * nE;
+    const double width = (nE - 1) * eg->de_eV + 40.0 * eg->kT_eV;
+    int steps = (int)std::ceil(std::log2(std::max(width / kFermiTol, 1.0))) + 2;
+    steps = std::min(steps, kFermiMaxIter);
+    const int rounds = (steps + kWideDepth - 1) / kWideDepth;
+    k_fermi_init<<<2, kFermiThreads, sm, st>>>(dos_sum, nE, dV, eg->e0_eV, eg->de_eV, eg->kT_eV, eg->n_electrons, D,
+                                               fstate);
+    for (int r = 0; r < rounds; ++r)
+        k_fermi_round<<<kWideNodes, kFermiThreads, sm, st>>>(D, nE, eg->e0_eV, eg->de_eV, eg->kT_eV, eg->n_electrons,
+                                                             kFermiTol, kFermiMaxIter, fstate, r);
+    k_fermi_final<<<1, kFermiThreads, sm, st>>>(D, nE, eg->e0_eV, eg->de_eV, eg->kT_eV, kFermiTol, kFermiMaxIter,
+                                                fstate, rounds, w0d, w0f, scal);
+}
+
 // Bernoulli numbers B_0..B_n (B_1 = -1/2) from sum_{k=0}^{m} C(m+1, k) B_k = 0
 std::vector<double> bernoulli(int n) {
     std::vector<double> B(n + 1, 0.0);
@@ -404,7 +541,7 @@ int integrate(Ctx* c, const void* ldos, int64_t P, double volume, const mala_ene
     const int dens_blocks = (int)std::min<int64_t>(std::max<int64_t>(1, (P + kDensWarps - 1) / kDensWarps),
                                                    (int64_t)c->num_sms * 16);
     const size_t n_part = std::max<size_t>((size_t)ntile * nE, (size_t)dens_blocks);
-    const size_t doubles = 3 * (size_t)nE + (nE + 1) / 2 + 16 + n_part;
+    const size_t doubles = 3 * (size_t)nE + (nE + 1) / 2 + 16 + kFermiStateDoubles + n_part;
     MALA_TRY(c->ws_red.reserve(c, sizeof(double) * doubles));
     double* dsum = c->ws_red.as<double>();
     double* D = dsum + nE;
@@ -412,7 +549,8 @@ int integrate(Ctx* c, const void* ldos, int64_t P, double volume, const mala_ene
     float* w0f = reinterpret_cast<float*>(w0d + nE);
     double* scal = w0d + nE + (nE + 1) / 2;
     double* nsum = scal + 8;
-    double* part = scal + 16;
+    double* fstate = scal + 16;
+    double* part = fstate + kFermiStateDoubles;
     const bool mixed = prec == MALA_MIXED;
     if (!dos_sum) {
         if (P > 0) {
@@ -431,9 +569,7 @@ int integrate(Ctx* c, const void* ldos, int64_t P, double volume, const mala_ene
         dos_sum = dsum;
     }
     const double dV = volume / (double)(P > 0 ? P : 1);
-    MALA_PROF(c, "k_fermi", st,
-              (k_fermi<<<1, kFermiThreads, sizeof(double) * nE, st>>>(dos_sum, nE, dV, eg->e0_eV, eg->de_eV, eg->kT_eV,
-                                                                      eg->n_electrons, 1e-12, 200, D, w0d, w0f, scal)));
+    MALA_PROF(c, "k_fermi", st, launch_fermi(dos_sum, nE, dV, eg, D, w0d, w0f, scal, fstate, st));
     if (P > 0 && density) {
         if (mixed)
             MALA_PROF(c, "k_density", st,
@@ -518,12 +654,12 @@ int integrate_noalloc(Ctx* c, const void* ldos, int64_t P, double volume, const 
     const int dens_blocks = (int)std::min<int64_t>(std::max<int64_t>(1, (P + kDensWarps - 1) / kDensWarps),
                                                    (int64_t)c->num_sms * 16);
     const size_t n_part = std::max<size_t>(dos_sum ? 0 : (size_t)ntile * nE, (size_t)dens_blocks);
-    const size_t need = 3 * (size_t)nE + (nE + 1) / 2 + 16 + n_part;
+    const size_t need = 3 * (size_t)nE + (nE + 1) / 2 + 16 + kFermiStateDoubles + n_part;
     if (need > kStaticScratchDoubles)
         return fail(MALA_ERR_UNSUPPORTED,
                     "mala_integrate_noalloc: %zu scratch doubles needed, the static array holds %zu "
                     "(ceil(P/128) * n_E must stay below about %zu when dos_sum_dev is NULL)",
-                    need, kStaticScratchDoubles, kStaticScratchDoubles - 3 * (size_t)nE - nE / 2 - 16);
+                    need, kStaticScratchDoubles, kStaticScratchDoubles - 3 * (size_t)nE - nE / 2 - 16 - kFermiStateDoubles);
     // the same layout as the workspace path; every buffer is rewritten before it is read
     double* dsum = scratch;
     double* D = dsum + nE;
@@ -531,7 +667,8 @@ int integrate_noalloc(Ctx* c, const void* ldos, int64_t P, double volume, const 
     float* w0f = reinterpret_cast<float*>(w0d + nE);
     double* scal = w0d + nE + (nE + 1) / 2;
     double* nsum = scal + 8;
-    double* part = scal + 16;
+    double* fstate = scal + 16;
+    double* part = fstate + kFermiStateDoubles;
     const bool mixed = prec == MALA_MIXED;
     if (!dos_sum) {
         if (P > 0) {
@@ -547,8 +684,7 @@ int integrate_noalloc(Ctx* c, const void* ldos, int64_t P, double volume, const 
         dos_sum = dsum;
     }
     const double dV = volume / (double)(P > 0 ? P : 1);
-    k_fermi<<<1, kFermiThreads, sizeof(double) * nE, st>>>(dos_sum, nE, dV, eg->e0_eV, eg->de_eV, eg->kT_eV,
-                                                           eg->n_electrons, 1e-12, 200, D, w0d, w0f, scal);
+    launch_fermi(dos_sum, nE, dV, eg, D, w0d, w0f, scal, fstate, st);
     if (P > 0 && density) {
         if (mixed)
             k_density_bf16<<<dens_blocks, kDensWarps * 32, 0, st>>>(static_cast<const __nv_bfloat16*>(ldos), P, nE, w0f,

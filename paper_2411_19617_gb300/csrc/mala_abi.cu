@@ -114,7 +114,8 @@ static int run_descriptors(Ctx* c, const mala_snapshot* snap, const mala_bispect
         int64_t chunk = (int64_t)(chunk_budget / per_tile);
         if (chunk < 1) chunk = 1;
         if (chunk > g.n_tiles) chunk = g.n_tiles;
-        MALA_TRY(c->ws_u.reserve(c, (size_t)chunk * nh * 32 * 2 * sizeof(T)));
+        // FP32 keeps tiles in pairs: room for an even number of tiles
+        MALA_TRY(c->ws_u.reserve(c, (size_t)((chunk + 1) & ~int64_t(1)) * nh * 32 * 2 * sizeof(T)));
         MALA_TRY(c->ws_nbr_ab.reserve(c, (size_t)chunk * kmax * 32 * 4 * sizeof(T)));
         MALA_TRY(c->ws_nbr_c.reserve(c, (size_t)chunk * kmax * 32 * sizeof(T)));
         MALA_TRY(c->ws_nbr_cnt.reserve(c, (size_t)chunk * 32 * sizeof(int)));
@@ -149,7 +150,9 @@ static int run_descriptors(Ctx* c, const mala_snapshot* snap, const mala_bispect
         MALA_CUDA_TRY(cudaStreamSynchronize(st));
         if (c->host_ints[1]) return fail(MALA_ERR_INVALID_ARG, "species index outside 0..n_species-1");
         if (c->host_ints[2]) {
+            const int code = c->host_ints[2];
             cudaMemsetAsync(c->tables.err_d, 0, sizeof(int), st);
+            if (code == 2) return fail(MALA_ERR_TIMEOUT, "compute_zi/bi: a copy into shared memory did not complete in time");
             return fail(MALA_ERR_UNSUPPORTED, "a bispectrum partial sum exceeded 1e9 (outside the fixed-point range)");
         }
         const int maxcnt = c->host_ints[0];

@@ -20,7 +20,9 @@
 // seed, and accumulates c_k * coefficient with compensated (Kahan) summation.
 // The normalisation N and the self term are applied once at the end.  Output:
 // the half set of u (rows ma < J/2, plus the middle row's columns <= J/2 for
-// even J) in [tile][element][lane] layout.
+// even J).  FP64: [tile][element][lane] (re, im).  FP32: tiles in pairs,
+// [pair][element][lane] (re A, re B, im A, im B) with A the even tile of the
+// pair and B the odd one, the layout compute_zi/bi works in.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -136,10 +138,24 @@ __device__ __forceinline__ void load_nbr(const typename AB4<T>::type* __restrict
     }
 }
 
+// element `slot` of the lane's point; uo is the tile's (FP64) or the tile
+// pair's (FP32) block, h the tile's half of the pair
+template <class T>
+__device__ __forceinline__ void store_u(typename C2<T>::type* __restrict__ uo, int h, int slot, int lane,
+                                        typename C2<T>::type o) {
+    if constexpr (sizeof(T) == 8) {
+        uo[(size_t)slot * 32 + lane] = o;
+    } else {
+        float* q = reinterpret_cast<float*>(uo) + ((size_t)slot * 32 + lane) * 4 + h;
+        q[0] = o.x;
+        q[2] = o.y;
+    }
+}
+
 template <class T, int TJ, int MB, int L0, int L1>
 __device__ __forceinline__ void ui_segment(const typename AB4<T>::type* __restrict__ ab_t,
                                            const T* __restrict__ cw_t, int cnt, int kwarp, int lane, T wself,
-                                           bool store, typename C2<T>::type* __restrict__ uo) {
+                                           bool store, typename C2<T>::type* __restrict__ uo, int h) {
     constexpr int NE = seg_offset(MB, L0, L1 + 1);
     T sr[NE], si[NE], cr[NE], ci[NE];
 #pragma unroll
@@ -205,7 +221,7 @@ __device__ __forceinline__ void ui_segment(const typename AB4<T>::type* __restri
                     o.x = sg * vr_;
                     o.y = -sg * vi_;
                 }
-                uo[(size_t)slot * 32 + lane] = o;
+                store_u<T>(uo, h, slot, lane, o);
             }
         }
     }
@@ -215,12 +231,12 @@ __device__ __forceinline__ void ui_segment(const typename AB4<T>::type* __restri
 // fetches one segment's code at a time.
 template <class T, int TJ, int I>
 __device__ __forceinline__ void run_segments(const typename AB4<T>::type* ab_t, const T* cw_t, int cnt, int kwarp,
-                                             int lane, T wself, bool store, typename C2<T>::type* uo) {
+                                             int lane, T wself, bool store, typename C2<T>::type* uo, int h) {
     if constexpr (I < Plan<T, TJ>::value.n) {
         constexpr Seg sg = Plan<T, TJ>::value.s[I];
-        ui_segment<T, TJ, sg.mb, sg.l0, sg.l1>(ab_t, cw_t, cnt, kwarp, lane, wself, store, uo);
+        ui_segment<T, TJ, sg.mb, sg.l0, sg.l1>(ab_t, cw_t, cnt, kwarp, lane, wself, store, uo, h);
         __syncthreads();
-        run_segments<T, TJ, I + 1>(ab_t, cw_t, cnt, kwarp, lane, wself, store, uo);
+        run_segments<T, TJ, I + 1>(ab_t, cw_t, cnt, kwarp, lane, wself, store, uo, h);
     }
 }
 
@@ -240,8 +256,9 @@ __global__ void __launch_bounds__(UiWarps<T>::value * 32, 1)
     const int kw = __reduce_max_sync(0xffffffffu, n);
     const auto* ab_t = ab + (size_t)tls * kmax * 32;
     const T* cw_t = cw + (size_t)tls * kmax * 32;
-    auto* uo = u + (size_t)tls * n_half(TJ) * 32;
-    run_segments<T, TJ, 0>(ab_t, cw_t, n, kw, lane, wself, live, uo);
+    // FP64: one block per tile; FP32: one block of two float2 per element and lane per tile pair
+    auto* uo = (sizeof(T) == 8) ? u + (size_t)tls * n_half(TJ) * 32 : u + (size_t)(tls >> 1) * n_half(TJ) * 32 * 2;
+    run_segments<T, TJ, 0>(ab_t, cw_t, n, kw, lane, wself, live, uo, (int)(tls & 1));
 }
 
 // half set -> full (J+1)^2 blocks per point, point-major (for tests / the ABI)
@@ -268,8 +285,17 @@ __global__ void k_u_expand(int tj, const typename C2<T>::type* __restrict__ uh, 
         const int ma = r / (J + 1), mb = r % (J + 1);
         bool direct = (2 * ma < J) || (2 * ma == J && 2 * mb <= J);
         int sma = direct ? ma : J - ma, smb = direct ? mb : J - mb;
-        const auto v = uh[((size_t)tl * nh + hoff(J) + sma * (J + 1) + smb) * 32 + lane];
-        T re = v.x, im = v.y;
+        const int slot = hoff(J) + sma * (J + 1) + smb;
+        T re, im;
+        if constexpr (sizeof(T) == 8) {
+            const auto v = uh[((size_t)tl * nh + slot) * 32 + lane];
+            re = v.x;
+            im = v.y;
+        } else {
+            const float* q = reinterpret_cast<const float*>(uh) + (((size_t)(tl >> 1) * nh + slot) * 32 + lane) * 4 + (tl & 1);
+            re = q[0];
+            im = q[2];
+        }
         if (!direct) {
             const T sg = ((sma - smb) & 1) ? T(-1) : T(1);
             re = sg * re;
@@ -311,6 +337,11 @@ int upload_ui_tables() {
 template <class T>
 void launch_ui(int twojmax, const NbrOut& nb, double wself, int64_t ntiles, T* u_half, cudaStream_t st) {
     if (ntiles <= 0) return;
+    if (sizeof(T) == 4 && (ntiles & 1)) {
+        // odd tile count: the B half of the last pair holds no tile; keep it finite (zero)
+        const size_t pair_floats = (size_t)n_half(twojmax) * 32 * 4;
+        cudaMemsetAsync(u_half + (size_t)(ntiles >> 1) * pair_floats, 0, pair_floats * sizeof(float), st);
+    }
     switch (twojmax) {
         case 0: launch_ui_tj<T, 0>(nb, wself, ntiles, u_half, st); break;
         case 2: launch_ui_tj<T, 2>(nb, wself, ntiles, u_half, st); break;

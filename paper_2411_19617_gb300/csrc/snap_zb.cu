@@ -187,11 +187,14 @@ template <>
 void launch_zb<float>(Ctx* c, int twojmax, const float* u_half, const SnapGeom& g, int64_t tile0, int64_t ntiles,
                       float* B, cudaStream_t st) {
     if (ntiles <= 0) return;
-    const size_t smem = sizeof(float4) * (size_t)n_half(twojmax) * 32 + sizeof(long long) * (size_t)n_triples(twojmax) * 64;
+    const size_t smem = sizeof(float4) * (size_t)n_half(twojmax) * 32 +
+                        sizeof(long long) * (size_t)n_triples(twojmax) * 64 + 2 * sizeof(uint64_t) + 64 * sizeof(long long);
     cudaFuncSetAttribute(k_zb_units, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const int k = twojmax / 2;
-    k_zb_units<<<(unsigned)((ntiles + 1) / 2), kZbUWarps * 32, smem, st>>>(
-        twojmax, reinterpret_cast<const float2*>(u_half), g, tile0, ntiles, c->tables.tri_d + c->tables.tri_off[k],
+    const int64_t npairs = (ntiles + 1) / 2;
+    const int grid = (int)std::min<int64_t>(npairs, std::max(1, c->num_sms));
+    k_zb_units<<<(unsigned)grid, kZbUWarps * 32, smem, st>>>(
+        twojmax, reinterpret_cast<const float4*>(u_half), g, tile0, ntiles, c->tables.tri_d + c->tables.tri_off[k],
         c->tables.tri_n[k], c->tables.units_d + c->tables.unit_off[k], B, c->tables.err_d);
 }
 

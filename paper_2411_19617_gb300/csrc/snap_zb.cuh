@@ -393,58 +393,128 @@ __device__ __forceinline__ float2 triple_dispatch(int id, uint32_t su, const uns
     }
 }
 
+// 64-bit fixed point (2^-32 units) -> float: the two words converted apart
+__device__ __forceinline__ float from_fixed(long long q) {
+    return (float)(int)(q >> 32) + (float)(unsigned)(q & 0xffffffffull) * 2.3283064365386963e-10f;  // 2^-32
+}
+
+__device__ __forceinline__ bool zb_wait(uint32_t bar, uint32_t phase) {
+    const long long t0 = clock64();
+    for (;;) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(bar), "r"(phase)
+            : "memory");
+        if (ok) return true;
+        if (clock64() - t0 > 2000000000LL) return false;  // about a second
+    }
+}
+
+// one tile pair's u block (global) -> shared memory, completing on `bar`
+__device__ __forceinline__ void zb_fetch(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+// Persistent: CTA b takes tile pairs b, b + gridDim.x, ...  A pair's u block
+// (128 KB at twojmax 10) comes in by one bulk copy; the next pair's block is
+// meanwhile pulled into L2, so the copy reads L2 rather than HBM.
 // tri: per triple of this twojmax, int4 (global id, first unit, unit count, output column)
 __global__ void __launch_bounds__(kZbUWarps * 32, 1)
-    k_zb_units(int tj, const float2* __restrict__ u, SnapGeom g, int64_t tile0, int64_t ntiles,
+    k_zb_units(int tj, const float4* __restrict__ u, SnapGeom g, int64_t tile0, int64_t ntiles,
                const int4* __restrict__ tri, int ntri, const unsigned short* __restrict__ units,
                float* __restrict__ B, int* __restrict__ err) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nh = n_half(tj);
     const int nB = n_triples(tj);
-    float4* su4 = reinterpret_cast<float4*>(smem_raw);
-    unsigned long long* sacc = reinterpret_cast<unsigned long long*>(smem_raw + sizeof(float4) * (size_t)nh * 32);
-    const int64_t tA = 2 * (int64_t)blockIdx.x;  // local tiles tA (points A) and tA + 1 (points B)
-    if (tA >= ntiles) return;
-    const bool hasB = tA + 1 < ntiles;
-    {
-        const float2* srcA = u + (size_t)tA * nh * 32;
-        const float2* srcB = u + (size_t)(tA + 1) * nh * 32;
-        for (int idx = threadIdx.x; idx < nh * 32; idx += blockDim.x) {
-            const float2 a = __ldg(srcA + idx);
-            const float2 b = hasB ? __ldg(srcB + idx) : make_float2(0.f, 0.f);
-            su4[idx] = make_float4(a.x, b.x, a.y, b.y);
-        }
-        for (int i = threadIdx.x; i < nB * 64; i += blockDim.x) sacc[i] = 0ull;
-    }
-    __syncthreads();
+    const uint32_t ubytes = (uint32_t)nh * 32u * 16u;
+    const uint32_t sbuf0 = (uint32_t)__cvta_generic_to_shared(smem_raw);
+    unsigned long long* sacc = reinterpret_cast<unsigned long long*>(smem_raw + (size_t)ubytes);  // [nB][64]
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sacc + (size_t)nB * 64);
+    long long* spix = reinterpret_cast<long long*>(bars + 2);  // [64] grid point of each (tile, lane), -1 if none
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t su = (uint32_t)__cvta_generic_to_shared(su4) + (uint32_t)lane * 16u;
-    bool bad = false;
-    for (int t = 0; t < ntri; ++t) {
-        const int4 d = __ldg(tri + t);  // (gid, start, count, column)
-        const int first = ((warp - d.y) % kZbUWarps + kZbUWarps) % kZbUWarps;
-        if (first >= d.z) continue;
-        const float2 acc = triple_dispatch<0, n_triples(kTJMax)>(d.x, su, units + d.y, d.z, first);
-        bad |= !(fabsf(acc.x) < kFixLimit) || !(fabsf(acc.y) < kFixLimit);
-        atomicAdd(&sacc[d.w * 64 + lane], (unsigned long long)__double2ll_rn((double)acc.x * kFixScale));
-        atomicAdd(&sacc[d.w * 64 + 32 + lane], (unsigned long long)__double2ll_rn((double)acc.y * kFixScale));
+    const int64_t npairs = (ntiles + 1) / 2;
+    const uint32_t bar0 = (uint32_t)__cvta_generic_to_shared(&bars[0]);
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    for (int i = threadIdx.x; i < nB * 64; i += blockDim.x) sacc[i] = 0ull;
+    __syncthreads();
+    uint32_t ph = 0;
+    bool bad = false, stalled = false, inflight = false;
+    for (int64_t pr = blockIdx.x; pr < npairs; pr += gridDim.x) {
+        if (threadIdx.x == 0) {
+            zb_fetch(sbuf0, u + (size_t)pr * nh * 32, ubytes, bar0);
+            inflight = true;
+            const int64_t nxt = pr + gridDim.x;
+            if (nxt < npairs)
+                asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(u + (size_t)nxt * nh * 32), "r"(ubytes)
+                             : "memory");
+        }
+        const bool got = zb_wait(bar0, ph);
+        ph ^= 1u;
+        inflight = false;
+        if (!__syncthreads_and(got)) {
+            stalled = true;
+            if (threadIdx.x == 0) inflight = !got;
+            break;
+        }
+        const uint32_t su = sbuf0 + (uint32_t)lane * 16u;
+        for (int t = 0; t < ntri; ++t) {
+            const int4 d = __ldg(tri + t);  // (gid, start, count, column)
+            const int first = ((warp - d.y) % kZbUWarps + kZbUWarps) % kZbUWarps;
+            if (first >= d.z) continue;
+            const float2 acc = triple_dispatch<0, n_triples(kTJMax)>(d.x, su, units + d.y, d.z, first);
+            bad |= !(fabsf(acc.x) < kFixLimit) || !(fabsf(acc.y) < kFixLimit);
+            atomicAdd(&sacc[d.w * 64 + lane], (unsigned long long)__double2ll_rn((double)acc.x * kFixScale));
+            atomicAdd(&sacc[d.w * 64 + 32 + lane], (unsigned long long)__double2ll_rn((double)acc.y * kFixScale));
+        }
+        __syncthreads();
+        // grid points of the pair's 64 (tile, lane) slots
+        const bool hasB = 2 * pr + 1 < ntiles;
+        if (threadIdx.x < 64) {
+            const int pl = threadIdx.x, l = pl & 31;
+            long long q = -1;
+            if (!(pl >> 5) || hasB) {
+                const int64_t tile = tile0 + 2 * pr + (pl >> 5);
+                const int tx = (int)(tile % g.tiles[0]);
+                const int ty = (int)((tile / g.tiles[0]) % g.tiles[1]);
+                const int tz = (int)(tile / ((int64_t)g.tiles[0] * g.tiles[1]));
+                const int ix = tx * kTileX + (l % kTileX);
+                const int iy = ty * kTileY + ((l / kTileX) % kTileY);
+                const int iz = tz * kTileZ + l / (kTileX * kTileY);
+                if (ix < g.grid[0] && iy < g.grid[1] && iz < g.grid[2])
+                    q = ix + (int64_t)g.grid[0] * (iy + (int64_t)g.grid[1] * iz);
+            }
+            spix[pl] = q;
+        }
+        // fixed point -> float into the (consumed) u buffer as [slot][nB | 1], accumulators reset
+        const int ldo = nB | 1;
+        float* out = reinterpret_cast<float*>(smem_raw);
+        for (int i = threadIdx.x; i < nB * 64; i += blockDim.x) {
+            const int t = i >> 6, pl = i & 63;
+            out[pl * ldo + t] = from_fixed((long long)sacc[i]);
+            sacc[i] = 0ull;
+        }
+        __syncthreads();
+        for (int pl = warp; pl < 64; pl += kZbUWarps) {
+            const long long q = spix[pl];
+            if (q < 0) continue;
+            for (int t = lane; t < nB; t += 32) B[(size_t)q * nB + t] = out[pl * ldo + t];
+        }
+        __syncthreads();
     }
     if (__any_sync(0xffffffffu, bad) && lane == 0) atomicExch(err, 1);
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < 64 * nB; idx += blockDim.x) {
-        const int pl = idx / nB, t = idx % nB;  // pl: 0..31 tile A, 32..63 tile B
-        const int l = pl & 31;
-        const int64_t tile = tile0 + tA + (pl >> 5);
-        if ((pl >> 5) && !hasB) continue;
-        const int tx = (int)(tile % g.tiles[0]);
-        const int ty = (int)((tile / g.tiles[0]) % g.tiles[1]);
-        const int tz = (int)(tile / ((int64_t)g.tiles[0] * g.tiles[1]));
-        const int ix = tx * kTileX + (l % kTileX);
-        const int iy = ty * kTileY + ((l / kTileX) % kTileY);
-        const int iz = tz * kTileZ + l / (kTileX * kTileY);
-        if (ix >= g.grid[0] || iy >= g.grid[1] || iz >= g.grid[2]) continue;
-        const int64_t p = ix + (int64_t)g.grid[0] * (iy + (int64_t)g.grid[1] * iz);
-        B[(size_t)p * nB + t] = (float)((double)(long long)sacc[t * 64 + pl] * (1.0 / kFixScale));
+    if (threadIdx.x == 0) {
+        if (stalled) atomicExch(err, 2);
+        // after a stalled wait: let the copy still in flight land before the CTA exits
+        if (inflight) zb_wait(bar0, ph ^ 1u);
     }
 }
 
