@@ -48,6 +48,10 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=16,
+                    help="requests of the serving comparison (0 skips it)")
+    ap.add_argument("--serve-max-atoms", type=int, default=512,
+                    help="atom-count cap of the serving sample (bounds the FP64 arm's time)")
     return ap.parse_args()
 
 
@@ -129,6 +133,67 @@ def setup_workload(ctx, api, wl, torch):
     return snap, bp, mlp, model, eg, ne
 
 
+def pct(v, q):
+    v = sorted(v)
+    if not v:
+        return None
+    k = min(len(v) - 1, max(0, int(np.ceil(q / 100.0 * len(v))) - 1))
+    return v[k]
+
+
+def serving_compare(ctx, api, wl, model, bp, eg, n_req, nmax):
+    """The same Poisson arrival schedule served two ways: MIXED requests through
+    mala_submit/mala_poll (continuous batching over the serving slots) and the
+    plain FP64 path one snapshot at a time (mala_predict, FP64_PLAIN).  Latency
+    is completion minus arrival, queueing included."""
+    trace = wl.serving_trace(n_req, rate_per_s=200.0, seed=5, nmin=32, nmax=nmax)
+    # a reachable electron count per request: N(mu = 0) of its own (MIXED) DOS, untimed
+    ne = []
+    for rq in trace:
+        r = ctx.predict(rq.snapshot, bp, model, eg, api.MIXED, n_electrons=0.0, raise_on_bracket=False)
+        ne.append(ctx.electron_count(r["dos"], eg, 0.0))
+    pts = [rq.snapshot.n_points for rq in trace]
+    ctx.predict(trace[0].snapshot, bp, model, eg, api.FP64_PLAIN, n_electrons=ne[0])  # warm the FP64 path
+
+    def served():
+        lat, pending, i = [], {}, 0
+        t0 = time.perf_counter()
+        while i < len(trace) or pending:
+            now = time.perf_counter() - t0
+            while i < len(trace) and trace[i].arrival_s <= now:
+                tk = ctx.submit(trace[i].snapshot, bp, model, eg, api.MIXED, n_electrons=ne[i])
+                pending[tk] = trace[i].arrival_s
+                i += 1
+            for tk in list(pending):
+                if ctx.poll(tk) is not None:
+                    lat.append(time.perf_counter() - t0 - pending.pop(tk))
+                    ctx.release(tk)
+            time.sleep(0.0002)
+        return lat, time.perf_counter() - t0
+
+    def plain():
+        lat = []
+        t0 = time.perf_counter()
+        for i, rq in enumerate(trace):
+            wait = rq.arrival_s - (time.perf_counter() - t0)
+            if wait > 0:
+                time.sleep(wait)
+            ctx.predict(rq.snapshot, bp, model, eg, api.FP64_PLAIN, n_electrons=ne[i])
+            lat.append(time.perf_counter() - t0 - rq.arrival_s)
+        return lat, time.perf_counter() - t0
+
+    def summary(lat, span):
+        return {"p50_ms": 1e3 * pct(lat, 50), "p99_ms": 1e3 * pct(lat, 99), "max_ms": 1e3 * max(lat),
+                "points_per_s": sum(pts) / span}
+
+    lm, sm = served()
+    lp, sp = plain()
+    return {"requests": len(trace), "grid_points": int(sum(pts)),
+            "trace": f"Poisson arrivals at 200/s (seed 5), Al or Be bulk at 0.2 A spacing, N log-uniform in "
+                     f"[32, {nmax}]; twojmax 10, MLP 91-400-400-250, 250 energies",
+            "served_mixed": summary(lm, sm), "plain_fp64_single": summary(lp, sp)}
+
+
 def kernel_hash(*names):
     h = hashlib.sha256()
     for n in names:
@@ -178,13 +243,15 @@ def oracle_sample(snap, bp, mlp_raw, eg, wl, n_points, nthreads):
 
 
 def sample_size(snap, bp, mlp_raw, eg, wl, target_s, nthreads):
-    """Points whose oracle run takes about target_s (fixed cost + per-point cost
-    estimated from two small samples)."""
-    t1 = oracle_sample(snap, bp, mlp_raw, eg, wl, 64, nthreads)
-    t2 = oracle_sample(snap, bp, mlp_raw, eg, wl, 512, nthreads)
-    per_point = max((t2 - t1) / 448.0, 1e-7)
-    fixed = max(t1 - 64 * per_point, 0.0)
-    return int(min(snap.n_points, max(256, (target_s - fixed) / per_point)))
+    """Points whose oracle run takes about target_s: fixed cost + per-point cost
+    from two samples, the per-point cost never taken below half the larger
+    sample's average (so timing noise cannot inflate the sample)."""
+    n1, n2 = 256, 2048
+    t1 = oracle_sample(snap, bp, mlp_raw, eg, wl, n1, nthreads)
+    t2 = oracle_sample(snap, bp, mlp_raw, eg, wl, n2, nthreads)
+    per_point = max((t2 - t1) / (n2 - n1), 0.5 * t2 / n2, 1e-9)
+    fixed = max(t1 - n1 * per_point, 0.0)
+    return int(min(snap.n_points, max(n1, (target_s - fixed) / per_point)))
 
 
 def cpu_baseline(snap, bp, mlp_raw, eg, wl, target_s):
@@ -327,6 +394,9 @@ def run_ours(args):
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
             cpu = cpu_baseline(snap, bp, wl.config(2)[2], eg, wl, args.cpu_seconds)
+        serving = None
+        if world == 1 and args.serve_requests > 0:
+            serving = serving_compare(ctx, api, wl, model, bp, eg, args.serve_requests, args.serve_max_atoms)
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -336,7 +406,8 @@ def run_ours(args):
                            "l2": "working set larger than L2 (u: 1.5 GB, neighbour records 0.9 GB, LDOS 0.36 GB)",
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-                "clocks": clk, "kernels": kernels, "fermi_eV": r["fermi"], "band_energy_eV": r["band_energy"]}
+                "clocks": clk, "kernels": kernels, "serving": serving,
+                "fermi_eV": r["fermi"], "band_energy_eV": r["band_energy"]}
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

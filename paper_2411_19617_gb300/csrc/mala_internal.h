@@ -181,6 +181,7 @@ struct SnapDev {
     int* bin_atoms = nullptr; // [n]
     int* bin_fill = nullptr;  // [n_bins]
     int* maxcnt = nullptr;    // [4] device counters (max count, overflow flags)
+    double* gcoord = nullptr; // grid coordinates (i / N_d) L_d: [grid0] | [grid1] | [grid2]
 };
 
 int stage_snapshot(Ctx* c, const mala_snapshot* snap, const mala_bispectrum_params* bp,

@@ -118,15 +118,34 @@ __global__ void k_sort_bins(int nbins, const int* __restrict__ start, int* __res
     }
 }
 
+// grid coordinates r_d(i) = (i / N_d) L_d of each axis, in the exact FP64 form
+__global__ void k_grid_coords(SnapGeom g, double* __restrict__ gc) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n0 = g.grid[0], n1 = g.grid[1], n2 = g.grid[2];
+    if (i < n0) gc[i] = grid_coord(i, n0, g.L[0]);
+    else if (i < n0 + n1) gc[i] = grid_coord(i - n0, n1, g.L[1]);
+    else if (i < n0 + n1 + n2) gc[i] = grid_coord(i - n0 - n1, n2, g.L[2]);
+}
+
+// s * L for an image shift s, equal to __dmul_rn(s, L) (exact for |s| <= 1)
+__device__ __forceinline__ double shift_mul(int s, double L) {
+    if (s == 0) return 0.0;
+    if (s == 1) return L;
+    if (s == -1) return -L;
+    return __dmul_rn((double)s, L);
+}
+
 // ---- neighbour search ------------------------------------------------------
 
 constexpr int kWarpsPerBlock = 4;
-constexpr int kCand = 256;  // candidate buffer per warp (flushed when full)
+constexpr int kCand = 128;  // candidate buffer per warp (flushed when full)
 
 struct Cand {
-    float x, y, z;  // image position relative to the tile origin (FP32)
+    double ux, uy, uz;  // image position (FP64, as the exact test forms it)
+    float x, y, z;      // the same relative to the tile origin (FP32)
     int atom;
-    int shift;      // packed (sx+512) | (sy+512) << 10 | (sz+512) << 20
+    int shift;          // packed (sx+512) | (sy+512) << 10 | (sz+512) << 20
+    int pad;
 };
 
 __device__ __forceinline__ int pack_shift(int sx, int sy, int sz) {
@@ -194,17 +213,19 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     const bool valid = ix < g.grid[0] && iy < g.grid[1] && iz < g.grid[2];
     const int64_t p = valid ? (int64_t)ix + (int64_t)g.grid[0] * ((int64_t)iy + (int64_t)g.grid[1] * iz) : -1;
 
-    // tile box (FP64) and origin
+    // tile box (FP64) and origin, from the per-axis coordinate tables
     double lo[3], hi[3], r[3];
     {
         const int i0[3] = {tx * kTileX, ty * kTileY, tz * kTileZ};
         const int ext[3] = {kTileX, kTileY, kTileZ};
         const int ii[3] = {ix, iy, iz};
+        const double* gc = sd.gcoord;
         for (int d = 0; d < 3; ++d) {
-            int last = min(i0[d] + ext[d] - 1, g.grid[d] - 1);
-            lo[d] = grid_coord(i0[d], g.grid[d], g.L[d]);
-            hi[d] = grid_coord(last, g.grid[d], g.L[d]);
-            r[d] = grid_coord(min(ii[d], g.grid[d] - 1), g.grid[d], g.L[d]);
+            const int last = min(i0[d] + ext[d] - 1, g.grid[d] - 1);
+            lo[d] = __ldg(gc + i0[d]);
+            hi[d] = __ldg(gc + last);
+            r[d] = __ldg(gc + min(ii[d], g.grid[d] - 1));
+            gc += g.grid[d];
         }
     }
     const float prx = (float)(r[0] - lo[0]), pry = (float)(r[1] - lo[1]), prz = (float)(r[2] - lo[2]);
@@ -217,9 +238,12 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 
     int ib_lo[3], ib_hi[3];
     for (int d = 0; d < 3; ++d) {
-        const double m = rcut + 1e-6;
-        int a = (int)floor((lo[d] - m) / g.bs[d]);
-        int b = (int)floor((hi[d] + m) / g.bs[d]);
+        // a superset of the bins that can hold a neighbour: the margin covers
+        // the rounding of the reciprocal against the binning's FP64 division
+        const double m = rcut + 1e-4;
+        const double ibs = 1.0 / g.bs[d];
+        int a = (int)floor((lo[d] - m) * ibs);
+        int b = (int)floor((hi[d] + m) * ibs);
         if (!g.periodic[d]) {
             a = max(a, 0);
             b = min(b, g.nb[d] - 1);
@@ -251,15 +275,9 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
             unpack_shift(cd.shift, sx, sy, sz);
             double dx = 0, dy = 0, dz = 0;
             if (valid && (in || decide64)) {
-                const double tx_ = __dmul_rn((double)sx, g.L[0]);
-                const double ty_ = __dmul_rn((double)sy, g.L[1]);
-                const double tz_ = __dmul_rn((double)sz, g.L[2]);
-                const double ux = __dadd_rn(wx[cd.atom], tx_);
-                const double uy = __dadd_rn(wy[cd.atom], ty_);
-                const double uz = __dadd_rn(wz[cd.atom], tz_);
-                dx = __dsub_rn(ux, r[0]);
-                dy = __dsub_rn(uy, r[1]);
-                dz = __dsub_rn(uz, r[2]);
+                dx = __dsub_rn(cd.ux, r[0]);
+                dy = __dsub_rn(cd.uy, r[1]);
+                dz = __dsub_rn(cd.uz, r[2]);
                 if (decide64) {
                     const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
                     in = d2 < rc2;
@@ -291,17 +309,18 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     for (int bz_ = ib_lo[2]; bz_ <= ib_hi[2]; ++bz_) {
         const int jz = ((bz_ % g.nb[2]) + g.nb[2]) % g.nb[2];
         const int sz = (bz_ - jz) / g.nb[2];
+        const double tz_ = shift_mul(sz, g.L[2]);
         for (int by_ = ib_lo[1]; by_ <= ib_hi[1]; ++by_) {
             const int jy = ((by_ % g.nb[1]) + g.nb[1]) % g.nb[1];
             const int sy = (by_ - jy) / g.nb[1];
+            const double ty_ = shift_mul(sy, g.L[1]);
             for (int bx_ = ib_lo[0]; bx_ <= ib_hi[0]; ++bx_) {
                 const int jx = ((bx_ % g.nb[0]) + g.nb[0]) % g.nb[0];
                 const int sx = (bx_ - jx) / g.nb[0];
                 const int b = jx + g.nb[0] * (jy + g.nb[1] * jz);
                 const int st = sd.bin_start[b], cnt = sd.bin_start[b + 1] - st;
-                const double tx_ = __dmul_rn((double)sx, g.L[0]);
-                const double ty_ = __dmul_rn((double)sy, g.L[1]);
-                const double tz_ = __dmul_rn((double)sz, g.L[2]);
+                if (cnt == 0) continue;
+                const double tx_ = shift_mul(sx, g.L[0]);
                 for (int q0 = 0; q0 < cnt; q0 += 32) {
                     const int q = q0 + lane;
                     bool keep = false;
@@ -311,6 +330,9 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
                         const double ux = __dadd_rn(wx[a], tx_);
                         const double uy = __dadd_rn(wy[a], ty_);
                         const double uz = __dadd_rn(wz[a], tz_);
+                        cd.ux = ux;
+                        cd.uy = uy;
+                        cd.uz = uz;
                         cd.x = (float)(ux - lo[0]);
                         cd.y = (float)(uy - lo[1]);
                         cd.z = (float)(uz - lo[2]);
@@ -379,6 +401,8 @@ int stage_snapshot(Ctx* c, const mala_snapshot* snap, const mala_bispectrum_para
     const size_t o_bfill = take(sizeof(int) * (size_t)nbins);
     const size_t o_max = take(sizeof(int) * 4);
     const size_t o_wtab = take(sizeof(double) * (size_t)ns);
+    const int ngc = g.grid[0] + g.grid[1] + g.grid[2];
+    const size_t o_gc = take(sizeof(double) * (size_t)(ngc > 0 ? ngc : 1));
     MALA_TRY(c->ws_atoms.reserve(c, off));
     char* base = c->ws_atoms.as<char>();
     double* pos_d = (double*)(base + o_pos);
@@ -392,6 +416,7 @@ int stage_snapshot(Ctx* c, const mala_snapshot* snap, const mala_bispectrum_para
     sd->bin_fill = (int*)(base + o_bfill);
     sd->maxcnt = (int*)(base + o_max);
     double* wtab = (double*)(base + o_wtab);
+    sd->gcoord = (double*)(base + o_gc);
 
     if (n > 0) {
         MALA_CUDA_TRY(cudaMemcpyAsync(pos_d, snap->pos, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st));
@@ -410,6 +435,7 @@ int stage_snapshot(Ctx* c, const mala_snapshot* snap, const mala_bispectrum_para
                                                                   sd->wsp, sd->bin_of, bcount, sd->maxcnt + 1)));
     }
     MALA_PROF(c, "k_scan_bins", st, (k_scan_bins<<<1, 1024, 0, st>>>(nbins, bcount, sd->bin_start)));
+    if (ngc > 0) MALA_PROF(c, "k_grid_coords", st, (k_grid_coords<<<(ngc + 127) / 128, 128, 0, st>>>(g, sd->gcoord)));
     if (n > 0) {
         MALA_PROF(c, "k_fill_bins", st,
                   (k_fill_bins<<<(n + 127) / 128, 128, 0, st>>>(n, sd->bin_of, sd->bin_start, sd->bin_fill,
