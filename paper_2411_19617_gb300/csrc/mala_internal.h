@@ -182,6 +182,7 @@ struct SnapDev {
     int* bin_fill = nullptr;  // [n_bins]
     int* maxcnt = nullptr;    // [4] device counters (max count, overflow flags)
     double* gcoord = nullptr; // grid coordinates (i / N_d) L_d: [grid0] | [grid1] | [grid2]
+    float* wposf = nullptr;   // [6][n] wrapped positions as float pairs: x_hi, y_hi, z_hi, x_lo, y_lo, z_lo
 };
 
 int stage_snapshot(Ctx* c, const mala_snapshot* snap, const mala_bispectrum_params* bp,

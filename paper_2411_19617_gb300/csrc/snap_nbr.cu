@@ -13,10 +13,15 @@
 //    guard band |d^2 - R_cut^2| < 1e-4 R_cut^2, and inside it the exact FP64
 //    expression ((x_a + s L) - r)^2 summed as (dx^2 + dy^2) + dz^2 with no
 //    fused multiply-add, so membership agrees bit for bit with that definition.
+//    Positions relative to the tile origin are carried as unevaluated float
+//    pairs (hi + lo, error-free sums), so the offsets fed to the FP32
+//    Cayley-Klein map are as accurate as a rounded FP64 difference without
+//    using the (slow) FP64 pipe per neighbour.
 //    Accepted neighbours are written as Cayley-Klein parameters (a, b) and the
 //    weight w_eta f_c(r) in [tile][k][lane] layout for the U-matrix kernel.
 #include <cuda_runtime.h>
 
+#include <climits>
 #include <cstdint>
 
 #include "mala_internal.h"
@@ -42,8 +47,8 @@ __device__ __forceinline__ double grid_coord(int i, int n, double L) {
 
 __global__ void k_stage_atoms(int n, const double* __restrict__ pos, const int* __restrict__ species,
                               const double* __restrict__ wsp_tab, int nspecies, SnapGeom g,
-                              double* __restrict__ wpos, float* __restrict__ wsp, int* __restrict__ bin_of,
-                              int* __restrict__ bin_count, int* __restrict__ err) {
+                              double* __restrict__ wpos, float* __restrict__ wposf, float* __restrict__ wsp,
+                              int* __restrict__ bin_of, int* __restrict__ bin_count, int* __restrict__ err) {
     int a = blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= n) return;
     int bc[3];
@@ -51,6 +56,9 @@ __global__ void k_stage_atoms(int n, const double* __restrict__ pos, const int* 
         double x = pos[3 * a + d];
         if (g.periodic[d]) x = wrap_coord(x, g.L[d]);
         wpos[(size_t)d * n + a] = x;
+        const float xh = (float)x;
+        wposf[(size_t)d * n + a] = xh;
+        wposf[(size_t)(3 + d) * n + a] = (float)(x - (double)xh);
         double q = floor(x / g.bs[d]);
         int b = (q < 0.0) ? 0 : (q >= (double)g.nb[d] ? g.nb[d] - 1 : (int)q);
         bc[d] = b;
@@ -127,6 +135,27 @@ __global__ void k_grid_coords(SnapGeom g, double* __restrict__ gc) {
     else if (i < n0 + n1 + n2) gc[i] = grid_coord(i - n0 - n1, n2, g.L[2]);
 }
 
+// error-free sum: s + e == a + b exactly (Knuth)
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// (a_hi + a_lo) + (b_hi + b_lo) as a float pair
+__device__ __forceinline__ void pair_add(float ah, float al, float bh, float bl, float& h, float& l) {
+    float s, e;
+    two_sum(ah, bh, s, e);
+    const float t = __fadd_rn(__fadd_rn(al, bl), e);
+    h = __fadd_rn(s, t);
+    l = __fsub_rn(t, __fsub_rn(h, s));
+}
+
+__device__ __forceinline__ void split_pair(double v, float& h, float& l) {
+    h = (float)v;
+    l = (float)(v - (double)h);
+}
+
 // s * L for an image shift s, equal to __dmul_rn(s, L) (exact for |s| <= 1)
 __device__ __forceinline__ double shift_mul(int s, double L) {
     if (s == 0) return 0.0;
@@ -141,11 +170,10 @@ constexpr int kWarpsPerBlock = 4;
 constexpr int kCand = 128;  // candidate buffer per warp (flushed when full)
 
 struct Cand {
-    double ux, uy, uz;  // image position (FP64, as the exact test forms it)
-    float x, y, z;      // the same relative to the tile origin (FP32)
+    float x, y, z;      // image position relative to the tile origin: high floats
+    float lx, ly, lz;   // and low floats (x + lx to about 2^-48 relative)
     int atom;
     int shift;          // packed (sx+512) | (sy+512) << 10 | (sz+512) << 20
-    int pad;
 };
 
 __device__ __forceinline__ int pack_shift(int sx, int sy, int sz) {
@@ -228,7 +256,10 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
             gc += g.grid[d];
         }
     }
-    const float prx = (float)(r[0] - lo[0]), pry = (float)(r[1] - lo[1]), prz = (float)(r[2] - lo[2]);
+    float prx, pry, prz, plx, ply, plz;  // point relative to the tile origin, float pairs
+    split_pair(r[0] - lo[0], prx, plx);
+    split_pair(r[1] - lo[1], pry, ply);
+    split_pair(r[2] - lo[2], prz, plz);
     const float bx = (float)(hi[0] - lo[0]), by = (float)(hi[1] - lo[1]), bz = (float)(hi[2] - lo[2]);
     const double rc2 = __dmul_rn(rcut, rcut);
     const float rc2f = (float)rc2;
@@ -274,10 +305,14 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
             int sx, sy, sz;
             unpack_shift(cd.shift, sx, sy, sz);
             double dx = 0, dy = 0, dz = 0;
-            if (valid && (in || decide64)) {
-                dx = __dsub_rn(cd.ux, r[0]);
-                dy = __dsub_rn(cd.uy, r[1]);
-                dz = __dsub_rn(cd.uz, r[2]);
+            // the exact FP64 offsets: inside the guard band, and for every neighbour of the FP64 path
+            if (valid && (decide64 || (in && sizeof(T) == 8))) {
+                const double ux = __dadd_rn(wx[cd.atom], shift_mul(sx, g.L[0]));
+                const double uy = __dadd_rn(wy[cd.atom], shift_mul(sy, g.L[1]));
+                const double uz = __dadd_rn(wz[cd.atom], shift_mul(sz, g.L[2]));
+                dx = __dsub_rn(ux, r[0]);
+                dy = __dsub_rn(uy, r[1]);
+                dz = __dsub_rn(uz, r[2]);
                 if (decide64) {
                     const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
                     in = d2 < rc2;
@@ -287,7 +322,22 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
                 if (count < kmax) {
                     typename AB<T>::type ab;
                     T fc;
-                    cayley_klein<T>((T)dx, (T)dy, (T)dz, inv_range, rmin0_t, rfac0_pi, ab, fc);
+                    T ex, ey, ez;
+                    if constexpr (sizeof(T) == 8) {
+                        ex = dx;
+                        ey = dy;
+                        ez = dz;
+                    } else {
+                        // (candidate - point) from the float pairs, rounded once at the end
+                        float h, l;
+                        pair_add(cd.x, cd.lx, -prx, -plx, h, l);
+                        ex = h;
+                        pair_add(cd.y, cd.ly, -pry, -ply, h, l);
+                        ey = h;
+                        pair_add(cd.z, cd.lz, -prz, -plz, h, l);
+                        ez = h;
+                    }
+                    cayley_klein<T>(ex, ey, ez, inv_range, rmin0_t, rfac0_pi, ab, fc);
                     const size_t o = ((size_t)tl * kmax + count) * 32 + lane;
                     out_ab[o] = ab;
                     out_cw[o] = (T)sd.wsp[cd.atom] * fc;
@@ -306,36 +356,44 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
         nc = 0;
     };
 
+    // image offset minus tile origin per axis, as float pairs, refreshed when the shift changes
+    const float* fxh = sd.wposf;
+    const float* fyh = sd.wposf + n;
+    const float* fzh = sd.wposf + 2 * (size_t)n;
+    const float* fxl = sd.wposf + 3 * (size_t)n;
+    const float* fyl = sd.wposf + 4 * (size_t)n;
+    const float* fzl = sd.wposf + 5 * (size_t)n;
     for (int bz_ = ib_lo[2]; bz_ <= ib_hi[2]; ++bz_) {
         const int jz = ((bz_ % g.nb[2]) + g.nb[2]) % g.nb[2];
         const int sz = (bz_ - jz) / g.nb[2];
-        const double tz_ = shift_mul(sz, g.L[2]);
+        float ozh, ozl;
+        split_pair(shift_mul(sz, g.L[2]) - lo[2], ozh, ozl);
         for (int by_ = ib_lo[1]; by_ <= ib_hi[1]; ++by_) {
             const int jy = ((by_ % g.nb[1]) + g.nb[1]) % g.nb[1];
             const int sy = (by_ - jy) / g.nb[1];
-            const double ty_ = shift_mul(sy, g.L[1]);
+            float oyh, oyl;
+            split_pair(shift_mul(sy, g.L[1]) - lo[1], oyh, oyl);
+            int sx_prev = INT_MIN;
+            float oxh = 0.f, oxl = 0.f;
             for (int bx_ = ib_lo[0]; bx_ <= ib_hi[0]; ++bx_) {
                 const int jx = ((bx_ % g.nb[0]) + g.nb[0]) % g.nb[0];
                 const int sx = (bx_ - jx) / g.nb[0];
                 const int b = jx + g.nb[0] * (jy + g.nb[1] * jz);
                 const int st = sd.bin_start[b], cnt = sd.bin_start[b + 1] - st;
                 if (cnt == 0) continue;
-                const double tx_ = shift_mul(sx, g.L[0]);
+                if (sx != sx_prev) {
+                    split_pair(shift_mul(sx, g.L[0]) - lo[0], oxh, oxl);
+                    sx_prev = sx;
+                }
                 for (int q0 = 0; q0 < cnt; q0 += 32) {
                     const int q = q0 + lane;
                     bool keep = false;
                     Cand cd;
                     if (q < cnt) {
                         const int a = sd.bin_atoms[st + q];
-                        const double ux = __dadd_rn(wx[a], tx_);
-                        const double uy = __dadd_rn(wy[a], ty_);
-                        const double uz = __dadd_rn(wz[a], tz_);
-                        cd.ux = ux;
-                        cd.uy = uy;
-                        cd.uz = uz;
-                        cd.x = (float)(ux - lo[0]);
-                        cd.y = (float)(uy - lo[1]);
-                        cd.z = (float)(uz - lo[2]);
+                        pair_add(__ldg(fxh + a), __ldg(fxl + a), oxh, oxl, cd.x, cd.lx);
+                        pair_add(__ldg(fyh + a), __ldg(fyl + a), oyh, oyl, cd.y, cd.ly);
+                        pair_add(__ldg(fzh + a), __ldg(fzl + a), ozh, ozl, cd.z, cd.lz);
                         cd.atom = a;
                         cd.shift = pack_shift(sx, sy, sz);
                         // distance from the image to the tile box
@@ -392,6 +450,7 @@ int stage_snapshot(Ctx* c, const mala_snapshot* snap, const mala_bispectrum_para
     };
     const size_t o_pos = take(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
     const size_t o_wpos = take(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
+    const size_t o_wposf = take(sizeof(float) * 6 * (size_t)(n > 0 ? n : 1));
     const size_t o_sp = take(sizeof(int) * (size_t)(n > 0 ? n : 1));
     const size_t o_wsp = take(sizeof(float) * (size_t)(n > 0 ? n : 1));
     const size_t o_binof = take(sizeof(int) * (size_t)(n > 0 ? n : 1));
@@ -407,6 +466,7 @@ int stage_snapshot(Ctx* c, const mala_snapshot* snap, const mala_bispectrum_para
     char* base = c->ws_atoms.as<char>();
     double* pos_d = (double*)(base + o_pos);
     sd->wpos = (double*)(base + o_wpos);
+    sd->wposf = (float*)(base + o_wposf);
     int* sp_d = (int*)(base + o_sp);
     sd->wsp = (float*)(base + o_wsp);
     sd->bin_of = (int*)(base + o_binof);
@@ -432,7 +492,8 @@ int stage_snapshot(Ctx* c, const mala_snapshot* snap, const mala_bispectrum_para
         MALA_PROF(c, "k_stage_atoms", st,
                   (k_stage_atoms<<<(n + 127) / 128, 128, 0, st>>>(n, pos_d, snap->species ? sp_d : nullptr,
                                                                   (bp && bp->weights) ? wtab : nullptr, ns, g, sd->wpos,
-                                                                  sd->wsp, sd->bin_of, bcount, sd->maxcnt + 1)));
+                                                                  sd->wposf, sd->wsp, sd->bin_of, bcount,
+                                                                  sd->maxcnt + 1)));
     }
     MALA_PROF(c, "k_scan_bins", st, (k_scan_bins<<<1, 1024, 0, st>>>(nbins, bcount, sd->bin_start)));
     if (ngc > 0) MALA_PROF(c, "k_grid_coords", st, (k_grid_coords<<<(ngc + 127) / 128, 128, 0, st>>>(g, sd->gcoord)));

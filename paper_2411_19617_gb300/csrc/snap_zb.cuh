@@ -221,7 +221,6 @@ __global__ void __launch_bounds__(kZbWarps * 32)
 // integer addition is associative, so B does not depend on the warp order.
 
 constexpr int kZbUWarps = 16;
-constexpr double kFixScale = 4294967296.0;  // 2^32
 constexpr float kFixLimit = 1.0e9f;          // |partial| bound that keeps 16 partials inside int64
 
 __device__ __forceinline__ float4 lds4(uint32_t addr) {
@@ -393,6 +392,22 @@ __device__ __forceinline__ float2 triple_dispatch(int id, uint32_t su, const uns
     }
 }
 
+// Float -> 64-bit fixed point (2^-32 units), rounded to nearest with ties away
+// from zero, by integer operations on the float's fields (no FP64); requires
+// |v| < kFixLimit (v * 2^32 < 2^62).
+__device__ __forceinline__ long long to_fixed(float v) {
+    const uint32_t b = __float_as_uint(v);
+    const int e = (int)((b >> 23) & 0xffu);
+    if (e == 0) return 0;  // zero, or below 2^-126
+    const unsigned long long m = (b & 0x7fffffu) | 0x800000u;
+    const int sh = e - 118;  // v * 2^32 = m * 2^(e - 150 + 32)
+    unsigned long long q;
+    if (sh >= 0) q = m << sh;
+    else if (sh > -25) q = (m + (1ull << (-sh - 1))) >> (-sh);
+    else q = 0;
+    return (b >> 31) ? -(long long)q : (long long)q;
+}
+
 // 64-bit fixed point (2^-32 units) -> float: the two words converted apart
 __device__ __forceinline__ float from_fixed(long long q) {
     return (float)(int)(q >> 32) + (float)(unsigned)(q & 0xffffffffull) * 2.3283064365386963e-10f;  // 2^-32
@@ -471,9 +486,10 @@ __global__ void __launch_bounds__(kZbUWarps * 32, 1)
             const int first = ((warp - d.y) % kZbUWarps + kZbUWarps) % kZbUWarps;
             if (first >= d.z) continue;
             const float2 acc = triple_dispatch<0, n_triples(kTJMax)>(d.x, su, units + d.y, d.z, first);
-            bad |= !(fabsf(acc.x) < kFixLimit) || !(fabsf(acc.y) < kFixLimit);
-            atomicAdd(&sacc[d.w * 64 + lane], (unsigned long long)__double2ll_rn((double)acc.x * kFixScale));
-            atomicAdd(&sacc[d.w * 64 + 32 + lane], (unsigned long long)__double2ll_rn((double)acc.y * kFixScale));
+            const bool ok = fabsf(acc.x) < kFixLimit && fabsf(acc.y) < kFixLimit;
+            bad |= !ok;
+            atomicAdd(&sacc[d.w * 64 + lane], (unsigned long long)(ok ? to_fixed(acc.x) : 0ll));
+            atomicAdd(&sacc[d.w * 64 + 32 + lane], (unsigned long long)(ok ? to_fixed(acc.y) : 0ll));
         }
         __syncthreads();
         // grid points of the pair's 64 (tile, lane) slots
