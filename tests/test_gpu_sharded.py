@@ -52,10 +52,10 @@ def test_slabs_reproduce_the_whole_grid_fp64(world):
     assert parts[0]["fermi"] == pytest.approx(whole["fermi"], abs=1e-10)
     assert parts[0]["band_energy"] == pytest.approx(whole["band_energy"], rel=1e-10)
     dens = np.concatenate([p["density"] for p in parts])
-    np.testing.assert_allclose(dens, whole["density"].cpu().numpy(), rtol=1e-10)
+    np.testing.assert_allclose(dens, whole["density"].cpu().numpy(), rtol=1e-10, atol=1e-12)
     # and the oracle
     assert parts[0]["fermi"] == pytest.approx(ref["fermi"], abs=1e-9)
     assert parts[0]["band_energy"] == pytest.approx(ref["band_energy"], rel=1e-10)
-    np.testing.assert_allclose(dens, ref["density"], rtol=1e-10)
+    np.testing.assert_allclose(dens, ref["density"], rtol=1e-10, atol=1e-12)
     local = sum(dV * float(np.sum(p["density"])) for p in parts)
     assert local == pytest.approx(ne, rel=1e-6)
