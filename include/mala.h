@@ -166,6 +166,15 @@ int mala_neighbor_lists(mala_ctx* ctx, const mala_snapshot* snap, double rcut, i
 int mala_descriptors(mala_ctx* ctx, const mala_snapshot* snap, const mala_bispectrum_params* bp,
                      void* B_dev, mala_precision precision, void* stream);
 
+/* Descriptors of n snapshots (snaps[0..n), any mix of atom counts, cells and
+ * grids, one bispectrum setting) in one sequence of launches: the snapshots'
+ * grid tiles are numbered one after another and every kernel launch walks
+ * tiles of several snapshots.  B_dev holds the snapshots' rows in order,
+ * [sum_i P_i][n_B] (P_i = the product of snaps[i].grid); each snapshot's rows
+ * are bit for bit those mala_descriptors gives for it alone. */
+int mala_descriptors_batch(mala_ctx* ctx, int32_t n, const mala_snapshot* snaps, const mala_bispectrum_params* bp,
+                           void* B_dev, mala_precision precision, void* stream);
+
 /* Expansion coefficients u^J of Eq. (SNAPExpansion) for every grid point,
  * J = 0..twojmax, device complex output u_dev[P][sum_J (J+1)^2][2] (row-major
  * [ma][mb] blocks in increasing J; float for MIXED, double for FP64_PLAIN). */
@@ -236,6 +245,21 @@ int mala_electron_count(mala_ctx* ctx, const double* dos_host, const mala_energy
 int mala_predict(mala_ctx* ctx, const mala_snapshot* snap, const mala_bispectrum_params* bp,
                  const mala_model* model, const mala_energy_grid* eg, mala_precision precision,
                  void* density_host, mala_result* result, void* stream);
+
+/* The whole path for n snapshots at once (Sec. "Observable calculation" per
+ * snapshot): descriptors of all snapshots as in mala_descriptors_batch, the
+ * network over all their points in one launch, then the integrals of each
+ * snapshot with its own energy grid / electron count egs[i].  results[i]
+ * describes snapshot i: its B, LDOS and density pointers are its rows inside
+ * the context's workspace (valid until the next call on the context), its
+ * dos points to library-owned host memory.  density_host (host [sum_i P_i],
+ * float for MIXED, double for FP64_PLAIN; may be NULL) receives n(r) of all
+ * snapshots in order.  A snapshot whose electron count has no bracket gets
+ * status MALA_ERR_FERMI_BRACKET in its result; the call returns the first
+ * failure (MALA_OK when all succeeded).  Synchronises `stream`. */
+int mala_predict_batch(mala_ctx* ctx, int32_t n, const mala_snapshot* snaps, const mala_bispectrum_params* bp,
+                       const mala_model* model, const mala_energy_grid* egs, mala_precision precision,
+                       void* density_host, mala_result* results, void* stream);
 
 /* ---- serving ------------------------------------------------------------ */
 

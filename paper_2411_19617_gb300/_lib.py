@@ -84,6 +84,11 @@ PROTOTYPES = {
                                       C.POINTER(C.c_double)]),
     "mala_predict": (C.c_int, [C.c_void_p, C.POINTER(Snapshot), C.POINTER(BispectrumParams), C.c_void_p,
                                C.POINTER(EnergyGrid), C.c_int, C.c_void_p, C.POINTER(Result), C.c_void_p]),
+    "mala_predict_batch": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(Snapshot), C.POINTER(BispectrumParams),
+                                     C.c_void_p, C.POINTER(EnergyGrid), C.c_int, C.c_void_p, C.POINTER(Result),
+                                     C.c_void_p]),
+    "mala_descriptors_batch": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(Snapshot), C.POINTER(BispectrumParams),
+                                         C.c_void_p, C.c_int, C.c_void_p]),
     "mala_submit": (C.c_int, [C.c_void_p, C.POINTER(Snapshot), C.POINTER(BispectrumParams), C.c_void_p,
                               C.POINTER(EnergyGrid), C.c_int, C.POINTER(C.c_uint64)]),
     "mala_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.POINTER(Result)]),

@@ -212,6 +212,45 @@ class Context:
                                      _stream_ptr(stream)), "mala_descriptors")
         return out
 
+    def descriptors_batch(self, snaps, bp, precision: int = MIXED, out=None, stream=None):
+        """B of several snapshots in one pass: rows of snapshot i follow those of
+        snapshot i-1 ([sum P_i][n_B] on the GPU)."""
+        torch = _torch()
+        args = [_SnapshotArgs(s) for s in snaps]
+        arr = (_lib.Snapshot * len(args))(*[a.c for a in args])
+        P = sum(int(np.prod(s.grid)) for s in snaps)
+        nB = n_descriptors(bp.twojmax)
+        dt = torch.float32 if precision == MIXED else torch.float64
+        if out is None:
+            out = torch.empty((P, nB), dtype=dt, device=torch.device("cuda", self.device))
+        b = _BParamsArgs(bp)
+        check(lib().mala_descriptors_batch(self.h, len(args), arr, C.byref(b.c), C.c_void_p(out.data_ptr()),
+                                           int(precision), _stream_ptr(stream)), "mala_descriptors_batch")
+        return out
+
+    def predict_batch(self, snaps, bp, model: "Model", egs, precision: int = MIXED, n_electrons=None,
+                      density_host=None, stream=None, raise_on_bracket: bool = True):
+        """The whole path for several snapshots at once; egs is one energy grid
+        or one per snapshot, n_electrons None or one per snapshot.  Returns one
+        result dict per snapshot (device tensors alias the context's workspace)."""
+        n = len(snaps)
+        if not isinstance(egs, (list, tuple)):
+            egs = [egs] * n
+        nes = [None] * n if n_electrons is None else list(n_electrons)
+        args = [_SnapshotArgs(s) for s in snaps]
+        arr = (_lib.Snapshot * n)(*[a.c for a in args])
+        eargs = [_EnergyGridArgs(eg, ne) for eg, ne in zip(egs, nes)]
+        earr = (_lib.EnergyGrid * n)(*[e.c for e in eargs])
+        res = (_lib.Result * n)()
+        b = _BParamsArgs(bp)
+        rc = lib().mala_predict_batch(self.h, n, arr, C.byref(b.c), model.h, earr, int(precision),
+                                      density_host.ctypes.data_as(C.c_void_p) if density_host is not None else None,
+                                      res, _stream_ptr(stream))
+        if rc != _lib.MALA_ERR_FERMI_BRACKET or raise_on_bracket:
+            check(rc, "mala_predict_batch")
+        out = [_result_dict(res[i], precision) for i in range(n)]
+        return out
+
     def expansion_coefficients(self, snap, bp, precision: int = MIXED, stream=None):
         """u[P][sum_J (J+1)^2] complex (as [..., 2] real) on the GPU."""
         torch = _torch()

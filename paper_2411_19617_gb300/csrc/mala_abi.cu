@@ -96,15 +96,43 @@ static cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s
 
 // ---- descriptor step ------------------------------------------------------
 
-// Run neighbour search + compute_ui + compute_zi/bi over the snapshot in
-// chunks of tiles.  B (device, [P][nB]) and/or u_full (device,
-// [P][n_full][2]) may be NULL.  dbg: optional neighbour-list output.
+// Run neighbour search + compute_ui + compute_zi/bi over n snapshots in
+// chunks of tiles.  The snapshots' tiles are numbered one after another, so a
+// chunk (and each launch) may hold tiles of several snapshots; B rows are the
+// snapshots' points in order (device, [sum P][nB]).  B and/or u_full (device,
+// [P][n_full][2], a lone snapshot only) may be NULL.  dbg: optional neighbour-list
+// output (a lone snapshot only).
 template <class T>
-static int run_descriptors(Ctx* c, const mala_snapshot* snap, const mala_bispectrum_params* bp, T* B, T* u_full,
-                           NbrOut* dbg, cudaStream_t st) {
-    SnapDev sd;
-    MALA_TRY(stage_snapshot(c, snap, bp, bp->rcut, &sd, st));
-    const SnapGeom& g = sd.g;
+static int run_descriptors(Ctx* c, int nsnap, const mala_snapshot* snaps, const mala_bispectrum_params* bp, T* B,
+                           T* u_full, NbrOut* dbg, cudaStream_t st) {
+    if (nsnap < 1) return fail(MALA_ERR_INVALID_ARG, "no snapshots");
+    if ((u_full || dbg) && nsnap != 1) return fail(MALA_ERR_INVALID_ARG, "u or neighbour-list output needs one snapshot");
+    // staging: one workspace region per snapshot
+    std::vector<size_t> off(nsnap + 1, 0);
+    for (int i = 0; i < nsnap; ++i) off[i + 1] = off[i] + snapshot_ws_bytes(&snaps[i], bp, bp->rcut);
+    MALA_TRY(c->ws_atoms.reserve(c, off[nsnap] + 256));
+    std::vector<BatchSnap> hb(nsnap);
+    int64_t tiles = 0, rows = 0;
+    for (int i = 0; i < nsnap; ++i) {
+        MALA_TRY(stage_snapshot_at(&snaps[i], bp, bp->rcut, &hb[i].sd, c->ws_atoms.as<char>() + off[i], c, st));
+        hb[i].tile_off = tiles;
+        hb[i].row_off = rows;
+        tiles += hb[i].sd.g.n_tiles;
+        rows += hb[i].sd.g.P;
+    }
+    MALA_TRY(c->ws_batch.reserve(c, sizeof(BatchSnap) * nsnap + 256));
+    BatchSnap* bs = c->ws_batch.as<BatchSnap>();
+    // pinned staging of the table: the copy is ordered on the stream like the kernels
+    if (c->host_batch_len < (size_t)nsnap) {
+        if (c->host_batch) cudaFreeHost(c->host_batch);
+        c->host_batch = nullptr;
+        c->host_batch_len = 0;
+        MALA_CUDA_TRY(cudaMallocHost(&c->host_batch, sizeof(BatchSnap) * nsnap));
+        c->host_batch_len = nsnap;
+    }
+    MALA_CUDA_TRY(cudaStreamSynchronize(st));  // the previous table copy has been consumed
+    memcpy(c->host_batch, hb.data(), sizeof(BatchSnap) * nsnap);  // BatchSnap is trivially copyable
+    MALA_CUDA_TRY(cudaMemcpyAsync(bs, c->host_batch, sizeof(BatchSnap) * nsnap, cudaMemcpyHostToDevice, st));
     const int tj = bp->twojmax;
     const int nh = n_half(tj);
     int kmax = c->kmax_hint;
@@ -113,7 +141,7 @@ static int run_descriptors(Ctx* c, const mala_snapshot* snap, const mala_bispect
         const size_t chunk_budget = (size_t)4 << 30;
         int64_t chunk = (int64_t)(chunk_budget / per_tile);
         if (chunk < 1) chunk = 1;
-        if (chunk > g.n_tiles) chunk = g.n_tiles;
+        if (chunk > tiles) chunk = tiles;
         // FP32 keeps tiles in pairs: room for an even number of tiles
         MALA_TRY(c->ws_u.reserve(c, (size_t)((chunk + 1) & ~int64_t(1)) * nh * 32 * 2 * sizeof(T)));
         MALA_TRY(c->ws_nbr_ab.reserve(c, (size_t)chunk * kmax * 32 * 4 * sizeof(T)));
@@ -130,32 +158,39 @@ static int run_descriptors(Ctx* c, const mala_snapshot* snap, const mala_bispect
             nb.dbg_counts = dbg->dbg_counts;
             nb.dbg_cap = dbg->dbg_cap;
         }
-        MALA_CUDA_TRY(cudaMemsetAsync(sd.maxcnt, 0, sizeof(int), st));
-        for (int64_t t0 = 0; t0 < g.n_tiles; t0 += chunk) {
-            const int64_t nt = (g.n_tiles - t0) < chunk ? (g.n_tiles - t0) : chunk;
+        for (int i = 0; i < nsnap; ++i) MALA_CUDA_TRY(cudaMemsetAsync(hb[i].sd.maxcnt, 0, sizeof(int), st));
+        for (int64_t t0 = 0; t0 < tiles; t0 += chunk) {
+            const int64_t nt = (tiles - t0) < chunk ? (tiles - t0) : chunk;
             if (sizeof(T) == 4)
-                MALA_PROF(c, "k_neighbors", st, launch_neighbors(sd, bp->rcut, bp->rfac0, bp->rmin0, t0, nt, nb, st));
+                MALA_PROF(c, "k_neighbors", st, launch_neighbors(bs, nsnap, bp->rcut, bp->rfac0, bp->rmin0, t0, nt, nb, st));
             else
-                MALA_PROF(c, "k_neighbors", st, launch_neighbors_f64(sd, bp->rcut, bp->rfac0, bp->rmin0, t0, nt, nb, st));
+                MALA_PROF(c, "k_neighbors", st,
+                          launch_neighbors_f64(bs, nsnap, bp->rcut, bp->rfac0, bp->rmin0, t0, nt, nb, st));
             if (B || u_full) {
                 T* uh = c->ws_u.as<T>();
                 MALA_PROF(c, "k_ui", st, launch_ui<T>(tj, nb, bp->wself, nt, uh, st));
-                if (B) MALA_PROF(c, "k_zb", st, launch_zb<T>(c, tj, uh, g, t0, nt, B, st));
-                if (u_full) MALA_PROF(c, "k_u_expand", st, launch_u_expand<T>(tj, uh, g, t0, nt, u_full, st));
+                if (B) MALA_PROF(c, "k_zb", st, launch_zb<T>(c, tj, uh, bs, nsnap, t0, nt, nb.cnt, bp->wself, B, st));
+                if (u_full) MALA_PROF(c, "k_u_expand", st, launch_u_expand<T>(tj, uh, hb[0].sd.g, t0, nt, u_full, st));
             }
         }
         MALA_CUDA_TRY(cudaGetLastError());
-        MALA_CUDA_TRY(cudaMemcpyAsync(c->host_ints, sd.maxcnt, sizeof(int) * 2, cudaMemcpyDeviceToHost, st));
+        // per snapshot: max neighbour count, species flag
+        std::vector<int> flags(2 * (size_t)nsnap);
+        for (int i = 0; i < nsnap; ++i)
+            MALA_CUDA_TRY(cudaMemcpyAsync(&flags[2 * i], hb[i].sd.maxcnt, sizeof(int) * 2, cudaMemcpyDeviceToHost, st));
         MALA_CUDA_TRY(cudaMemcpyAsync(c->host_ints + 2, c->tables.err_d, sizeof(int), cudaMemcpyDeviceToHost, st));
         MALA_CUDA_TRY(cudaStreamSynchronize(st));
-        if (c->host_ints[1]) return fail(MALA_ERR_INVALID_ARG, "species index outside 0..n_species-1");
+        int maxcnt = 0;
+        for (int i = 0; i < nsnap; ++i) {
+            if (flags[2 * i + 1]) return fail(MALA_ERR_INVALID_ARG, "species index outside 0..n_species-1 (snapshot %d)", i);
+            maxcnt = std::max(maxcnt, flags[2 * i]);
+        }
         if (c->host_ints[2]) {
             const int code = c->host_ints[2];
             cudaMemsetAsync(c->tables.err_d, 0, sizeof(int), st);
             if (code == 2) return fail(MALA_ERR_TIMEOUT, "compute_zi/bi: a copy into shared memory did not complete in time");
             return fail(MALA_ERR_UNSUPPORTED, "a bispectrum partial sum exceeded 1e9 (outside the fixed-point range)");
         }
-        const int maxcnt = c->host_ints[0];
         if (dbg) dbg->kmax = maxcnt;
         if (maxcnt <= kmax) {
             if (maxcnt > c->kmax_hint) c->kmax_hint = maxcnt;
@@ -169,8 +204,14 @@ static int run_descriptors(Ctx* c, const mala_snapshot* snap, const mala_bispect
 
 int snap_descriptors(Ctx* c, const mala_snapshot* snap, const mala_bispectrum_params* bp, void* B, void* u_full,
                      mala_precision prec, cudaStream_t st) {
-    if (prec == MALA_MIXED) return run_descriptors<float>(c, snap, bp, (float*)B, (float*)u_full, nullptr, st);
-    return run_descriptors<double>(c, snap, bp, (double*)B, (double*)u_full, nullptr, st);
+    if (prec == MALA_MIXED) return run_descriptors<float>(c, 1, snap, bp, (float*)B, (float*)u_full, nullptr, st);
+    return run_descriptors<double>(c, 1, snap, bp, (double*)B, (double*)u_full, nullptr, st);
+}
+
+int snap_descriptors_batch(Ctx* c, int n, const mala_snapshot* snaps, const mala_bispectrum_params* bp, void* B,
+                           mala_precision prec, cudaStream_t st) {
+    if (prec == MALA_MIXED) return run_descriptors<float>(c, n, snaps, bp, (float*)B, nullptr, nullptr, st);
+    return run_descriptors<double>(c, n, snaps, bp, (double*)B, nullptr, nullptr, st);
 }
 
 // ---- per-kernel event timing ---------------------------------------------
@@ -283,6 +324,7 @@ void mala_destroy(mala_ctx* c) {
     if (c->host_ints) cudaFreeHost(c->host_ints);
     if (c->host_scalars) cudaFreeHost(c->host_scalars);
     if (c->host_dos) cudaFreeHost(c->host_dos);
+    if (c->host_batch) cudaFreeHost(c->host_batch);
     delete c;
 }
 
@@ -331,7 +373,7 @@ int mala_neighbor_lists(mala_ctx* c, const mala_snapshot* snap, double rcut, int
     dbg.dbg_shifts = shifts_dev;
     dbg.dbg_counts = counts_dev;
     dbg.dbg_cap = cap;
-    int rc = run_descriptors<float>(c, snap, &bp, nullptr, nullptr, &dbg, as_stream(stream));
+    int rc = run_descriptors<float>(c, 1, snap, &bp, nullptr, nullptr, &dbg, as_stream(stream));
     if (rc == MALA_OK && max_count) *max_count = dbg.kmax;
     return rc;
 }
@@ -346,6 +388,19 @@ int mala_descriptors(mala_ctx* c, const mala_snapshot* snap, const mala_bispectr
     std::lock_guard<std::mutex> lk(c->mu);
     MALA_CUDA_TRY(cudaSetDevice(c->device));
     return snap_descriptors(c, snap, bp, B_dev, nullptr, precision, as_stream(stream));
+}
+
+int mala_descriptors_batch(mala_ctx* c, int32_t n, const mala_snapshot* snaps, const mala_bispectrum_params* bp,
+                           void* B_dev, mala_precision precision, void* stream) {
+    if (!c) return fail(MALA_ERR_INVALID_ARG, "context is NULL");
+    if (n < 1 || !snaps) return fail(MALA_ERR_INVALID_ARG, "need n >= 1 snapshots");
+    for (int i = 0; i < n; ++i) MALA_TRY(check_snapshot(&snaps[i]));
+    MALA_TRY(check_bparams(bp));
+    if (!B_dev) return fail(MALA_ERR_INVALID_ARG, "B output is NULL");
+    if (precision != MALA_MIXED && precision != MALA_FP64_PLAIN) return fail(MALA_ERR_INVALID_ARG, "bad precision");
+    std::lock_guard<std::mutex> lk(c->mu);
+    MALA_CUDA_TRY(cudaSetDevice(c->device));
+    return snap_descriptors_batch(c, n, snaps, bp, B_dev, precision, as_stream(stream));
 }
 
 int mala_expansion_coefficients(mala_ctx* c, const mala_snapshot* snap, const mala_bispectrum_params* bp,

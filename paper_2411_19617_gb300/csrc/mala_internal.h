@@ -140,12 +140,15 @@ struct Ctx {
     SnapTables tables;
     int num_sms = 0;
     // workspaces of the synchronous path
-    DevBuf ws_atoms, ws_bins, ws_nbr_ab, ws_nbr_c, ws_nbr_cnt, ws_u, ws_misc, ws_B, ws_ldos,
+    DevBuf ws_atoms, ws_batch, ws_bins, ws_nbr_ab, ws_nbr_c, ws_nbr_cnt, ws_u, ws_misc, ws_B, ws_ldos,
         ws_dens, ws_dos, ws_tile_dos, ws_units, ws_mlp64, ws_red, ws_w;
     double* host_dos = nullptr;     // pinned [max N_E]
     size_t host_dos_len = 0;
     double* host_scalars = nullptr; // pinned small buffer
     int* host_ints = nullptr;       // pinned small buffer
+    std::vector<double> batch_dos;  // host D(e) of every snapshot of the last mala_predict_batch
+    void* host_batch = nullptr;     // pinned staging of the descriptor batch table
+    size_t host_batch_len = 0;      // entries it holds
     std::mutex mu;                  // serialises synchronous calls on this context
     std::mutex prof_mu;
     Prof prof;
@@ -185,8 +188,19 @@ struct SnapDev {
     float* wposf = nullptr;   // [6][n] wrapped positions as float pairs: x_hi, y_hi, z_hi, x_lo, y_lo, z_lo
 };
 
-int stage_snapshot(Ctx* c, const mala_snapshot* snap, const mala_bispectrum_params* bp,
-                   double rcut, SnapDev* sd, cudaStream_t st);
+// One snapshot of a batch: its staged atoms and where its tiles and grid
+// points sit in the batch's numbering (a lone snapshot is a batch of one).
+struct BatchSnap {
+    SnapDev sd;
+    int64_t tile_off;  // first tile in the batch's tile numbering
+    int64_t row_off;   // first row of its points in the batch's B / LDOS rows
+};
+
+// bytes of device workspace one snapshot's staging needs (rcut = the cutoff)
+size_t snapshot_ws_bytes(const mala_snapshot* snap, const mala_bispectrum_params* bp, double rcut);
+// stage one snapshot into the workspace at `base` (snapshot_ws_bytes long)
+int stage_snapshot_at(const mala_snapshot* snap, const mala_bispectrum_params* bp, double rcut, SnapDev* sd,
+                      char* base, Ctx* c, cudaStream_t st);
 
 // neighbour records of every tile: ab[tile][k][32] float4 (Cayley-Klein a, b),
 // cw[tile][k][32] float (w * f_c), cnt[tile][32]; optional debug output of the
@@ -203,24 +217,26 @@ struct NbrOut {
     int dbg_cap = 0;
 };
 
-void launch_neighbors(const SnapDev& sd, double rcut, double rfac0, double rmin0, int64_t tile0,
+// tiles [tile0, tile0 + ntiles) of the batch bs[0..nsnap) (device array)
+void launch_neighbors(const BatchSnap* bs, int nsnap, double rcut, double rfac0, double rmin0, int64_t tile0,
                       int64_t ntiles, const NbrOut& out, cudaStream_t st);
-void launch_neighbors_f64(const SnapDev& sd, double rcut, double rfac0, double rmin0, int64_t tile0,
+void launch_neighbors_f64(const BatchSnap* bs, int nsnap, double rcut, double rfac0, double rmin0, int64_t tile0,
                           int64_t ntiles, const NbrOut& out, cudaStream_t st);
 
 // u half storage [tile][n_half][32] complex
 template <class T>
 void launch_ui(int twojmax, const NbrOut& nb, double wself, int64_t ntiles, T* u_half, cudaStream_t st);
 
+// nbr_cnt: the chunk's neighbour counts [tile][32]; wself: the self-term weight
 template <class T>
-void launch_zb(Ctx* c, int twojmax, const T* u_half, const SnapGeom& g, int64_t tile0, int64_t ntiles,
-               T* B, cudaStream_t st);
+void launch_zb(Ctx* c, int twojmax, const T* u_half, const BatchSnap* bs, int nsnap, int64_t tile0, int64_t ntiles,
+               const int* nbr_cnt, double wself, T* B, cudaStream_t st);
 template <>
-void launch_zb<float>(Ctx* c, int twojmax, const float* u_half, const SnapGeom& g, int64_t tile0,
-                      int64_t ntiles, float* B, cudaStream_t st);
+void launch_zb<float>(Ctx* c, int twojmax, const float* u_half, const BatchSnap* bs, int nsnap, int64_t tile0,
+                      int64_t ntiles, const int* nbr_cnt, double wself, float* B, cudaStream_t st);
 template <>
-void launch_zb<double>(Ctx* c, int twojmax, const double* u_half, const SnapGeom& g, int64_t tile0,
-                       int64_t ntiles, double* B, cudaStream_t st);
+void launch_zb<double>(Ctx* c, int twojmax, const double* u_half, const BatchSnap* bs, int nsnap, int64_t tile0,
+                       int64_t ntiles, const int* nbr_cnt, double wself, double* B, cudaStream_t st);
 
 template <class T>
 void launch_u_expand(int twojmax, const T* u_half, const SnapGeom& g, int64_t tile0, int64_t ntiles,
@@ -232,6 +248,20 @@ int upload_ui_tables();
 int upload_zb_lists_f64(const int* lists, int bytes);
 int snap_descriptors(Ctx* c, const mala_snapshot* snap, const mala_bispectrum_params* bp, void* B,
                      void* u_full, mala_precision prec, cudaStream_t st);
+// descriptors of n snapshots in one pass of launches; B rows concatenated in snapshot order
+int snap_descriptors_batch(Ctx* c, int n, const mala_snapshot* snaps, const mala_bispectrum_params* bp, void* B,
+                           mala_precision prec, cudaStream_t st);
+
+// the batch's snapshot holding global tile t (bs sorted by tile_off, bs[0].tile_off = 0)
+__device__ __forceinline__ int batch_find(const BatchSnap* bs, int n, int64_t t) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (bs[mid].tile_off <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
 
 // ---- network and integrals ---------------------------------------------------
 

@@ -247,6 +247,7 @@ void server_stop(Ctx* c) {
         cudaFreeHost(s->host_ints);
         cudaFreeHost(s->host_scalars);
         if (s->host_dos) cudaFreeHost(s->host_dos);
+        if (s->host_batch) cudaFreeHost(s->host_batch);
     }
     delete sv;
     c->server = nullptr;
@@ -363,6 +364,62 @@ int mala_predict(mala_ctx* c, const mala_snapshot* snap, const mala_bispectrum_p
         MALA_CUDA_TRY(cudaStreamSynchronize(st));
     }
     return rc;
+}
+
+int mala_predict_batch(mala_ctx* c, int32_t n, const mala_snapshot* snaps, const mala_bispectrum_params* bp,
+                       const mala_model* m, const mala_energy_grid* egs, mala_precision prec, void* density_host,
+                       mala_result* res, void* stream) {
+    if (!c || !res || !snaps || !egs) return fail(MALA_ERR_INVALID_ARG, "NULL argument");
+    if (n < 1) return fail(MALA_ERR_INVALID_ARG, "need n >= 1 snapshots");
+    memset(res, 0, sizeof(mala_result) * (size_t)n);
+    for (int i = 0; i < n; ++i) {
+        MALA_TRY(check_path_args(&snaps[i], bp, m, &egs[i], prec));
+        if (egs[i].n_E != egs[0].n_E) return fail(MALA_ERR_INVALID_ARG, "energy grids of a batch need one n_E");
+    }
+    std::lock_guard<std::mutex> lk(c->mu);
+    MALA_CUDA_TRY(cudaSetDevice(c->device));
+    std::vector<int64_t> row(n + 1, 0);
+    for (int i = 0; i < n; ++i) row[i + 1] = row[i] + (int64_t)snaps[i].grid[0] * snaps[i].grid[1] * snaps[i].grid[2];
+    const int64_t P = row[n];
+    const int nB = n_triples(bp->twojmax), nE = egs[0].n_E;
+    const size_t e = prec == MALA_MIXED ? 4 : 8, l = prec == MALA_MIXED ? 2 : 8;
+    MALA_TRY(c->ws_B.reserve(c, (size_t)P * nB * e + 256));
+    MALA_TRY(c->ws_ldos.reserve(c, (size_t)P * nE * l + 256));
+    MALA_TRY(c->ws_dens.reserve(c, (size_t)P * e + 256));
+    cudaStream_t st = as_stream(stream);
+    char* B = c->ws_B.as<char>();
+    char* L = c->ws_ldos.as<char>();
+    char* D = c->ws_dens.as<char>();
+    MALA_TRY(snap_descriptors_batch(c, n, snaps, bp, B, prec, st));
+    MALA_TRY(mlp_forward(c, m, B, P, L, nullptr, prec, st));
+    c->batch_dos.assign((size_t)n * nE, 0.0);
+    int first_rc = MALA_OK;
+    for (int i = 0; i < n; ++i) {
+        const int64_t Pi = row[i + 1] - row[i];
+        double eF = 0.0, Eb = 0.0, Ne = 0.0;
+        const int rc = integrate(c, L + (size_t)row[i] * nE * l, Pi, cell_volume(&snaps[i]), &egs[i], nullptr,
+                                 D + (size_t)row[i] * e, c->batch_dos.data() + (size_t)i * nE, &eF, &Eb, &Ne, prec,
+                                 st);
+        if (rc != MALA_OK && rc != MALA_ERR_FERMI_BRACKET) return rc;
+        if (rc != MALA_OK && first_rc == MALA_OK) first_rc = rc;
+        mala_result& r = res[i];
+        r.status = rc;
+        r.n_B = nB;
+        r.n_E = nE;
+        r.n_points = Pi;
+        r.fermi_eV = eF;
+        r.band_energy_eV = Eb;
+        r.electron_count = Ne;
+        r.dos = c->batch_dos.data() + (size_t)i * nE;
+        r.B_dev = B + (size_t)row[i] * nB * e;
+        r.ldos_dev = L + (size_t)row[i] * nE * l;
+        r.density_dev = D + (size_t)row[i] * e;
+    }
+    if (density_host) {
+        MALA_CUDA_TRY(cudaMemcpyAsync(density_host, D, (size_t)P * e, cudaMemcpyDeviceToHost, st));
+        MALA_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    return first_rc;
 }
 
 int mala_submit(mala_ctx* c, const mala_snapshot* snap, const mala_bispectrum_params* bp, const mala_model* m,

@@ -221,15 +221,17 @@ __device__ __forceinline__ void cayley_klein(T dx, T dy, T dz, T inv_range, T rm
 
 template <class T>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
-    k_neighbors(SnapDev sd, double rcut, double rfac0, double rmin0, int64_t tile0, int64_t ntiles,
-                typename AB<T>::type* __restrict__ out_ab, T* __restrict__ out_cw, int* __restrict__ out_cnt,
-                int kmax, int* __restrict__ dbg_atoms, int* __restrict__ dbg_shifts,
+    k_neighbors(const BatchSnap* __restrict__ batch, int nsnap, double rcut, double rfac0, double rmin0, int64_t tile0,
+                int64_t ntiles, typename AB<T>::type* __restrict__ out_ab, T* __restrict__ out_cw,
+                int* __restrict__ out_cnt, int kmax, int* __restrict__ dbg_atoms, int* __restrict__ dbg_shifts,
                 int* __restrict__ dbg_counts, int dbg_cap) {
     __shared__ Cand cand[kWarpsPerBlock][kCand];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t tl = (int64_t)blockIdx.x * kWarpsPerBlock + warp;  // local tile index
+    const int64_t tl = (int64_t)blockIdx.x * kWarpsPerBlock + warp;  // tile index within this launch
     if (tl >= ntiles) return;
-    const int64_t tile = tile0 + tl;
+    const int si = batch_find(batch, nsnap, tile0 + tl);
+    const SnapDev sd = batch[si].sd;
+    const int64_t tile = tile0 + tl - batch[si].tile_off;  // tile index within its snapshot
     const SnapGeom& g = sd.g;
     const int n = g.n_atoms;
     const int tx = (int)(tile % g.tiles[0]);
@@ -420,9 +422,17 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 
 }  // namespace
 
-int stage_snapshot(Ctx* c, const mala_snapshot* snap, const mala_bispectrum_params* bp, double rcut,
-                   SnapDev* sd, cudaStream_t st) {
-    SnapGeom& g = sd->g;
+namespace {
+
+// geometry of a snapshot and the byte offsets of its staging workspace
+struct StageLayout {
+    size_t o_pos, o_wpos, o_wposf, o_sp, o_wsp, o_binof, o_batoms, o_bstart, o_bcount, o_bfill, o_max, o_wtab, o_gc;
+    size_t bytes;
+    int ngc, ns;
+};
+
+StageLayout stage_layout(const mala_snapshot* snap, const mala_bispectrum_params* bp, double rcut, SnapGeom& g) {
+    StageLayout lay{};
     g.n_atoms = snap->n_atoms;
     for (int d = 0; d < 3; ++d) {
         g.L[d] = snap->cell[d][d];
@@ -448,22 +458,45 @@ int stage_snapshot(Ctx* c, const mala_snapshot* snap, const mala_bispectrum_para
         off += (bytes + 255) & ~size_t(255);
         return o;
     };
-    const size_t o_pos = take(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
-    const size_t o_wpos = take(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
-    const size_t o_wposf = take(sizeof(float) * 6 * (size_t)(n > 0 ? n : 1));
-    const size_t o_sp = take(sizeof(int) * (size_t)(n > 0 ? n : 1));
-    const size_t o_wsp = take(sizeof(float) * (size_t)(n > 0 ? n : 1));
-    const size_t o_binof = take(sizeof(int) * (size_t)(n > 0 ? n : 1));
-    const size_t o_batoms = take(sizeof(int) * (size_t)(n > 0 ? n : 1));
-    const size_t o_bstart = take(sizeof(int) * (size_t)(nbins + 1));
-    const size_t o_bcount = take(sizeof(int) * (size_t)nbins);
-    const size_t o_bfill = take(sizeof(int) * (size_t)nbins);
-    const size_t o_max = take(sizeof(int) * 4);
-    const size_t o_wtab = take(sizeof(double) * (size_t)ns);
-    const int ngc = g.grid[0] + g.grid[1] + g.grid[2];
-    const size_t o_gc = take(sizeof(double) * (size_t)(ngc > 0 ? ngc : 1));
-    MALA_TRY(c->ws_atoms.reserve(c, off));
-    char* base = c->ws_atoms.as<char>();
+    lay.o_pos = take(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
+    lay.o_wpos = take(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
+    lay.o_wposf = take(sizeof(float) * 6 * (size_t)(n > 0 ? n : 1));
+    lay.o_sp = take(sizeof(int) * (size_t)(n > 0 ? n : 1));
+    lay.o_wsp = take(sizeof(float) * (size_t)(n > 0 ? n : 1));
+    lay.o_binof = take(sizeof(int) * (size_t)(n > 0 ? n : 1));
+    lay.o_batoms = take(sizeof(int) * (size_t)(n > 0 ? n : 1));
+    lay.o_bstart = take(sizeof(int) * (size_t)(nbins + 1));
+    lay.o_bcount = take(sizeof(int) * (size_t)nbins);
+    lay.o_bfill = take(sizeof(int) * (size_t)nbins);
+    lay.o_max = take(sizeof(int) * 4);
+    lay.o_wtab = take(sizeof(double) * (size_t)ns);
+    lay.ngc = g.grid[0] + g.grid[1] + g.grid[2];
+    const int ngc = lay.ngc;
+    lay.o_gc = take(sizeof(double) * (size_t)(ngc > 0 ? ngc : 1));
+    lay.bytes = off;
+    lay.ns = ns;
+    return lay;
+}
+
+}  // namespace
+
+size_t snapshot_ws_bytes(const mala_snapshot* snap, const mala_bispectrum_params* bp, double rcut) {
+    SnapGeom g{};
+    return stage_layout(snap, bp, rcut, g).bytes;
+}
+
+int stage_snapshot_at(const mala_snapshot* snap, const mala_bispectrum_params* bp, double rcut, SnapDev* sd,
+                      char* base, Ctx* c, cudaStream_t st) {
+    SnapGeom& g = sd->g;
+    const StageLayout lay = stage_layout(snap, bp, rcut, g);
+    const int n = g.n_atoms;
+    const int nbins = g.n_bins;
+    const int ns = lay.ns;
+    const int ngc = lay.ngc;
+    const size_t o_pos = lay.o_pos, o_wpos = lay.o_wpos, o_wposf = lay.o_wposf, o_sp = lay.o_sp, o_wsp = lay.o_wsp,
+                 o_binof = lay.o_binof, o_batoms = lay.o_batoms, o_bstart = lay.o_bstart, o_bcount = lay.o_bcount,
+                 o_bfill = lay.o_bfill, o_max = lay.o_max, o_wtab = lay.o_wtab, o_gc = lay.o_gc;
+
     double* pos_d = (double*)(base + o_pos);
     sd->wpos = (double*)(base + o_wpos);
     sd->wposf = (float*)(base + o_wposf);
@@ -509,24 +542,24 @@ int stage_snapshot(Ctx* c, const mala_snapshot* snap, const mala_bispectrum_para
 }
 
 template <class T>
-static void launch_neighbors_t(const SnapDev& sd, double rcut, double rfac0, double rmin0, int64_t tile0,
+static void launch_neighbors_t(const BatchSnap* bs, int nsnap, double rcut, double rfac0, double rmin0, int64_t tile0,
                                int64_t ntiles, const NbrOut& out, cudaStream_t st) {
     if (ntiles <= 0) return;
     const unsigned blocks = (unsigned)((ntiles + kWarpsPerBlock - 1) / kWarpsPerBlock);
     k_neighbors<T><<<blocks, kWarpsPerBlock * 32, 0, st>>>(
-        sd, rcut, rfac0, rmin0, tile0, ntiles, reinterpret_cast<typename AB<T>::type*>(out.ab),
+        bs, nsnap, rcut, rfac0, rmin0, tile0, ntiles, reinterpret_cast<typename AB<T>::type*>(out.ab),
         reinterpret_cast<T*>(out.cw), out.cnt, out.kmax, out.dbg_atoms, out.dbg_shifts, out.dbg_counts,
         out.dbg_cap);
 }
 
-void launch_neighbors(const SnapDev& sd, double rcut, double rfac0, double rmin0, int64_t tile0,
+void launch_neighbors(const BatchSnap* bs, int nsnap, double rcut, double rfac0, double rmin0, int64_t tile0,
                       int64_t ntiles, const NbrOut& out, cudaStream_t st) {
-    launch_neighbors_t<float>(sd, rcut, rfac0, rmin0, tile0, ntiles, out, st);
+    launch_neighbors_t<float>(bs, nsnap, rcut, rfac0, rmin0, tile0, ntiles, out, st);
 }
 
-void launch_neighbors_f64(const SnapDev& sd, double rcut, double rfac0, double rmin0, int64_t tile0,
+void launch_neighbors_f64(const BatchSnap* bs, int nsnap, double rcut, double rfac0, double rmin0, int64_t tile0,
                           int64_t ntiles, const NbrOut& out, cudaStream_t st) {
-    launch_neighbors_t<double>(sd, rcut, rfac0, rmin0, tile0, ntiles, out, st);
+    launch_neighbors_t<double>(bs, nsnap, rcut, rfac0, rmin0, tile0, ntiles, out, st);
 }
 
 }  // namespace mala

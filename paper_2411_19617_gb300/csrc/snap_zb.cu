@@ -168,6 +168,16 @@ int upload_cg_tables(Ctx* c) {
                     ++gid;
                 }
         c->tables.unit_off[tj / 2] = ubase;
+        {
+            // J + 1 per output column of this twojmax (index-set order)
+            float jp1[n_triples(kTJMax)] = {0};
+            int col = 0;
+            for (int j1 = 0; j1 <= tj; ++j1)
+                for (int j2 = 0; j2 <= j1; ++j2)
+                    for (int j = 0; j <= tj; ++j)
+                        if (triple_ok(j1, j2, j, tj)) jp1[col++] = (float)(j + 1);
+            MALA_CUDA_TRY(cudaMemcpyToSymbol(c_zb_jp1, jp1, sizeof(jp1), sizeof(jp1) * (tj / 2)));
+        }
         c->tables.tri_n[tj / 2] = lid;
     }
     const size_t tri_bytes = sizeof(int) * tri.size();
@@ -184,8 +194,8 @@ int upload_cg_tables(Ctx* c) {
 }
 
 template <>
-void launch_zb<float>(Ctx* c, int twojmax, const float* u_half, const SnapGeom& g, int64_t tile0, int64_t ntiles,
-                      float* B, cudaStream_t st) {
+void launch_zb<float>(Ctx* c, int twojmax, const float* u_half, const BatchSnap* bs, int nsnap, int64_t tile0,
+                      int64_t ntiles, const int* nbr_cnt, double wself, float* B, cudaStream_t st) {
     if (ntiles <= 0) return;
     const size_t smem = sizeof(float4) * (size_t)n_half(twojmax) * 32 +
                         sizeof(long long) * (size_t)n_triples(twojmax) * 64 + 2 * sizeof(uint64_t) + 64 * sizeof(long long);
@@ -194,8 +204,9 @@ void launch_zb<float>(Ctx* c, int twojmax, const float* u_half, const SnapGeom& 
     const int64_t npairs = (ntiles + 1) / 2;
     const int grid = (int)std::min<int64_t>(npairs, std::max(1, c->num_sms));
     k_zb_units<<<(unsigned)grid, kZbUWarps * 32, smem, st>>>(
-        twojmax, reinterpret_cast<const float4*>(u_half), g, tile0, ntiles, c->tables.tri_d + c->tables.tri_off[k],
-        c->tables.tri_n[k], c->tables.units_d + c->tables.unit_off[k], B, c->tables.err_d);
+        twojmax, reinterpret_cast<const float4*>(u_half), bs, nsnap, tile0, ntiles, c->tables.tri_d + c->tables.tri_off[k],
+        c->tables.tri_n[k], c->tables.units_d + c->tables.unit_off[k], nbr_cnt, (float)(wself * wself * wself), B,
+        c->tables.err_d);
 }
 
 }  // namespace mala

@@ -21,6 +21,10 @@ static __constant__ float2 c_cg2[kCgSize];
 // per supported twojmax (index tj/2): [warp][slot] = global triple id | (local index << 8), -1 = end
 static __constant__ int c_zb_list[kTJMax / 2 + 1][kZbWarps][kZbMaxList];
 
+// per supported twojmax (index tj/2): J + 1 of every output column, for the
+// closed form of points without neighbours
+static __constant__ float c_zb_jp1[kTJMax / 2 + 1][n_triples(kTJMax)];
+
 namespace {
 
 template <class T> struct C2;
@@ -155,8 +159,8 @@ __device__ __forceinline__ T zb_dispatch(int id, const typename C2<T>::type* su,
 
 template <class T>
 __global__ void __launch_bounds__(kZbWarps * 32)
-    k_zb(int tj, const typename C2<T>::type* __restrict__ u, SnapGeom g, int64_t tile0, int64_t ntiles,
-         const T* __restrict__ gcg, T* __restrict__ B) {
+    k_zb(int tj, const typename C2<T>::type* __restrict__ u, const BatchSnap* __restrict__ batch, int nsnap,
+         int64_t tile0, int64_t ntiles, const T* __restrict__ gcg, T* __restrict__ B) {
     using V = typename C2<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nh = n_half(tj);
@@ -184,7 +188,10 @@ __global__ void __launch_bounds__(kZbWarps * 32)
         sB[loc * 32 + lane] = b;
     }
     __syncthreads();
-    const int64_t tile = tile0 + tl;
+    const int si = batch_find(batch, nsnap, tile0 + tl);
+    const SnapGeom& g = batch[si].sd.g;
+    const int64_t row0 = batch[si].row_off;
+    const int64_t tile = tile0 + tl - batch[si].tile_off;
     const int tx = (int)(tile % g.tiles[0]);
     const int ty = (int)((tile / g.tiles[0]) % g.tiles[1]);
     const int tz = (int)(tile / ((int64_t)g.tiles[0] * g.tiles[1]));
@@ -194,7 +201,7 @@ __global__ void __launch_bounds__(kZbWarps * 32)
         const int iy = ty * kTileY + ((l / kTileX) % kTileY);
         const int iz = tz * kTileZ + l / (kTileX * kTileY);
         if (ix >= g.grid[0] || iy >= g.grid[1] || iz >= g.grid[2]) continue;
-        const int64_t p = ix + (int64_t)g.grid[0] * (iy + (int64_t)g.grid[1] * iz);
+        const int64_t p = row0 + ix + (int64_t)g.grid[0] * (iy + (int64_t)g.grid[1] * iz);
         B[(size_t)p * nB + t] = sB[t * 32 + l];
     }
 }
@@ -441,9 +448,10 @@ __device__ __forceinline__ void zb_fetch(uint32_t dst, const void* src, uint32_t
 // meanwhile pulled into L2, so the copy reads L2 rather than HBM.
 // tri: per triple of this twojmax, int4 (global id, first unit, unit count, output column)
 __global__ void __launch_bounds__(kZbUWarps * 32, 1)
-    k_zb_units(int tj, const float4* __restrict__ u, SnapGeom g, int64_t tile0, int64_t ntiles,
+    k_zb_units(int tj, const float4* __restrict__ u, const BatchSnap* __restrict__ batch, int nsnap, int64_t tile0,
+               int64_t ntiles,
                const int4* __restrict__ tri, int ntri, const unsigned short* __restrict__ units,
-               float* __restrict__ B, int* __restrict__ err) {
+               const int* __restrict__ nbr_cnt, float wself3, float* __restrict__ B, int* __restrict__ err) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nh = n_half(tj);
     const int nB = n_triples(tj);
@@ -464,24 +472,34 @@ __global__ void __launch_bounds__(kZbUWarps * 32, 1)
     uint32_t ph = 0;
     bool bad = false, stalled = false, inflight = false;
     for (int64_t pr = blockIdx.x; pr < npairs; pr += gridDim.x) {
+        const bool hasB = 2 * pr + 1 < ntiles;
+        // a pair whose 64 points have no neighbour has u^J = w_self I for every
+        // J, hence Z = w_self^2 I (orthonormal coupling coefficients) and
+        // B = w_self^3 (J + 1): no copy, no contraction
+        const int my_cnt = (threadIdx.x < 32 || (threadIdx.x < 64 && hasB)) ? __ldg(nbr_cnt + 64 * pr + threadIdx.x) : 0;
+        const bool vacuum = !__syncthreads_or(threadIdx.x < 64 && my_cnt > 0);
         if (threadIdx.x == 0) {
-            zb_fetch(sbuf0, u + (size_t)pr * nh * 32, ubytes, bar0);
-            inflight = true;
+            if (!vacuum) {
+                zb_fetch(sbuf0, u + (size_t)pr * nh * 32, ubytes, bar0);
+                inflight = true;
+            }
             const int64_t nxt = pr + gridDim.x;
             if (nxt < npairs)
                 asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(u + (size_t)nxt * nh * 32), "r"(ubytes)
                              : "memory");
         }
-        const bool got = zb_wait(bar0, ph);
-        ph ^= 1u;
-        inflight = false;
-        if (!__syncthreads_and(got)) {
-            stalled = true;
-            if (threadIdx.x == 0) inflight = !got;
-            break;
+        if (!vacuum) {
+            const bool got = zb_wait(bar0, ph);
+            ph ^= 1u;
+            inflight = false;
+            if (!__syncthreads_and(got)) {
+                stalled = true;
+                if (threadIdx.x == 0) inflight = !got;
+                break;
+            }
         }
         const uint32_t su = sbuf0 + (uint32_t)lane * 16u;
-        for (int t = 0; t < ntri; ++t) {
+        for (int t = 0; t < ntri && !vacuum; ++t) {
             const int4 d = __ldg(tri + t);  // (gid, start, count, column)
             const int first = ((warp - d.y) % kZbUWarps + kZbUWarps) % kZbUWarps;
             if (first >= d.z) continue;
@@ -493,12 +511,14 @@ __global__ void __launch_bounds__(kZbUWarps * 32, 1)
         }
         __syncthreads();
         // grid points of the pair's 64 (tile, lane) slots
-        const bool hasB = 2 * pr + 1 < ntiles;
         if (threadIdx.x < 64) {
             const int pl = threadIdx.x, l = pl & 31;
             long long q = -1;
             if (!(pl >> 5) || hasB) {
-                const int64_t tile = tile0 + 2 * pr + (pl >> 5);
+                const int64_t gt = tile0 + 2 * pr + (pl >> 5);
+                const int si = batch_find(batch, nsnap, gt);
+                const SnapGeom& g = batch[si].sd.g;
+                const int64_t tile = gt - batch[si].tile_off;
                 const int tx = (int)(tile % g.tiles[0]);
                 const int ty = (int)((tile / g.tiles[0]) % g.tiles[1]);
                 const int tz = (int)(tile / ((int64_t)g.tiles[0] * g.tiles[1]));
@@ -506,17 +526,24 @@ __global__ void __launch_bounds__(kZbUWarps * 32, 1)
                 const int iy = ty * kTileY + ((l / kTileX) % kTileY);
                 const int iz = tz * kTileZ + l / (kTileX * kTileY);
                 if (ix < g.grid[0] && iy < g.grid[1] && iz < g.grid[2])
-                    q = ix + (int64_t)g.grid[0] * (iy + (int64_t)g.grid[1] * iz);
+                    q = batch[si].row_off + ix + (int64_t)g.grid[0] * (iy + (int64_t)g.grid[1] * iz);
             }
             spix[pl] = q;
         }
         // fixed point -> float into the (consumed) u buffer as [slot][nB | 1], accumulators reset
         const int ldo = nB | 1;
         float* out = reinterpret_cast<float*>(smem_raw);
-        for (int i = threadIdx.x; i < nB * 64; i += blockDim.x) {
-            const int t = i >> 6, pl = i & 63;
-            out[pl * ldo + t] = from_fixed((long long)sacc[i]);
-            sacc[i] = 0ull;
+        if (vacuum) {
+            for (int i = threadIdx.x; i < nB * 64; i += blockDim.x) {
+                const int t = i >> 6, pl = i & 63;
+                out[pl * ldo + t] = wself3 * c_zb_jp1[tj / 2][t];
+            }
+        } else {
+            for (int i = threadIdx.x; i < nB * 64; i += blockDim.x) {
+                const int t = i >> 6, pl = i & 63;
+                out[pl * ldo + t] = from_fixed((long long)sacc[i]);
+                sacc[i] = 0ull;
+            }
         }
         __syncthreads();
         for (int pl = warp; pl < 64; pl += kZbUWarps) {
@@ -538,12 +565,12 @@ __global__ void __launch_bounds__(kZbUWarps * 32, 1)
 
 
 template <class T>
-inline void zb_launch_impl(const void*, int twojmax, const T* u_half, const SnapGeom& g,
+inline void zb_launch_impl(const void*, int twojmax, const T* u_half, const BatchSnap* bs, int nsnap,
                            int64_t tile0, int64_t ntiles, const T* gcg, T* B, cudaStream_t st) {
     using V = typename C2<T>::type;
     const size_t smem = sizeof(V) * (size_t)n_half(twojmax) * 32 + sizeof(T) * (size_t)n_triples(twojmax) * 32;
-    k_zb<T><<<(unsigned)ntiles, kZbWarps * 32, smem, st>>>(twojmax, reinterpret_cast<const V*>(u_half), g, tile0,
-                                                            ntiles, gcg, B);
+    k_zb<T><<<(unsigned)ntiles, kZbWarps * 32, smem, st>>>(twojmax, reinterpret_cast<const V*>(u_half), bs, nsnap,
+                                                            tile0, ntiles, gcg, B);
 }
 
 }  // namespace mala
