@@ -90,3 +90,26 @@ def test_boron_cluster_batch_matches_oracle_on_sampled_points():
         # scale errors by each component's RMS over the sample
         assert descriptor_error(got, ref) < 1e-5, f"cluster {i}"
         row += s.n_points
+
+
+def test_batch_with_empty_and_single_point_snapshots():
+    # a snapshot without atoms (closed form w_self^3 (J+1)), a 1x1x1 grid and a ragged one in one batch
+    need_gpu()
+    from paper_2411_19617_gb300 import api
+    c = ctx()
+    bp = wl.BispectrumParams(twojmax=8, rcut=4.676, wself=1.25)
+    empty = wl.Snapshot(pos=np.zeros((0, 3)), species=np.zeros(0, np.int32), cell=np.diag([7.0] * 3),
+                        grid=(5, 3, 3))
+    one = wl.al_fcc(2, 0.1, 1, seed=4)
+    ragged = wl.al_fcc(2, 0.1, 7, seed=5)
+    snaps = [empty, one, ragged, empty]
+    Bb = c.descriptors_batch(snaps, bp).double().cpu().numpy()
+    tr = oracle.triples(8)
+    closed = 1.25 ** 3 * (tr[:, 2] + 1)
+    np.testing.assert_allclose(Bb[:empty.n_points], np.broadcast_to(closed, (empty.n_points, len(tr))), rtol=1e-6)
+    np.testing.assert_allclose(Bb[-empty.n_points:], np.broadcast_to(closed, (empty.n_points, len(tr))), rtol=1e-6)
+    row = empty.n_points
+    for s in (one, ragged):
+        ref = oracle.bispectrum_grid(s, bp, nthreads=8)
+        assert descriptor_error(Bb[row:row + s.n_points], ref) < 1e-5
+        row += s.n_points

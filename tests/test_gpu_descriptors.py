@@ -133,6 +133,25 @@ def test_descriptors_boron_clusters_sampled():
         assert descriptor_error(B[pts], ref) < TOL32
 
 
+def test_descriptors_be_slab_full_size_sampled():
+    # the stacking-fault slab, ~2e7 points streamed in tile chunks: bulk, fault plane and vacuum
+    need_gpu()
+    from paper_2411_19617_gb300 import api
+    snaps, bp, *_ = wl.config(4)
+    snap = snaps[0]
+    B = ctx().descriptors(snap, bp, api.MIXED)
+    pts = wl.sample_points(snap.n_points, 120, seed=44)
+    got = B[torch_index(pts, B.device)].double().cpu().numpy()
+    ref = oracle.bispectrum_grid(snap, bp, points=pts, nthreads=8)
+    assert descriptor_error(got, ref) < TOL32
+    del B
+
+
+def torch_index(pts, device):
+    import torch
+    return torch.as_tensor(pts, device=device)
+
+
 def test_descriptors_empty_cell_is_self_term_only():
     # no atoms: u^J = wself I, so B_{J1 J2 J} = wself^3 (J+1) (Clebsch-Gordan orthonormality)
     need_gpu()
