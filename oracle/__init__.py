@@ -18,7 +18,8 @@ Contents, each following the passage of the paper cited at the function:
   polylogarithms that the CUDA path evaluates;
 * ``fermi_level``: bisection on N(mu) - N_e (Sec. "Observable calculation");
 * ``observables``: D(e) of Eq. (DOS.from.ldos), n(r) of Eq. (density.from.ldos),
-  the band energy of Eq. (band.energy).
+  the band energy of Eq. (band.energy) and the entropy contribution -tau S_s of
+  Eq. (electronicentropyDOS) (``entropy_weights`` / ``entropy_term``).
 
 Parity pins for every function live in ``tests/test_oracle_*.py``.
 """
@@ -333,6 +334,48 @@ def fermi_level(D: np.ndarray, e0: float, de: float, kT: float, n_electrons: flo
     return 0.5 * (lo + hi)
 
 
+def entropy_weights(e0: float, de: float, n_E: int, mu: float, kT: float) -> np.ndarray:
+    """w^S_xi = int hat_xi(e) s(beta (e - mu)) de with
+    s = -[f ln f + (1 - f) ln(1 - f)], the integrand of Eq. (electronicentropyDOS)
+    in units of k_B, for the piecewise-linear reading of D(e) between grid
+    points.  s is computed from its definition with f = f_beta (terms with
+    f = 0 or 1 vanish); each (interval, hat) piece by QUADPACK, split at mu."""
+    from scipy.integrate import quad
+
+    if n_E < 2:
+        raise ValueError("need at least two energies")
+
+    def s_of(e):
+        x = (e - mu) / kT
+        f = 0.5 * (1.0 - math.tanh(0.5 * x))
+        g = 1.0 - f
+        out = 0.0
+        if f > 0.0:
+            out -= f * math.log(f)
+        if g > 0.0:
+            out -= g * math.log(g)
+        return out
+
+    w = np.zeros(n_E, np.float64)
+    for i in range(n_E - 1):
+        a = e0 + i * de
+        bnd = e0 + (i + 1) * de
+        pts = [mu] if a < mu < bnd else None
+        left = lambda e, bnd=bnd: (bnd - e) / de * s_of(e)
+        right = lambda e, a=a: (e - a) / de * s_of(e)
+        for k, g in ((i, left), (i + 1, right)):
+            val, _ = quad(g, a, bnd, points=pts, epsabs=1e-15, epsrel=1e-13, limit=200)
+            w[k] += val
+    return w
+
+
+def entropy_term(D: np.ndarray, mu: float, e0: float, de: float, kT: float) -> float:
+    """The free-energy contribution -tau S_s of Eq. (KSfreeenergy) in eV, with
+    S_s from Eq. (electronicentropyDOS): -kT sum_xi w^S_xi D_xi."""
+    wS = entropy_weights(e0, de, len(D), mu, kT)
+    return float(-kT * np.dot(wS, np.asarray(D, np.float64)))
+
+
 def dos(ldos: np.ndarray, dV: float) -> np.ndarray:
     """Eq. (DOS.from.ldos) on the grid: D_xi = dV sum_r L(r, xi)."""
     return dV * np.sum(np.asarray(ldos, np.float64), axis=0)
@@ -348,4 +391,5 @@ def observables(ldos: np.ndarray, dV: float, e0: float, de: float, kT: float, n_
     w1 = integration_weights(1, e0, de, L.shape[1], eF, kT)
     n = L @ w0
     Eb = float(np.dot(w1, D))
-    return {"dos": D, "fermi": eF, "band_energy": Eb, "density": n, "w0": w0, "w1": w1}
+    TS = entropy_term(D, eF, e0, de, kT)
+    return {"dos": D, "fermi": eF, "band_energy": Eb, "entropy_term": TS, "density": n, "w0": w0, "w1": w1}

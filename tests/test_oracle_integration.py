@@ -166,3 +166,40 @@ def test_electron_count_invariant_and_band_energy():
     w1 = oracle.integration_weights(1, e0, de, n_E, obs["fermi"], kT)
     assert obs["band_energy"] == pytest.approx(float(w1 @ D), rel=1e-14)
     np.testing.assert_allclose(obs["dos"], dV * L.sum(axis=0), rtol=1e-14)
+
+
+# ---- entropy contribution (Eq. electronicentropyDOS) ------------------------
+
+def test_entropy_of_a_flat_dos_is_pi2_over_3():
+    # int s(x) dx over the real line = pi^2/3, so a constant D0 gives
+    # S_s / k_B = D0 kT pi^2 / 3 (mu deep inside the grid: the tails are below 1e-15)
+    kT, D0 = 0.05, 2.5
+    e0, de, n_E = -3.0, 0.25, 25
+    D = np.full(n_E, D0)
+    TS = oracle.entropy_term(D, 0.0, e0, de, kT)
+    assert TS == pytest.approx(-kT * D0 * kT * math.pi ** 2 / 3.0, rel=1e-11)
+
+
+def test_entropy_sommerfeld_for_a_smooth_dos():
+    # S_s / k_B = (pi^2 / 3) kT D(mu) + (7 pi^4 / 90) kT^3 D''(mu) for a quadratic DOS (fine grid)
+    e0, de, n_E = -2.0, 0.002, 2001
+    e = e0 + de * np.arange(n_E)
+    D = 1.0 + 0.3 * e + 0.2 * e ** 2
+    for kT in (0.01, 0.02):
+        mu = 0.1
+        TS = oracle.entropy_term(D, mu, e0, de, kT)
+        Dmu = 1.0 + 0.3 * mu + 0.2 * mu ** 2
+        # next term: kT^3 D''(mu) / 2 * int x^2 s(x) dx = kT^3 D''(mu) / 2 * 7 pi^4 / 45; the
+        # quadratic D has no higher one
+        ref = -kT * (math.pi ** 2 / 3.0 * kT * Dmu + 0.5 * 0.4 * kT ** 3 * 7 * math.pi ** 4 / 45.0)
+        assert TS == pytest.approx(ref, rel=2e-5)
+
+
+def test_entropy_vanishes_at_zero_temperature_and_is_symmetric():
+    e0, de, n_E = -1.0, 0.1, 21
+    rng = np.random.default_rng(2)
+    D = rng.uniform(0.5, 1.5, n_E)
+    assert abs(oracle.entropy_term(D, 0.03, e0, de, 1e-6)) < 1e-9
+    # s(x) = s(-x): mirroring the DOS about mu mirrors nothing
+    w = oracle.entropy_weights(e0, de, n_E, 0.0, 0.05)
+    np.testing.assert_allclose(w, w[::-1], rtol=1e-10, atol=1e-15)
