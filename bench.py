@@ -407,7 +407,7 @@ def run_ours(args):
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
                 "clocks": clk, "kernels": kernels, "serving": serving,
-                "fermi_eV": r["fermi"], "band_energy_eV": r["band_energy"]}
+                "fermi_eV": r["fermi"], "band_energy_eV": r["band_energy"], "entropy_term_eV": r["entropy_term"]}
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -113,6 +113,7 @@ typedef struct {
     const void* ldos_dev;        /* device [P][n_E] (bf16 for MIXED, double for FP64_PLAIN) */
     const void* density_dev;     /* device [P] (float for MIXED, double for FP64_PLAIN) */
     double submit_to_done_s;     /* serving latency (mala_poll only) */
+    double entropy_term_eV;      /* -tau S_s, Eqs. (electronicentropyDOS), (KSfreeenergy) */
 } mala_result;
 
 /* ---- context ------------------------------------------------------------ */
@@ -200,11 +201,15 @@ int mala_ldos_forward(mala_ctx* ctx, const mala_model* model, const void* B_dev,
  * in closed form through Li2/Li3.  dos_sum_dev (device [N_E], may be NULL)
  * supplies precomputed column sums (mala_ldos_forward's); otherwise they are
  * computed from ldos_dev.  Host outputs (any may be NULL): dos_host[N_E],
- * fermi_eV, band_energy_eV, electron_count (dV sum_r n(r) in FP64). */
+ * fermi_eV, band_energy_eV, electron_count (dV sum_r n(r) in FP64) and
+ * entropy_term_eV = -tau S_s = -kT sum_xi wS_xi D_xi, the entropy contribution
+ * to the free energy (Eqs. electronicentropyDOS, KSfreeenergy), wS the exact
+ * integrals of the interpolant times -[f ln f + (1-f) ln(1-f)], also in closed
+ * form through Li2/Li3. */
 int mala_integrate(mala_ctx* ctx, const void* ldos_dev, int64_t P, double cell_volume,
                    const mala_energy_grid* eg, const double* dos_sum_dev, void* density_dev,
                    double* dos_host, double* fermi_eV, double* band_energy_eV,
-                   double* electron_count, mala_precision precision, void* stream);
+                   double* electron_count, double* entropy_term_eV, mala_precision precision, void* stream);
 
 /* mala_integrate without any allocation.  The paper has no counterpart: this
  * entry point exists for callers that cannot allocate device memory (their
@@ -226,7 +231,8 @@ int mala_integrate(mala_ctx* ctx, const void* ldos_dev, int64_t P, double cell_v
 int mala_integrate_noalloc(mala_ctx* ctx, const void* ldos_dev, int64_t P, double cell_volume,
                            const mala_energy_grid* eg, const double* dos_sum_dev, void* density_dev,
                            double* dos_host, double* fermi_eV, double* band_energy_eV,
-                           double* electron_count, mala_precision precision, void* stream);
+                           double* electron_count, double* entropy_term_eV, mala_precision precision,
+                           void* stream);
 
 /* Electron count N(mu) = sum_xi w0_xi(mu) D_xi of a density of states D (host
  * [n_E], the values mala_integrate returns in dos_host) at chemical potential

@@ -52,7 +52,7 @@ class Result(C.Structure):
     _fields_ = [("status", C.c_int32), ("n_B", C.c_int32), ("n_E", C.c_int32), ("n_points", C.c_int64),
                 ("fermi_eV", C.c_double), ("band_energy_eV", C.c_double), ("electron_count", C.c_double),
                 ("dos", C.POINTER(C.c_double)), ("B_dev", C.c_void_p), ("ldos_dev", C.c_void_p),
-                ("density_dev", C.c_void_p), ("submit_to_done_s", C.c_double)]
+                ("density_dev", C.c_void_p), ("submit_to_done_s", C.c_double), ("entropy_term_eV", C.c_double)]
 
 
 # name -> (restype, argtypes); every function declared in include/mala.h
@@ -76,10 +76,12 @@ PROTOTYPES = {
                                     C.c_int, C.c_void_p]),
     "mala_integrate": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_double, C.POINTER(EnergyGrid),
                                  C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_double),
-                                 C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int, C.c_void_p]),
+                                 C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int,
+                                 C.c_void_p]),
     "mala_integrate_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_double, C.POINTER(EnergyGrid),
                                          C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_double),
-                                         C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int, C.c_void_p]),
+                                         C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int,
+                                         C.c_void_p]),
     "mala_electron_count": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(EnergyGrid), C.c_double,
                                       C.POINTER(C.c_double)]),
     "mala_predict": (C.c_int, [C.c_void_p, C.POINTER(Snapshot), C.POINTER(BispectrumParams), C.c_void_p,

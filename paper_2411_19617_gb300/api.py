@@ -136,7 +136,8 @@ class Model:
 def _result_dict(r: "_lib.Result", precision: int):
     torch = _torch()
     out = {"status": int(r.status), "fermi": float(r.fermi_eV), "band_energy": float(r.band_energy_eV),
-           "electron_count": float(r.electron_count), "n_points": int(r.n_points), "n_B": int(r.n_B),
+           "electron_count": float(r.electron_count), "entropy_term": float(r.entropy_term_eV),
+           "n_points": int(r.n_points), "n_B": int(r.n_B),
            "n_E": int(r.n_E), "latency_s": float(r.submit_to_done_s)}
     out["dos"] = np.ctypeslib.as_array(r.dos, shape=(r.n_E,)).copy() if r.dos else None
     fdt = torch.float32 if precision == MIXED else torch.float64
@@ -280,7 +281,7 @@ class Context:
 
     def integrate(self, ldos, volume: float, eg, precision: int = MIXED, dos_sum=None, n_electrons=None,
                   density: bool = True, stream=None, raise_on_bracket: bool = True):
-        """D(e), Fermi level, band energy, electron count and n(r) of an LDOS."""
+        """D(e), Fermi level, band energy, entropy term -tau S_s, electron count and n(r) of an LDOS."""
         torch = _torch()
         P = int(ldos.shape[0])
         dev = torch.device("cuda", self.device)
@@ -289,16 +290,16 @@ class Context:
             dens = torch.empty(P, dtype=torch.float32 if precision == MIXED else torch.float64, device=dev)
         e = _EnergyGridArgs(eg, n_electrons)
         D = np.zeros(int(eg.n_E))
-        eF, Eb, Ne = C.c_double(0), C.c_double(0), C.c_double(0)
+        eF, Eb, Ne, TS = C.c_double(0), C.c_double(0), C.c_double(0), C.c_double(0)
         rc = lib().mala_integrate(self.h, C.c_void_p(ldos.data_ptr()), P, float(volume), C.byref(e.c),
                                   C.c_void_p(dos_sum.data_ptr()) if dos_sum is not None else None,
                                   C.c_void_p(dens.data_ptr()) if dens is not None else None,
-                                  D.ctypes.data_as(C.c_void_p), C.byref(eF), C.byref(Eb), C.byref(Ne),
+                                  D.ctypes.data_as(C.c_void_p), C.byref(eF), C.byref(Eb), C.byref(Ne), C.byref(TS),
                                   int(precision), _stream_ptr(stream))
         if rc != _lib.MALA_ERR_FERMI_BRACKET or raise_on_bracket:
             check(rc, "mala_integrate")
         return {"status": rc, "dos": D, "fermi": eF.value, "band_energy": Eb.value, "electron_count": Ne.value,
-                "density": dens}
+                "entropy_term": TS.value, "density": dens}
 
     def electron_count(self, D, eg, mu: float) -> float:
         """N(mu) = sum_xi w0_xi(mu) D_xi on the GPU."""

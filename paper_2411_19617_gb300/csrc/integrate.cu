@@ -7,6 +7,7 @@
 //              decisions, so the iterates are those of plain bisection
 //   E_b      = sum_xi w1_xi(e_F) D_xi                      (Eq. band.energy)
 //   n(r)     = sum_xi w0_xi(e_F) LDOS(r, xi)              (Eq. density.from.ldos)
+//   -tau S_s = -kT sum_xi wS_xi(e_F) D_xi                  (Eqs. electronicentropyDOS, KSfreeenergy)
 // with w_n,xi(mu) = int hat_xi(e) e^n f((e - mu)/kT) de the exact weights of
 // the piecewise-linear interpolant between energy-grid points
 // (Eqs. ldosintegralgeneral / ldosintegralsummation).
@@ -15,7 +16,9 @@
 // z = -e^-y:
 //   H0(y) = -L,  H1(y) = -y L + Li2(z),  H2(y) = -y^2 L + 2 y Li2(z) + 2 Li3(z)
 // are antiderivatives of f, y f, y^2 f (the polylogarithm form of f,
-// Eq. fermidiracspecial).  Below the Fermi level (x < 0) f(x) = 1 - f(-x) turns
+// Eq. fermidiracspecial).  For the entropy density s = -[f ln f + (1-f) ln(1-f)]
+// = L + y f(y) (even in y):  A0(y) = 2 Li2(z) - y L and
+// A1(y) = 3 y Li2(z) + 3 Li3(z) - y^2 L are antiderivatives of s and y s.  Below the Fermi level (x < 0) f(x) = 1 - f(-x) turns
 // every piece into an exact polynomial integral minus an integral over y >= 0,
 // so no large terms cancel.  Li2 and Li3 on z in [-1, 0) are summed from their
 // Bernoulli-number expansions in u = -ln(1 - z), |u| <= ln 2:
@@ -68,6 +71,47 @@ __device__ __forceinline__ void hfun(double y, double& h0, double& h1, double& h
     h0 = -L;
     h1 = -y * L + li2;
     h2 = -y * y * L + 2.0 * y * li2 + 2.0 * li3;
+}
+
+// antiderivatives of s(y) and y s(y), valid for y >= 0 (leading terms beyond y = 40)
+__device__ __forceinline__ void sfun(double y, double& a0, double& a1) {
+    if (y > 40.0) {
+        const double e = exp(-y);
+        a0 = -(y + 2.0) * e;
+        a1 = -((y + 3.0) * y + 3.0) * e;
+        return;
+    }
+    const double L = log1p(exp(-y));
+    const double u = -L;
+    const double li2 = horner(c_li2, u), li3 = horner(c_li3, u);
+    a0 = 2.0 * li2 - y * L;
+    a1 = 3.0 * y * li2 + 3.0 * li3 - y * y * L;
+}
+
+// S_k = int_a^b (e - a)^k s((e - mu)/kT) de, k = 0, 1
+__device__ void entropy_moments(double a, double b, double mu, double kT, double& S0, double& S1) {
+    const double ikT = 1.0 / kT;
+    const double xa = (a - mu) * ikT, xb = (b - mu) * ikT;
+    double s0 = 0.0, s1 = 0.0;  // int (x - xa)^k s(x) dx over [xa, xb]
+    const double p0 = fmax(xa, 0.0);
+    if (xb > p0) {
+        double a0, a1, b0, b1;
+        sfun(p0, a0, a1);
+        sfun(xb, b0, b1);
+        s0 += b0 - a0;
+        s1 += (b1 - a1) - xa * (b0 - a0);
+    }
+    // x < 0: s(x) = s(-x), y = -x in [-x1, -xa]; (x - xa) = -(y + xa)
+    const double x1 = fmin(xb, 0.0);
+    if (x1 > xa) {
+        double a0, a1, b0, b1;
+        sfun(-x1, a0, a1);
+        sfun(-xa, b0, b1);
+        s0 += b0 - a0;
+        s1 -= (b1 - a1) + xa * (b0 - a0);
+    }
+    S0 = kT * s0;
+    S1 = kT * kT * s1;
 }
 
 // M_k = int_a^b (e - a)^k f((e - mu)/kT) de, k = 0, 1, 2
@@ -286,7 +330,7 @@ __global__ void __launch_bounds__(kFermiThreads) k_fermi_round(const double* __r
     if (threadIdx.x == 0) fs[kFsNodes + (r & 1) * 128 + blockIdx.x] = f;
 }
 
-// scal: [0] e_F, [1] E_b, [2] status (0 ok, 1 no bracket), [3] N(e_F), [4] iterations
+// scal: [0] e_F, [1] E_b, [2] status (0 ok, 1 no bracket), [3] N(e_F), [4] iterations, [5] -tau S_s
 __global__ void __launch_bounds__(kFermiThreads) k_fermi_final(const double* __restrict__ Dg, int nE, double e0,
                                                                double de, double kT, double tol, int max_iter,
                                                                const double* __restrict__ fs, int rounds,
@@ -298,24 +342,29 @@ __global__ void __launch_bounds__(kFermiThreads) k_fermi_final(const double* __r
     stage_D(Dg, nE, sD);
     const double eF = b.exact ? b.lo : 0.5 * (b.lo + b.hi);
     const int status = b.status, it = b.it;
-    // weights at e_F, the band energy and the electron count
-    double pn = 0.0, pe = 0.0;
+    // weights at e_F, the band energy, the entropy term and the electron count
+    double pn = 0.0, pe = 0.0, ps = 0.0;
     for (int x = threadIdx.x; x < nE; x += blockDim.x) {
-        double w0 = 0.0, w1 = 0.0;
+        double w0 = 0.0, w1 = 0.0, ws = 0.0;
         const double ex = e0 + x * de;
         if (x > 0) {  // right half of hat_x on [e_{x-1}, e_x]
             const double a = e0 + (x - 1) * de;
-            double M0, M1, M2;
+            double M0, M1, M2, S0, S1;
             interval_moments(a, ex, eF, kT, M0, M1, M2);
+            entropy_moments(a, ex, eF, kT, S0, S1);
             w0 += M1 / de;
             w1 += (a * M1 + M2) / de;
+            ws += S1 / de;
         }
         if (x < nE - 1) {  // left half of hat_x on [e_x, e_{x+1}]
-            double M0, M1, M2;
+            double M0, M1, M2, S0, S1;
             interval_moments(ex, ex + de, eF, kT, M0, M1, M2);
+            entropy_moments(ex, ex + de, eF, kT, S0, S1);
             w0 += M0 - M1 / de;
             w1 += ex * M0 + M1 - (ex * M1 + M2) / de;
+            ws += S0 - S1 / de;
         }
+        ps += ws * sD[x];
         w0d[x] = w0;
         w0f[x] = (float)w0;
         pn += w0 * sD[x];
@@ -323,12 +372,14 @@ __global__ void __launch_bounds__(kFermiThreads) k_fermi_final(const double* __r
     }
     const double Nf = block_sum(pn, sred);
     const double Eb = block_sum(pe, sred);
+    const double Sk = block_sum(ps, sred);  // S_s / k_B
     if (threadIdx.x == 0) {
         scal[0] = eF;
         scal[1] = Eb;
         scal[2] = (double)status;
         scal[3] = Nf;
         scal[4] = (double)it;
+        scal[5] = -kT * Sk;  // -tau S_s in eV
     }
 }
 
@@ -533,7 +584,7 @@ int electron_count_at(Ctx* c, const double* D_host, const mala_energy_grid* eg, 
 }
 
 int integrate(Ctx* c, const void* ldos, int64_t P, double volume, const mala_energy_grid* eg, const double* dos_sum,
-              void* density, double* dos_host, double* fermi, double* eb, double* ne, mala_precision prec,
+              void* density, double* dos_host, double* fermi, double* eb, double* ne, double* ts, mala_precision prec,
               cudaStream_t st) {
     const int nE = eg->n_E;
     // workspace: dsum[nE] | D[nE] | w0d[nE] | w0f[nE] (float) | scal[8] | nsum[1] | partial rows
@@ -600,6 +651,7 @@ int integrate(Ctx* c, const void* ldos, int64_t P, double volume, const mala_ene
     if (fermi) *fermi = hs[0];
     if (eb) *eb = hs[1];
     if (ne) *ne = dV * hs[8];
+    if (ts) *ts = hs[5];
     if (hs[2] != 0.0)
         return fail(MALA_ERR_FERMI_BRACKET, "N(mu) - N_e has no sign change on [e0 - 20 kT, e_max + 20 kT]");
     return MALA_OK;
@@ -646,7 +698,7 @@ int scratch_address(int device, double** out) {
 
 int integrate_noalloc(Ctx* c, const void* ldos, int64_t P, double volume, const mala_energy_grid* eg,
                       const double* dos_sum, void* density, double* dos_host, double* fermi, double* eb, double* ne,
-                      mala_precision prec, cudaStream_t st) {
+                      double* ts, mala_precision prec, cudaStream_t st) {
     const int nE = eg->n_E;
     double* scratch = nullptr;
     MALA_TRY(scratch_address(c->device, &scratch));
@@ -705,6 +757,7 @@ int integrate_noalloc(Ctx* c, const void* ldos, int64_t P, double volume, const 
     if (fermi) *fermi = hs[0];
     if (eb) *eb = hs[1];
     if (ne) *ne = dV * hs[8];
+    if (ts) *ts = hs[5];
     if (hs[2] != 0.0)
         return fail(MALA_ERR_FERMI_BRACKET, "N(mu) - N_e has no sign change on [e0 - 20 kT, e_max + 20 kT]");
     return MALA_OK;

@@ -269,14 +269,15 @@ int model_upload(Ctx* c, const mala_mlp_desc* d, Model* m);
 void server_stop(Ctx* c);
 int integrate_noalloc(Ctx* c, const void* ldos, int64_t P, double volume, const mala_energy_grid* eg,
                       const double* dos_sum, void* density, double* dos_host, double* fermi, double* eb, double* ne,
-                      mala_precision prec, cudaStream_t st);
+                      double* ts, mala_precision prec, cudaStream_t st);
 int electron_count_at(Ctx* c, const double* D_host, const mala_energy_grid* eg, double mu, double* out,
                       cudaStream_t st);
 void model_free(Model* m);
 int mlp_forward(Ctx* c, const Model* m, const void* B, int64_t P, void* ldos, double* dos_sum,
                 mala_precision prec, cudaStream_t st);
+// ts: the entropy term -tau S_s (eV) of Eqs. electronicentropyDOS / KSfreeenergy, may be NULL
 int integrate(Ctx* c, const void* ldos, int64_t P, double volume, const mala_energy_grid* eg,
               const double* dos_sum, void* density, double* dos_host, double* fermi, double* eb,
-              double* ne, mala_precision prec, cudaStream_t st);
+              double* ne, double* ts, mala_precision prec, cudaStream_t st);
 
 }  // namespace mala

@@ -56,7 +56,8 @@ static int run_path(Ctx* c, const mala_snapshot* snap, const mala_bispectrum_par
     MALA_TRY(snap_descriptors(c, snap, bp, B, nullptr, prec, st));
     MALA_TRY(mlp_forward(c, m, B, P, ldos, dos_sum, prec, st));
     double eF = 0.0, Eb = 0.0, Ne = 0.0;
-    int rc = integrate(c, ldos, P, cell_volume(snap), eg, dos_sum, dens, dos_host, &eF, &Eb, &Ne, prec, st);
+    double TS = 0.0;
+    int rc = integrate(c, ldos, P, cell_volume(snap), eg, dos_sum, dens, dos_host, &eF, &Eb, &Ne, &TS, prec, st);
     res->status = rc;
     res->n_B = n_triples(bp->twojmax);
     res->n_E = eg->n_E;
@@ -64,6 +65,7 @@ static int run_path(Ctx* c, const mala_snapshot* snap, const mala_bispectrum_par
     res->fermi_eV = eF;
     res->band_energy_eV = Eb;
     res->electron_count = Ne;
+    res->entropy_term_eV = TS;
     res->B_dev = B;
     res->ldos_dev = ldos;
     res->density_dev = dens;
@@ -305,7 +307,8 @@ int mala_ldos_forward(mala_ctx* c, const mala_model* m, const void* B_dev, int64
 
 int mala_integrate(mala_ctx* c, const void* ldos_dev, int64_t P, double cell_volume_, const mala_energy_grid* eg,
                    const double* dos_sum_dev, void* density_dev, double* dos_host, double* fermi_eV,
-                   double* band_energy_eV, double* electron_count, mala_precision precision, void* stream) {
+                   double* band_energy_eV, double* electron_count, double* entropy_term_eV, mala_precision precision,
+                   void* stream) {
     if (!c || P < 0 || (P > 0 && !ldos_dev && !dos_sum_dev)) return fail(MALA_ERR_INVALID_ARG, "bad arguments");
     MALA_TRY(check_egrid(eg));
     if (!(cell_volume_ > 0.0)) return fail(MALA_ERR_INVALID_ARG, "cell volume must be > 0");
@@ -314,13 +317,13 @@ int mala_integrate(mala_ctx* c, const void* ldos_dev, int64_t P, double cell_vol
     std::lock_guard<std::mutex> lk(c->mu);
     MALA_CUDA_TRY(cudaSetDevice(c->device));
     return integrate(c, ldos_dev, P, cell_volume_, eg, dos_sum_dev, density_dev, dos_host, fermi_eV, band_energy_eV,
-                     electron_count, precision, as_stream(stream));
+                     electron_count, entropy_term_eV, precision, as_stream(stream));
 }
 
 int mala_integrate_noalloc(mala_ctx* c, const void* ldos_dev, int64_t P, double cell_volume_,
                            const mala_energy_grid* eg, const double* dos_sum_dev, void* density_dev, double* dos_host,
                            double* fermi_eV, double* band_energy_eV, double* electron_count,
-                           mala_precision precision, void* stream) {
+                           double* entropy_term_eV, mala_precision precision, void* stream) {
     if (!c || P < 0 || (P > 0 && !ldos_dev && !dos_sum_dev)) return fail(MALA_ERR_INVALID_ARG, "bad arguments");
     MALA_TRY(check_egrid(eg));
     if (!(cell_volume_ > 0.0)) return fail(MALA_ERR_INVALID_ARG, "cell volume must be > 0");
@@ -329,7 +332,7 @@ int mala_integrate_noalloc(mala_ctx* c, const void* ldos_dev, int64_t P, double 
     std::lock_guard<std::mutex> lk(c->mu);
     MALA_CUDA_TRY(cudaSetDevice(c->device));
     return integrate_noalloc(c, ldos_dev, P, cell_volume_, eg, dos_sum_dev, density_dev, dos_host, fermi_eV,
-                             band_energy_eV, electron_count, precision, as_stream(stream));
+                             band_energy_eV, electron_count, entropy_term_eV, precision, as_stream(stream));
 }
 
 int mala_electron_count(mala_ctx* c, const double* dos_host, const mala_energy_grid* eg, double mu, double* count) {
@@ -396,10 +399,10 @@ int mala_predict_batch(mala_ctx* c, int32_t n, const mala_snapshot* snaps, const
     int first_rc = MALA_OK;
     for (int i = 0; i < n; ++i) {
         const int64_t Pi = row[i + 1] - row[i];
-        double eF = 0.0, Eb = 0.0, Ne = 0.0;
+        double eF = 0.0, Eb = 0.0, Ne = 0.0, TS = 0.0;
         const int rc = integrate(c, L + (size_t)row[i] * nE * l, Pi, cell_volume(&snaps[i]), &egs[i], nullptr,
-                                 D + (size_t)row[i] * e, c->batch_dos.data() + (size_t)i * nE, &eF, &Eb, &Ne, prec,
-                                 st);
+                                 D + (size_t)row[i] * e, c->batch_dos.data() + (size_t)i * nE, &eF, &Eb, &Ne, &TS,
+                                 prec, st);
         if (rc != MALA_OK && rc != MALA_ERR_FERMI_BRACKET) return rc;
         if (rc != MALA_OK && first_rc == MALA_OK) first_rc = rc;
         mala_result& r = res[i];
@@ -410,6 +413,7 @@ int mala_predict_batch(mala_ctx* c, int32_t n, const mala_snapshot* snaps, const
         r.fermi_eV = eF;
         r.band_energy_eV = Eb;
         r.electron_count = Ne;
+        r.entropy_term_eV = TS;
         r.dos = c->batch_dos.data() + (size_t)i * nE;
         r.B_dev = B + (size_t)row[i] * nB * e;
         r.ldos_dev = L + (size_t)row[i] * nE * l;

@@ -53,6 +53,7 @@ def test_fp64_integrals_match_oracle(nE, de, e0, P):
     np.testing.assert_allclose(out["dos"], ref["dos"], rtol=1e-12)
     assert out["fermi"] == pytest.approx(ref["fermi"], abs=1e-9)
     assert out["band_energy"] == pytest.approx(ref["band_energy"], rel=1e-10, abs=1e-10)
+    assert out["entropy_term"] == pytest.approx(ref["entropy_term"], rel=1e-10, abs=1e-12)
     np.testing.assert_allclose(out["density"].cpu().numpy(), ref["density"], rtol=1e-10, atol=1e-12)
     assert out["electron_count"] == pytest.approx(Ne, rel=1e-9)
     # the library's own electron count at the oracle's Fermi level
@@ -87,6 +88,7 @@ def test_mixed_integrals_match_oracle_on_the_same_bf16_values():
     np.testing.assert_allclose(out["dos"], ref["dos"], rtol=2e-6)
     assert out["fermi"] == pytest.approx(ref["fermi"], abs=1e-5)
     assert out["band_energy"] == pytest.approx(ref["band_energy"], rel=2e-6)
+    assert out["entropy_term"] == pytest.approx(ref["entropy_term"], rel=2e-6)
     np.testing.assert_allclose(out["density"].double().cpu().numpy(), ref["density"], rtol=2e-6, atol=1e-7)
     assert out["electron_count"] == pytest.approx(Ne, rel=1e-6)
 
@@ -116,3 +118,21 @@ def test_fermi_bracket_error():
     np.testing.assert_allclose(out["dos"], np.ones(11) * 32.0, rtol=1e-14)
     with pytest.raises(_lib.MalaError):
         ctx().integrate(torch.from_numpy(L).cuda(), 32.0, eg, api.FP64_PLAIN, n_electrons=-1.0)
+
+
+@pytest.mark.parametrize("kT", [0.0259, 0.3, 1e-3])
+def test_entropy_term_matches_oracle_across_temperatures(kT):
+    # closed forms (Li2/Li3 antiderivatives of s and y s) against quadrature of the definition
+    torch = need_gpu()
+    from paper_2411_19617_gb300 import api
+    eg = wl.EnergyGrid(n_E=60, e0_eV=-3.0, de_eV=0.1, kT_eV=kT)
+    P = 4000
+    L = _synthetic_ldos(P, eg, seed=21)
+    vol = 900.0
+    D = oracle.dos(L, vol / P)
+    Ne = oracle.electron_count(D, 0.05, eg.e0_eV, eg.de_eV, eg.kT_eV)
+    ref = oracle.observables(L, vol / P, eg.e0_eV, eg.de_eV, eg.kT_eV, Ne)
+    out = ctx().integrate(torch.from_numpy(L).cuda(), vol, eg, api.FP64_PLAIN, n_electrons=Ne)
+    assert out["fermi"] == pytest.approx(ref["fermi"], abs=1e-9)
+    assert out["entropy_term"] == pytest.approx(ref["entropy_term"], rel=1e-9, abs=1e-13)
+    assert out["entropy_term"] <= 0.0

@@ -34,11 +34,11 @@ def _call(fn, ctx, ldos, P, vol, eg, ne, dos_sum, dens, precision, stream):
     e = _lib.EnergyGrid()
     e.n_E, e.e0_eV, e.de_eV, e.kT_eV, e.n_electrons = eg.n_E, eg.e0_eV, eg.de_eV, eg.kT_eV, ne
     D = np.zeros(eg.n_E)
-    eF, Eb, Ne = C.c_double(0), C.c_double(0), C.c_double(0)
+    eF, Eb, Ne, TS = C.c_double(0), C.c_double(0), C.c_double(0), C.c_double(0)
     rc = fn(ctx.h, C.c_void_p(ldos.data_ptr()), P, vol, C.byref(e),
             C.c_void_p(dos_sum.data_ptr()) if dos_sum is not None else None, C.c_void_p(dens.data_ptr()),
-            D.ctypes.data_as(C.c_void_p), C.byref(eF), C.byref(Eb), C.byref(Ne), precision, stream)
-    return rc, D, eF.value, Eb.value, Ne.value, dens.double().cpu().numpy()
+            D.ctypes.data_as(C.c_void_p), C.byref(eF), C.byref(Eb), C.byref(Ne), C.byref(TS), precision, stream)
+    return rc, D, eF.value, Eb.value, Ne.value, dens.double().cpu().numpy(), TS.value
 
 
 @pytest.mark.parametrize("precision", ["mixed", "fp64"])
@@ -75,6 +75,7 @@ def test_noalloc_matches_integrate_twice(precision, with_dos_sum):
             assert got[3] == pytest.approx(ref[3], rel=rtol)
             assert got[4] == pytest.approx(ref[4], rel=rtol)
             np.testing.assert_allclose(got[5], ref[5], rtol=rtol, atol=1e-12)
+            assert got[6] == pytest.approx(ref[6], rel=rtol)
     ctx.close()
 
 
