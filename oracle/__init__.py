@@ -10,6 +10,8 @@ Contents, each following the passage of the paper cited at the function:
 
 * descriptors (C, ``mala_oracle.c``): neighbours by brute force, explicit
   SU(2) representation matrices, Racah Clebsch-Gordan coefficients, Z and B;
+* ``gaussian_grid``: the Gaussian representation of the atoms on the grid
+  (Sec. "Total energy calculation", Eq. structfact_function);
 * ``mlp_forward``: the feed-forward network of Eq. (ffnn) in FP64;
 * ``integration_weights``: w_xi = int hat_xi(e) e^n f_beta(e - mu) de for the
   piecewise-linear reading of the LDOS/DOS between energy-grid points
@@ -159,6 +161,26 @@ def neighbor_lists(snap, rcut: float, points: Optional[np.ndarray] = None, cap: 
     if np.any(counts > cap):
         raise ValueError("neighbour capacity exceeded")
     return counts, atoms, shifts
+
+
+def gaussian_grid(snap, rcut: float, sigma: float, points: Optional[np.ndarray] = None) -> np.ndarray:
+    """Gaussian descriptors: the Gaussian representation of the atomic positions
+    sampled on the grid (Eq. structfact_function with f a Gaussian of width
+    sigma): G(r) = sum over the neighbours (atom, image) of r within rcut (the
+    exact membership rule of ``neighbor_lists``) of exp(-|R + sL - r|^2 / (2 sigma^2))."""
+    L, _, grid = _cell_args(snap)
+    pts = np.arange(snap.n_points) if points is None else np.asarray(points, np.int64)
+    counts, atoms, shifts = neighbor_lists(snap, rcut, points=pts)
+    wrapped = wrap_positions(snap)
+    out = np.zeros(len(pts))
+    for i, p in enumerate(pts):
+        n = counts[i]
+        if n == 0:
+            continue
+        r = grid_point(snap, int(p))
+        d = wrapped[atoms[i, :n]] + shifts[i, :n] * np.asarray(L)[None, :] - r[None, :]
+        out[i] = float(np.sum(np.exp(-np.sum(d * d, axis=1) / (2.0 * sigma * sigma))))
+    return out
 
 
 def bispectrum_grid(snap, bp, points: Optional[np.ndarray] = None, nthreads: int = 1) -> np.ndarray:

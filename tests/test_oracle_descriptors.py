@@ -367,3 +367,42 @@ def test_lattice_translation_invariance():
     moved = (ix + 1) % 6 + (pts - ix)
     B3 = oracle.bispectrum_grid(snap3, bp, points=moved)
     np.testing.assert_allclose(B3, B0, rtol=1e-9)
+
+
+# ---- Gaussian descriptors (Eq. structfact_function with a Gaussian f) ------------
+
+def _gauss_cell(seed, n=3, L=6.0, grid=24):
+    from paper_2411_19617_gb300 import workloads as wl
+    rng = np.random.default_rng(seed)
+    return wl.Snapshot(pos=rng.uniform(0.0, L, size=(n, 3)), species=np.zeros(n, np.int32),
+                       cell=np.diag([L, L, L]), grid=(grid, grid, grid))
+
+
+def test_gaussian_grid_integrates_to_the_gaussian_mass():
+    # periodic cell, grid spacing sigma/2, cutoff 8 sigma: the Riemann sum of a
+    # periodic Gaussian sum equals its integral N (2 pi sigma^2)^(3/2) up to
+    # exp(-2 pi^2 sigma^2 / h^2) (Poisson summation) and the mass beyond 8 sigma
+    sigma = 0.5
+    snap = _gauss_cell(1)
+    G = oracle.gaussian_grid(snap, 8 * sigma, sigma)
+    dV = snap.volume / snap.n_points
+    assert dV * G.sum() == pytest.approx(snap.n_atoms * (2 * np.pi * sigma ** 2) ** 1.5, rel=1e-9)
+
+
+def test_gaussian_grid_single_atom_on_a_grid_point():
+    from paper_2411_19617_gb300 import workloads as wl
+    snap = wl.Snapshot(pos=np.array([[2.5, 5.0, 7.5]]), species=np.zeros(1, np.int32),
+                       cell=np.diag([10.0, 10.0, 10.0]), grid=(20, 20, 20))
+    p = 5 + 20 * (10 + 20 * 15)  # the grid point at (2.5, 5.0, 7.5)
+    G = oracle.gaussian_grid(snap, 3.0, 0.4, points=np.array([p, p + 1]))
+    assert G[0] == 1.0
+    assert G[1] == pytest.approx(np.exp(-0.5 ** 2 / (2 * 0.4 ** 2)), rel=1e-14)
+
+
+def test_gaussian_grid_lattice_translation_invariance():
+    snap = _gauss_cell(2, grid=10)
+    G = oracle.gaussian_grid(snap, 2.0, 0.45)
+    from paper_2411_19617_gb300 import workloads as wl
+    moved = wl.Snapshot(pos=snap.pos + np.array([6.0, -12.0, 6.0]), species=snap.species, cell=snap.cell,
+                        grid=snap.grid)
+    np.testing.assert_allclose(oracle.gaussian_grid(moved, 2.0, 0.45), G, rtol=1e-12, atol=1e-300)
