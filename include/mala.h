@@ -176,6 +176,15 @@ int mala_descriptors(mala_ctx* ctx, const mala_snapshot* snap, const mala_bispec
 int mala_descriptors_batch(mala_ctx* ctx, int32_t n, const mala_snapshot* snaps, const mala_bispectrum_params* bp,
                            void* B_dev, mala_precision precision, void* stream);
 
+/* Gaussian descriptors (Sec. "Total energy calculation", Eq. structfact_function
+ * with a Gaussian f, the "Gaussian representation" of the atomic positions):
+ * for every grid point r, G(r) = sum over atoms alpha and periodic images s
+ * with |R_alpha + s L - r| < rcut (the membership rule of mala_neighbor_lists)
+ * of exp(-|R_alpha + s L - r|^2 / (2 sigma^2)).  G_dev: device [P], float for
+ * MALA_MIXED (offsets as float pairs, FP32 sum), double for MALA_FP64_PLAIN. */
+int mala_gaussian_descriptors(mala_ctx* ctx, const mala_snapshot* snap, double rcut, double sigma, void* G_dev,
+                              mala_precision precision, void* stream);
+
 /* Expansion coefficients u^J of Eq. (SNAPExpansion) for every grid point,
  * J = 0..twojmax, device complex output u_dev[P][sum_J (J+1)^2][2] (row-major
  * [ma][mb] blocks in increasing J; float for MIXED, double for FP64_PLAIN). */

@@ -89,6 +89,8 @@ PROTOTYPES = {
     "mala_predict_batch": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(Snapshot), C.POINTER(BispectrumParams),
                                      C.c_void_p, C.POINTER(EnergyGrid), C.c_int, C.c_void_p, C.POINTER(Result),
                                      C.c_void_p]),
+    "mala_gaussian_descriptors": (C.c_int, [C.c_void_p, C.POINTER(Snapshot), C.c_double, C.c_double, C.c_void_p,
+                                            C.c_int, C.c_void_p]),
     "mala_descriptors_batch": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(Snapshot), C.POINTER(BispectrumParams),
                                          C.c_void_p, C.c_int, C.c_void_p]),
     "mala_submit": (C.c_int, [C.c_void_p, C.POINTER(Snapshot), C.POINTER(BispectrumParams), C.c_void_p,

@@ -213,6 +213,19 @@ class Context:
                                      _stream_ptr(stream)), "mala_descriptors")
         return out
 
+    def gaussian_descriptors(self, snap, rcut: float, sigma: float, precision: int = MIXED, out=None, stream=None):
+        """G[P] = sum over neighbours within rcut of exp(-d^2 / (2 sigma^2)) on the GPU."""
+        torch = _torch()
+        P = int(np.prod(snap.grid))
+        dt = torch.float32 if precision == MIXED else torch.float64
+        if out is None:
+            out = torch.empty(P, dtype=dt, device=torch.device("cuda", self.device))
+        a = _SnapshotArgs(snap)
+        check(lib().mala_gaussian_descriptors(self.h, C.byref(a.c), float(rcut), float(sigma),
+                                              C.c_void_p(out.data_ptr()), int(precision), _stream_ptr(stream)),
+              "mala_gaussian_descriptors")
+        return out
+
     def descriptors_batch(self, snaps, bp, precision: int = MIXED, out=None, stream=None):
         """B of several snapshots in one pass: rows of snapshot i follow those of
         snapshot i-1 ([sum P_i][n_B] on the GPU)."""

@@ -135,7 +135,8 @@ static int run_descriptors(Ctx* c, int nsnap, const mala_snapshot* snaps, const 
     MALA_CUDA_TRY(cudaMemcpyAsync(bs, c->host_batch, sizeof(BatchSnap) * nsnap, cudaMemcpyHostToDevice, st));
     const int tj = bp->twojmax;
     const int nh = n_half(tj);
-    int kmax = c->kmax_hint;
+    const bool gauss_mode = dbg && dbg->gauss;  // Gaussian descriptors: no neighbour records
+    int kmax = gauss_mode ? 0 : c->kmax_hint;
     for (int attempt = 0; attempt < 3; ++attempt) {
         const size_t per_tile = (size_t)nh * 32 * 2 * sizeof(T) + (size_t)kmax * 32 * (5 * sizeof(T)) + 32 * sizeof(int);
         const size_t chunk_budget = (size_t)4 << 30;
@@ -157,6 +158,8 @@ static int run_descriptors(Ctx* c, int nsnap, const mala_snapshot* snaps, const 
             nb.dbg_shifts = dbg->dbg_shifts;
             nb.dbg_counts = dbg->dbg_counts;
             nb.dbg_cap = dbg->dbg_cap;
+            nb.gauss = dbg->gauss;
+            nb.gauss_inv2s2 = dbg->gauss_inv2s2;
         }
         for (int i = 0; i < nsnap; ++i) MALA_CUDA_TRY(cudaMemsetAsync(hb[i].sd.maxcnt, 0, sizeof(int), st));
         for (int64_t t0 = 0; t0 < tiles; t0 += chunk) {
@@ -192,6 +195,7 @@ static int run_descriptors(Ctx* c, int nsnap, const mala_snapshot* snaps, const 
             return fail(MALA_ERR_UNSUPPORTED, "a bispectrum partial sum exceeded 1e9 (outside the fixed-point range)");
         }
         if (dbg) dbg->kmax = maxcnt;
+        if (gauss_mode) return MALA_OK;
         if (maxcnt <= kmax) {
             if (maxcnt > c->kmax_hint) c->kmax_hint = maxcnt;
             return MALA_OK;
@@ -206,6 +210,16 @@ int snap_descriptors(Ctx* c, const mala_snapshot* snap, const mala_bispectrum_pa
                      mala_precision prec, cudaStream_t st) {
     if (prec == MALA_MIXED) return run_descriptors<float>(c, 1, snap, bp, (float*)B, (float*)u_full, nullptr, st);
     return run_descriptors<double>(c, 1, snap, bp, (double*)B, (double*)u_full, nullptr, st);
+}
+
+int snap_gaussian(Ctx* c, const mala_snapshot* snap, double rcut, double sigma, void* G, mala_precision prec,
+                  cudaStream_t st) {
+    mala_bispectrum_params bp = {0, rcut, 0.99363, 0.0, 1.0, 0, nullptr};
+    NbrOut gd;
+    gd.gauss = G;
+    gd.gauss_inv2s2 = 1.0 / (2.0 * sigma * sigma);
+    if (prec == MALA_MIXED) return run_descriptors<float>(c, 1, snap, &bp, nullptr, nullptr, &gd, st);
+    return run_descriptors<double>(c, 1, snap, &bp, nullptr, nullptr, &gd, st);
 }
 
 int snap_descriptors_batch(Ctx* c, int n, const mala_snapshot* snaps, const mala_bispectrum_params* bp, void* B,
@@ -401,6 +415,19 @@ int mala_descriptors_batch(mala_ctx* c, int32_t n, const mala_snapshot* snaps, c
     std::lock_guard<std::mutex> lk(c->mu);
     MALA_CUDA_TRY(cudaSetDevice(c->device));
     return snap_descriptors_batch(c, n, snaps, bp, B_dev, precision, as_stream(stream));
+}
+
+int mala_gaussian_descriptors(mala_ctx* c, const mala_snapshot* snap, double rcut, double sigma, void* G_dev,
+                              mala_precision precision, void* stream) {
+    if (!c) return fail(MALA_ERR_INVALID_ARG, "context is NULL");
+    MALA_TRY(check_snapshot(snap));
+    if (!(rcut > 0.0) || !std::isfinite(rcut)) return fail(MALA_ERR_INVALID_ARG, "rcut must be > 0");
+    if (!(sigma > 0.0) || !std::isfinite(sigma)) return fail(MALA_ERR_INVALID_ARG, "sigma must be > 0");
+    if (!G_dev) return fail(MALA_ERR_INVALID_ARG, "output is NULL");
+    if (precision != MALA_MIXED && precision != MALA_FP64_PLAIN) return fail(MALA_ERR_INVALID_ARG, "bad precision");
+    std::lock_guard<std::mutex> lk(c->mu);
+    MALA_CUDA_TRY(cudaSetDevice(c->device));
+    return snap_gaussian(c, snap, rcut, sigma, G_dev, precision, as_stream(stream));
 }
 
 int mala_expansion_coefficients(mala_ctx* c, const mala_snapshot* snap, const mala_bispectrum_params* bp,

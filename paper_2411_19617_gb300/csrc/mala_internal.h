@@ -215,6 +215,10 @@ struct NbrOut {
     int* dbg_shifts = nullptr; // [P][dbg_cap][3]
     int* dbg_counts = nullptr; // [P]
     int dbg_cap = 0;
+    // Gaussian descriptors: when set, each point's sum of exp(-d^2 / (2 sigma^2))
+    // over its neighbours goes to gauss[row] (float or double) instead of records
+    void* gauss = nullptr;
+    double gauss_inv2s2 = 0.0;  // 1 / (2 sigma^2)
 };
 
 // tiles [tile0, tile0 + ntiles) of the batch bs[0..nsnap) (device array)
@@ -248,6 +252,9 @@ int upload_ui_tables();
 int upload_zb_lists_f64(const int* lists, int bytes);
 int snap_descriptors(Ctx* c, const mala_snapshot* snap, const mala_bispectrum_params* bp, void* B,
                      void* u_full, mala_precision prec, cudaStream_t st);
+// Gaussian descriptors G(r) of one snapshot into G (float for MIXED, double for FP64_PLAIN)
+int snap_gaussian(Ctx* c, const mala_snapshot* snap, double rcut, double sigma, void* G, mala_precision prec,
+                  cudaStream_t st);
 // descriptors of n snapshots in one pass of launches; B rows concatenated in snapshot order
 int snap_descriptors_batch(Ctx* c, int n, const mala_snapshot* snaps, const mala_bispectrum_params* bp, void* B,
                            mala_precision prec, cudaStream_t st);

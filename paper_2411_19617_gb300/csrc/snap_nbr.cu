@@ -193,6 +193,8 @@ __device__ __forceinline__ void sincos_t(float x, float* s, float* c) { sincosf(
 __device__ __forceinline__ void sincos_t(double x, double* s, double* c) { ::sincos(x, s, c); }
 __device__ __forceinline__ float cospi_t(float x) { return cospif(x); }
 __device__ __forceinline__ double cospi_t(double x) { return ::cospi(x); }
+__device__ __forceinline__ float exp_t(float x) { return expf(x); }
+__device__ __forceinline__ double exp_t(double x) { return ::exp(x); }
 __device__ __forceinline__ float sqrt_t(float x) { return sqrtf(x); }
 __device__ __forceinline__ double sqrt_t(double x) { return ::sqrt(x); }
 
@@ -219,12 +221,12 @@ __device__ __forceinline__ void cayley_klein(T dx, T dy, T dz, T inv_range, T rm
     }
 }
 
-template <class T>
+template <class T, bool GAUSS>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     k_neighbors(const BatchSnap* __restrict__ batch, int nsnap, double rcut, double rfac0, double rmin0, int64_t tile0,
                 int64_t ntiles, typename AB<T>::type* __restrict__ out_ab, T* __restrict__ out_cw,
                 int* __restrict__ out_cnt, int kmax, int* __restrict__ dbg_atoms, int* __restrict__ dbg_shifts,
-                int* __restrict__ dbg_counts, int dbg_cap) {
+                int* __restrict__ dbg_counts, int dbg_cap, T* __restrict__ gauss, T g_inv2s2) {
     __shared__ Cand cand[kWarpsPerBlock][kCand];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t tl = (int64_t)blockIdx.x * kWarpsPerBlock + warp;  // tile index within this launch
@@ -290,7 +292,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     const T rmin0_t = T(rmin0);
 
     int count = 0;
-    int nc = 0;  // candidates buffered
+    T gsum = T(0);  // Gaussian descriptor of the lane's point
+    int nc = 0;     // candidates buffered
     Cand* cw = cand[warp];
     const double* wx = sd.wpos;
     const double* wy = sd.wpos + n;
@@ -321,7 +324,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
                 }
             }
             if (valid && in) {
-                if (count < kmax) {
+                if (GAUSS || count < kmax) {
                     typename AB<T>::type ab;
                     T fc;
                     T ex, ey, ez;
@@ -339,10 +342,14 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
                         pair_add(cd.z, cd.lz, -prz, -plz, h, l);
                         ez = h;
                     }
-                    cayley_klein<T>(ex, ey, ez, inv_range, rmin0_t, rfac0_pi, ab, fc);
-                    const size_t o = ((size_t)tl * kmax + count) * 32 + lane;
-                    out_ab[o] = ab;
-                    out_cw[o] = (T)sd.wsp[cd.atom] * fc;
+                    if constexpr (GAUSS) {
+                        gsum += exp_t(-(ex * ex + ey * ey + ez * ez) * g_inv2s2);
+                    } else {
+                        cayley_klein<T>(ex, ey, ez, inv_range, rmin0_t, rfac0_pi, ab, fc);
+                        const size_t o = ((size_t)tl * kmax + count) * 32 + lane;
+                        out_ab[o] = ab;
+                        out_cw[o] = (T)sd.wsp[cd.atom] * fc;
+                    }
                 }
                 if (dbg_atoms && count < dbg_cap) {
                     dbg_atoms[(size_t)p * dbg_cap + count] = cd.atom;
@@ -414,6 +421,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
         }
     }
     flush();
+    if constexpr (GAUSS)
+        if (valid) gauss[batch[si].row_off + p] = gsum;
     if (valid && dbg_counts) dbg_counts[p] = count;
     out_cnt[tl * 32 + lane] = valid ? min(count, kmax) : 0;
     const int wmax = __reduce_max_sync(0xffffffffu, valid ? count : 0);
@@ -546,10 +555,11 @@ static void launch_neighbors_t(const BatchSnap* bs, int nsnap, double rcut, doub
                                int64_t ntiles, const NbrOut& out, cudaStream_t st) {
     if (ntiles <= 0) return;
     const unsigned blocks = (unsigned)((ntiles + kWarpsPerBlock - 1) / kWarpsPerBlock);
-    k_neighbors<T><<<blocks, kWarpsPerBlock * 32, 0, st>>>(
+    auto kern = out.gauss ? k_neighbors<T, true> : k_neighbors<T, false>;
+    kern<<<blocks, kWarpsPerBlock * 32, 0, st>>>(
         bs, nsnap, rcut, rfac0, rmin0, tile0, ntiles, reinterpret_cast<typename AB<T>::type*>(out.ab),
         reinterpret_cast<T*>(out.cw), out.cnt, out.kmax, out.dbg_atoms, out.dbg_shifts, out.dbg_counts,
-        out.dbg_cap);
+        out.dbg_cap, reinterpret_cast<T*>(out.gauss), (T)out.gauss_inv2s2);
 }
 
 void launch_neighbors(const BatchSnap* bs, int nsnap, double rcut, double rfac0, double rmin0, int64_t tile0,
