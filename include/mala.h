@@ -227,7 +227,7 @@ int mala_integrate(mala_ctx* ctx, const void* ldos_dev, int64_t P, double cell_v
  * synchronisation an allocation may imply).  Arguments, outputs and results
  * are those of mala_integrate; every scratch buffer comes from one fixed
  * static device array of MALA_NOALLOC_SCRATCH_BYTES that each GPU loading the
- * library holds until the process exits.  Limit: 3.5 n_E + 296 + max(
+ * library holds until the process exits.  Limit: 9.5 n_E + 296 + max(
  * ceil(P/128) n_E [only when dos_sum_dev is NULL], min(ceil(P/8), 16 x SMs))
  * doubles must fit in the array; larger sizes return MALA_ERR_UNSUPPORTED
  * with the numbers in the message.  The first call on a device looks up the

@@ -330,10 +330,37 @@ __global__ void __launch_bounds__(kFermiThreads) k_fermi_round(const double* __r
     if (threadIdx.x == 0) fs[kFsNodes + (r & 1) * 128 + blockIdx.x] = f;
 }
 
+// Weights at e_F, one thread per energy interval [e_i, e_{i+1}], spread over
+// many CTAs (the closed forms are FP64-heavy): the interval's moments give the
+// right part of hat_i and the left part of hat_{i+1}; iv[i] holds
+// (w0, w1, wS) of hat_i's part and (w0, w1, wS) of hat_{i+1}'s part.
+constexpr int kIvPerCta = 32;
+
+__global__ void __launch_bounds__(kIvPerCta) k_fermi_intervals(int nE, double e0, double de, double kT, double tol,
+                                                              int max_iter, const double* __restrict__ fs, int rounds,
+                                                              double* __restrict__ iv) {
+    const Bracket b = round_start(fs, rounds, e0, de, kT, nE, tol, max_iter);
+    const double eF = b.exact ? b.lo : 0.5 * (b.lo + b.hi);
+    const int i = blockIdx.x * kIvPerCta + threadIdx.x;
+    if (i >= nE - 1) return;
+    const double a = e0 + i * de;
+    double M0, M1, M2, S0, S1;
+    interval_moments(a, a + de, eF, kT, M0, M1, M2);
+    entropy_moments(a, a + de, eF, kT, S0, S1);
+    double* o = iv + 6 * (size_t)i;
+    o[0] = M0 - M1 / de;                          // hat_i: (e_{i+1} - e) / de
+    o[1] = a * M0 + M1 - (a * M1 + M2) / de;
+    o[2] = S0 - S1 / de;
+    o[3] = M1 / de;                               // hat_{i+1}: (e - e_i) / de
+    o[4] = (a * M1 + M2) / de;
+    o[5] = S1 / de;
+}
+
 // scal: [0] e_F, [1] E_b, [2] status (0 ok, 1 no bracket), [3] N(e_F), [4] iterations, [5] -tau S_s
 __global__ void __launch_bounds__(kFermiThreads) k_fermi_final(const double* __restrict__ Dg, int nE, double e0,
                                                                double de, double kT, double tol, int max_iter,
                                                                const double* __restrict__ fs, int rounds,
+                                                               const double* __restrict__ iv,
                                                                double* __restrict__ w0d, float* __restrict__ w0f,
                                                                double* __restrict__ scal) {
     extern __shared__ double sD[];
@@ -342,33 +369,27 @@ __global__ void __launch_bounds__(kFermiThreads) k_fermi_final(const double* __r
     stage_D(Dg, nE, sD);
     const double eF = b.exact ? b.lo : 0.5 * (b.lo + b.hi);
     const int status = b.status, it = b.it;
-    // weights at e_F, the band energy, the entropy term and the electron count
+    // node weights from the two intervals beside each node; band energy, entropy term, electron count
     double pn = 0.0, pe = 0.0, ps = 0.0;
     for (int x = threadIdx.x; x < nE; x += blockDim.x) {
         double w0 = 0.0, w1 = 0.0, ws = 0.0;
-        const double ex = e0 + x * de;
         if (x > 0) {  // right half of hat_x on [e_{x-1}, e_x]
-            const double a = e0 + (x - 1) * de;
-            double M0, M1, M2, S0, S1;
-            interval_moments(a, ex, eF, kT, M0, M1, M2);
-            entropy_moments(a, ex, eF, kT, S0, S1);
-            w0 += M1 / de;
-            w1 += (a * M1 + M2) / de;
-            ws += S1 / de;
+            const double* o = iv + 6 * (size_t)(x - 1);
+            w0 += o[3];
+            w1 += o[4];
+            ws += o[5];
         }
         if (x < nE - 1) {  // left half of hat_x on [e_x, e_{x+1}]
-            double M0, M1, M2, S0, S1;
-            interval_moments(ex, ex + de, eF, kT, M0, M1, M2);
-            entropy_moments(ex, ex + de, eF, kT, S0, S1);
-            w0 += M0 - M1 / de;
-            w1 += ex * M0 + M1 - (ex * M1 + M2) / de;
-            ws += S0 - S1 / de;
+            const double* o = iv + 6 * (size_t)x;
+            w0 += o[0];
+            w1 += o[1];
+            ws += o[2];
         }
-        ps += ws * sD[x];
         w0d[x] = w0;
         w0f[x] = (float)w0;
         pn += w0 * sD[x];
         pe += w1 * sD[x];
+        ps += ws * sD[x];
     }
     const double Nf = block_sum(pn, sred);
     const double Eb = block_sum(pe, sred);
@@ -515,8 +536,10 @@ constexpr double kFermiTol = 1e-12;
 constexpr int kFermiMaxIter = 200;
 
 // init, enough rounds of 7 steps to shrink the bracket below the tolerance, final
+// fstate: kFermiStateDoubles, then 6 n_E doubles of interval weights
 void launch_fermi(const double* dos_sum, int nE, double dV, const mala_energy_grid* eg, double* D, double* w0d,
                   float* w0f, double* scal, double* fstate, cudaStream_t st) {
+    double* iv = fstate + kFermiStateDoubles;
     const size_t sm = sizeof(double) * nE;
     const double width = (nE - 1) * eg->de_eV + 40.0 * eg->kT_eV;
     int steps = (int)std::ceil(std::log2(std::max(width / kFermiTol, 1.0))) + 2;
@@ -527,8 +550,10 @@ void launch_fermi(const double* dos_sum, int nE, double dV, const mala_energy_gr
     for (int r = 0; r < rounds; ++r)
         k_fermi_round<<<kWideNodes, kFermiThreads, sm, st>>>(D, nE, eg->e0_eV, eg->de_eV, eg->kT_eV, eg->n_electrons,
                                                              kFermiTol, kFermiMaxIter, fstate, r);
+    k_fermi_intervals<<<(nE - 1 + kIvPerCta - 1) / kIvPerCta, kIvPerCta, 0, st>>>(
+        nE, eg->e0_eV, eg->de_eV, eg->kT_eV, kFermiTol, kFermiMaxIter, fstate, rounds, iv);
     k_fermi_final<<<1, kFermiThreads, sm, st>>>(D, nE, eg->e0_eV, eg->de_eV, eg->kT_eV, kFermiTol, kFermiMaxIter,
-                                                fstate, rounds, w0d, w0f, scal);
+                                                fstate, rounds, iv, w0d, w0f, scal);
 }
 
 // Bernoulli numbers B_0..B_n (B_1 = -1/2) from sum_{k=0}^{m} C(m+1, k) B_k = 0
@@ -592,7 +617,7 @@ int integrate(Ctx* c, const void* ldos, int64_t P, double volume, const mala_ene
     const int dens_blocks = (int)std::min<int64_t>(std::max<int64_t>(1, (P + kDensWarps - 1) / kDensWarps),
                                                    (int64_t)c->num_sms * 16);
     const size_t n_part = std::max<size_t>((size_t)ntile * nE, (size_t)dens_blocks);
-    const size_t doubles = 3 * (size_t)nE + (nE + 1) / 2 + 16 + kFermiStateDoubles + n_part;
+    const size_t doubles = 3 * (size_t)nE + (nE + 1) / 2 + 16 + kFermiStateDoubles + 6 * (size_t)nE + n_part;
     MALA_TRY(c->ws_red.reserve(c, sizeof(double) * doubles));
     double* dsum = c->ws_red.as<double>();
     double* D = dsum + nE;
@@ -601,7 +626,7 @@ int integrate(Ctx* c, const void* ldos, int64_t P, double volume, const mala_ene
     double* scal = w0d + nE + (nE + 1) / 2;
     double* nsum = scal + 8;
     double* fstate = scal + 16;
-    double* part = fstate + kFermiStateDoubles;
+    double* part = fstate + kFermiStateDoubles + 6 * (size_t)nE;
     const bool mixed = prec == MALA_MIXED;
     if (!dos_sum) {
         if (P > 0) {
@@ -706,12 +731,13 @@ int integrate_noalloc(Ctx* c, const void* ldos, int64_t P, double volume, const 
     const int dens_blocks = (int)std::min<int64_t>(std::max<int64_t>(1, (P + kDensWarps - 1) / kDensWarps),
                                                    (int64_t)c->num_sms * 16);
     const size_t n_part = std::max<size_t>(dos_sum ? 0 : (size_t)ntile * nE, (size_t)dens_blocks);
-    const size_t need = 3 * (size_t)nE + (nE + 1) / 2 + 16 + kFermiStateDoubles + n_part;
+    const size_t need = 3 * (size_t)nE + (nE + 1) / 2 + 16 + kFermiStateDoubles + 6 * (size_t)nE + n_part;
     if (need > kStaticScratchDoubles)
         return fail(MALA_ERR_UNSUPPORTED,
                     "mala_integrate_noalloc: %zu scratch doubles needed, the static array holds %zu "
                     "(ceil(P/128) * n_E must stay below about %zu when dos_sum_dev is NULL)",
-                    need, kStaticScratchDoubles, kStaticScratchDoubles - 3 * (size_t)nE - nE / 2 - 16 - kFermiStateDoubles);
+                    need, kStaticScratchDoubles,
+                    kStaticScratchDoubles - 9 * (size_t)nE - nE / 2 - 16 - kFermiStateDoubles);
     // the same layout as the workspace path; every buffer is rewritten before it is read
     double* dsum = scratch;
     double* D = dsum + nE;
@@ -720,7 +746,7 @@ int integrate_noalloc(Ctx* c, const void* ldos, int64_t P, double volume, const 
     double* scal = w0d + nE + (nE + 1) / 2;
     double* nsum = scal + 8;
     double* fstate = scal + 16;
-    double* part = fstate + kFermiStateDoubles;
+    double* part = fstate + kFermiStateDoubles + 6 * (size_t)nE;
     const bool mixed = prec == MALA_MIXED;
     if (!dos_sum) {
         if (P > 0) {
