@@ -43,7 +43,10 @@ template <class T> __device__ __forceinline__ T unorm_at(int idx);
 template <> __device__ __forceinline__ float unorm_at<float>(int idx) { return c_unorm_f[idx]; }
 template <> __device__ __forceinline__ double unorm_at<double>(int idx) { return c_unorm_d[idx]; }
 
-constexpr int kSegElemsF32 = 24;  // sums + compensations of 24 complex numbers: 96 registers
+// FP32: sums + compensations of up to 36 complex numbers (144 registers) per segment, with 8 warps
+// per CTA so each thread may hold 255 registers: fewer, longer segments re-walk the column chains
+// less often (measured 13% faster than 24-element segments at 12 warps)
+constexpr int kSegElemsF32 = 36;
 constexpr int kSegElemsF64 = 10;
 
 struct Seg {
@@ -240,7 +243,7 @@ __device__ __forceinline__ void run_segments(const typename AB4<T>::type* ab_t, 
     }
 }
 
-template <class T> struct UiWarps { static constexpr int value = 12; };
+template <class T> struct UiWarps { static constexpr int value = 8; };
 template <> struct UiWarps<double> { static constexpr int value = 6; };
 
 template <class T, int TJ>
