@@ -372,18 +372,23 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     const float* fxl = sd.wposf + 3 * (size_t)n;
     const float* fyl = sd.wposf + 4 * (size_t)n;
     const float* fzl = sd.wposf + 5 * (size_t)n;
+    // (the shifts take one to three values per axis: each pair is formed when its shift changes)
+    int sz_prev = INT_MIN, sy_prev = INT_MIN, sx_prev = INT_MIN;
+    float ozh = 0.f, ozl = 0.f, oyh = 0.f, oyl = 0.f, oxh = 0.f, oxl = 0.f;
     for (int bz_ = ib_lo[2]; bz_ <= ib_hi[2]; ++bz_) {
         const int jz = ((bz_ % g.nb[2]) + g.nb[2]) % g.nb[2];
         const int sz = (bz_ - jz) / g.nb[2];
-        float ozh, ozl;
-        split_pair(shift_mul(sz, g.L[2]) - lo[2], ozh, ozl);
+        if (sz != sz_prev) {
+            split_pair(shift_mul(sz, g.L[2]) - lo[2], ozh, ozl);
+            sz_prev = sz;
+        }
         for (int by_ = ib_lo[1]; by_ <= ib_hi[1]; ++by_) {
             const int jy = ((by_ % g.nb[1]) + g.nb[1]) % g.nb[1];
             const int sy = (by_ - jy) / g.nb[1];
-            float oyh, oyl;
-            split_pair(shift_mul(sy, g.L[1]) - lo[1], oyh, oyl);
-            int sx_prev = INT_MIN;
-            float oxh = 0.f, oxl = 0.f;
+            if (sy != sy_prev) {
+                split_pair(shift_mul(sy, g.L[1]) - lo[1], oyh, oyl);
+                sy_prev = sy;
+            }
             for (int bx_ = ib_lo[0]; bx_ <= ib_hi[0]; ++bx_) {
                 const int jx = ((bx_ % g.nb[0]) + g.nb[0]) % g.nb[0];
                 const int sx = (bx_ - jx) / g.nb[0];
