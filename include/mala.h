@@ -281,7 +281,12 @@ int mala_predict_batch(mala_ctx* ctx, int32_t n, const mala_snapshot* snaps, con
 /* Queue a prediction.  The library copies every input (the caller may free
  * them on return), admits the request when its device memory fits in the
  * budget, and runs it on the GPU concurrently with other admitted requests.
- * Non-blocking; *ticket identifies the request. */
+ * A free serving slot takes the oldest queued request that fits together with
+ * the later queued ones of the same network, precision, bispectrum setting and
+ * n_E (up to 16 requests, 8e6 grid points, within the budget) and runs them as
+ * one batch (mala_predict_batch's path): LDOS rows are those of a lone run bit
+ * for bit; the DOS sums, hence the integrals, may differ from a lone run in the
+ * last bits.  Non-blocking; *ticket identifies the request. */
 int mala_submit(mala_ctx* ctx, const mala_snapshot* snap, const mala_bispectrum_params* bp,
                 const mala_model* model, const mala_energy_grid* eg, mala_precision precision,
                 uint64_t* ticket);
@@ -290,7 +295,8 @@ int mala_submit(mala_ctx* ctx, const mala_snapshot* snap, const mala_bispectrum_
 int mala_poll(mala_ctx* ctx, uint64_t ticket, mala_result* out);
 /* Block until the ticket completes or timeout_s passes (MALA_ERR_TIMEOUT). */
 int mala_wait(mala_ctx* ctx, uint64_t ticket, double timeout_s, mala_result* out);
-/* Free the device outputs of a completed request. */
+/* Free the device outputs of a completed request (a batch's shared outputs
+ * are freed when its last request is released). */
 int mala_release(mala_ctx* ctx, uint64_t ticket);
 
 #ifdef __cplusplus

@@ -12,6 +12,7 @@
 // concurrently on the GPU.  Outputs stay on the device until mala_release.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -91,7 +92,61 @@ static size_t path_output_bytes(int64_t P, int nB, int nE, mala_precision prec) 
     return (size_t)P * nB * e + (size_t)P * nE * l + (size_t)P * e + (size_t)nE * 8 + 4 * 256;
 }
 
+// descriptors -> LDOS -> integrals for n snapshots into the given device buffers
+// (rows of snapshot i at row[i]): descriptors of all snapshots in one pass of
+// launches, the network over all rows in one launch, the integrals per
+// snapshot.  A lone snapshot takes its DOS column sums from the network's
+// epilogue (dos_sum, may be NULL otherwise), so n = 1 is exactly run_path.
+// dos_host[i]: host [n_E] per snapshot.  Returns the first per-snapshot
+// failure other than MALA_ERR_FERMI_BRACKET, else the first bracket error,
+// else MALA_OK; res[i].status holds each snapshot's own status.
+static int run_path_batch(Ctx* c, int n, const mala_snapshot* const* snaps, const mala_bispectrum_params* bp,
+                          const Model* m, const mala_energy_grid* const* egs, mala_precision prec, char* B, char* L,
+                          char* D, double* dos_sum, double* const* dos_host, mala_result* const* res,
+                          cudaStream_t st) {
+    if (n == 1) return run_path(c, snaps[0], bp, m, egs[0], prec, B, L, D, dos_sum, res[0], dos_host[0], st);
+    std::vector<int64_t> row(n + 1, 0);
+    std::vector<mala_snapshot> sv(n);
+    for (int i = 0; i < n; ++i) {
+        sv[i] = *snaps[i];
+        row[i + 1] = row[i] + (int64_t)snaps[i]->grid[0] * snaps[i]->grid[1] * snaps[i]->grid[2];
+    }
+    const int nB = n_triples(bp->twojmax), nE = egs[0]->n_E;
+    const size_t e = prec == MALA_MIXED ? 4 : 8, l = prec == MALA_MIXED ? 2 : 8;
+    MALA_TRY(snap_descriptors_batch(c, n, sv.data(), bp, B, prec, st));
+    MALA_TRY(mlp_forward(c, m, B, row[n], L, nullptr, prec, st));
+    int first_rc = MALA_OK;
+    for (int i = 0; i < n; ++i) {
+        const int64_t Pi = row[i + 1] - row[i];
+        double eF = 0.0, Eb = 0.0, Ne = 0.0, TS = 0.0;
+        const int rc = integrate(c, L + (size_t)row[i] * nE * l, Pi, cell_volume(snaps[i]), egs[i], nullptr,
+                                 D + (size_t)row[i] * e, dos_host[i], &eF, &Eb, &Ne, &TS, prec, st);
+        if (rc != MALA_OK && rc != MALA_ERR_FERMI_BRACKET) return rc;
+        if (rc != MALA_OK && first_rc == MALA_OK) first_rc = rc;
+        mala_result& r = *res[i];
+        r.status = rc;
+        r.n_B = nB;
+        r.n_E = nE;
+        r.n_points = Pi;
+        r.fermi_eV = eF;
+        r.band_energy_eV = Eb;
+        r.electron_count = Ne;
+        r.entropy_term_eV = TS;
+        r.B_dev = B + (size_t)row[i] * nB * e;
+        r.ldos_dev = L + (size_t)row[i] * nE * l;
+        r.density_dev = D + (size_t)row[i] * e;
+    }
+    return first_rc;
+}
+
 // ---- serving ---------------------------------------------------------------
+
+// device outputs of one served batch, shared by its requests until the last release
+struct OutBuf {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+    int refs = 0;
+};
 
 struct Request {
     uint64_t ticket = 0;
@@ -109,8 +164,7 @@ struct Request {
     int state = 0;  // 0 queued, 1 running, 2 done
     int status = MALA_PENDING;
     std::string error;
-    void* buf = nullptr;  // outputs: B | LDOS | density | dos_sum
-    size_t buf_bytes = 0;
+    OutBuf* out = nullptr;  // the batch's outputs: B | LDOS | density rows of all its requests, then dos_sum
     std::vector<double> dos;
     mala_result res{};
     std::chrono::steady_clock::time_point t_submit, t_done;
@@ -129,73 +183,125 @@ struct Server {
     int running = 0;
 };
 
-static void carve(Request* r, void* base, void** B, void** L, void** D, double** S) {
-    const size_t e = r->prec == MALA_MIXED ? 4 : 8, l = r->prec == MALA_MIXED ? 2 : 8;
-    const int nB = n_triples(r->bp.twojmax), nE = r->eg.n_E;
-    auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
-    char* p = static_cast<char*>(base);
-    *B = p;
-    p += al((size_t)r->P * nB * e);
-    *L = p;
-    p += al((size_t)r->P * nE * l);
-    *D = p;
-    p += al((size_t)r->P * e);
-    *S = reinterpret_cast<double*>(p);
+// requests that may share one batch: same network, precision, bispectrum setting and n_E
+static bool batchable(const Request* a, const Request* b) {
+    if (a->model != b->model || a->prec != b->prec || a->eg.n_E != b->eg.n_E) return false;
+    const mala_bispectrum_params &p = a->bp, &q = b->bp;
+    if (p.twojmax != q.twojmax || p.rcut != q.rcut || p.rfac0 != q.rfac0 || p.rmin0 != q.rmin0 || p.wself != q.wself ||
+        p.n_species != q.n_species || (p.weights == nullptr) != (q.weights == nullptr))
+        return false;
+    return a->weights == b->weights;
 }
+
+constexpr int kServeBatchMax = 16;                // requests per batch
+constexpr int64_t kServeBatchPoints = 8000000;    // grid points per batch
 
 static void worker_loop(Server* sv, Ctx* slot) {
     cudaSetDevice(slot->device);
     for (;;) {
-        Request* r = nullptr;
+        std::vector<Request*> batch;
+        size_t batch_bytes = 0;
         {
             std::unique_lock<std::mutex> lk(sv->mu);
             for (;;) {
                 if (sv->stop) return;
-                // oldest queued request whose outputs fit in the budget
+                // the oldest queued request whose outputs fit in the budget, then every later
+                // compatible one while the batch still fits (continuous batching)
                 Ctx* root = sv->root;
-                for (auto it = sv->queue.begin(); it != sv->queue.end(); ++it) {
+                int64_t pts = 0;
+                for (auto it = sv->queue.begin(); it != sv->queue.end();) {
                     Request* q = sv->reqs[*it].get();
-                    const bool fits = !root->budget || root->used + q->out_bytes <= root->budget || sv->running == 0;
-                    if (fits) {
-                        r = q;
-                        sv->queue.erase(it);
+                    const bool first = batch.empty();
+                    if (!first && ((int)batch.size() >= kServeBatchMax || !batchable(batch[0], q) ||
+                                   pts + q->P > kServeBatchPoints)) {
+                        ++it;
+                        continue;
+                    }
+                    const bool fits = !root->budget || root->used + batch_bytes + q->out_bytes <= root->budget ||
+                                      (first && sv->running == 0);
+                    if (!fits) {
+                        if (first) {
+                            ++it;
+                            continue;
+                        }
                         break;
                     }
+                    batch.push_back(q);
+                    batch_bytes += q->out_bytes;
+                    pts += q->P;
+                    it = sv->queue.erase(it);
                 }
-                if (r) break;
+                if (!batch.empty()) break;
                 sv->cv_work.wait(lk);
             }
-            r->state = 1;
+            for (Request* r : batch) r->state = 1;
             ++sv->running;
+            if (!sv->root->budget || sv->root->used + batch_bytes <= sv->root->budget) sv->root->used += batch_bytes;
+            else batch_bytes = 0;  // over budget: reported below, nothing allocated
         }
         int rc = MALA_OK;
-        Ctx* root = sv->root;
-        if (root->budget && root->used + r->out_bytes > root->budget) {
-            rc = fail(MALA_ERR_OOM, "request of %zu bytes does not fit in the HBM budget", r->out_bytes);
-        } else if (cudaMalloc(&r->buf, r->out_bytes) != cudaSuccess) {
-            cudaGetLastError();
-            r->buf = nullptr;
-            rc = fail(MALA_ERR_OOM, "cudaMalloc(%zu) for request outputs failed", r->out_bytes);
+        const int n = (int)batch.size();
+        OutBuf* ob = nullptr;
+        if (batch_bytes == 0) {
+            rc = fail(MALA_ERR_OOM, "request of %zu bytes does not fit in the HBM budget", batch[0]->out_bytes);
         } else {
-            root->used += r->out_bytes;
-            r->buf_bytes = r->out_bytes;
-            void *B, *L, *D;
-            double* S;
-            carve(r, r->buf, &B, &L, &D, &S);
-            r->dos.assign(r->eg.n_E, 0.0);
+            ob = new OutBuf();
+            ob->bytes = batch_bytes;
+            ob->refs = n;
+            if (cudaMalloc(&ob->ptr, batch_bytes) != cudaSuccess) {
+                cudaGetLastError();
+                ob->ptr = nullptr;
+                rc = fail(MALA_ERR_OOM, "cudaMalloc(%zu) for request outputs failed", batch_bytes);
+            }
+        }
+        if (rc == MALA_OK) {
+            // carve: B rows | LDOS rows | density rows of all requests, then each request's dos_sum
+            const Request* r0 = batch[0];
+            const size_t e = r0->prec == MALA_MIXED ? 4 : 8, l = r0->prec == MALA_MIXED ? 2 : 8;
+            const int nB = n_triples(r0->bp.twojmax), nE = r0->eg.n_E;
+            int64_t P = 0;
+            for (Request* r : batch) P += r->P;
+            auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+            char* p = static_cast<char*>(ob->ptr);
+            char* B = p;
+            p += al((size_t)P * nB * e);
+            char* L = p;
+            p += al((size_t)P * nE * l);
+            char* D = p;
+            p += al((size_t)P * e);
+            double* S = reinterpret_cast<double*>(p);
+            std::vector<const mala_snapshot*> snaps(n);
+            std::vector<const mala_energy_grid*> egs(n);
+            std::vector<double*> dh(n);
+            std::vector<mala_result*> res(n);
+            for (int i = 0; i < n; ++i) {
+                Request* r = batch[i];
+                r->dos.assign(nE, 0.0);
+                snaps[i] = &r->snap;
+                egs[i] = &r->eg;
+                dh[i] = r->dos.data();
+                res[i] = &r->res;
+            }
             std::lock_guard<std::mutex> lk(slot->mu);
-            rc = run_path(slot, &r->snap, &r->bp, r->model, &r->eg, r->prec, B, L, D, S, &r->res, r->dos.data(),
-                          slot->stream);
+            rc = run_path_batch(slot, n, snaps.data(), &r0->bp, r0->model, egs.data(), r0->prec, B, L, D, S, dh.data(),
+                                res.data(), slot->stream);
         }
         {
             std::lock_guard<std::mutex> lk(sv->mu);
-            r->status = rc;
-            if (rc != MALA_OK) r->error = mala_last_error();
-            r->t_done = std::chrono::steady_clock::now();
-            r->res.status = rc;
-            r->res.dos = r->dos.empty() ? nullptr : r->dos.data();
-            r->res.submit_to_done_s = std::chrono::duration<double>(r->t_done - r->t_submit).count();
-            r->state = 2;
+            const std::string err = rc != MALA_OK ? std::string(mala_last_error()) : std::string();
+            const auto now = std::chrono::steady_clock::now();
+            for (Request* r : batch) {
+                // per-request status: its own bracket result inside a good batch, else the batch's error
+                const int st = (rc == MALA_OK || rc == MALA_ERR_FERMI_BRACKET) && ob ? r->res.status : rc;
+                r->status = st;
+                if (st != MALA_OK) r->error = st == rc ? err : std::string("N(mu) - N_e has no sign change");
+                r->out = ob;
+                r->t_done = now;
+                r->res.status = st;
+                r->res.dos = r->dos.empty() ? nullptr : r->dos.data();
+                r->res.submit_to_done_s = std::chrono::duration<double>(r->t_done - r->t_submit).count();
+                r->state = 2;
+            }
             --sv->running;
         }
         sv->cv_done.notify_all();
@@ -238,11 +344,15 @@ void server_stop(Ctx* c) {
     }
     sv->cv_work.notify_all();
     for (auto& t : sv->workers) t.join();
+    std::vector<OutBuf*> outs;
     for (auto& kv : sv->reqs)
-        if (kv.second->buf) {
-            cudaFree(kv.second->buf);
-            c->used -= kv.second->buf_bytes;
-        }
+        if (kv.second->out && std::find(outs.begin(), outs.end(), kv.second->out) == outs.end())
+            outs.push_back(kv.second->out);
+    for (OutBuf* ob : outs) {
+        if (ob->ptr) cudaFree(ob->ptr);
+        c->used -= ob->bytes;
+        delete ob;
+    }
     for (auto& s : sv->slots) {
         cudaStreamSynchronize(s->stream);
         cudaStreamDestroy(s->stream);
@@ -393,32 +503,22 @@ int mala_predict_batch(mala_ctx* c, int32_t n, const mala_snapshot* snaps, const
     char* B = c->ws_B.as<char>();
     char* L = c->ws_ldos.as<char>();
     char* D = c->ws_dens.as<char>();
-    MALA_TRY(snap_descriptors_batch(c, n, snaps, bp, B, prec, st));
-    MALA_TRY(mlp_forward(c, m, B, P, L, nullptr, prec, st));
     c->batch_dos.assign((size_t)n * nE, 0.0);
-    int first_rc = MALA_OK;
+    MALA_TRY(c->ws_dos.reserve(c, (size_t)nE * 8 + 256));
+    std::vector<const mala_snapshot*> sp(n);
+    std::vector<const mala_energy_grid*> ep(n);
+    std::vector<double*> dh(n);
+    std::vector<mala_result*> rp(n);
     for (int i = 0; i < n; ++i) {
-        const int64_t Pi = row[i + 1] - row[i];
-        double eF = 0.0, Eb = 0.0, Ne = 0.0, TS = 0.0;
-        const int rc = integrate(c, L + (size_t)row[i] * nE * l, Pi, cell_volume(&snaps[i]), &egs[i], nullptr,
-                                 D + (size_t)row[i] * e, c->batch_dos.data() + (size_t)i * nE, &eF, &Eb, &Ne, &TS,
-                                 prec, st);
-        if (rc != MALA_OK && rc != MALA_ERR_FERMI_BRACKET) return rc;
-        if (rc != MALA_OK && first_rc == MALA_OK) first_rc = rc;
-        mala_result& r = res[i];
-        r.status = rc;
-        r.n_B = nB;
-        r.n_E = nE;
-        r.n_points = Pi;
-        r.fermi_eV = eF;
-        r.band_energy_eV = Eb;
-        r.electron_count = Ne;
-        r.entropy_term_eV = TS;
-        r.dos = c->batch_dos.data() + (size_t)i * nE;
-        r.B_dev = B + (size_t)row[i] * nB * e;
-        r.ldos_dev = L + (size_t)row[i] * nE * l;
-        r.density_dev = D + (size_t)row[i] * e;
+        sp[i] = &snaps[i];
+        ep[i] = &egs[i];
+        dh[i] = c->batch_dos.data() + (size_t)i * nE;
+        rp[i] = &res[i];
     }
+    const int first_rc = run_path_batch(c, n, sp.data(), bp, m, ep.data(), prec, B, L, D, c->ws_dos.as<double>(),
+                                        dh.data(), rp.data(), st);
+    if (first_rc != MALA_OK && first_rc != MALA_ERR_FERMI_BRACKET) return first_rc;
+    for (int i = 0; i < n; ++i) res[i].dos = dh[i];
     if (density_host) {
         MALA_CUDA_TRY(cudaMemcpyAsync(density_host, D, (size_t)P * e, cudaMemcpyDeviceToHost, st));
         MALA_CUDA_TRY(cudaStreamSynchronize(st));
@@ -505,10 +605,12 @@ int mala_release(mala_ctx* c, uint64_t ticket) {
         if (it->second->state != 2) return fail(MALA_ERR_INVALID_ARG, "request %llu is still running", (unsigned long long)ticket);
         r = std::move(it->second);
         sv->reqs.erase(it);
-    }
-    if (r->buf) {
-        cudaFree(r->buf);
-        c->used -= r->buf_bytes;
+        if (r->out && --r->out->refs == 0) {
+            if (r->out->ptr) cudaFree(r->out->ptr);
+            c->used -= r->out->bytes;
+            delete r->out;
+        }
+        r->out = nullptr;
     }
     sv->cv_work.notify_all();
     return MALA_OK;

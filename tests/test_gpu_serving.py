@@ -1,7 +1,8 @@
 """Serving loop: requests of different sizes admitted while others run give
-the same results as when run alone (the kernels are deterministic, so the
-comparison is bit for bit), every ticket completes, and the HBM budget gates
-admission."""
+the results they give alone, every ticket completes, and the HBM budget gates
+admission.  Queued compatible requests are served as one batch: the network
+rows are then the same computation (bit for bit), while the DOS sums run over
+another blocking of the same BF16 values, so the integrals agree to rounding."""
 import numpy as np
 import pytest
 
@@ -37,14 +38,16 @@ def test_results_alone_equal_results_in_the_mix():
         Ne = c.electron_count(first["dos"], eg, 0.0)
         dens = np.zeros(s.n_points, np.float32)
         r = c.predict(s, bp, model, eg, api.MIXED, n_electrons=Ne, density_host=dens)
-        alone.append((Ne, dens, r["fermi"], r["band_energy"], r["dos"].copy()))
+        alone.append((Ne, dens, r["fermi"], r["band_energy"], r["dos"].copy(), r["ldos"].float().cpu().numpy()))
     tickets = [c.submit(s, bp, model, eg, api.MIXED, n_electrons=alone[i][0]) for i, s in enumerate(snaps)]
     for i, t in enumerate(tickets):
         r = c.wait(t, timeout_s=120.0)
-        Ne, dens, eF, Eb, D = alone[i]
-        np.testing.assert_array_equal(r["density"].cpu().numpy(), dens)
-        np.testing.assert_array_equal(r["dos"], D)
-        assert r["fermi"] == eF and r["band_energy"] == Eb
+        Ne, dens, eF, Eb, D, L = alone[i]
+        np.testing.assert_array_equal(r["ldos"].float().cpu().numpy(), L)
+        np.testing.assert_allclose(r["dos"], D, rtol=1e-6)
+        assert r["fermi"] == pytest.approx(eF, abs=1e-6)
+        assert r["band_energy"] == pytest.approx(Eb, rel=1e-6)
+        np.testing.assert_allclose(r["density"].cpu().numpy(), dens, rtol=1e-5, atol=1e-6)
         assert r["latency_s"] > 0.0
         assert c.poll(t) is not None
         c.release(t)
