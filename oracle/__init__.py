@@ -21,7 +21,10 @@ Contents, each following the passage of the paper cited at the function:
 * ``fermi_level``: bisection on N(mu) - N_e (Sec. "Observable calculation");
 * ``observables``: D(e) of Eq. (DOS.from.ldos), n(r) of Eq. (density.from.ldos),
   the band energy of Eq. (band.energy) and the entropy contribution -tau S_s of
-  Eq. (electronicentropyDOS) (``entropy_weights`` / ``entropy_term``).
+  Eq. (electronicentropyDOS) (``entropy_weights`` / ``entropy_term``);
+* ``oracle.forces``: the band-energy forces of Eqs. (forces, forcesmala) --
+  dE_b/dD at fixed N_e, the network's vector-Jacobian product and the
+  descriptor adjoint, by torch autograd of a differentiable FP64 restatement.
 
 Parity pins for every function live in ``tests/test_oracle_*.py``.
 """
