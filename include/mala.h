@@ -250,6 +250,50 @@ int mala_integrate_noalloc(mala_ctx* ctx, const void* ldos_dev, int64_t P, doubl
 int mala_electron_count(mala_ctx* ctx, const double* dos_host, const mala_energy_grid* eg, double mu,
                         double* count);
 
+/* ---- band-energy forces (Sec. "Total energy calculation", Eqs. forces and
+ * forcesmala with E = E_b of Eq. band.energy) ------------------------------
+ *
+ * f_alpha = -dE_b/dR_alpha = -(dE_b/d LDOS)(d LDOS/dB)(dB/dR_alpha), evaluated
+ * right to left as the paper prescribes: a vector per grid point, the
+ * network's backward pass, then the descriptor adjoint.  Each factor has its
+ * own entry point.  MALA_MIXED: FP32 descriptors and u, FP32 backward pass
+ * (cuBLAS SGEMM for the dense products), FP32 adjoint, forces summed per atom
+ * in 2^-40 fixed point (order-independent).  MALA_FP64_PLAIN: the same in
+ * FP64.  Synchronous; forces_host is [n_atoms][3] doubles in eV/Angstrom. */
+
+/* dE_b/dD_xi at fixed electron number (the first factor divided by dV):
+ * E_b = sum w1_xi(mu) D_xi with mu(D) fixed by N(mu) = eg->n_electrons, so
+ * dE_b/dD_xi = w1_xi - mu~ w0_xi with mu~ = (dE_b/dmu)/(dN/dmu) at fixed D
+ * (closed forms for the piecewise-linear D, FP64).  dos_host: D (host, [n_E]);
+ * grad_host (host, [n_E]); *fermi the Fermi level, *mu_tilde = mu~ (either may
+ * be NULL).  Errors: MALA_ERR_FERMI_BRACKET as in mala_integrate,
+ * MALA_ERR_UNSUPPORTED when dN/dmu = 0. */
+int mala_band_energy_gradient(mala_ctx* ctx, const double* dos_host, const mala_energy_grid* eg,
+                              double* grad_host, double* fermi, double* mu_tilde, void* stream);
+
+/* The network's vector-Jacobian product: beta[p][j] = sum_e v[e] dLDOS[p][e]/dB[p][j]
+ * for every row of B (device, [P][n_B], float for MALA_MIXED, double for
+ * MALA_FP64_PLAIN) into beta_dev (device, same type and shape); v_host: host
+ * [n_E] doubles.  LeakyReLU derivatives use sigma'(0) = slope. */
+int mala_ldos_backward(mala_ctx* ctx, const mala_model* model, const void* B_dev, int64_t P,
+                       const double* v_host, void* beta_dev, mala_precision precision, void* stream);
+
+/* The descriptor adjoint: forces_host[a][k] = -sum_r sum_j beta[r][j] dB(r, j)/dR_{a,k}
+ * over every grid point r of the snapshot (beta_dev: device [P][n_B], float for
+ * MALA_MIXED, double for MALA_FP64_PLAIN, rows in grid order).  The neighbour
+ * sets are those of mala_neighbor_lists; positions enter through every
+ * periodic image. */
+int mala_descriptor_forces(mala_ctx* ctx, const mala_snapshot* snap, const mala_bispectrum_params* bp,
+                           const void* beta_dev, double* forces_host, mala_precision precision, void* stream);
+
+/* The whole chain: the forward path of mala_predict (result in *res, device
+ * pointers into the context's workspace as there) followed by the three
+ * factors; forces_host: [n_atoms][3].  On MALA_ERR_FERMI_BRACKET no forces are
+ * written. */
+int mala_band_forces(mala_ctx* ctx, const mala_snapshot* snap, const mala_bispectrum_params* bp,
+                     const mala_model* model, const mala_energy_grid* eg, mala_precision precision,
+                     double* forces_host, mala_result* res, void* stream);
+
 /* ---- the whole path ----------------------------------------------------- */
 
 /* Descriptors -> LDOS -> integrals for one snapshot.  Intermediate B and LDOS

@@ -168,6 +168,37 @@ def _cg_table(j1: int, j2: int, j: int) -> np.ndarray:
     return C
 
 
+_ZT = {}
+
+
+def _z_terms(j1: int, j2: int, j: int):
+    """Every term of Z^{j}_{j1 j2}: (output element ma (j+1) + mb, C[ma][m1a] C[mb][m1b],
+    element of u^{j1}, element of u^{j2}), for the contraction written out in
+    ``bispectrum_torch``."""
+    key = (j1, j2, j)
+    if key not in _ZT:
+        C = _cg_table(j1, j2, j)
+        e_out, coef, i1, i2 = [], [], [], []
+        for ma in range(j + 1):
+            m = 2 * ma - j
+            for mb in range(j + 1):
+                mp = 2 * mb - j
+                for m1a in range(j1 + 1):
+                    m2 = m - (2 * m1a - j1)
+                    if abs(m2) > j2 or C[ma, m1a] == 0.0:
+                        continue
+                    for m1b in range(j1 + 1):
+                        m2p = mp - (2 * m1b - j1)
+                        if abs(m2p) > j2 or C[mb, m1b] == 0.0:
+                            continue
+                        e_out.append(ma * (j + 1) + mb)
+                        coef.append(C[ma, m1a] * C[mb, m1b])
+                        i1.append(m1a * (j1 + 1) + m1b)
+                        i2.append(((m2 + j2) // 2) * (j2 + 1) + (m2p + j2) // 2)
+        _ZT[key] = (np.array(e_out, np.int64), np.array(coef), np.array(i1, np.int64), np.array(i2, np.int64))
+    return _ZT[key]
+
+
 def bispectrum_torch(snap, bp, pos_t, points: np.ndarray):
     """B[np][n_triples] as a torch function of the positions pos_t [n_atoms, 3]
     (complex128 intermediates)."""
@@ -203,25 +234,13 @@ def bispectrum_torch(snap, bp, pos_t, points: np.ndarray):
     tr = triples(tj)
     out = []
     for j1, j2, j in tr:
-        C = _cg_table(j1, j2, j)
-        Z = torch.zeros((npt, j + 1, j + 1), dtype=torch.complex128)
-        for ma in range(j + 1):
-            m = 2 * ma - j
-            for mb in range(j + 1):
-                mp = 2 * mb - j
-                acc = torch.zeros(npt, dtype=torch.complex128)
-                for m1a in range(j1 + 1):
-                    m2 = m - (2 * m1a - j1)
-                    if abs(m2) > j2 or C[ma, m1a] == 0.0:
-                        continue
-                    for m1b in range(j1 + 1):
-                        m2p = mp - (2 * m1b - j1)
-                        if abs(m2p) > j2 or C[mb, m1b] == 0.0:
-                            continue
-                        acc = acc + (C[ma, m1a] * C[mb, m1b]) * u[j1][:, m1a, m1b] * u[j2][:, (m2 + j2) // 2,
-                                                                                         (m2p + j2) // 2]
-                Z[:, ma, mb] = acc
-        out.append((torch.conj(u[j]) * Z).real.sum(dim=(1, 2)))
+        # Z_{ma mb} = sum over (m1a, m1b) of C[ma][m1a] C[mb][m1b] u^{j1}_{m1a m1b} u^{j2}_{m2a m2b}
+        e_out, coef, i1, i2 = _z_terms(int(j1), int(j2), int(j))
+        u1 = u[j1].reshape(npt, -1)
+        u2 = u[j2].reshape(npt, -1)
+        prod = torch.tensor(coef, dtype=torch.complex128)[None, :] * u1[:, i1] * u2[:, i2]
+        Z = torch.zeros((npt, (j + 1) ** 2), dtype=torch.complex128).index_add(1, torch.tensor(e_out), prod)
+        out.append((torch.conj(u[j].reshape(npt, -1)) * Z).real.sum(dim=1))
     return torch.stack(out, dim=1)
 
 

@@ -93,6 +93,16 @@ PROTOTYPES = {
                                             C.c_int, C.c_void_p]),
     "mala_descriptors_batch": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(Snapshot), C.POINTER(BispectrumParams),
                                          C.c_void_p, C.c_int, C.c_void_p]),
+    "mala_band_energy_gradient": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(EnergyGrid),
+                                            C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                            C.c_void_p]),
+    "mala_ldos_backward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_double),
+                                     C.c_void_p, C.c_int, C.c_void_p]),
+    "mala_descriptor_forces": (C.c_int, [C.c_void_p, C.POINTER(Snapshot), C.POINTER(BispectrumParams), C.c_void_p,
+                                         C.POINTER(C.c_double), C.c_int, C.c_void_p]),
+    "mala_band_forces": (C.c_int, [C.c_void_p, C.POINTER(Snapshot), C.POINTER(BispectrumParams), C.c_void_p,
+                                   C.POINTER(EnergyGrid), C.c_int, C.POINTER(C.c_double), C.POINTER(Result),
+                                   C.c_void_p]),
     "mala_submit": (C.c_int, [C.c_void_p, C.POINTER(Snapshot), C.POINTER(BispectrumParams), C.c_void_p,
                               C.POINTER(EnergyGrid), C.c_int, C.POINTER(C.c_uint64)]),
     "mala_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.POINTER(Result)]),

@@ -340,6 +340,52 @@ class Context:
         out["status"] = rc
         return out
 
+    # ---- band-energy forces (Eqs. forces / forcesmala) ----------------------------
+
+    def band_energy_gradient(self, D, eg, n_electrons=None, stream=None):
+        """dE_b/dD at fixed electron number: {"grad", "fermi", "mu_tilde"}."""
+        D = np.ascontiguousarray(D, dtype=np.float64)
+        e = _EnergyGridArgs(eg, n_electrons)
+        g = np.zeros(len(D))
+        eF, mt = C.c_double(0.0), C.c_double(0.0)
+        dp = C.POINTER(C.c_double)
+        check(lib().mala_band_energy_gradient(self.h, D.ctypes.data_as(dp), C.byref(e.c), g.ctypes.data_as(dp),
+                                              C.byref(eF), C.byref(mt), _stream_ptr(stream)),
+              "mala_band_energy_gradient")
+        return {"grad": g, "fermi": eF.value, "mu_tilde": mt.value}
+
+    def ldos_backward(self, model: Model, B, v, precision: int = MIXED, out=None, stream=None):
+        """beta[p][j] = sum_e v[e] dLDOS[p][e]/dB[p][j] on the GPU (B: device [P][n_B])."""
+        torch = _torch()
+        v = np.ascontiguousarray(v, dtype=np.float64)
+        if out is None:
+            out = torch.empty_like(B)
+        check(lib().mala_ldos_backward(self.h, model.h, C.c_void_p(B.data_ptr()), int(B.shape[0]),
+                                       v.ctypes.data_as(C.POINTER(C.c_double)), C.c_void_p(out.data_ptr()),
+                                       int(precision), _stream_ptr(stream)), "mala_ldos_backward")
+        return out
+
+    def descriptor_forces(self, snap, bp, beta, precision: int = MIXED, stream=None):
+        """F[a][k] = -sum_r sum_j beta[r][j] dB(r, j)/dR_{a,k} (beta: device [P][n_B]); numpy [n_atoms][3]."""
+        a, b = _SnapshotArgs(snap), _BParamsArgs(bp)
+        F = np.zeros((len(snap.pos), 3))
+        check(lib().mala_descriptor_forces(self.h, C.byref(a.c), C.byref(b.c), C.c_void_p(beta.data_ptr()),
+                                           F.ctypes.data_as(C.POINTER(C.c_double)), int(precision),
+                                           _stream_ptr(stream)), "mala_descriptor_forces")
+        return F
+
+    def band_forces(self, snap, bp, model: Model, eg, precision: int = MIXED, n_electrons=None, stream=None):
+        """The forward path of predict() and f = -dE_b/dR: the result dict plus "forces" [n_atoms][3]."""
+        a, b, e = _SnapshotArgs(snap), _BParamsArgs(bp), _EnergyGridArgs(eg, n_electrons)
+        r = _lib.Result()
+        F = np.zeros((len(snap.pos), 3))
+        check(lib().mala_band_forces(self.h, C.byref(a.c), C.byref(b.c), model.h, C.byref(e.c), int(precision),
+                                     F.ctypes.data_as(C.POINTER(C.c_double)), C.byref(r), _stream_ptr(stream)),
+              "mala_band_forces")
+        out = _result_dict(r, precision)
+        out["forces"] = F
+        return out
+
     # ---- serving ----------------------------------------------------------------
 
     def submit(self, snap, bp, model: Model, eg, precision: int = MIXED, n_electrons=None) -> int:

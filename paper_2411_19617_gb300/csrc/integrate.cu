@@ -404,6 +404,61 @@ __global__ void __launch_bounds__(kFermiThreads) k_fermi_final(const double* __r
     }
 }
 
+// dE_b/dD_x at fixed N_e (the first factor of Eq. forcesmala for E = E_b).
+// E_b = sum_x w1_x(mu) D_x with mu fixed by N(mu) = sum_x w0_x(mu) D_x = N_e, so
+// dE_b/dD_x = w1_x - mu~ w0_x, mu~ = (d/dmu sum w1 D) / (d/dmu sum w0 D).
+// For the piecewise-linear D(e), integrating -df/de by parts over each
+// interval [a, b] with slope s = (D_{i+1} - D_i) / de leaves boundary terms
+// (which telescope to the two ends) and moments of f:
+//   d/dmu N   = D_0 f(e_0) - D_n f(e_n) + sum_i s_i M0_i,
+//   d/dmu E_b = e_0 D_0 f(e_0) - e_n D_n f(e_n) + sum_i ((D_i + s_i a_i) M0_i + 2 s_i M1_i).
+// One block; mom: 3 n_E doubles of scratch; out[0] = mu~ (NaN when d/dmu N = 0).
+__global__ void __launch_bounds__(kFermiThreads) k_egrad(const double* __restrict__ D, int nE, double e0, double de,
+                                                         double kT, const double* __restrict__ scal, double gscale,
+                                                         double* __restrict__ mom, double* __restrict__ g,
+                                                         double* __restrict__ out) {
+    __shared__ double sred[33];
+    const double mu = scal[0];
+    double pn = 0.0, pe = 0.0;
+    for (int i = threadIdx.x; i < nE - 1; i += blockDim.x) {
+        const double a = e0 + i * de;
+        double M0, M1, M2;
+        interval_moments(a, a + de, mu, kT, M0, M1, M2);
+        mom[3 * i] = M0;
+        mom[3 * i + 1] = M1;
+        mom[3 * i + 2] = M2;
+        const double sl = (D[i + 1] - D[i]) / de;
+        pn += sl * M0;
+        pe += (D[i] + sl * a) * M0 + 2.0 * sl * M1;
+    }
+    double dn = block_sum(pn, sred);
+    double dE = block_sum(pe, sred);
+    const double en = e0 + (nE - 1) * de;
+    const double xa = (e0 - mu) / kT, xb = (en - mu) / kT;
+    const double fa = xa > 0.0 ? exp(-xa) / (1.0 + exp(-xa)) : 1.0 / (1.0 + exp(xa));
+    const double fb = xb > 0.0 ? exp(-xb) / (1.0 + exp(-xb)) : 1.0 / (1.0 + exp(xb));
+    dn += D[0] * fa - D[nE - 1] * fb;
+    dE += e0 * D[0] * fa - en * D[nE - 1] * fb;
+    const double mt = dn != 0.0 ? dE / dn : nan("");
+    for (int x = threadIdx.x; x < nE; x += blockDim.x) {
+        double w0 = 0.0, w1 = 0.0;
+        if (x > 0) {  // right half of hat_x on [e_{x-1}, e_x]
+            const double a = e0 + (x - 1) * de;
+            const double* m = mom + 3 * (size_t)(x - 1);
+            w0 += m[1] / de;
+            w1 += (a * m[1] + m[2]) / de;
+        }
+        if (x < nE - 1) {  // left half of hat_x on [e_x, e_{x+1}]
+            const double a = e0 + x * de;
+            const double* m = mom + 3 * (size_t)x;
+            w0 += m[0] - m[1] / de;
+            w1 += a * m[0] + m[1] - (a * m[1] + m[2]) / de;
+        }
+        g[x] = gscale * (w1 - mt * w0);
+    }
+    if (threadIdx.x == 0) out[0] = mt;
+}
+
 // column sums over blocks of 128 rows (FP32 in row order, as the network
 // epilogue forms them) -> FP64 partial rows
 template <class TL>
@@ -605,6 +660,35 @@ int electron_count_at(Ctx* c, const double* D_host, const mala_energy_grid* eg, 
     MALA_CUDA_TRY(cudaMemcpyAsync(c->host_scalars + 16, d + nE, sizeof(double), cudaMemcpyDeviceToHost, st));
     MALA_CUDA_TRY(cudaStreamSynchronize(st));
     *out = c->host_scalars[16];
+    return MALA_OK;
+}
+
+int energy_gradient(Ctx* c, const double* dos_sum, double dV, const mala_energy_grid* eg, double gscale,
+                    double* g_dev, double* fermi, double* mu_tilde, cudaStream_t st) {
+    const int nE = eg->n_E;
+    // workspace: D[nE] | w0d[nE] | w0f[nE] (float) | scal[16] | fstate (+ 6 nE interval weights) | mom[3 nE]
+    const size_t doubles = 2 * (size_t)nE + (nE + 1) / 2 + 16 + kFermiStateDoubles + 6 * (size_t)nE + 3 * (size_t)nE;
+    MALA_TRY(c->ws_force_g.reserve(c, sizeof(double) * doubles));
+    double* D = c->ws_force_g.as<double>();
+    double* w0d = D + nE;
+    float* w0f = reinterpret_cast<float*>(w0d + nE);
+    double* scal = w0d + nE + (nE + 1) / 2;
+    double* fstate = scal + 16;
+    double* mom = fstate + kFermiStateDoubles + 6 * (size_t)nE;
+    MALA_PROF(c, "k_fermi", st, launch_fermi(dos_sum, nE, dV, eg, D, w0d, w0f, scal, fstate, st));
+    MALA_PROF(c, "k_egrad", st,
+              (k_egrad<<<1, kFermiThreads, 0, st>>>(D, nE, eg->e0_eV, eg->de_eV, eg->kT_eV, scal, gscale, mom, g_dev,
+                                                    scal + 8)));
+    MALA_CUDA_TRY(cudaGetLastError());
+    MALA_CUDA_TRY(cudaMemcpyAsync(c->host_scalars, scal, sizeof(double) * 9, cudaMemcpyDeviceToHost, st));
+    MALA_CUDA_TRY(cudaStreamSynchronize(st));
+    const double* hs = c->host_scalars;
+    if (fermi) *fermi = hs[0];
+    if (mu_tilde) *mu_tilde = hs[8];
+    if (hs[2] != 0.0)
+        return fail(MALA_ERR_FERMI_BRACKET, "N(mu) - N_e has no sign change on [e0 - 20 kT, e_max + 20 kT]");
+    if (!std::isfinite(hs[8]))
+        return fail(MALA_ERR_UNSUPPORTED, "dN/dmu = 0 at the Fermi level: dE_b/dD is undefined");
     return MALA_OK;
 }
 

@@ -206,6 +206,12 @@ static int run_descriptors(Ctx* c, int nsnap, const mala_snapshot* snaps, const 
     return fail(MALA_ERR_UNSUPPORTED, "neighbour capacity could not be established");
 }
 
+int snap_descriptors_full(Ctx* c, const mala_snapshot* snap, const mala_bispectrum_params* bp, void* B,
+                          void* u_full, NbrOut* nl, mala_precision prec, cudaStream_t st) {
+    if (prec == MALA_MIXED) return run_descriptors<float>(c, 1, snap, bp, (float*)B, (float*)u_full, nl, st);
+    return run_descriptors<double>(c, 1, snap, bp, (double*)B, (double*)u_full, nl, st);
+}
+
 int snap_descriptors(Ctx* c, const mala_snapshot* snap, const mala_bispectrum_params* bp, void* B, void* u_full,
                      mala_precision prec, cudaStream_t st) {
     if (prec == MALA_MIXED) return run_descriptors<float>(c, 1, snap, bp, (float*)B, (float*)u_full, nullptr, st);
@@ -323,6 +329,7 @@ void mala_destroy(mala_ctx* c) {
     cudaSetDevice(c->device);
     server_stop(c);
     cudaDeviceSynchronize();
+    cublas_release(c);
     {
         // networks outliving their context keep only their host object
         std::lock_guard<std::mutex> lk(c->models_mu);

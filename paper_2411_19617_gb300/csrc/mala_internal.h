@@ -125,6 +125,13 @@ struct Model {
     size_t bytes = 0;
 };
 
+// tables of the descriptor adjoint (Y contraction lists) for one twojmax, in Ctx::ws_ftab
+struct ForceTables {
+    int tj = -1;
+    int ncoup = 0, list_len = 0, nh = 0;
+    size_t off[10] = {0};
+};
+
 struct SnapStage;  // per-call staging of one snapshot (atoms, bins, neighbours)
 
 // One queued or running request of the serving loop.
@@ -142,6 +149,11 @@ struct Ctx {
     // workspaces of the synchronous path
     DevBuf ws_atoms, ws_batch, ws_bins, ws_nbr_ab, ws_nbr_c, ws_nbr_cnt, ws_u, ws_misc, ws_B, ws_ldos,
         ws_dens, ws_dos, ws_tile_dos, ws_units, ws_mlp64, ws_red, ws_w;
+    // workspaces of the force path
+    ForceTables ftab;
+    DevBuf ws_ftab, ws_force_y, ws_force_aux, ws_force_u, ws_force_nbr, ws_force_beta, ws_force_mlp, ws_force_g,
+        ws_force_bt;
+    void* cublas = nullptr;  // cuBLAS handle of the network's backward GEMMs (created on first use)
     double* host_dos = nullptr;     // pinned [max N_E]
     size_t host_dos_len = 0;
     double* host_scalars = nullptr; // pinned small buffer
@@ -178,7 +190,7 @@ struct SnapGeom {
 struct SnapDev {
     SnapGeom g;
     double* wpos = nullptr;   // [3][n] wrapped positions (SoA)
-    float* wsp = nullptr;     // [n] element weight
+    double* wsp = nullptr;    // [n] element weight (FP64; the FP32 path rounds it once)
     int* bin_of = nullptr;    // [n]
     int* bin_start = nullptr; // [n_bins + 1]
     int* bin_atoms = nullptr; // [n]
@@ -273,6 +285,24 @@ __device__ __forceinline__ int batch_find(const BatchSnap* bs, int n, int64_t t)
 // ---- network and integrals ---------------------------------------------------
 
 int model_upload(Ctx* c, const mala_mlp_desc* d, Model* m);
+
+// ---- force path --------------------------------------------------------------
+
+double clebsch_gordan(int j1, int m1, int j2, int m2, int j, int m);  // twice-units
+// descriptors with the full u and neighbour lists of one snapshot (nl.dbg_* outputs set by the caller)
+int snap_descriptors_full(Ctx* c, const mala_snapshot* snap, const mala_bispectrum_params* bp, void* B,
+                          void* u_full, NbrOut* nl, mala_precision prec, cudaStream_t st);
+// F_host[n_atoms][3] = -sum_r sum_j beta[r][j] dB(r, j)/dR from the staged snapshot sd
+template <class T>
+int descriptor_adjoint(Ctx* c, const SnapDev& sd, const mala_snapshot* snap, const mala_bispectrum_params* bp,
+                       const T* u_full, const T* beta, const NbrOut& nl, double* F_host, cudaStream_t st);
+// beta[P][n_B] = sum_e v[e] dLDOS[p][e]/dB[p][:] (v device [n_E]); float for MIXED, double for FP64_PLAIN
+int mlp_backward(Ctx* c, const Model* m, const void* B, int64_t P, const double* v_dev, void* beta,
+                 mala_precision prec, cudaStream_t st);
+void cublas_release(Ctx* c);
+// dE_b/dD at fixed N_e for D = dV * dos_sum: g_dev[n_E] = gscale * dE_b/dD; *fermi, *mu_tilde (host)
+int energy_gradient(Ctx* c, const double* dos_sum, double dV, const mala_energy_grid* eg, double gscale,
+                    double* g_dev, double* fermi, double* mu_tilde, cudaStream_t st);
 void server_stop(Ctx* c);
 int integrate_noalloc(Ctx* c, const void* ldos, int64_t P, double volume, const mala_energy_grid* eg,
                       const double* dos_sum, void* density, double* dos_host, double* fermi, double* eb, double* ne,

@@ -365,6 +365,45 @@ void server_stop(Ctx* c) {
     c->server = nullptr;
 }
 
+// ---- forces (Eqs. forces / forcesmala with E = E_b) --------------------------
+
+// descriptors of one snapshot with the full u (ws_force_u) and complete
+// neighbour lists (ws_force_nbr: counts[P] | atoms[P][cap] | shifts[P][cap][3]);
+// the capacity grows until every list fits.  B may be NULL.
+static int stage_force_descriptors(Ctx* c, const mala_snapshot* snap, const mala_bispectrum_params* bp,
+                                   mala_precision prec, void* B, NbrOut* nl, cudaStream_t st) {
+    const int64_t P = (int64_t)snap->grid[0] * snap->grid[1] * snap->grid[2];
+    const size_t e = prec == MALA_MIXED ? 4 : 8;
+    MALA_TRY(c->ws_force_u.reserve(c, e * 2 * (size_t)n_full(bp->twojmax) * (size_t)std::max<int64_t>(P, 1) + 256));
+    int cap = std::max(32, (c->kmax_hint + 7) & ~7);
+    for (int attempt = 0; attempt < 3; ++attempt) {
+        const size_t Pp = (size_t)((P + 63) & ~int64_t(63));
+        MALA_TRY(c->ws_force_nbr.reserve(c, sizeof(int) * Pp * (1 + 4 * (size_t)cap) + 256));
+        NbrOut d;
+        d.dbg_counts = c->ws_force_nbr.as<int>();
+        d.dbg_atoms = d.dbg_counts + Pp;
+        d.dbg_shifts = d.dbg_atoms + Pp * cap;
+        d.dbg_cap = cap;
+        MALA_TRY(snap_descriptors_full(c, snap, bp, B, c->ws_force_u.ptr, &d, prec, st));
+        if (d.kmax <= cap) {
+            *nl = d;
+            return MALA_OK;
+        }
+        cap = (d.kmax + 7) & ~7;
+    }
+    return fail(MALA_ERR_UNSUPPORTED, "neighbour-list capacity for the force step could not be established");
+}
+
+static int adjoint_of_staged(Ctx* c, const mala_snapshot* snap, const mala_bispectrum_params* bp, mala_precision prec,
+                             const void* beta, const NbrOut& nl, double* F, cudaStream_t st) {
+    const SnapDev& sd = static_cast<const BatchSnap*>(c->host_batch)[0].sd;
+    if (prec == MALA_MIXED)
+        return descriptor_adjoint<float>(c, sd, snap, bp, c->ws_force_u.as<float>(), static_cast<const float*>(beta),
+                                         nl, F, st);
+    return descriptor_adjoint<double>(c, sd, snap, bp, c->ws_force_u.as<double>(), static_cast<const double*>(beta),
+                                      nl, F, st);
+}
+
 }  // namespace mala
 
 using namespace mala;
@@ -614,6 +653,106 @@ int mala_release(mala_ctx* c, uint64_t ticket) {
     }
     sv->cv_work.notify_all();
     return MALA_OK;
+}
+
+int mala_band_energy_gradient(mala_ctx* c, const double* dos_host, const mala_energy_grid* eg, double* grad_host,
+                              double* fermi, double* mu_tilde, void* stream) {
+    if (!c || !dos_host || !grad_host) return fail(MALA_ERR_INVALID_ARG, "NULL argument");
+    MALA_TRY(check_egrid(eg));
+    std::lock_guard<std::mutex> lk(c->mu);
+    MALA_CUDA_TRY(cudaSetDevice(c->device));
+    cudaStream_t st = as_stream(stream);
+    const int nE = eg->n_E;
+    MALA_TRY(c->ws_w.reserve(c, sizeof(double) * 2 * (size_t)nE + 256));
+    double* D = c->ws_w.as<double>();
+    double* g = D + nE;
+    MALA_CUDA_TRY(cudaMemcpyAsync(D, dos_host, sizeof(double) * nE, cudaMemcpyHostToDevice, st));
+    double eF = 0.0, mt = 0.0;
+    const int rc = energy_gradient(c, D, 1.0, eg, 1.0, g, &eF, &mt, st);
+    if (fermi) *fermi = eF;
+    if (mu_tilde) *mu_tilde = mt;
+    if (rc != MALA_OK) return rc;
+    MALA_CUDA_TRY(cudaMemcpyAsync(grad_host, g, sizeof(double) * nE, cudaMemcpyDeviceToHost, st));
+    MALA_CUDA_TRY(cudaStreamSynchronize(st));
+    return MALA_OK;
+}
+
+int mala_ldos_backward(mala_ctx* c, const mala_model* m, const void* B_dev, int64_t P, const double* v_host,
+                       void* beta_dev, mala_precision prec, void* stream) {
+    if (!c || !m || !v_host || (P > 0 && (!B_dev || !beta_dev))) return fail(MALA_ERR_INVALID_ARG, "NULL argument");
+    if (P < 0) return fail(MALA_ERR_INVALID_ARG, "P < 0");
+    if (prec != MALA_MIXED && prec != MALA_FP64_PLAIN) return fail(MALA_ERR_INVALID_ARG, "bad precision");
+    std::lock_guard<std::mutex> lk(c->mu);
+    MALA_CUDA_TRY(cudaSetDevice(c->device));
+    cudaStream_t st = as_stream(stream);
+    const int nE = m->dims[m->n_layers];
+    MALA_TRY(c->ws_w.reserve(c, sizeof(double) * (size_t)nE + 256));
+    MALA_CUDA_TRY(cudaMemcpyAsync(c->ws_w.ptr, v_host, sizeof(double) * nE, cudaMemcpyHostToDevice, st));
+    MALA_TRY(mlp_backward(c, m, B_dev, P, c->ws_w.as<double>(), beta_dev, prec, st));
+    MALA_CUDA_TRY(cudaStreamSynchronize(st));
+    return MALA_OK;
+}
+
+int mala_descriptor_forces(mala_ctx* c, const mala_snapshot* snap, const mala_bispectrum_params* bp,
+                           const void* beta_dev, double* forces_host, mala_precision prec, void* stream) {
+    if (!c || !forces_host) return fail(MALA_ERR_INVALID_ARG, "NULL argument");
+    MALA_TRY(check_snapshot(snap));
+    MALA_TRY(check_bparams(bp));
+    if (prec != MALA_MIXED && prec != MALA_FP64_PLAIN) return fail(MALA_ERR_INVALID_ARG, "bad precision");
+    const int64_t P = (int64_t)snap->grid[0] * snap->grid[1] * snap->grid[2];
+    if (P > 0 && !beta_dev) return fail(MALA_ERR_INVALID_ARG, "beta is NULL");
+    std::lock_guard<std::mutex> lk(c->mu);
+    MALA_CUDA_TRY(cudaSetDevice(c->device));
+    cudaStream_t st = as_stream(stream);
+    NbrOut nl;
+    MALA_TRY(stage_force_descriptors(c, snap, bp, prec, nullptr, &nl, st));
+    return adjoint_of_staged(c, snap, bp, prec, beta_dev, nl, forces_host, st);
+}
+
+int mala_band_forces(mala_ctx* c, const mala_snapshot* snap, const mala_bispectrum_params* bp, const mala_model* m,
+                     const mala_energy_grid* eg, mala_precision prec, double* forces_host, mala_result* res,
+                     void* stream) {
+    if (!c || !res || !forces_host) return fail(MALA_ERR_INVALID_ARG, "NULL argument");
+    memset(res, 0, sizeof(*res));
+    MALA_TRY(check_path_args(snap, bp, m, eg, prec));
+    std::lock_guard<std::mutex> lk(c->mu);
+    MALA_CUDA_TRY(cudaSetDevice(c->device));
+    cudaStream_t st = as_stream(stream);
+    const int64_t P = (int64_t)snap->grid[0] * snap->grid[1] * snap->grid[2];
+    const int nB = n_triples(bp->twojmax), nE = eg->n_E;
+    const size_t e = prec == MALA_MIXED ? 4 : 8, l = prec == MALA_MIXED ? 2 : 8;
+    MALA_TRY(c->ws_B.reserve(c, (size_t)P * nB * e + 256));
+    MALA_TRY(c->ws_ldos.reserve(c, (size_t)P * nE * l + 256));
+    MALA_TRY(c->ws_dens.reserve(c, (size_t)P * e + 256));
+    MALA_TRY(c->ws_dos.reserve(c, (size_t)nE * 8 + 256));
+    MALA_TRY(c->ws_w.reserve(c, sizeof(double) * (size_t)nE + 256));
+    // forward: descriptors (with u and neighbour lists), LDOS, integrals
+    NbrOut nl;
+    MALA_TRY(stage_force_descriptors(c, snap, bp, prec, c->ws_B.ptr, &nl, st));
+    MALA_TRY(mlp_forward(c, m, c->ws_B.ptr, P, c->ws_ldos.ptr, c->ws_dos.as<double>(), prec, st));
+    double eF = 0.0, Eb = 0.0, Ne = 0.0, TS = 0.0;
+    const double vol = cell_volume(snap), dV = vol / (double)(P > 0 ? P : 1);
+    int rc = integrate(c, c->ws_ldos.ptr, P, vol, eg, c->ws_dos.as<double>(), c->ws_dens.ptr, nullptr, &eF, &Eb, &Ne,
+                       &TS, prec, st);
+    res->status = rc;
+    res->n_B = nB;
+    res->n_E = nE;
+    res->n_points = P;
+    res->fermi_eV = eF;
+    res->band_energy_eV = Eb;
+    res->electron_count = Ne;
+    res->entropy_term_eV = TS;
+    res->B_dev = c->ws_B.ptr;
+    res->ldos_dev = c->ws_ldos.ptr;
+    res->density_dev = c->ws_dens.ptr;
+    res->dos = c->host_dos;
+    if (rc != MALA_OK) return rc;
+    // backward: dE_b/dLDOS = dV dE_b/dD (the same vector at every point), network, descriptors
+    double mt = 0.0;
+    MALA_TRY(energy_gradient(c, c->ws_dos.as<double>(), dV, eg, dV, c->ws_w.as<double>(), nullptr, &mt, st));
+    MALA_TRY(c->ws_force_bt.reserve(c, (size_t)P * nB * e + 256));
+    MALA_TRY(mlp_backward(c, m, c->ws_B.ptr, P, c->ws_w.as<double>(), c->ws_force_bt.ptr, prec, st));
+    return adjoint_of_staged(c, snap, bp, prec, c->ws_force_bt.ptr, nl, forces_host, st);
 }
 
 }  // extern "C"

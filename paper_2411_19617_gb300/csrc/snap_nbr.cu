@@ -47,7 +47,7 @@ __device__ __forceinline__ double grid_coord(int i, int n, double L) {
 
 __global__ void k_stage_atoms(int n, const double* __restrict__ pos, const int* __restrict__ species,
                               const double* __restrict__ wsp_tab, int nspecies, SnapGeom g,
-                              double* __restrict__ wpos, float* __restrict__ wposf, float* __restrict__ wsp,
+                              double* __restrict__ wpos, float* __restrict__ wposf, double* __restrict__ wsp,
                               int* __restrict__ bin_of, int* __restrict__ bin_count, int* __restrict__ err) {
     int a = blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= n) return;
@@ -68,7 +68,7 @@ __global__ void k_stage_atoms(int n, const double* __restrict__ pos, const int* 
         atomicExch(err, 1);
         s = 0;
     }
-    wsp[a] = (float)(wsp_tab ? wsp_tab[s] : 1.0);
+    wsp[a] = wsp_tab ? wsp_tab[s] : 1.0;
     int b = bc[0] + g.nb[0] * (bc[1] + g.nb[1] * bc[2]);
     bin_of[a] = b;
     atomicAdd(&bin_count[b], 1);
@@ -476,7 +476,7 @@ StageLayout stage_layout(const mala_snapshot* snap, const mala_bispectrum_params
     lay.o_wpos = take(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
     lay.o_wposf = take(sizeof(float) * 6 * (size_t)(n > 0 ? n : 1));
     lay.o_sp = take(sizeof(int) * (size_t)(n > 0 ? n : 1));
-    lay.o_wsp = take(sizeof(float) * (size_t)(n > 0 ? n : 1));
+    lay.o_wsp = take(sizeof(double) * (size_t)(n > 0 ? n : 1));
     lay.o_binof = take(sizeof(int) * (size_t)(n > 0 ? n : 1));
     lay.o_batoms = take(sizeof(int) * (size_t)(n > 0 ? n : 1));
     lay.o_bstart = take(sizeof(int) * (size_t)(nbins + 1));
@@ -515,7 +515,7 @@ int stage_snapshot_at(const mala_snapshot* snap, const mala_bispectrum_params* b
     sd->wpos = (double*)(base + o_wpos);
     sd->wposf = (float*)(base + o_wposf);
     int* sp_d = (int*)(base + o_sp);
-    sd->wsp = (float*)(base + o_wsp);
+    sd->wsp = (double*)(base + o_wsp);
     sd->bin_of = (int*)(base + o_binof);
     sd->bin_atoms = (int*)(base + o_batoms);
     sd->bin_start = (int*)(base + o_bstart);

@@ -81,6 +81,8 @@ double triple_cost(int j1, int j2, int j) {
 
 }  // namespace
 
+double clebsch_gordan(int j1, int m1, int j2, int m2, int j, int m) { return cg_racah(j1, m1, j2, m2, j, m); }
+
 int upload_cg_tables(Ctx* c) {
     std::vector<double> tab(kCgSize, 0.0);
     std::vector<float2> tabf(kCgSize, make_float2(0.f, 0.f));
