@@ -52,6 +52,8 @@ def parse():
                     help="requests of the serving comparison (0 skips it)")
     ap.add_argument("--serve-max-atoms", type=int, default=512,
                     help="atom-count cap of the serving sample (bounds the FP64 arm's time)")
+    ap.add_argument("--forces-calls", type=int, default=3,
+                    help="timed calls of the band-energy forces leg (0 skips it)")
     return ap.parse_args()
 
 
@@ -192,6 +194,45 @@ def serving_compare(ctx, api, wl, model, bp, eg, n_req, nmax):
             "trace": f"Poisson arrivals at 200/s (seed 5), Al or Be bulk at 0.2 A spacing, N log-uniform in "
                      f"[32, {nmax}]; twojmax 10, MLP 91-400-400-250, 250 energies",
             "served_mixed": summary(lm, sm), "plain_fp64_single": summary(lp, sp)}
+
+
+def forces_leg(ctx, api, roofline, model, snap, bp, eg, ne, calls, peak_tflops):
+    """mala_band_forces (forward path + dE_b/dD + network backward + descriptor
+    adjoint) on the bench workload: ms per call and the adjoint kernels' share."""
+    import torch
+    counts, _, _, _ = ctx.neighbor_lists(snap, bp.rcut, cap=0)
+    pairs = int(counts.sum().item())
+    P = int(np.prod(snap.grid))
+    ctx.band_forces(snap, bp, model, eg, api.MIXED, n_electrons=ne)  # tables, workspaces
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(calls):
+        out = ctx.band_forces(snap, bp, model, eg, api.MIXED, n_electrons=ne)
+    ev1.record()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / calls
+    ctx.profile(True)
+    ctx.band_forces(snap, bp, model, eg, api.MIXED, n_electrons=ne)
+    kern = {}
+    for k in ("k_neighbors", "k_ui", "k_u_expand", "k_zb", "k_mlp", "k_fermi", "k_egrad", "k_bwd_elementwise", "k_yi",
+              "k_force"):
+        t, n = ctx.profile_get(k)
+        kern[k] = {"ms": t, "launches": n}
+    ctx.profile(False)
+    yi_f = roofline.yi_flops_per_point(bp.twojmax) * P
+    fo_f = roofline.force_flops_per_pair(bp.twojmax) * pairs
+    roof = {}
+    for name, flops in (("k_yi", yi_f), ("k_force", fo_f)):
+        t = kern[name]["ms"] / max(kern[name]["launches"], 1)
+        ach = flops / (t / 1e3) / 1e12 if t > 0 else 0.0
+        roof[name] = {"bound": "alu", "achieved": ach, "peak": peak_tflops, "unit": "TFLOP/s",
+                      "frac": ach / peak_tflops, "flops": flops}
+    F = out["forces"]
+    return {"ms_per_call": ms, "grid_points_per_s": P / (ms / 1e3), "atoms": int(len(snap.pos)),
+            "neighbour_pairs": pairs, "precision": "f32 descriptors/u/backward/adjoint, bf16 forward network, "
+                                                   "f64 dE_b/dD, forces summed in 2^-40 fixed point",
+            "max_abs_force_eV_per_A": float(np.max(np.abs(F))), "kernels": kern, "roofline": roof}
 
 
 def kernel_hash(*names):
@@ -397,6 +438,9 @@ def run_ours(args):
         serving = None
         if world == 1 and args.serve_requests > 0:
             serving = serving_compare(ctx, api, wl, model, bp, eg, args.serve_requests, args.serve_max_atoms)
+        forces = None
+        if world == 1 and args.forces_calls > 0:
+            forces = forces_leg(ctx, api, roofline, model, snap, bp, eg, ne, args.forces_calls, peak)
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -406,7 +450,7 @@ def run_ours(args):
                            "l2": "working set larger than L2 (u: 1.5 GB, neighbour records 0.9 GB, LDOS 0.36 GB)",
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-                "clocks": clk, "kernels": kernels, "serving": serving,
+                "clocks": clk, "kernels": kernels, "serving": serving, "forces": forces,
                 "fermi_eV": r["fermi"], "band_energy_eV": r["band_energy"], "entropy_term_eV": r["entropy_term"]}
         print(json.dumps(line), flush=True)
     if dist:

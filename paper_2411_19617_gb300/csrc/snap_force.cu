@@ -46,7 +46,7 @@ namespace mala {
 
 namespace {
 
-constexpr int kYiWarps = 8;
+constexpr int kYiWarps = 32;  // one CTA per SM shares the staged u; the warps hide load latency
 constexpr int kForceWarps = 8;
 constexpr double kFixScale = 1099511627776.0;  // 2^40
 constexpr double kFixMax = 4194304.0;          // |contribution| < 2^22 eV/A
@@ -133,16 +133,34 @@ __global__ void __launch_bounds__(kYiWarps * 32) k_yi(int tj, const T* __restric
         if (h < 0) break;
         T yr = T(0), yi = T(0);
         for (int g = tab.grp_off[h]; g < tab.grp_off[h + 1]; ++g) {
-            T zr = T(0), zi = T(0);
-            for (int q = tab.term_off[g]; q < tab.term_off[g + 1]; ++q) {
+            // two independent accumulators, four terms in flight
+            T zr0 = T(0), zi0 = T(0), zr1 = T(0), zi1 = T(0);
+            int q = tab.term_off[g];
+            const int q1 = tab.term_off[g + 1];
+            for (; q + 4 <= q1; q += 4) {
+                const YTerm<T> t0 = terms[q], t1 = terms[q + 1], t2 = terms[q + 2], t3 = terms[q + 3];
+                const C x0 = us[t0.ia * NP + pt], y0 = us[t0.ib * NP + pt];
+                const C x1 = us[t1.ia * NP + pt], y1 = us[t1.ib * NP + pt];
+                const C x2 = us[t2.ia * NP + pt], y2 = us[t2.ib * NP + pt];
+                const C x3 = us[t3.ia * NP + pt], y3 = us[t3.ib * NP + pt];
+                zr0 += t0.c * (x0.x * y0.x - x0.y * y0.y);
+                zi0 += t0.c * (x0.x * y0.y + x0.y * y0.x);
+                zr1 += t1.c * (x1.x * y1.x - x1.y * y1.y);
+                zi1 += t1.c * (x1.x * y1.y + x1.y * y1.x);
+                zr0 += t2.c * (x2.x * y2.x - x2.y * y2.y);
+                zi0 += t2.c * (x2.x * y2.y + x2.y * y2.x);
+                zr1 += t3.c * (x3.x * y3.x - x3.y * y3.y);
+                zi1 += t3.c * (x3.x * y3.y + x3.y * y3.x);
+            }
+            for (; q < q1; ++q) {
                 const YTerm<T> tm = terms[q];
                 const C x = us[tm.ia * NP + pt], y = us[tm.ib * NP + pt];
-                zr += tm.c * (x.x * y.x - x.y * y.y);
-                zi += tm.c * (x.x * y.y + x.y * y.x);
+                zr0 += tm.c * (x.x * y.x - x.y * y.y);
+                zi0 += tm.c * (x.x * y.y + x.y * y.x);
             }
             const T b = be[tab.grp_cpl[g] * NP + pt];
-            yr += b * zr;
-            yi += b * zi;
+            yr += b * (zr0 + zr1);
+            yi += b * (zi0 + zi1);
         }
         if (p < P) {
             const int4 el = tab.elem[h];

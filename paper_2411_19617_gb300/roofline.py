@@ -76,5 +76,51 @@ GB300_SMS = 152
 FP32_LANES_PER_SM = 128
 
 
+def yi_terms_half(twojmax: int):
+    """(terms, groups) of the adjoint contraction Y^J over the half set: for every
+    coupling c <- (a, b) that a triple (j1, j2, j) brings in its three roles
+    (j <- j1 j2, j1 <- j j2, j2 <- j j1), every Y element (ma, mb) of the half set
+    of c takes the Clebsch-Gordan pairs (m1a, m1b) whose partners lie inside b."""
+    coup = set()
+    for (j1, j2, j) in triples(twojmax):
+        for (c, a, b) in ((j, j1, j2), (j1, j, j2), (j2, j, j1)):
+            coup.add((c, max(a, b), min(a, b)))
+    terms = groups = 0
+    for (c, a, b) in coup:
+        rows = []
+        for ma in range(c + 1):
+            m = 2 * ma - c
+            rows.append(sum(1 for m1a in range(a + 1) if abs(m - (2 * m1a - a)) <= b))
+        for ma in range(c + 1):
+            for mb in range(c + 1):
+                if 2 * ma > c or (2 * ma == c and 2 * mb > c):
+                    continue
+                n = rows[ma] * rows[mb]
+                terms += n
+                groups += 1 if n else 0
+    return terms, groups
+
+
+def yi_flops_per_point(twojmax: int) -> int:
+    """10 flop per term (complex product scaled by C C, accumulated), 4 per coupling group."""
+    t, g = yi_terms_half(twojmax)
+    return 10 * t + 4 * g
+
+
+def force_flops_per_pair(twojmax: int) -> int:
+    """The column-chain walk of one (point, neighbour) pair: per chain c and level J the
+    G_0 dot (4 flop per coefficient) and, below the top level, four complex dots
+    (32 flop per coefficient) and the linear-form product (16 per output coefficient);
+    16 per coefficient of each chain's starting power beta^c."""
+    f = 0
+    for c in range(twojmax + 1):
+        f += 16 * (c + 1) if c > 0 else 0
+        for J in range(c, twojmax + 1):
+            f += 4 * (J + 1)
+            if J < twojmax:
+                f += 32 * (J + 1) + 16 * (J + 2)
+    return f
+
+
 def fp32_peak_tflops(sm_mhz: float) -> float:
     return GB300_SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
