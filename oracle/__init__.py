@@ -24,7 +24,10 @@ Contents, each following the passage of the paper cited at the function:
   Eq. (electronicentropyDOS) (``entropy_weights`` / ``entropy_term``);
 * ``oracle.forces``: the band-energy forces of Eqs. (forces, forcesmala) --
   dE_b/dD at fixed N_e, the network's vector-Jacobian product and the
-  descriptor adjoint, by torch autograd of a differentiable FP64 restatement.
+  descriptor adjoint, by torch autograd of a differentiable FP64 restatement;
+* ``oracle.ace``: grid-centred ACE descriptors (Sec. "Atomic cluster expansion
+  descriptors"): Chebyshev x spherical-harmonic grid basis and its N = 1, 2, 3
+  invariants with generalized Clebsch-Gordan coefficients.
 
 Parity pins for every function live in ``tests/test_oracle_*.py``.
 """
