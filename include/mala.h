@@ -320,6 +320,40 @@ int mala_predict_batch(mala_ctx* ctx, int32_t n, const mala_snapshot* snaps, con
                        const mala_model* model, const mala_energy_grid* egs, mala_precision precision,
                        void* density_host, mala_result* results, void* stream);
 
+/* ---- grid-centred ACE descriptors (Sec. "Atomic cluster expansion
+ * descriptors", Eqs. unweighted_ionicdensity .. ace_grid) ------------------
+ *
+ * Grid basis A_{mu n l m}(r) = sum over the neighbours of r of species mu (all
+ * periodic images within rcut, the membership rule of mala_neighbor_lists) of
+ * R_n(|d|) Y_l^m(d/|d|), d = R_alpha - r, with
+ * R_n(r) = T_n(1 - 2r/rcut) (1 + cos(pi r/rcut))/2 (Chebyshev polynomials of the
+ * first kind) and complex orthonormal spherical harmonics (Condon-Shortley
+ * phase); no element weights, no self term; an atom on the grid point adds to
+ * l = 0 only.  Invariants, column order:
+ *   N = 1: A_{mu n 0 0}, for (mu, n), n < nmax1;
+ *   N = 2: sum_m <l m l -m|0 0> A_{c1 l m} A_{c2 l -m}, for channel pairs c1 <= c2
+ *          of (mu, n), n < nmax2 (lexicographic), then l = 0..lmax2;
+ *   N = 3: sum <l1 m1 l2 m2|l3 M><l3 M l3 -M|0 0> A_{c1 l1 m1} A_{c2 l2 m2} A_{c3 l3 -M}
+ *          for sorted triples c1 <= c2 <= c3 of channels (mu, n, l), n < nmax3,
+ *          l <= lmax3 (lexicographic), |l1 - l2| <= l3 <= l1 + l2, l1 + l2 + l3 even.
+ * Limits: n_species <= 8, max(nmax) <= 16, max(lmax) <= 8,
+ * n_species x max(nmax) x (lmax+1)(lmax+2)/2 <= 1024 (MALA_ERR_UNSUPPORTED beyond). */
+typedef struct {
+    double rcut;        /* Angstrom */
+    int32_t n_species;  /* snapshot species indices must lie in 0..n_species-1 */
+    int32_t nmax1;      /* radial functions of the N = 1 columns */
+    int32_t nmax2, lmax2;
+    int32_t nmax3, lmax3;
+} mala_ace_params;
+
+/* Number of ACE columns for the parameters (host only, no context). */
+int mala_ace_count(const mala_ace_params* params, int32_t* n_desc);
+
+/* ACE descriptors D[P][n_desc] (device; float for MALA_MIXED, double for
+ * MALA_FP64_PLAIN) of one snapshot.  Synchronous. */
+int mala_ace_descriptors(mala_ctx* ctx, const mala_snapshot* snap, const mala_ace_params* params, void* D_dev,
+                         mala_precision precision, void* stream);
+
 /* ---- serving ------------------------------------------------------------ */
 
 /* Queue a prediction.  The library copies every input (the caller may free

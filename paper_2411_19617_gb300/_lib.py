@@ -48,6 +48,11 @@ class EnergyGrid(C.Structure):
                 ("n_electrons", C.c_double)]
 
 
+class AceParams(C.Structure):
+    _fields_ = [("rcut", C.c_double), ("n_species", C.c_int32), ("nmax1", C.c_int32), ("nmax2", C.c_int32),
+                ("lmax2", C.c_int32), ("nmax3", C.c_int32), ("lmax3", C.c_int32)]
+
+
 class Result(C.Structure):
     _fields_ = [("status", C.c_int32), ("n_B", C.c_int32), ("n_E", C.c_int32), ("n_points", C.c_int64),
                 ("fermi_eV", C.c_double), ("band_energy_eV", C.c_double), ("electron_count", C.c_double),
@@ -103,6 +108,9 @@ PROTOTYPES = {
     "mala_band_forces": (C.c_int, [C.c_void_p, C.POINTER(Snapshot), C.POINTER(BispectrumParams), C.c_void_p,
                                    C.POINTER(EnergyGrid), C.c_int, C.POINTER(C.c_double), C.POINTER(Result),
                                    C.c_void_p]),
+    "mala_ace_count": (C.c_int, [C.POINTER(AceParams), C.POINTER(C.c_int32)]),
+    "mala_ace_descriptors": (C.c_int, [C.c_void_p, C.POINTER(Snapshot), C.POINTER(AceParams), C.c_void_p, C.c_int,
+                                       C.c_void_p]),
     "mala_submit": (C.c_int, [C.c_void_p, C.POINTER(Snapshot), C.POINTER(BispectrumParams), C.c_void_p,
                               C.POINTER(EnergyGrid), C.c_int, C.POINTER(C.c_uint64)]),
     "mala_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.POINTER(Result)]),

@@ -65,6 +65,24 @@ class _BParamsArgs:
         self.c = p
 
 
+def _ace_args(ap) -> "_lib.AceParams":
+    """Any object with rcut, n_species, nmax1, nmax2, lmax2, nmax3, lmax3."""
+    p = _lib.AceParams()
+    p.rcut = float(ap.rcut)
+    p.n_species = int(ap.n_species)
+    p.nmax1, p.nmax2, p.lmax2 = int(ap.nmax1), int(ap.nmax2), int(ap.lmax2)
+    p.nmax3, p.lmax3 = int(ap.nmax3), int(ap.lmax3)
+    return p
+
+
+def ace_count(ap) -> int:
+    """Number of ACE descriptor columns for the parameters."""
+    n = C.c_int32(0)
+    p = _ace_args(ap)
+    check(lib().mala_ace_count(C.byref(p), C.byref(n)), "mala_ace_count")
+    return int(n.value)
+
+
 class _EnergyGridArgs:
     def __init__(self, eg, n_electrons: Optional[float] = None):
         e = _lib.EnergyGrid()
@@ -224,6 +242,18 @@ class Context:
         check(lib().mala_gaussian_descriptors(self.h, C.byref(a.c), float(rcut), float(sigma),
                                               C.c_void_p(out.data_ptr()), int(precision), _stream_ptr(stream)),
               "mala_gaussian_descriptors")
+        return out
+
+    def ace_descriptors(self, snap, ap, precision: int = MIXED, out=None, stream=None):
+        """Grid-centred ACE descriptors D[P][ace_count(ap)] on the GPU (float32 for MIXED, float64 for FP64_PLAIN)."""
+        torch = _torch()
+        P = int(np.prod(snap.grid))
+        dt = torch.float32 if precision == MIXED else torch.float64
+        if out is None:
+            out = torch.empty((P, ace_count(ap)), dtype=dt, device=torch.device("cuda", self.device))
+        a, p = _SnapshotArgs(snap), _ace_args(ap)
+        check(lib().mala_ace_descriptors(self.h, C.byref(a.c), C.byref(p), C.c_void_p(out.data_ptr()),
+                                         int(precision), _stream_ptr(stream)), "mala_ace_descriptors")
         return out
 
     def descriptors_batch(self, snaps, bp, precision: int = MIXED, out=None, stream=None):

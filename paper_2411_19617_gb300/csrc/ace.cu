@@ -1,0 +1,381 @@
+// ace.cu -- grid-centred ACE descriptors (paper Sec. "Atomic cluster expansion
+// descriptors", Eqs. unweighted_ionicdensity, gridatom_basis, grid_base,
+// product_grid_basis, ace_grid) for body orders N = 1, 2, 3.
+//
+// Grid basis: A_{mu n l m}(r) = sum over the neighbours of r of species mu of
+// R_n(|d|) Y_l^m(d/|d|), with R_n(r) = T_n(1 - 2r/r_cut) (1 + cos(pi r/r_cut))/2
+// (Chebyshev of the scaled distance, vanishing smoothly at the cutoff) and
+// complex orthonormal Y_l^m (Condon-Shortley).  Y_l^m = N_lm Ptilde_l^m(z) (x + i y)^m
+// for the unit vector (x, y, z), where Ptilde_l^m = P_l^m / sin^m(theta) obeys
+//   Ptilde_m^m = (-1)^m (2m-1)!!,  Ptilde_{m+1}^m = (2m+1) z Ptilde_m^m,
+//   (l - m) Ptilde_l^m = (2l-1) z Ptilde_{l-1}^m - (l+m-1) Ptilde_{l-2}^m,
+// a polynomial form that needs no angle and no division at the poles; only
+// m >= 0 is stored (A_{l,-m} = (-1)^m conj(A_{l,m}) for a real density).
+// Invariants: N = 1: A_{mu n 0 0}; N = 2: sum_m <l m l -m|0 0> A_{c1 l m} A_{c2 l -m};
+// N = 3: sum <l1 m1 l2 m2|l3 M><l3 M l3 -M|0 0> A_{c1 l1 m1} A_{c2 l2 m2} A_{c3 l3 -M}.
+//
+// Mapping: one warp per grid point (persistent).  Lanes take neighbours; each
+// lane evaluates R_n and Y_l^m of its neighbour, and a butterfly reduction over
+// the warp (fixed order: deterministic) adds each A element into the warp's
+// shared-memory copy of A.  The lanes then take descriptor columns and contract
+// A with host-built coefficient lists; each row is written coalesced.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <vector>
+
+#include "mala_internal.h"
+
+namespace mala {
+
+namespace {
+
+constexpr int kAceWarps = 4;
+constexpr int kAceLMax = 8;                                   // largest l compiled
+constexpr int kAceLM = (kAceLMax + 1) * (kAceLMax + 2) / 2;   // (l, m >= 0) pairs
+constexpr int kAceNMax = 16;
+constexpr int kAceSpecies = 8;
+constexpr int kAceMaxA = 1024;                                 // complex A elements per point
+
+template <class T> struct Cx;
+template <> struct Cx<float> { using type = float2; };
+template <> struct Cx<double> { using type = double2; };
+
+// descriptor column: kind 1, 2, 3; channel bases into A (mu n block * n_lm); l values; coefficient list
+struct AceCol {
+    int kind, a1, a2, a3, l1, l2, l3, c_off, c_cnt;
+};
+struct AceCoef {
+    double c;
+    int m1, m2;
+};
+
+struct AceArgs {
+    int64_t P;
+    int cap;
+    const int* cnt;
+    const int* atoms;
+    const int* shifts;
+    const int* species;  // [n_atoms] or NULL
+    const double* wpos;  // [3][n_atoms]
+    const double* gcoord;
+    int n_atoms, grid[3];
+    double L[3];
+    double rcut;
+    int lmax, nmax, n_species, n_lm, nA, n_desc;
+    const AceCol* cols;
+    const AceCoef* coefs;
+    const double* ynorm;  // N_lm by (l, m >= 0) index
+};
+
+__device__ __forceinline__ int lm_index(int l, int m) { return l * (l + 1) / 2 + m; }
+
+template <class T>
+__device__ __forceinline__ typename Cx<T>::type a_at(const typename Cx<T>::type* A, int base, int l, int m) {
+    typename Cx<T>::type v = A[base + lm_index(l, m < 0 ? -m : m)];
+    if (m < 0) {
+        const T s = (m & 1) ? T(-1) : T(1);
+        v.x = s * v.x;
+        v.y = -s * v.y;
+    }
+    return v;
+}
+
+template <class T>
+__global__ void __launch_bounds__(kAceWarps * 32) k_ace(AceArgs g, T* __restrict__ out) {
+    using C = typename Cx<T>::type;
+    extern __shared__ __align__(16) unsigned char smem_ace[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    C* A = reinterpret_cast<C*>(smem_ace) + (size_t)warp * g.nA;
+    for (int64_t p = (int64_t)blockIdx.x * kAceWarps + warp; p < g.P; p += (int64_t)gridDim.x * kAceWarps) {
+        for (int e = lane; e < g.nA; e += 32) {
+            A[e].x = T(0);
+            A[e].y = T(0);
+        }
+        __syncwarp();
+        const int n = min(g.cnt[p], g.cap);
+        const int ix = (int)(p % g.grid[0]);
+        const int iy = (int)((p / g.grid[0]) % g.grid[1]);
+        const int iz = (int)(p / ((int64_t)g.grid[0] * g.grid[1]));
+        const double rx = g.gcoord[ix], ry = g.gcoord[g.grid[0] + iy], rz = g.gcoord[g.grid[0] + g.grid[1] + iz];
+        for (int k0 = 0; k0 < n; k0 += 32) {
+            const int k = k0 + lane;
+            bool valid = k < n;
+            int sp = -1;
+            T ux = T(0), uy = T(0), uz = T(1), xs = T(0), fc = T(0);
+            bool center = false;
+            if (valid) {
+                const size_t q = (size_t)p * g.cap + k;
+                const int a = g.atoms[q];
+                sp = g.species ? g.species[a] : 0;
+                const double dx = (g.wpos[a] + g.shifts[3 * q] * g.L[0]) - rx;
+                const double dy = (g.wpos[g.n_atoms + a] + g.shifts[3 * q + 1] * g.L[1]) - ry;
+                const double dz = (g.wpos[2 * g.n_atoms + a] + g.shifts[3 * q + 2] * g.L[2]) - rz;
+                const T r = (T)sqrt(dx * dx + dy * dy + dz * dz);
+                center = !(r > T(0));
+                if (!center) {
+                    ux = (T)dx / r;
+                    uy = (T)dy / r;
+                    uz = (T)dz / r;
+                }
+                xs = T(1) - T(2) * r / (T)g.rcut;
+                T cp;
+                if constexpr (sizeof(T) == 4) cp = cospif(r / (float)g.rcut);
+                else cp = cospi(r / g.rcut);
+                fc = T(0.5) * (T(1) + cp);
+            }
+            // Y_l^m (m >= 0) of the lane's neighbour
+            T yr[kAceLM], yi[kAceLM];
+            {
+                T pmm = T(1);             // Ptilde_m^m
+                T er = T(1), ei = T(0);   // (x + i y)^m
+#pragma unroll
+                for (int m = 0; m <= kAceLMax; ++m) {
+                    if (m > 0) {
+                        pmm *= -T(2 * m - 1);
+                        const T nr = er * ux - ei * uy, ni = er * uy + ei * ux;
+                        er = nr;
+                        ei = ni;
+                    }
+                    T p2 = T(0), p1 = pmm;
+#pragma unroll
+                    for (int l = m; l <= kAceLMax; ++l) {
+                        T pl;
+                        if (l == m) pl = pmm;
+                        else if (l == m + 1) pl = T(2 * m + 1) * uz * pmm;
+                        else pl = (T(2 * l - 1) * uz * p1 - T(l + m - 1) * p2) / T(l - m);
+                        if (l > m) {
+                            p2 = p1;
+                            p1 = pl;
+                        }
+                        const T nrm = (T)g.ynorm[lm_index(l, m)] * (center && l > 0 ? T(0) : T(1));
+                        yr[lm_index(l, m)] = nrm * pl * er;
+                        yi[lm_index(l, m)] = nrm * pl * ei;
+                    }
+                }
+            }
+            // radial functions by the Chebyshev recurrence; reduce each A element over the warp
+            for (int s = 0; s < g.n_species; ++s) {
+                const bool mine = valid && sp == s;
+                T t0 = T(1), t1 = xs;
+                for (int nn = 0; nn < g.nmax; ++nn) {
+                    T tn;
+                    if (nn == 0) tn = T(1);
+                    else if (nn == 1) tn = xs;
+                    else {
+                        tn = T(2) * xs * t1 - t0;
+                        t0 = t1;
+                        t1 = tn;
+                    }
+                    const T rn = mine ? tn * fc : T(0);
+                    const int base = (s * g.nmax + nn) * g.n_lm;
+#pragma unroll
+                    for (int l = 0; l <= kAceLMax; ++l) {
+                        if (l > g.lmax) break;
+#pragma unroll
+                        for (int m = 0; m <= l; ++m) {
+                            T vr = rn * yr[lm_index(l, m)], vi = rn * yi[lm_index(l, m)];
+#pragma unroll
+                            for (int o = 16; o > 0; o >>= 1) {
+                                vr += __shfl_xor_sync(0xffffffffu, vr, o);
+                                vi += __shfl_xor_sync(0xffffffffu, vi, o);
+                            }
+                            if (lane == 0) {
+                                A[base + lm_index(l, m)].x += vr;
+                                A[base + lm_index(l, m)].y += vi;
+                            }
+                        }
+                    }
+                }
+            }
+            __syncwarp();
+        }
+        __syncwarp();
+        // invariants
+        T* o = out + (size_t)p * g.n_desc;
+        for (int d = lane; d < g.n_desc; d += 32) {
+            const AceCol cl = g.cols[d];
+            T v = T(0);
+            if (cl.kind == 1) {
+                v = A[cl.a1].x;
+            } else if (cl.kind == 2) {
+                const int l = cl.l1;
+                const T inv = T(1) / sqrt(T(2 * l + 1));
+                for (int m = -l; m <= l; ++m) {
+                    const C x = a_at<T>(A, cl.a1, l, m), y = a_at<T>(A, cl.a2, l, -m);
+                    const T cg = (((l - m) & 1) ? -inv : inv);  // <l m l -m | 0 0>
+                    v += cg * (x.x * y.x - x.y * y.y);
+                }
+            } else {
+                for (int q = cl.c_off; q < cl.c_off + cl.c_cnt; ++q) {
+                    const AceCoef cf = g.coefs[q];
+                    const C x = a_at<T>(A, cl.a1, cl.l1, cf.m1), y = a_at<T>(A, cl.a2, cl.l2, cf.m2);
+                    const C z = a_at<T>(A, cl.a3, cl.l3, -(cf.m1 + cf.m2));
+                    const T pr = x.x * y.x - x.y * y.y, pi_ = x.x * y.y + x.y * y.x;
+                    v += (T)cf.c * (pr * z.x - pi_ * z.y);
+                }
+            }
+            o[d] = v;
+        }
+        __syncwarp();
+    }
+}
+
+}  // namespace
+
+// columns in the order of the documented enumeration; returns the count
+static int ace_columns(const mala_ace_params* ap, std::vector<AceCol>* cols, std::vector<AceCoef>* coefs) {
+    const int ns = ap->n_species;
+    const int nmax = std::max(ap->nmax1, std::max(ap->nmax2, ap->nmax3));
+    const int lmax = std::max(ap->lmax2, ap->lmax3);
+    const int nlm = (lmax + 1) * (lmax + 2) / 2;
+    auto base = [&](int mu, int n) { return (mu * nmax + n) * nlm; };
+    std::vector<AceCol> cl;
+    std::vector<AceCoef> cf;
+    for (int mu = 0; mu < ns; ++mu)
+        for (int n = 0; n < ap->nmax1; ++n) cl.push_back(AceCol{1, base(mu, n), 0, 0, 0, 0, 0, 0, 0});
+    std::vector<std::pair<int, int>> ch2;
+    for (int mu = 0; mu < ns; ++mu)
+        for (int n = 0; n < ap->nmax2; ++n) ch2.push_back({mu, n});
+    for (size_t i = 0; i < ch2.size(); ++i)
+        for (size_t j = i; j < ch2.size(); ++j)
+            for (int l = 0; l <= ap->lmax2; ++l)
+                cl.push_back(AceCol{2, base(ch2[i].first, ch2[i].second), base(ch2[j].first, ch2[j].second), 0, l, l,
+                                    0, 0, 0});
+    struct Ch3 {
+        int mu, n, l;
+    };
+    std::vector<Ch3> ch3;
+    for (int mu = 0; mu < ns; ++mu)
+        for (int n = 0; n < ap->nmax3; ++n)
+            for (int l = 0; l <= ap->lmax3; ++l) ch3.push_back({mu, n, l});
+    std::vector<int> lists((size_t)(lmax + 1) * (lmax + 1) * (lmax + 1) * 2, -1);  // (l1,l2,l3) -> off, cnt
+    auto coef_list = [&](int l1, int l2, int l3, int* off, int* cnt) {
+        const size_t key = ((size_t)l1 * (lmax + 1) + l2) * (lmax + 1) + l3;
+        if (lists[2 * key] < 0) {
+            lists[2 * key] = (int)cf.size();
+            for (int m1 = -l1; m1 <= l1; ++m1)
+                for (int m2 = -l2; m2 <= l2; ++m2) {
+                    const int M = m1 + m2;
+                    if (M < -l3 || M > l3) continue;
+                    const double c = clebsch_gordan(2 * l1, 2 * m1, 2 * l2, 2 * m2, 2 * l3, 2 * M) *
+                                     clebsch_gordan(2 * l3, 2 * M, 2 * l3, -2 * M, 0, 0);
+                    if (c != 0.0) cf.push_back(AceCoef{c, m1, m2});
+                }
+            lists[2 * key + 1] = (int)cf.size() - lists[2 * key];
+        }
+        *off = lists[2 * key];
+        *cnt = lists[2 * key + 1];
+    };
+    for (size_t i = 0; i < ch3.size(); ++i)
+        for (size_t j = i; j < ch3.size(); ++j)
+            for (size_t k = j; k < ch3.size(); ++k) {
+                const int l1 = ch3[i].l, l2 = ch3[j].l, l3 = ch3[k].l;
+                if (l3 < std::abs(l1 - l2) || l3 > l1 + l2 || ((l1 + l2 + l3) & 1)) continue;
+                int off = 0, cnt = 0;
+                coef_list(l1, l2, l3, &off, &cnt);
+                cl.push_back(AceCol{3, base(ch3[i].mu, ch3[i].n), base(ch3[j].mu, ch3[j].n), base(ch3[k].mu, ch3[k].n),
+                                    l1, l2, l3, off, cnt});
+            }
+    if (cols) *cols = cl;
+    if (coefs) *coefs = cf;
+    return (int)cl.size();
+}
+
+int ace_count(const mala_ace_params* ap) { return ace_columns(ap, nullptr, nullptr); }
+
+int check_ace_params(const mala_ace_params* ap) {
+    if (!ap) return fail(MALA_ERR_INVALID_ARG, "ACE parameters are NULL");
+    if (!(ap->rcut > 0.0) || !std::isfinite(ap->rcut)) return fail(MALA_ERR_INVALID_ARG, "rcut must be > 0");
+    if (ap->n_species < 1 || ap->n_species > kAceSpecies)
+        return fail(MALA_ERR_UNSUPPORTED, "n_species must be 1..%d", kAceSpecies);
+    if (ap->nmax1 < 0 || ap->nmax2 < 0 || ap->nmax3 < 0 || ap->lmax2 < 0 || ap->lmax3 < 0)
+        return fail(MALA_ERR_INVALID_ARG, "negative ACE sizes");
+    const int nmax = std::max(ap->nmax1, std::max(ap->nmax2, ap->nmax3));
+    const int lmax = std::max(ap->lmax2, ap->lmax3);
+    if (nmax < 1 || nmax > kAceNMax) return fail(MALA_ERR_UNSUPPORTED, "radial count must be 1..%d", kAceNMax);
+    if (lmax > kAceLMax) return fail(MALA_ERR_UNSUPPORTED, "lmax must be <= %d", kAceLMax);
+    if (ap->n_species * nmax * (lmax + 1) * (lmax + 2) / 2 > kAceMaxA)
+        return fail(MALA_ERR_UNSUPPORTED, "n_species x nmax x (lmax+1)(lmax+2)/2 must be <= %d", kAceMaxA);
+    return MALA_OK;
+}
+
+// ACE descriptors of one snapshot from its staged atoms and complete neighbour lists
+int ace_from_lists(Ctx* c, const SnapDev& sd, const mala_snapshot* snap, const mala_ace_params* ap,
+                   const NbrOut& nl, void* out, mala_precision prec, cudaStream_t st) {
+    std::vector<AceCol> cols;
+    std::vector<AceCoef> coefs;
+    const int nd = ace_columns(ap, &cols, &coefs);
+    const int nmax = std::max(ap->nmax1, std::max(ap->nmax2, ap->nmax3));
+    const int lmax = std::max(ap->lmax2, ap->lmax3);
+    const int nlm = (lmax + 1) * (lmax + 2) / 2;
+    const int na = sd.g.n_atoms;
+    // N_lm for every compiled (l, m >= 0): the kernel evaluates Y up to kAceLMax
+    std::vector<double> yn(kAceLM);
+    for (int l = 0; l <= kAceLMax; ++l)
+        for (int m = 0; m <= l; ++m) {
+            double r = 1.0;  // (l - m)! / (l + m)!
+            for (int k = l - m + 1; k <= l + m; ++k) r /= (double)k;
+            yn[l * (l + 1) / 2 + m] = std::sqrt((2.0 * l + 1.0) / (4.0 * 3.14159265358979323846) * r);
+        }
+    auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+    const size_t b_cols = al(sizeof(AceCol) * std::max<size_t>(cols.size(), 1));
+    const size_t b_coef = al(sizeof(AceCoef) * std::max<size_t>(coefs.size(), 1));
+    const size_t b_yn = al(sizeof(double) * kAceLM);
+    const size_t b_sp = al(sizeof(int) * std::max(na, 1));
+    MALA_TRY(c->ws_ace.reserve(c, b_cols + b_coef + b_yn + b_sp));
+    char* base = c->ws_ace.as<char>();
+    AceCol* d_cols = reinterpret_cast<AceCol*>(base);
+    AceCoef* d_coef = reinterpret_cast<AceCoef*>(base + b_cols);
+    double* d_yn = reinterpret_cast<double*>(base + b_cols + b_coef);
+    int* d_sp = reinterpret_cast<int*>(base + b_cols + b_coef + b_yn);
+    // the tables are host vectors of this call: copy synchronously before they go out of scope
+    if (!cols.empty()) MALA_CUDA_TRY(cudaMemcpyAsync(d_cols, cols.data(), sizeof(AceCol) * cols.size(), cudaMemcpyHostToDevice, st));
+    if (!coefs.empty()) MALA_CUDA_TRY(cudaMemcpyAsync(d_coef, coefs.data(), sizeof(AceCoef) * coefs.size(), cudaMemcpyHostToDevice, st));
+    MALA_CUDA_TRY(cudaMemcpyAsync(d_yn, yn.data(), sizeof(double) * kAceLM, cudaMemcpyHostToDevice, st));
+    if (na > 0 && snap->species)
+        MALA_CUDA_TRY(cudaMemcpyAsync(d_sp, snap->species, sizeof(int) * na, cudaMemcpyHostToDevice, st));
+    AceArgs g;
+    g.P = sd.g.P;
+    g.cap = nl.dbg_cap;
+    g.cnt = nl.dbg_counts;
+    g.atoms = nl.dbg_atoms;
+    g.shifts = nl.dbg_shifts;
+    g.species = snap->species ? d_sp : nullptr;
+    g.wpos = sd.wpos;
+    g.gcoord = sd.gcoord;
+    g.n_atoms = na;
+    for (int k = 0; k < 3; ++k) {
+        g.grid[k] = sd.g.grid[k];
+        g.L[k] = sd.g.L[k];
+    }
+    g.rcut = ap->rcut;
+    g.lmax = lmax;
+    g.nmax = nmax;
+    g.n_species = ap->n_species;
+    g.n_lm = nlm;
+    g.nA = ap->n_species * nmax * nlm;
+    g.n_desc = nd;
+    g.cols = d_cols;
+    g.coefs = d_coef;
+    g.ynorm = d_yn;
+    if (g.P > 0 && nd > 0) {
+        const int64_t want = (g.P + kAceWarps - 1) / kAceWarps;
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)c->num_sms * 8));
+        if (prec == MALA_MIXED) {
+            const size_t smem = sizeof(float2) * (size_t)g.nA * kAceWarps;
+            MALA_PROF(c, "k_ace", st, (k_ace<float><<<grid, kAceWarps * 32, smem, st>>>(g, static_cast<float*>(out))));
+        } else {
+            const size_t smem = sizeof(double2) * (size_t)g.nA * kAceWarps;
+            cudaFuncSetAttribute(k_ace<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            MALA_PROF(c, "k_ace", st, (k_ace<double><<<grid, kAceWarps * 32, smem, st>>>(g, static_cast<double*>(out))));
+        }
+        MALA_CUDA_TRY(cudaGetLastError());
+    }
+    MALA_CUDA_TRY(cudaStreamSynchronize(st));
+    return MALA_OK;
+}
+
+}  // namespace mala

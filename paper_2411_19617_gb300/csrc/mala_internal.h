@@ -152,7 +152,7 @@ struct Ctx {
     // workspaces of the force path
     ForceTables ftab;
     DevBuf ws_ftab, ws_force_y, ws_force_aux, ws_force_u, ws_force_nbr, ws_force_beta, ws_force_mlp, ws_force_g,
-        ws_force_bt;
+        ws_force_bt, ws_ace;
     void* cublas = nullptr;  // cuBLAS handle of the network's backward GEMMs (created on first use)
     double* host_dos = nullptr;     // pinned [max N_E]
     size_t host_dos_len = 0;
@@ -300,6 +300,12 @@ int descriptor_adjoint(Ctx* c, const SnapDev& sd, const mala_snapshot* snap, con
 int mlp_backward(Ctx* c, const Model* m, const void* B, int64_t P, const double* v_dev, void* beta,
                  mala_precision prec, cudaStream_t st);
 void cublas_release(Ctx* c);
+// ACE descriptors (ace.cu): parameter check, column count, descriptors from a staged snapshot and its
+// complete neighbour lists (nl.dbg_*), out: [P][n_desc] float (MIXED) or double
+int check_ace_params(const mala_ace_params* ap);
+int ace_count(const mala_ace_params* ap);
+int ace_from_lists(Ctx* c, const SnapDev& sd, const mala_snapshot* snap, const mala_ace_params* ap,
+                   const NbrOut& nl, void* out, mala_precision prec, cudaStream_t st);
 // dE_b/dD at fixed N_e for D = dV * dos_sum: g_dev[n_E] = gscale * dE_b/dD; *fermi, *mu_tilde (host)
 int energy_gradient(Ctx* c, const double* dos_sum, double dV, const mala_energy_grid* eg, double gscale,
                     double* g_dev, double* fermi, double* mu_tilde, cudaStream_t st);

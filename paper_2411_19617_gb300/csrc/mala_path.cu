@@ -394,6 +394,30 @@ static int stage_force_descriptors(Ctx* c, const mala_snapshot* snap, const mala
     return fail(MALA_ERR_UNSUPPORTED, "neighbour-list capacity for the force step could not be established");
 }
 
+// complete neighbour lists of one snapshot (no descriptors) into ws_force_nbr
+static int stage_lists_only(Ctx* c, const mala_snapshot* snap, double rcut, int n_species, NbrOut* nl,
+                            cudaStream_t st) {
+    const int64_t P = (int64_t)snap->grid[0] * snap->grid[1] * snap->grid[2];
+    mala_bispectrum_params bp = {0, rcut, 0.99363, 0.0, 1.0, n_species, nullptr};
+    int cap = std::max(32, (c->kmax_hint + 7) & ~7);
+    for (int attempt = 0; attempt < 3; ++attempt) {
+        const size_t Pp = (size_t)((P + 63) & ~int64_t(63));
+        MALA_TRY(c->ws_force_nbr.reserve(c, sizeof(int) * Pp * (1 + 4 * (size_t)cap) + 256));
+        NbrOut d;
+        d.dbg_counts = c->ws_force_nbr.as<int>();
+        d.dbg_atoms = d.dbg_counts + Pp;
+        d.dbg_shifts = d.dbg_atoms + Pp * cap;
+        d.dbg_cap = cap;
+        MALA_TRY(snap_descriptors_full(c, snap, &bp, nullptr, nullptr, &d, MALA_MIXED, st));
+        if (d.kmax <= cap) {
+            *nl = d;
+            return MALA_OK;
+        }
+        cap = (d.kmax + 7) & ~7;
+    }
+    return fail(MALA_ERR_UNSUPPORTED, "neighbour-list capacity could not be established");
+}
+
 static int adjoint_of_staged(Ctx* c, const mala_snapshot* snap, const mala_bispectrum_params* bp, mala_precision prec,
                              const void* beta, const NbrOut& nl, double* F, cudaStream_t st) {
     const SnapDev& sd = static_cast<const BatchSnap*>(c->host_batch)[0].sd;
@@ -753,6 +777,30 @@ int mala_band_forces(mala_ctx* c, const mala_snapshot* snap, const mala_bispectr
     MALA_TRY(c->ws_force_bt.reserve(c, (size_t)P * nB * e + 256));
     MALA_TRY(mlp_backward(c, m, c->ws_B.ptr, P, c->ws_w.as<double>(), c->ws_force_bt.ptr, prec, st));
     return adjoint_of_staged(c, snap, bp, prec, c->ws_force_bt.ptr, nl, forces_host, st);
+}
+
+int mala_ace_count(const mala_ace_params* ap, int32_t* n_desc) {
+    if (!n_desc) return fail(MALA_ERR_INVALID_ARG, "NULL argument");
+    MALA_TRY(check_ace_params(ap));
+    *n_desc = ace_count(ap);
+    return MALA_OK;
+}
+
+int mala_ace_descriptors(mala_ctx* c, const mala_snapshot* snap, const mala_ace_params* ap, void* D_dev,
+                         mala_precision prec, void* stream) {
+    if (!c) return fail(MALA_ERR_INVALID_ARG, "context is NULL");
+    MALA_TRY(check_snapshot(snap));
+    MALA_TRY(check_ace_params(ap));
+    if (prec != MALA_MIXED && prec != MALA_FP64_PLAIN) return fail(MALA_ERR_INVALID_ARG, "bad precision");
+    const int64_t P = (int64_t)snap->grid[0] * snap->grid[1] * snap->grid[2];
+    if (P > 0 && !D_dev) return fail(MALA_ERR_INVALID_ARG, "output is NULL");
+    std::lock_guard<std::mutex> lk(c->mu);
+    MALA_CUDA_TRY(cudaSetDevice(c->device));
+    cudaStream_t st = as_stream(stream);
+    NbrOut nl;
+    MALA_TRY(stage_lists_only(c, snap, ap->rcut, ap->n_species, &nl, st));
+    const SnapDev& sd = static_cast<const BatchSnap*>(c->host_batch)[0].sd;
+    return ace_from_lists(c, sd, snap, ap, nl, D_dev, prec, st);
 }
 
 }  // extern "C"

@@ -43,3 +43,13 @@ def test_binding_raises_without_the_library(tmp_path):
             _lib.lib(str(tmp_path / "missing.so"))
     finally:
         _lib._lib = saved
+
+
+def test_ace_column_count_matches_the_oracle_enumeration():
+    # mala_ace_count runs on the host: the library's enumeration against the oracle's
+    from oracle import ace
+    from paper_2411_19617_gb300 import api
+    for ap in (ace.AceParams(rcut=4.676), ace.AceParams(rcut=5.0, n_species=2, nmax1=3, nmax2=3, lmax2=4, nmax3=2,
+                                                        lmax3=4), ace.AceParams(rcut=4.0, nmax1=1, nmax2=0, lmax2=0,
+                                                                                nmax3=1, lmax3=8)):
+        assert api.ace_count(ap) == len(ace.descriptor_index(ap))
