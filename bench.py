@@ -54,6 +54,7 @@ def parse():
                     help="atom-count cap of the serving sample (bounds the FP64 arm's time)")
     ap.add_argument("--forces-calls", type=int, default=3,
                     help="timed calls of the band-energy forces leg (0 skips it)")
+    ap.add_argument("--ace-calls", type=int, default=3, help="timed calls of the ACE descriptor leg (0 skips it)")
     return ap.parse_args()
 
 
@@ -233,6 +234,44 @@ def forces_leg(ctx, api, roofline, model, snap, bp, eg, ne, calls, peak_tflops):
             "neighbour_pairs": pairs, "precision": "f32 descriptors/u/backward/adjoint, bf16 forward network, "
                                                    "f64 dE_b/dD, forces summed in 2^-40 fixed point",
             "max_abs_force_eV_per_A": float(np.max(np.abs(F))), "kernels": kern, "roofline": roof}
+
+
+class AceSetting:
+    """ACE descriptor set timed beside the bench workload: 401 columns (8 N = 1, 147 N = 2, 246 N = 3)."""
+    rcut, n_species, nmax1, nmax2, lmax2, nmax3, lmax3 = 4.676, 1, 8, 6, 6, 3, 4
+
+
+def ace_leg(ctx, api, roofline, snap, calls, peak_tflops):
+    """mala_ace_descriptors on the bench snapshot: ms per call, points/s, k_ace's roofline."""
+    import torch
+    ap = AceSetting()
+    counts, _, _, _ = ctx.neighbor_lists(snap, ap.rcut, cap=0)
+    pairs = int(counts.sum().item())
+    P = int(np.prod(snap.grid))
+    out = ctx.ace_descriptors(snap, ap, api.MIXED)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(calls):
+        ctx.ace_descriptors(snap, ap, api.MIXED, out=out)
+    ev1.record()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / calls
+    ctx.profile(True)
+    ctx.ace_descriptors(snap, ap, api.MIXED, out=out)
+    kern = {}
+    for k in ("k_neighbors", "k_ace"):
+        t, n = ctx.profile_get(k)
+        kern[k] = {"ms": t, "launches": n}
+    ctx.profile(False)
+    flops = roofline.ace_flops(ap, pairs, P)
+    t = kern["k_ace"]["ms"]
+    ach = flops / (t / 1e3) / 1e12 if t > 0 else 0.0
+    return {"ms_per_call": ms, "grid_points_per_s": P / (ms / 1e3), "columns": int(out.shape[1]),
+            "setting": {k: getattr(ap, k) for k in ("rcut", "n_species", "nmax1", "nmax2", "lmax2", "nmax3", "lmax3")},
+            "neighbour_pairs": pairs, "kernels": kern,
+            "roofline": {"k_ace": {"bound": "alu", "achieved": ach, "peak": peak_tflops, "unit": "TFLOP/s",
+                                   "frac": ach / peak_tflops, "flops": flops}}}
 
 
 def kernel_hash(*names):
@@ -441,6 +480,9 @@ def run_ours(args):
         forces = None
         if world == 1 and args.forces_calls > 0:
             forces = forces_leg(ctx, api, roofline, model, snap, bp, eg, ne, args.forces_calls, peak)
+        ace_res = None
+        if world == 1 and args.ace_calls > 0:
+            ace_res = ace_leg(ctx, api, roofline, snap, args.ace_calls, peak)
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -450,7 +492,7 @@ def run_ours(args):
                            "l2": "working set larger than L2 (u: 1.5 GB, neighbour records 0.9 GB, LDOS 0.36 GB)",
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-                "clocks": clk, "kernels": kernels, "serving": serving, "forces": forces,
+                "clocks": clk, "kernels": kernels, "serving": serving, "forces": forces, "ace": ace_res,
                 "fermi_eV": r["fermi"], "band_energy_eV": r["band_energy"], "entropy_term_eV": r["entropy_term"]}
         print(json.dumps(line), flush=True)
     if dist:

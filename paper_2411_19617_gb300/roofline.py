@@ -122,5 +122,32 @@ def force_flops_per_pair(twojmax: int) -> int:
     return f
 
 
+def ace_flops(ap, pairs: int, points: int) -> int:
+    """Algorithmic FLOP of the ACE descriptors: per neighbour pair the spherical
+    harmonics (8 per (l, m >= 0)), the Chebyshev radial functions (3 per n) and the
+    grid-basis accumulation (4 per (n, l, m >= 0): real R times complex Y, added);
+    per point the invariants (N = 2: 4 per m; N = 3: 10 per (m1, m2) term)."""
+    nmax = max(ap.nmax1, ap.nmax2, ap.nmax3)
+    lmax = max(ap.lmax2, ap.lmax3)
+    nlm = (lmax + 1) * (lmax + 2) // 2
+    per_pair = 8 * nlm + 3 * nmax + 4 * nmax * nlm
+    ns = ap.n_species
+    n2ch = ns * ap.nmax2
+    per_point = (n2ch * (n2ch + 1) // 2) * sum(4 * (2 * l + 1) for l in range(ap.lmax2 + 1))
+    ch3 = [(mu, n, l) for mu in range(ns) for n in range(ap.nmax3) for l in range(ap.lmax3 + 1)]
+    terms = {}
+    for i in range(len(ch3)):
+        for j in range(i, len(ch3)):
+            for k in range(j, len(ch3)):
+                l1, l2, l3 = ch3[i][2], ch3[j][2], ch3[k][2]
+                if abs(l1 - l2) <= l3 <= l1 + l2 and (l1 + l2 + l3) % 2 == 0:
+                    key = (l1, l2, l3)
+                    if key not in terms:
+                        terms[key] = sum(1 for m1 in range(-l1, l1 + 1) for m2 in range(-l2, l2 + 1)
+                                         if abs(m1 + m2) <= l3)
+                    per_point += 10 * terms[key]
+    return per_pair * pairs + per_point * points
+
+
 def fp32_peak_tflops(sm_mhz: float) -> float:
     return GB300_SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
