@@ -67,10 +67,14 @@ struct AceArgs {
     int lmax, nmax, n_species, n_lm, nA, n_desc;
     const AceCol* cols;
     const AceCoef* coefs;
-    const double* ynorm;  // N_lm by (l, m >= 0) index
+    int stage;            // column and coefficient tables copied into shared memory
+    int n_coef;
 };
 
 __device__ __forceinline__ int lm_index(int l, int m) { return l * (l + 1) / 2 + m; }
+
+// N_lm = sqrt((2l+1)/(4 pi) (l-m)!/(l+m)!) by (l, m >= 0) index, every compiled l
+__constant__ double c_ace_ynorm[kAceLM];
 
 template <class T>
 __device__ __forceinline__ typename Cx<T>::type a_at(const typename Cx<T>::type* A, int base, int l, int m) {
@@ -83,12 +87,30 @@ __device__ __forceinline__ typename Cx<T>::type a_at(const typename Cx<T>::type*
     return v;
 }
 
+__host__ __device__ inline size_t ace_coef_bytes(int n_coef) { return ((size_t)n_coef * sizeof(AceCoef) + 15) & ~size_t(15); }
+__host__ __device__ inline size_t ace_table_bytes(int n_desc, int n_coef) {
+    return ace_coef_bytes(n_coef) + (((size_t)n_desc * sizeof(AceCol) + 15) & ~size_t(15));
+}
+
 template <class T>
 __global__ void __launch_bounds__(kAceWarps * 32) k_ace(AceArgs g, T* __restrict__ out) {
     using C = typename Cx<T>::type;
     extern __shared__ __align__(16) unsigned char smem_ace[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    C* A = reinterpret_cast<C*>(smem_ace) + (size_t)warp * g.nA;
+    // shared memory: [coefficients][columns] (when staged) | A of each warp
+    const size_t tab_bytes = g.stage ? ace_table_bytes(g.n_desc, g.n_coef) : 0;
+    const AceCoef* coefs = g.coefs;
+    const AceCol* cols = g.cols;
+    if (g.stage) {
+        AceCoef* sc = reinterpret_cast<AceCoef*>(smem_ace);
+        AceCol* scl = reinterpret_cast<AceCol*>(smem_ace + ace_coef_bytes(g.n_coef));
+        for (int i = threadIdx.x; i < g.n_coef; i += blockDim.x) sc[i] = g.coefs[i];
+        for (int i = threadIdx.x; i < g.n_desc; i += blockDim.x) scl[i] = g.cols[i];
+        __syncthreads();
+        coefs = sc;
+        cols = scl;
+    }
+    C* A = reinterpret_cast<C*>(smem_ace + tab_bytes) + (size_t)warp * g.nA;
     for (int64_t p = (int64_t)blockIdx.x * kAceWarps + warp; p < g.P; p += (int64_t)gridDim.x * kAceWarps) {
         for (int e = lane; e < g.nA; e += 32) {
             A[e].x = T(0);
@@ -150,7 +172,7 @@ __global__ void __launch_bounds__(kAceWarps * 32) k_ace(AceArgs g, T* __restrict
                             p2 = p1;
                             p1 = pl;
                         }
-                        const T nrm = (T)g.ynorm[lm_index(l, m)] * (center && l > 0 ? T(0) : T(1));
+                        const T nrm = (T)c_ace_ynorm[lm_index(l, m)] * (center && l > 0 ? T(0) : T(1));
                         yr[lm_index(l, m)] = nrm * pl * er;
                         yi[lm_index(l, m)] = nrm * pl * ei;
                     }
@@ -196,7 +218,7 @@ __global__ void __launch_bounds__(kAceWarps * 32) k_ace(AceArgs g, T* __restrict
         // invariants
         T* o = out + (size_t)p * g.n_desc;
         for (int d = lane; d < g.n_desc; d += 32) {
-            const AceCol cl = g.cols[d];
+            const AceCol cl = cols[d];
             T v = T(0);
             if (cl.kind == 1) {
                 v = A[cl.a1].x;
@@ -210,7 +232,7 @@ __global__ void __launch_bounds__(kAceWarps * 32) k_ace(AceArgs g, T* __restrict
                 }
             } else {
                 for (int q = cl.c_off; q < cl.c_off + cl.c_cnt; ++q) {
-                    const AceCoef cf = g.coefs[q];
+                    const AceCoef cf = coefs[q];
                     const C x = a_at<T>(A, cl.a1, cl.l1, cf.m1), y = a_at<T>(A, cl.a2, cl.l2, cf.m2);
                     const C z = a_at<T>(A, cl.a3, cl.l3, -(cf.m1 + cf.m2));
                     const T pr = x.x * y.x - x.y * y.y, pi_ = x.x * y.y + x.y * y.x;
@@ -323,18 +345,16 @@ int ace_from_lists(Ctx* c, const SnapDev& sd, const mala_snapshot* snap, const m
     auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
     const size_t b_cols = al(sizeof(AceCol) * std::max<size_t>(cols.size(), 1));
     const size_t b_coef = al(sizeof(AceCoef) * std::max<size_t>(coefs.size(), 1));
-    const size_t b_yn = al(sizeof(double) * kAceLM);
     const size_t b_sp = al(sizeof(int) * std::max(na, 1));
-    MALA_TRY(c->ws_ace.reserve(c, b_cols + b_coef + b_yn + b_sp));
+    MALA_TRY(c->ws_ace.reserve(c, b_cols + b_coef + b_sp));
     char* base = c->ws_ace.as<char>();
     AceCol* d_cols = reinterpret_cast<AceCol*>(base);
     AceCoef* d_coef = reinterpret_cast<AceCoef*>(base + b_cols);
-    double* d_yn = reinterpret_cast<double*>(base + b_cols + b_coef);
-    int* d_sp = reinterpret_cast<int*>(base + b_cols + b_coef + b_yn);
+    int* d_sp = reinterpret_cast<int*>(base + b_cols + b_coef);
     // the tables are host vectors of this call: copy synchronously before they go out of scope
     if (!cols.empty()) MALA_CUDA_TRY(cudaMemcpyAsync(d_cols, cols.data(), sizeof(AceCol) * cols.size(), cudaMemcpyHostToDevice, st));
     if (!coefs.empty()) MALA_CUDA_TRY(cudaMemcpyAsync(d_coef, coefs.data(), sizeof(AceCoef) * coefs.size(), cudaMemcpyHostToDevice, st));
-    MALA_CUDA_TRY(cudaMemcpyAsync(d_yn, yn.data(), sizeof(double) * kAceLM, cudaMemcpyHostToDevice, st));
+    MALA_CUDA_TRY(cudaMemcpyToSymbolAsync(c_ace_ynorm, yn.data(), sizeof(double) * kAceLM, 0, cudaMemcpyHostToDevice, st));
     if (na > 0 && snap->species)
         MALA_CUDA_TRY(cudaMemcpyAsync(d_sp, snap->species, sizeof(int) * na, cudaMemcpyHostToDevice, st));
     AceArgs g;
@@ -360,15 +380,18 @@ int ace_from_lists(Ctx* c, const SnapDev& sd, const mala_snapshot* snap, const m
     g.n_desc = nd;
     g.cols = d_cols;
     g.coefs = d_coef;
-    g.ynorm = d_yn;
+    g.n_coef = (int)coefs.size();
+    g.stage = ace_table_bytes(nd, g.n_coef) <= (size_t)96 * 1024 ? 1 : 0;
     if (g.P > 0 && nd > 0) {
         const int64_t want = (g.P + kAceWarps - 1) / kAceWarps;
         const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)c->num_sms * 8));
+        const size_t tb = g.stage ? ace_table_bytes(nd, g.n_coef) : 0;
         if (prec == MALA_MIXED) {
-            const size_t smem = sizeof(float2) * (size_t)g.nA * kAceWarps;
+            const size_t smem = tb + sizeof(float2) * (size_t)g.nA * kAceWarps;
+            cudaFuncSetAttribute(k_ace<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             MALA_PROF(c, "k_ace", st, (k_ace<float><<<grid, kAceWarps * 32, smem, st>>>(g, static_cast<float*>(out))));
         } else {
-            const size_t smem = sizeof(double2) * (size_t)g.nA * kAceWarps;
+            const size_t smem = tb + sizeof(double2) * (size_t)g.nA * kAceWarps;
             cudaFuncSetAttribute(k_ace<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             MALA_PROF(c, "k_ace", st, (k_ace<double><<<grid, kAceWarps * 32, smem, st>>>(g, static_cast<double*>(out))));
         }
