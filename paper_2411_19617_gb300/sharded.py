@@ -12,6 +12,11 @@ quantity that couples the slabs is the DOS D(e_xi) = dV sum_r L(r, xi)
 4. evaluates n(r) = sum_xi w0_xi(e_F) L(r, xi) (Eq. density.from.ldos) on its
    own rows; the electron-count check dV sum_r n(r) is all-reduced too.
 
+The band-energy forces (Eq. forcesmala with E = E_b) shard the same way: with
+the global D every rank forms the same dE_b/dD, runs the network's backward
+pass and the descriptor adjoint on its own rows, and the per-atom partial
+forces are all-reduced (sum) -- the second exchange step (``forces_sharded``).
+
 The per-rank arithmetic is delegated to a backend (``DeviceBackend`` runs it
 in the CUDA library); the module itself holds only the orchestration, so the
 exchange logic can be exercised with CPU ranks.
@@ -72,6 +77,27 @@ def integrate_sharded(backend, ldos_local, n_points_total: int, volume: float, e
             "density": dens, "electron_count": count}
 
 
+def forces_sharded(backend, snap, rows, volume: float, eg, n_electrons: float, group=None):
+    """f_alpha = -dE_b/dR_alpha with this rank holding grid rows [rows[0], rows[1]).
+
+    backend.forward(snap, rows) -> (B_local, ldos_local); backend.column_sums and
+    backend.integrate as for ``integrate_sharded``; backend.energy_gradient(D, eg,
+    n_electrons) -> dE_b/dD (host [n_E]); backend.ldos_backward(B_local, v) -> beta
+    rows; backend.descriptor_forces(snap, beta_local, rows) -> this rank's partial
+    forces [n_atoms][3].  Returns the integrate_sharded dict plus "forces" (the
+    all-reduced sum, the same bits on every rank)."""
+    P = int(np.prod(snap.grid))
+    r0, r1 = rows
+    B_loc, L_loc = backend.forward(snap, (r0, r1))
+    res = integrate_sharded(backend, L_loc, P, volume, eg, n_electrons, group=group)
+    g = np.asarray(backend.energy_gradient(res["dos"], eg, n_electrons), np.float64)
+    dV = float(volume) / float(P)
+    beta = backend.ldos_backward(B_loc, dV * g)
+    part = np.asarray(backend.descriptor_forces(snap, beta, (r0, r1)), np.float64)
+    res["forces"] = _allreduce_sum(part.reshape(-1), group).reshape(part.shape)
+    return res
+
+
 def _any_grid_of(ldos):
     """An energy grid with the LDOS's N_E (only the column sums are used)."""
     from .workloads import EnergyGrid
@@ -102,3 +128,33 @@ class DeviceBackend:
         vol_local = dV * int(ldos_local.shape[0])
         r = self.ctx.integrate(ldos_local, vol_local, eg, self.precision, dos_sum=ds, n_electrons=n_electrons)
         return {"fermi": r["fermi"], "band_energy": r["band_energy"], "density": r["density"].cpu().numpy()}
+
+    # ---- forces (needs bp and model: set by with_model) ----------------------
+
+    def with_model(self, bp, model):
+        self.bp, self.model = bp, model
+        return self
+
+    def forward(self, snap, rows):
+        """Descriptors of the snapshot (computed whole: the neighbour search is per
+        tile) and the LDOS of this rank's rows."""
+        r0, r1 = rows
+        B = self.ctx.descriptors(snap, self.bp, self.precision)[r0:r1].contiguous()
+        L, _ = self.ctx.ldos_forward(self.model, B, self.precision)
+        return B, L
+
+    def energy_gradient(self, D, eg, n_electrons):
+        return self.ctx.band_energy_gradient(D, eg, n_electrons=n_electrons)["grad"]
+
+    def ldos_backward(self, B_local, v):
+        return self.ctx.ldos_backward(self.model, B_local, v, self.precision)
+
+    def descriptor_forces(self, snap, beta_local, rows):
+        """The adjoint over the whole grid with beta zero outside this rank's rows
+        (zero rows contribute exactly nothing)."""
+        import torch
+        r0, r1 = rows
+        P = int(np.prod(snap.grid))
+        beta = torch.zeros((P, beta_local.shape[1]), dtype=beta_local.dtype, device=beta_local.device)
+        beta[r0:r1] = beta_local
+        return self.ctx.descriptor_forces(snap, self.bp, beta, self.precision)

@@ -59,3 +59,31 @@ def test_slabs_reproduce_the_whole_grid_fp64(world):
     np.testing.assert_allclose(dens, ref["density"], rtol=1e-10, atol=1e-12)
     local = sum(dV * float(np.sum(p["density"])) for p in parts)
     assert local == pytest.approx(ne, rel=1e-6)
+
+
+@pytest.mark.parametrize("world", [1, 2])
+def test_sharded_forces_pieces_reproduce_band_forces_fp64(world):
+    # the library backend's per-rank pieces, the two exchanges (DOS, forces) summed in-process
+    torch = need_gpu()
+    from paper_2411_19617_gb300 import api
+    c = ctx()
+    snap = wl.al_fcc(2, 0.15, 6, seed=8)
+    bp = wl.BispectrumParams(twojmax=4, rcut=4.676)
+    B = oracle.bispectrum_grid(snap, bp)
+    mlp = wl.random_mlp((B.shape[1], 16, 16, 21), seed=9, out_bias=1.0)
+    mlp = wl.with_input_scaling(mlp, B.mean(0), 1.0 / (B.std(0) + 1e-12))
+    eg = wl.EnergyGrid(n_E=21, e0_eV=-4.0, de_eV=0.4, kT_eV=0.1)
+    P, vol = snap.n_points, float(snap.volume)
+    dV = vol / P
+    L = oracle.mlp_forward(B, mlp.W, mlp.b, mlp.leaky_slope, mlp.in_shift, mlp.in_scale)
+    ne = oracle.electron_count(oracle.dos(L, dV), 0.0, eg.e0_eV, eg.de_eV, eg.kT_eV)
+    model = api.Model(c, mlp)
+    whole = c.band_forces(snap, bp, model, eg, api.FP64_PLAIN, n_electrons=ne)
+    be = sharded.DeviceBackend(c, api.FP64_PLAIN).with_model(bp, model)
+    slabs = [sharded.row_range(P, r, world) for r in range(world)]
+    parts = [be.forward(snap, rows) for rows in slabs]
+    sums = sum(be.column_sums(Lr) for _, Lr in parts)
+    g = be.energy_gradient(dV * sums, eg, ne)
+    F = sum(be.descriptor_forces(snap, be.ldos_backward(Br, dV * g), rows) for (Br, _), rows in zip(parts, slabs))
+    scale = np.max(np.abs(whole["forces"]))
+    np.testing.assert_allclose(F, whole["forces"], rtol=1e-9, atol=1e-9 * scale)
