@@ -12,7 +12,9 @@ Counts follow the definitions, not the kernels' instruction streams:
 """
 from __future__ import annotations
 
+from fractions import Fraction
 from functools import lru_cache
+from math import factorial
 
 
 def triples(twojmax: int):
@@ -21,22 +23,47 @@ def triples(twojmax: int):
 
 
 @lru_cache(maxsize=None)
+def cg_nonzero(j1: int, m1: int, j2: int, m2: int, j: int, m: int) -> bool:
+    """Whether <j1 m1 j2 m2 | j m> (twice-units) is nonzero: the selection rules, then
+    Racah's alternating sum evaluated exactly in rationals (the square-root prefactor
+    never vanishes for an allowed coupling; the sum has accidental zeros such as
+    <1 0 1 0 | 1 0>).  Used only to count the terms an algorithm needs."""
+    if m1 + m2 != m or abs(m1) > j1 or abs(m2) > j2 or abs(m) > j:
+        return False
+    if (j1 + m1) % 2 or (j2 + m2) % 2 or (j + m) % 2 or (j1 + j2 + j) % 2 or not abs(j1 - j2) <= j <= j1 + j2:
+        return False
+    A = (j1 + j2 - j) // 2
+    s = Fraction(0)
+    for k in range(A + 1):
+        d = ((j1 - m1) // 2 - k, (j2 + m2) // 2 - k, (j - j2 + m1) // 2 + k, (j - j1 - m2) // 2 + k)
+        if min(d) < 0:
+            continue
+        den = factorial(k) * factorial(A - k)
+        for x in d:
+            den *= factorial(x)
+        s += Fraction(-1 if k % 2 else 1, den)
+    return s != 0
+
+
+@lru_cache(maxsize=None)
 def zi_terms_half(twojmax: int) -> int:
-    """Coupling terms of the half set of Z.  For j1 == j2 the row pairs
+    """Coupling terms of the half set of Z whose two Clebsch-Gordan factors are
+    nonzero (the terms the contraction needs).  For j1 == j2 the row pairs
     (m1a, m2a) and (m2a, m1a) give the same product (the two Clebsch-Gordan
     factors change sign together under the exchange), so only m1a <= m2a
     is counted."""
     total = 0
     for (j1, j2, j) in triples(twojmax):
         d = (j1 + j2 - j) // 2
-
-        def nvalid(mb, sym=False):
-            return sum(1 for m1 in range(j1 + 1) if 0 <= mb - m1 + d <= j2 and (not sym or m1 <= mb - m1 + d))
-
         for ma in range(j + 1):
             for mb in range(j + 1):
-                if (2 * ma < j) or (2 * ma == j and 2 * mb <= j):
-                    total += nvalid(ma, sym=(j1 == j2)) * nvalid(mb)
+                if not ((2 * ma < j) or (2 * ma == j and 2 * mb <= j)):
+                    continue
+                rows = [m1 for m1 in range(j1 + 1) if 0 <= ma - m1 + d <= j2 and (j1 != j2 or m1 <= ma - m1 + d)
+                        and cg_nonzero(j1, 2 * m1 - j1, j2, 2 * (ma - m1 + d) - j2, j, 2 * ma - j)]
+                cols = [m1 for m1 in range(j1 + 1) if 0 <= mb - m1 + d <= j2
+                        and cg_nonzero(j1, 2 * m1 - j1, j2, 2 * (mb - m1 + d) - j2, j, 2 * mb - j)]
+                total += len(rows) * len(cols)
     return total
 
 
@@ -90,7 +117,8 @@ def yi_terms_half(twojmax: int):
         rows = []
         for ma in range(c + 1):
             m = 2 * ma - c
-            rows.append(sum(1 for m1a in range(a + 1) if abs(m - (2 * m1a - a)) <= b))
+            rows.append(sum(1 for m1a in range(a + 1) if abs(m - (2 * m1a - a)) <= b
+                            and cg_nonzero(a, 2 * m1a - a, b, m - (2 * m1a - a), c, m)))
         for ma in range(c + 1):
             for mb in range(c + 1):
                 if 2 * ma > c or (2 * ma == c and 2 * mb > c):
@@ -126,7 +154,8 @@ def ace_flops(ap, pairs: int, points: int) -> int:
     """Algorithmic FLOP of the ACE descriptors: per neighbour pair the spherical
     harmonics (8 per (l, m >= 0)), the Chebyshev radial functions (3 per n) and the
     grid-basis accumulation (4 per (n, l, m >= 0): real R times complex Y, added);
-    per point the invariants (N = 2: 4 per m; N = 3: 10 per (m1, m2) term)."""
+    per point the invariants (N = 2: 4 per m; N = 3: 10 per (m1, m2) term with a nonzero
+    Clebsch-Gordan factor)."""
     nmax = max(ap.nmax1, ap.nmax2, ap.nmax3)
     lmax = max(ap.lmax2, ap.lmax3)
     nlm = (lmax + 1) * (lmax + 2) // 2
@@ -144,7 +173,8 @@ def ace_flops(ap, pairs: int, points: int) -> int:
                     key = (l1, l2, l3)
                     if key not in terms:
                         terms[key] = sum(1 for m1 in range(-l1, l1 + 1) for m2 in range(-l2, l2 + 1)
-                                         if abs(m1 + m2) <= l3)
+                                         if abs(m1 + m2) <= l3
+                                         and cg_nonzero(2 * l1, 2 * m1, 2 * l2, 2 * m2, 2 * l3, 2 * (m1 + m2)))
                     per_point += 10 * terms[key]
     return per_pair * pairs + per_point * points
 
