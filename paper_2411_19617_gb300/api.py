@@ -83,6 +83,21 @@ def ace_count(ap) -> int:
     return int(n.value)
 
 
+def _check_tensor(t, shape, precision: int, name: str):
+    """A device tensor of the given shape and the precision's element type (float32
+    for MIXED, float64 for FP64_PLAIN), contiguous: the library reads raw rows."""
+    torch = _torch()
+    want = torch.float32 if precision == MIXED else torch.float64
+    if t.dtype != want:
+        raise ValueError(f"{name}: dtype {t.dtype}, expected {want} for this precision")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name}: shape {tuple(t.shape)}, expected {tuple(shape)}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: must be contiguous")
+    if not t.is_cuda:
+        raise ValueError(f"{name}: must be a CUDA tensor")
+
+
 class _EnergyGridArgs:
     def __init__(self, eg, n_electrons: Optional[float] = None):
         e = _lib.EnergyGrid()
@@ -251,6 +266,7 @@ class Context:
         dt = torch.float32 if precision == MIXED else torch.float64
         if out is None:
             out = torch.empty((P, ace_count(ap)), dtype=dt, device=torch.device("cuda", self.device))
+        _check_tensor(out, (P, ace_count(ap)), precision, "out")
         a, p = _SnapshotArgs(snap), _ace_args(ap)
         check(lib().mala_ace_descriptors(self.h, C.byref(a.c), C.byref(p), C.c_void_p(out.data_ptr()),
                                          int(precision), _stream_ptr(stream)), "mala_ace_descriptors")
@@ -388,8 +404,12 @@ class Context:
         """beta[p][j] = sum_e v[e] dLDOS[p][e]/dB[p][j] on the GPU (B: device [P][n_B])."""
         torch = _torch()
         v = np.ascontiguousarray(v, dtype=np.float64)
+        _check_tensor(B, (B.shape[0], model.dims[0]), precision, "B")
+        if len(v) != model.dims[-1]:
+            raise ValueError(f"v has {len(v)} entries, the network outputs {model.dims[-1]}")
         if out is None:
             out = torch.empty_like(B)
+        _check_tensor(out, B.shape, precision, "out")
         check(lib().mala_ldos_backward(self.h, model.h, C.c_void_p(B.data_ptr()), int(B.shape[0]),
                                        v.ctypes.data_as(C.POINTER(C.c_double)), C.c_void_p(out.data_ptr()),
                                        int(precision), _stream_ptr(stream)), "mala_ldos_backward")
@@ -397,6 +417,7 @@ class Context:
 
     def descriptor_forces(self, snap, bp, beta, precision: int = MIXED, stream=None):
         """F[a][k] = -sum_r sum_j beta[r][j] dB(r, j)/dR_{a,k} (beta: device [P][n_B]); numpy [n_atoms][3]."""
+        _check_tensor(beta, (int(np.prod(snap.grid)), n_descriptors(bp.twojmax)), precision, "beta")
         a, b = _SnapshotArgs(snap), _BParamsArgs(bp)
         F = np.zeros((len(snap.pos), 3))
         check(lib().mala_descriptor_forces(self.h, C.byref(a.c), C.byref(b.c), C.c_void_p(beta.data_ptr()),

@@ -53,3 +53,21 @@ def test_ace_column_count_matches_the_oracle_enumeration():
                                                         lmax3=4), ace.AceParams(rcut=4.0, nmax1=1, nmax2=0, lmax2=0,
                                                                                 nmax3=1, lmax3=8)):
         assert api.ace_count(ap) == len(ace.descriptor_index(ap))
+
+
+def test_force_bindings_check_dtype_and_shape_before_the_library():
+    # a beta of the wrong element type or shape never reaches the library
+    import numpy as np
+    import pytest
+    torch = pytest.importorskip("torch")
+    from paper_2411_19617_gb300 import api
+    from paper_2411_19617_gb300 import workloads as wl
+    snap = wl.al_fcc(2, 0.1, 4, seed=1)
+    bp = wl.BispectrumParams(twojmax=4, rcut=4.676)
+    ctx = api.Context.__new__(api.Context)  # no device needed: the checks come first
+    with pytest.raises(ValueError, match="dtype"):
+        ctx.descriptor_forces(snap, bp, torch.zeros((64, 14), dtype=torch.float64), api.MIXED)
+    with pytest.raises(ValueError, match="shape"):
+        ctx.descriptor_forces(snap, bp, torch.zeros((63, 14), dtype=torch.float32), api.MIXED)
+    with pytest.raises(ValueError, match="CUDA"):
+        ctx.descriptor_forces(snap, bp, torch.zeros((64, 14), dtype=torch.float32), api.MIXED)
