@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--forces-calls", type=int, default=3,
                     help="timed calls of the band-energy forces leg (0 skips it)")
     ap.add_argument("--ace-calls", type=int, default=3, help="timed calls of the ACE descriptor leg (0 skips it)")
+    ap.add_argument("--gauss-calls", type=int, default=3,
+                    help="timed calls of the Gaussian descriptor leg (0 skips it)")
     return ap.parse_args()
 
 
@@ -274,6 +276,32 @@ def ace_leg(ctx, api, roofline, snap, calls, peak_tflops):
                                    "frac": ach / peak_tflops, "flops": flops}}}
 
 
+def gaussian_leg(ctx, api, snap, calls):
+    """mala_gaussian_descriptors (rcut 4.676 A, sigma 0.5 A) on the bench snapshot: ms per call and
+    grid points / neighbour pairs per second.  The work is the neighbour search itself (candidate
+    tests per tile, FP64 only in the guard band), so no FLOP roofline is claimed.  A failure is
+    reported under this key and never costs the bench line."""
+    try:
+        import torch
+        rcut, sigma = 4.676, 0.5
+        counts, _, _, _ = ctx.neighbor_lists(snap, rcut, cap=0)
+        pairs = int(counts.sum().item())
+        P = int(np.prod(snap.grid))
+        out = ctx.gaussian_descriptors(snap, rcut, sigma, api.MIXED)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        for _ in range(calls):
+            ctx.gaussian_descriptors(snap, rcut, sigma, api.MIXED, out=out)
+        ev1.record()
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1) / calls
+        return {"ms_per_call": ms, "grid_points_per_s": P / (ms / 1e3), "neighbour_pairs": pairs,
+                "pairs_per_s": pairs / (ms / 1e3), "rcut_A": rcut, "sigma_A": sigma}
+    except Exception as e:  # reported, not raised
+        return {"error": f"{type(e).__name__}: {e}"}
+
+
 def kernel_hash(*names):
     h = hashlib.sha256()
     for n in names:
@@ -483,6 +511,9 @@ def run_ours(args):
         ace_res = None
         if world == 1 and args.ace_calls > 0:
             ace_res = ace_leg(ctx, api, roofline, snap, args.ace_calls, peak)
+        gauss_res = None
+        if world == 1 and args.gauss_calls > 0:
+            gauss_res = gaussian_leg(ctx, api, snap, args.gauss_calls)
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -492,7 +523,7 @@ def run_ours(args):
                            "l2": "working set larger than L2 (u: 1.5 GB, neighbour records 0.9 GB, LDOS 0.36 GB)",
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-                "clocks": clk, "kernels": kernels, "serving": serving, "forces": forces, "ace": ace_res,
+                "clocks": clk, "kernels": kernels, "serving": serving, "forces": forces, "ace": ace_res, "gaussian": gauss_res,
                 "fermi_eV": r["fermi"], "band_energy_eV": r["band_energy"], "entropy_term_eV": r["entropy_term"]}
         print(json.dumps(line), flush=True)
     if dist:
