@@ -22,7 +22,7 @@
  *      the u_j coupled with Clebsch-Gordan coefficients (Racah's closed form),
  *      over the index set whose size is Eq. (snap_dim).
  *
- * Readings where the paper is silent (each is listed in the design doc):
+ * Readings where the paper is silent:
  *   - cutoff function f_c(r) = (cos(pi (r-rmin0)/(rcut-rmin0)) + 1)/2 and the
  *     angle omega = rfac0 pi (r-rmin0)/(rcut-rmin0) of the SNAP formalism the
  *     paper cites;

@@ -27,7 +27,8 @@ from typing import List, Optional, Sequence, Tuple
 
 import numpy as np
 
-# Default SNAP-style hyperparameters of the cited formalism.
+# Default SNAP-style hyperparameters of the formalism the paper cites (rfac0, rmin0) and kT at room
+# temperature.
 RFAC0 = 0.99363
 RMIN0 = 0.0
 KT_ROOM_EV = 0.0259
@@ -235,7 +236,7 @@ def with_input_scaling(mlp: MLP, shift: np.ndarray, scale: np.ndarray) -> MLP:
 def config(idx: int):
     """Return (snapshots, bispectrum params, MLP, energy grid, precision) of a
     workload.  idx 1..5 follow the Al small / Al liquid-like / B clusters /
-    Be slab / serving-trace shapes (input recipe)."""
+    Be slab / serving-trace shapes of the paper's workloads."""
     if idx == 1:
         snap = al_fcc(2, 0.1, 18, seed=1)
         bp = BispectrumParams(twojmax=6, rcut=4.676)
