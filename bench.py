@@ -318,25 +318,80 @@ def load_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def traffic_per_launch(kernel_file_hash):
-    """DRAM bytes per launch of k_zb from the committed ncu summary, if it was
-    taken on the current kernel source; else None."""
+# source files whose text decides each kernel's DRAM traffic (hashed against the ncu capture)
+KERNEL_SOURCES = {
+    "k_zb": ("snap_zb.cu", "snap_zb.cuh", "snap_common.cuh"),
+    "k_ui": ("snap_ui.cu", "snap_common.cuh"),
+    "k_mlp": ("mlp_tc.cu",),
+    "k_density": ("integrate.cu",),
+    "k_neighbors": ("snap_nbr.cu", "snap_common.cuh"),
+}
+
+
+def traffic_per_launch(kernel):
+    """DRAM bytes (read + write) per launch of a kernel from the committed ncu
+    summary profiles/traffic.json, if it was taken on the current kernel source;
+    else None."""
     try:
-        with open(os.path.join(ROOT, "profiles", "k_zb_traffic.json")) as f:
-            t = json.load(f)
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            t = json.load(f).get(kernel)
     except (OSError, ValueError):
         return None
-    if t.get("kernel_hash") != kernel_file_hash:
+    if not t or t.get("kernel_hash") != kernel_hash(*KERNEL_SOURCES[kernel]):
         return None
     return t.get("dram_bytes_per_launch")
+
+
+def rooflines(kernels, roofline, P, pairs, bp, dims, n_e, peaks, peak_src, fp32):
+    """Roofline entry of every hot kernel: algorithmic work per launch (the
+    definitions' counts, not the instruction stream) over the kernel's mean
+    launch time from the library's CUDA events on the launching stream."""
+    out = {}
+
+    def entry(name, bound, work, peak, unit, source, **extra):
+        t = kernels[name]["ms_per_launch"] / 1e3
+        scale = 1e12 if unit == "TFLOP/s" else 1e9
+        ach = work / t / scale if t > 0 else 0.0
+        e = {"bound": bound, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak if peak else None,
+             "traffic": traffic_per_launch(name), "work_per_launch": work, "peak_source": source}
+        e.update(extra)
+        out[name] = e
+
+    fp32_peak, fp32_source = fp32
+    zb_f = roofline.zb_flops_per_point(bp.twojmax)
+    zb_full = roofline.zb_flops_per_point_full_count(bp.twojmax)
+    entry("k_zb", "alu", zb_f * P, fp32_peak, "TFLOP/s", fp32_source,
+          kernel="k_zb_units (compute_zi + compute_bi)", flop_per_point=zb_f,
+          algorithmic_bytes=roofline.zb_bytes_per_point(bp.twojmax) * P,
+          flop_per_point_full_count=zb_full,
+          frac_full_count=(zb_full * P / (kernels["k_zb"]["ms_per_launch"] / 1e3) / 1e12) / fp32_peak,
+          count_note=("flop_per_point: 10 per half-set coupling term with two nonzero Clebsch-Gordan factors, "
+                      "j1 = j2 row pairs once, + 4 per half-set Z element; flop_per_point_full_count: every "
+                      f"term of the full Z ({roofline.zi_terms_full(bp.twojmax)}) x 10 / 2 + 4 per full Z element"))
+    entry("k_ui", "alu", roofline.ui_flops_per_point(bp.twojmax, 1.0) * pairs, fp32_peak, "TFLOP/s", fp32_source,
+          kernel="k_ui (compute_ui, compensated sums)", flop_per_pair=roofline.ui_flops_per_point(bp.twojmax, 1.0),
+          pairs=pairs)
+    bf16 = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1700.0)))
+    entry("k_mlp", "tensor", roofline.mlp_flops_per_point(dims) * P, bf16, "TFLOP/s",
+          f"{peak_src} bf16_tflops_sustained (cuBLAS bf16 GEMM, seconds-long loop)",
+          kernel="k_mlp_tc (tcgen05 network + DOS partials)", flop_per_point=roofline.mlp_flops_per_point(dims))
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    entry("k_density", "hbm", roofline.density_bytes(P, n_e), hbm, "GB/s", f"{peak_src} hbm_gbs (copy)",
+          kernel="k_density (n(r), BF16 LDOS)", bytes_per_point=2 * n_e + 4)
+    entry("k_neighbors", "hbm", roofline.neighbor_bytes(pairs, P), hbm, "GB/s", f"{peak_src} hbm_gbs (copy)",
+          kernel="k_neighbors (neighbour records)", bytes_per_pair=20,
+          note="bytes it must write (records and counts); the search itself is latency bound (FP64 tile set-up, "
+               "candidate tests), so the fraction shows how far it is from the store stream")
+    return out
 
 
 # ---------------------------------------------------------------------------
 # oracle timing (CPU baseline / reference arm)
 
-def oracle_sample(snap, bp, mlp_raw, eg, wl, n_points, nthreads):
+def oracle_sample(snap, bp, mlp_raw, eg, wl, n_points, nthreads, keep=None):
     """Time the oracle over n grid points of the workload: descriptors, network,
-    DOS, Fermi level, band energy and density of the sample."""
+    DOS, Fermi level, band energy and density of the sample.  keep: a dict that
+    receives the sample's points and oracle descriptors (after the clock stops)."""
     import oracle
     pts = wl.sample_points(snap.n_points, n_points, seed=1234)
     t0 = time.perf_counter()
@@ -347,7 +402,10 @@ def oracle_sample(snap, bp, mlp_raw, eg, wl, n_points, nthreads):
     D = oracle.dos(L, dV)
     ne = oracle.electron_count(D, 0.0, eg.e0_eV, eg.de_eV, eg.kT_eV)
     oracle.observables(L, dV, eg.e0_eV, eg.de_eV, eg.kT_eV, ne)
-    return time.perf_counter() - t0
+    t = time.perf_counter() - t0
+    if keep is not None:
+        keep["points"], keep["B"] = pts, B
+    return t
 
 
 def sample_size(snap, bp, mlp_raw, eg, wl, target_s, nthreads):
@@ -362,14 +420,26 @@ def sample_size(snap, bp, mlp_raw, eg, wl, target_s, nthreads):
     return int(min(snap.n_points, max(n1, (target_s - fixed) / per_point)))
 
 
-def cpu_baseline(snap, bp, mlp_raw, eg, wl, target_s):
+def cpu_baseline(snap, bp, mlp_raw, eg, wl, target_s, keep=None):
     import oracle  # noqa: F401  (the CPU-baseline leg runs the oracle as it stands)
     nthreads = os.cpu_count() or 1
     n = sample_size(snap, bp, mlp_raw, eg, wl, target_s, nthreads)
-    t = oracle_sample(snap, bp, mlp_raw, eg, wl, n, nthreads)
+    t = oracle_sample(snap, bp, mlp_raw, eg, wl, n, nthreads, keep=keep)
     return {"value": n / t, "unit": UNIT, "cores": nthreads, "kind": "oracle",
             "sample": f"{n} random grid points of the workload (descriptors, network, DOS, Fermi level, band energy, "
                       f"density of the sample), {t:.1f} s wall on {nthreads} threads"}
+
+
+def descriptor_error(B_gpu, pts, B_ref):
+    """FP32 descriptors against the FP64 oracle on the CPU-baseline sample:
+    max |dB| / max(|B_ref|, floor) with the floor the component's RMS over the
+    sample (the gated reading) and 1e-3 of it (reported, not gated)."""
+    B = B_gpu[pts].double().cpu().numpy()
+    rms = np.sqrt(np.mean(B_ref ** 2, axis=0))
+    d = np.abs(B - B_ref)
+    return {"points": int(len(pts)), "max_rel_rms_floor": float(np.max(d / np.maximum(np.abs(B_ref), rms))),
+            "max_rel_1e-3_rms_floor": float(np.max(d / np.maximum(np.abs(B_ref), 1e-3 * rms))),
+            "gate": "1e-5 at the RMS floor"}
 
 
 # ---------------------------------------------------------------------------
@@ -415,6 +485,7 @@ def run_ours(args):
     ctx = api.Context(local)
     snap, bp, mlp, model, eg, ne = setup_workload(ctx, api, wl, torch)
     P = snap.n_points
+    pairs = int(ctx.neighbor_lists(snap, bp.rcut, cap=0)[0].sum().item())  # (point, neighbour) pairs
     stream = torch.cuda.current_stream()
 
     def step(density_host=None, s=snap):
@@ -483,34 +554,35 @@ def run_ours(args):
            "d2h_bytes_per_step": int(dens_pinned.nbytes + 8 * eg.n_E + 8 * 9),
            "p50_latency_ms": 1e3 * statistics.median(lat), "max_latency_ms": 1e3 * max(lat)}
 
-    # ---- roofline of the dominant kernel (compute_zi + compute_bi) ----
+    # ---- rooflines of the hot kernels; the dominant one (compute_zi + compute_bi) heads the line ----
     peaks, peak_src = load_peaks()
-    zb = kernels["k_zb"]
-    flops = roofline.zb_flops_per_point(bp.twojmax) * P
-    achieved = flops / (zb["ms_per_launch"] / 1e3) / 1e12
+    n_sms = int(props.multi_processor_count)
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    peak = roofline.fp32_peak_tflops(sm_max)
-    khash = kernel_hash("snap_zb.cu", "snap_zb.cuh", "snap_common.cuh")
-    roof = {"kernel": "k_zb (compute_zi + compute_bi)", "bound": "alu", "achieved": achieved, "peak": peak,
-            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic_per_launch(khash),
-            "algorithmic_bytes": roofline.zb_bytes_per_point(bp.twojmax) * P,
-            "peak_source": f"FP32 FMA: 152 SMs x 128 lanes x 2 flop x {sm_max:.0f} MHz ({peak_src} sm_max_mhz)",
-            "flop_per_point": roofline.zb_flops_per_point(bp.twojmax)}
+    fp32_scalar, fp32_packed = ctx.measure_fp32_peak()
+    fp32_peak = max(fp32_scalar, fp32_packed)
+    fp32 = (fp32_peak, f"measured FMA chains on every SM (scalar {fp32_scalar:.1f}, packed FP32x2 {fp32_packed:.1f} "
+                       f"TFLOP/s; the larger); nominal {n_sms} SMs x 128 lanes x 2 flop x {sm_max:.0f} MHz = "
+                       f"{roofline.fp32_peak_tflops(sm_max, n_sms):.1f}")
+    roofs = rooflines(kernels, roofline, P, pairs, bp, mlp.dims, eg.n_E, peaks, peak_src, fp32)
+    roof = dict(roofs["k_zb"])
 
     line = None
     if rank == 0:
         cpu = None
+        derr = None
         if world == 1 and not args.no_cpu_baseline:
-            cpu = cpu_baseline(snap, bp, wl.config(2)[2], eg, wl, args.cpu_seconds)
+            keep = {}
+            cpu = cpu_baseline(snap, bp, wl.config(2)[2], eg, wl, args.cpu_seconds, keep=keep)
+            derr = descriptor_error(ctx.descriptors(snap, bp, api.MIXED), keep["points"], keep["B"])
         serving = None
         if world == 1 and args.serve_requests > 0:
             serving = serving_compare(ctx, api, wl, model, bp, eg, args.serve_requests, args.serve_max_atoms)
         forces = None
         if world == 1 and args.forces_calls > 0:
-            forces = forces_leg(ctx, api, roofline, model, snap, bp, eg, ne, args.forces_calls, peak)
+            forces = forces_leg(ctx, api, roofline, model, snap, bp, eg, ne, args.forces_calls, fp32_peak)
         ace_res = None
         if world == 1 and args.ace_calls > 0:
-            ace_res = ace_leg(ctx, api, roofline, snap, args.ace_calls, peak)
+            ace_res = ace_leg(ctx, api, roofline, snap, args.ace_calls, fp32_peak)
         gauss_res = None
         if world == 1 and args.gauss_calls > 0:
             gauss_res = gaussian_leg(ctx, api, snap, args.gauss_calls)
@@ -522,7 +594,9 @@ def run_ours(args):
                            "f64 Fermi level and energy reductions",
                            "l2": "working set larger than L2 (u: 1.5 GB, neighbour records 0.9 GB, LDOS 0.36 GB)",
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+                "roofline": roof, "rooflines": roofs, "fp32_peak_tflops": {"scalar": fp32_scalar,
+                                                                           "packed": fp32_packed, "sms": n_sms},
+                "cpu_baseline": cpu, "descriptor_error": derr, "e2e": e2e, "gpu_launches": int(launches),
                 "clocks": clk, "kernels": kernels, "serving": serving, "forces": forces, "ace": ace_res, "gaussian": gauss_res,
                 "fermi_eV": r["fermi"], "band_energy_eV": r["band_energy"], "entropy_term_eV": r["entropy_term"]}
         print(json.dumps(line), flush=True)

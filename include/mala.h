@@ -139,6 +139,14 @@ size_t mala_device_bytes(const mala_ctx* ctx);
 int mala_profile(mala_ctx* ctx, int enable);
 int mala_profile_get(mala_ctx* ctx, const char* kernel, double* total_ms, int64_t* launches);
 
+/* The FP32 CUDA-core peak of the context's device, measured (no counterpart
+ * in the paper: it is the denominator of the descriptor kernels' roofline
+ * fractions).  Independent fused multiply-add chains on every SM, timed by
+ * CUDA events on the context's stream, best of three after a warm-up run, an
+ * FMA counted as two FLOP: *scalar_tflops with scalar FMAs, *packed_tflops
+ * with packed FP32x2 FMAs (either may be NULL).  Synchronous; about 10 ms. */
+int mala_measure_fp32_peak(mala_ctx* ctx, double* scalar_tflops, double* packed_tflops);
+
 /* ---- network ---------------------------------------------------------- */
 
 /* Upload a network once (BF16 copies for MALA_MIXED, FP64 for MALA_FP64_PLAIN);
@@ -228,10 +236,11 @@ int mala_integrate(mala_ctx* ctx, const void* ldos_dev, int64_t P, double cell_v
  * are those of mala_integrate; every scratch buffer comes from one fixed
  * static device array of MALA_NOALLOC_SCRATCH_BYTES that each GPU loading the
  * library holds until the process exits.  Limit: 9.5 n_E + 296 + max(
- * ceil(P/128) n_E [only when dos_sum_dev is NULL], min(ceil(P/8), 16 x SMs))
- * doubles must fit in the array; larger sizes return MALA_ERR_UNSUPPORTED
- * with the numbers in the message.  The first call on a device looks up the
- * array's device address (no allocation) and should come before any stream
+ * ceil(P/128) n_E [only when dos_sum_dev is NULL], the CTAs of the density
+ * pass [at most one per SM]) doubles must fit in the array; larger sizes
+ * return MALA_ERR_UNSUPPORTED with the numbers in the message.  Every call
+ * looks up the array's device address in the current context (a host-side
+ * query, no allocation); make the first call on a device before any stream
  * capture.  All calls share the array and leave their contents in it: calls
  * that overlap on the GPU (other streams or threads) race, so issue them one
  * at a time.  Host copies go through the context's pinned buffer and

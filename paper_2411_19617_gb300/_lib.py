@@ -69,6 +69,7 @@ PROTOTYPES = {
     "mala_device_bytes": (C.c_size_t, [C.c_void_p]),
     "mala_profile": (C.c_int, [C.c_void_p, C.c_int]),
     "mala_profile_get": (C.c_int, [C.c_void_p, C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
+    "mala_measure_fp32_peak": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "mala_model_create": (C.c_int, [C.c_void_p, C.POINTER(MLPDesc), C.POINTER(C.c_void_p)]),
     "mala_model_destroy": (None, [C.c_void_p]),
     "mala_neighbor_lists": (C.c_int, [C.c_void_p, C.POINTER(Snapshot), C.c_double, C.c_int32, C.c_void_p,

@@ -216,6 +216,12 @@ class Context:
         check(lib().mala_profile_get(self.h, kernel.encode(), C.byref(ms), C.byref(n)), "mala_profile_get")
         return float(ms.value), int(n.value)
 
+    def measure_fp32_peak(self):
+        """(scalar, packed FP32x2) FMA throughput of the device in TFLOP/s, measured."""
+        a, b = C.c_double(0.0), C.c_double(0.0)
+        check(lib().mala_measure_fp32_peak(self.h, C.byref(a), C.byref(b)), "mala_measure_fp32_peak")
+        return float(a.value), float(b.value)
+
     # ---- one step at a time --------------------------------------------
 
     def neighbor_lists(self, snap, rcut: float, cap: int = 128, stream=None):

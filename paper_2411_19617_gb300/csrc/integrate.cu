@@ -486,81 +486,200 @@ __global__ void k_sum_rows(const double* __restrict__ part, int64_t nt, int nE, 
     out[c] = s;
 }
 
-// n(r) = sum_xi w0_xi LDOS(r, xi): one warp per row, lanes over energies;
-// per-block FP64 partial sums of n for the electron-count check.
-constexpr int kDensWarps = 8;
+// n(r) = sum_xi w0_xi LDOS(r, xi): one streaming pass over the LDOS.
+// Persistent CTAs walk tiles of whole rows; a tile's bytes, rounded out to
+// 16-byte boundaries (the LDOS of a batch member may start anywhere), arrive in
+// shared memory by one cp.async.bulk, kDensStages tiles in flight per CTA, so
+// HBM sees large sequential reads with no per-thread loads outstanding.  In
+// shared memory a group of G lanes takes a row (lanes over energies, w0 held
+// in shared memory), the group's partial sums meet by shuffles.  Per-CTA FP64
+// partial sums of n give the electron-count check.  Every wait is bounded;
+// on expiry the CTA sets *err, lets its copies land and returns.
+constexpr int kDensThreads = 256;
+constexpr int kDensStages = 4;
+constexpr int kDensTileBytes = 32768;                      // payload of one stage
+constexpr int kDensStageBytes = kDensTileBytes + 32;       // + the 16-byte rounding at both ends
+constexpr long long kDensWaitCycles = 2000000000LL;        // about one second
 
-__global__ void __launch_bounds__(kDensWarps * 32) k_density_bf16(const __nv_bfloat16* __restrict__ L, int64_t P, int nE,
-                                                                  const float* __restrict__ w0, float* __restrict__ n,
-                                                                  double* __restrict__ part) {
-    __shared__ double sp[kDensWarps];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+struct DensPlan {
+    int rows;   // rows per tile
+    int G;      // lanes per row (power of two <= 32)
+};
+
+inline DensPlan dens_plan(int nE, int elem_bytes) {
+    DensPlan d;
+    int G = 1;
+    while (G < 32 && G * 8 < nE) G *= 2;  // about 8 or more energies per lane
+    const int rb = nE * elem_bytes;
+    int rows = std::max(1, kDensTileBytes / rb);
+    const int pass = kDensThreads / G;     // rows one pass over the CTA's threads covers
+    if (rows >= pass) rows -= rows % pass;
+    d.rows = rows;
+    d.G = G;
+    return d;
+}
+
+inline size_t dens_smem_bytes(int nE, int w_bytes) {
+    return (size_t)kDensStages * kDensStageBytes + (size_t)nE * w_bytes + kDensStages * 8 + 64 * 8 + 256;
+}
+
+__device__ __forceinline__ bool dens_try(uint32_t bar, uint32_t phase) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ bool dens_wait(uint32_t bar, uint32_t phase) {
+    const long long t0 = clock64();
+    while (!dens_try(bar, phase))
+        if (clock64() - t0 > kDensWaitCycles) return false;
+    return true;
+}
+
+template <class TL> __device__ __forceinline__ float dens_val(const unsigned char* p);
+template <> __device__ __forceinline__ float dens_val<__nv_bfloat16>(const unsigned char* p) {
+    return __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(p));
+}
+
+// tile t of rows [t R, t R + nr): its 16-byte-rounded byte range
+__device__ __forceinline__ void dens_range(const unsigned char* L, int64_t P, int R, int rb, int64_t t,
+                                           uintptr_t& a0, uint32_t& bytes, uint32_t& off, int& nr) {
+    const int64_t r0 = t * R;
+    nr = (int)min((int64_t)R, P - r0);
+    const uintptr_t s = reinterpret_cast<uintptr_t>(L) + (uintptr_t)(r0 * rb);
+    const uintptr_t e = s + (uintptr_t)nr * rb;
+    a0 = s & ~uintptr_t(15);
+    bytes = (uint32_t)(((e + 15) & ~uintptr_t(15)) - a0);
+    off = (uint32_t)(s - a0);
+}
+
+// TL: LDOS element (BF16 or FP64), TW: arithmetic and output type (float or double)
+template <class TL, class TW>
+__global__ void __launch_bounds__(kDensThreads) k_density(const TL* __restrict__ Lg, int64_t P, int nE, int R, int G,
+                                                          const TW* __restrict__ w0, TW* __restrict__ n,
+                                                          double* __restrict__ part, int* __restrict__ err) {
+    extern __shared__ __align__(128) unsigned char dsm[];
+    unsigned char* stage = dsm;
+    TW* sw = reinterpret_cast<TW*>(dsm + (size_t)kDensStages * kDensStageBytes);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(
+        (reinterpret_cast<uintptr_t>(sw + nE) + 7) & ~uintptr_t(7));
+    double* sred = reinterpret_cast<double*>(bars + kDensStages);
+    const unsigned char* L = reinterpret_cast<const unsigned char*>(Lg);
+    const int rb = nE * (int)sizeof(TL);
+    const int64_t ntiles = (P + R - 1) / R;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int g = tid & (G - 1), grp = tid / G, ngrp = kDensThreads / G;
+    for (int i = tid; i < nE; i += kDensThreads) sw[i] = w0[i];
+    if (tid == 0) {
+        for (int s2 = 0; s2 < kDensStages; ++s2)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"((uint32_t)__cvta_generic_to_shared(&bars[s2])));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    auto issue = [&](int64_t t, int s2) {
+        uintptr_t a0;
+        uint32_t bytes, off;
+        int nr;
+        dens_range(L, P, R, rb, t, a0, bytes, off, nr);
+        const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&bars[s2]);
+        const uint32_t dst = (uint32_t)__cvta_generic_to_shared(stage + (size_t)s2 * kDensStageBytes);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                     "l"(a0), "r"(bytes), "r"(bar)
+                     : "memory");
+    };
+    int issued = 0;  // tiles issued by this CTA (thread 0's count)
+    if (tid == 0)
+        for (int s2 = 0; s2 < kDensStages; ++s2) {
+            const int64_t t = (int64_t)blockIdx.x + (int64_t)s2 * gridDim.x;
+            if (t >= ntiles) break;
+            issue(t, s2);
+            ++issued;
+        }
     double acc = 0.0;
-    const int64_t stride = (int64_t)gridDim.x * kDensWarps;
-    if ((nE & 1) == 0) {
-        const int np = nE >> 1;
-        for (int64_t r = (int64_t)blockIdx.x * kDensWarps + warp; r < P; r += stride) {
-            const __nv_bfloat162* row = reinterpret_cast<const __nv_bfloat162*>(L + r * nE);
-            float s = 0.f;
-            for (int q = lane; q < np; q += 32) {
-                const float2 v = __bfloat1622float2(row[q]);
-                s = fmaf(v.x, __ldg(w0 + 2 * q), s);
-                s = fmaf(v.y, __ldg(w0 + 2 * q + 1), s);
+    bool ok = true;
+    int it = 0;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+        const int s2 = it % kDensStages;
+        const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&bars[s2]);
+        const bool got = dens_wait(bar, (uint32_t)((it / kDensStages) & 1));
+        if (!__syncthreads_and(got)) {
+            ok = false;
+            break;
+        }
+        uintptr_t a0;
+        uint32_t bytes, off;
+        int nr;
+        dens_range(L, P, R, rb, t, a0, bytes, off, nr);
+        const unsigned char* base = stage + (size_t)s2 * kDensStageBytes + off;
+        // rows of this tile: groups of G lanes, each lane a strided slice of the energies
+        const int npass = (nr + ngrp - 1) / ngrp;
+        for (int ps = 0; ps < npass; ++ps) {
+            const int r = ps * ngrp + grp;
+            TW s = TW(0);
+            if (r < nr) {
+                const unsigned char* row = base + (size_t)r * rb;
+                for (int c = g; c < nE; c += G) {
+                    TW v;
+                    if constexpr (sizeof(TL) == 2) v = dens_val<TL>(row + 2 * c);
+                    else v = *reinterpret_cast<const double*>(row + 8 * c);
+                    s = fma(v, sw[c], s);
+                }
             }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            if (lane == 0) {
-                n[r] = s;
+            for (int o = G >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (r < nr && g == 0) {
+                n[t * R + r] = s;
                 acc += (double)s;
             }
         }
-    } else {
-        for (int64_t r = (int64_t)blockIdx.x * kDensWarps + warp; r < P; r += stride) {
-            const __nv_bfloat16* row = L + r * nE;
-            float s = 0.f;
-            for (int q = lane; q < nE; q += 32) s = fmaf(__bfloat162float(row[q]), __ldg(w0 + q), s);
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            if (lane == 0) {
-                n[r] = s;
-                acc += (double)s;
+        __syncthreads();  // the stage is free again
+        if (tid == 0) {
+            const int64_t tn = t + (int64_t)kDensStages * gridDim.x;
+            if (tn < ntiles) {
+                issue(tn, s2);
+                ++issued;
             }
         }
     }
-    if (lane == 0) sp[warp] = acc;
+    if (!ok) {
+        if (tid == 0) {
+            atomicCAS(err, 0, 1);
+            // let the copies still in flight land before the CTA exits
+            for (int j = it; j < issued; ++j) {
+                const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&bars[j % kDensStages]);
+                dens_wait(bar, (uint32_t)((j / kDensStages) & 1));
+            }
+        }
+        __syncthreads();
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) sred[tid >> 5] = acc;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int w = 0; w < kDensWarps; ++w) t += sp[w];
-        part[blockIdx.x] = t;
+    if (tid == 0) {
+        double tsum = 0.0;
+        for (int w = 0; w < kDensThreads / 32; ++w) tsum += sred[w];
+        part[blockIdx.x] = tsum;
     }
 }
 
-__global__ void __launch_bounds__(kDensWarps * 32) k_density_f64(const double* __restrict__ L, int64_t P, int nE,
-                                                                 const double* __restrict__ w0, double* __restrict__ n,
-                                                                 double* __restrict__ part) {
-    __shared__ double sp[kDensWarps];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    double acc = 0.0;
-    const int64_t stride = (int64_t)gridDim.x * kDensWarps;
-    for (int64_t r = (int64_t)blockIdx.x * kDensWarps + warp; r < P; r += stride) {
-        const double* row = L + r * nE;
-        double s = 0.0;
-        for (int q = lane; q < nE; q += 32) s += row[q] * w0[q];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) {
-            n[r] = s;
-            acc += s;
-        }
-    }
-    if (lane == 0) sp[warp] = acc;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int w = 0; w < kDensWarps; ++w) t += sp[w];
-        part[blockIdx.x] = t;
-    }
+template <class TL, class TW>
+void launch_density(const TL* L, int64_t P, int nE, const TW* w0, TW* n, double* part, int grid, int* err,
+                    cudaStream_t st) {
+    const DensPlan d = dens_plan(nE, (int)sizeof(TL));
+    const size_t smem = dens_smem_bytes(nE, (int)sizeof(TW));
+    cudaFuncSetAttribute(k_density<TL, TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_density<TL, TW><<<grid, kDensThreads, smem, st>>>(L, P, nE, d.rows, d.G, w0, n, part, err);
+}
+
+// CTAs of the density pass: one per SM at most, never more than the tiles
+inline int density_grid(int64_t P, int nE, int elem_bytes, int num_sms) {
+    const DensPlan d = dens_plan(nE, elem_bytes);
+    const int64_t ntiles = (P + d.rows - 1) / d.rows;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, std::max(1, num_sms)));
 }
 
 // N(mu) for one mu (single block)
@@ -692,14 +811,25 @@ int energy_gradient(Ctx* c, const double* dos_sum, double dV, const mala_energy_
     return MALA_OK;
 }
 
+// error flags of the network (err_d[1]) and density (err_d[2]) kernels, read
+// into host_ints[8..9] by the caller's last copy; reset once reported
+static int check_device_flags(Ctx* c, cudaStream_t st) {
+    const int mlp = c->host_ints[8], dens = c->host_ints[9];
+    if (!mlp && !dens) return MALA_OK;
+    cudaMemsetAsync(c->tables.err_d + 1, 0, sizeof(int) * 2, st);
+    cudaStreamSynchronize(st);
+    if (mlp) return fail(MALA_ERR_TIMEOUT, "network kernel: a wait on a shared-memory barrier expired (code %d)", mlp);
+    return fail(MALA_ERR_TIMEOUT, "density pass: a copy into shared memory did not complete in time");
+}
+
 int integrate(Ctx* c, const void* ldos, int64_t P, double volume, const mala_energy_grid* eg, const double* dos_sum,
               void* density, double* dos_host, double* fermi, double* eb, double* ne, double* ts, mala_precision prec,
               cudaStream_t st) {
     const int nE = eg->n_E;
     // workspace: dsum[nE] | D[nE] | w0d[nE] | w0f[nE] (float) | scal[8] | nsum[1] | partial rows
     const int64_t ntile = (P + 127) / 128;
-    const int dens_blocks = (int)std::min<int64_t>(std::max<int64_t>(1, (P + kDensWarps - 1) / kDensWarps),
-                                                   (int64_t)c->num_sms * 16);
+    const bool mixed = prec == MALA_MIXED;
+    const int dens_blocks = density_grid(P, nE, mixed ? 2 : 8, c->num_sms);
     const size_t n_part = std::max<size_t>((size_t)ntile * nE, (size_t)dens_blocks);
     const size_t doubles = 3 * (size_t)nE + (nE + 1) / 2 + 16 + kFermiStateDoubles + 6 * (size_t)nE + n_part;
     MALA_TRY(c->ws_red.reserve(c, sizeof(double) * doubles));
@@ -711,7 +841,6 @@ int integrate(Ctx* c, const void* ldos, int64_t P, double volume, const mala_ene
     double* nsum = scal + 8;
     double* fstate = scal + 16;
     double* part = fstate + kFermiStateDoubles + 6 * (size_t)nE;
-    const bool mixed = prec == MALA_MIXED;
     if (!dos_sum) {
         if (P > 0) {
             if (mixed)
@@ -731,15 +860,15 @@ int integrate(Ctx* c, const void* ldos, int64_t P, double volume, const mala_ene
     const double dV = volume / (double)(P > 0 ? P : 1);
     MALA_PROF(c, "k_fermi", st, launch_fermi(dos_sum, nE, dV, eg, D, w0d, w0f, scal, fstate, st));
     if (P > 0 && density) {
+        int* derr = c->tables.err_d + 2;
         if (mixed)
             MALA_PROF(c, "k_density", st,
-                      (k_density_bf16<<<dens_blocks, kDensWarps * 32, 0, st>>>(static_cast<const __nv_bfloat16*>(ldos), P,
-                                                                              nE, w0f, static_cast<float*>(density),
-                                                                              part)));
+                      (launch_density<__nv_bfloat16, float>(static_cast<const __nv_bfloat16*>(ldos), P, nE, w0f,
+                                                            static_cast<float*>(density), part, dens_blocks, derr, st)));
         else
             MALA_PROF(c, "k_density", st,
-                      (k_density_f64<<<dens_blocks, kDensWarps * 32, 0, st>>>(static_cast<const double*>(ldos), P, nE,
-                                                                             w0d, static_cast<double*>(density), part)));
+                      (launch_density<double, double>(static_cast<const double*>(ldos), P, nE, w0d,
+                                                      static_cast<double*>(density), part, dens_blocks, derr, st)));
         MALA_PROF(c, "k_sum_vec", st, (k_sum_vec<<<1, 256, 0, st>>>(part, dens_blocks, nsum)));
     } else {
         MALA_CUDA_TRY(cudaMemsetAsync(nsum, 0, sizeof(double), st));
@@ -754,7 +883,9 @@ int integrate(Ctx* c, const void* ldos, int64_t P, double volume, const mala_ene
     }
     MALA_CUDA_TRY(cudaMemcpyAsync(c->host_scalars, scal, sizeof(double) * 9, cudaMemcpyDeviceToHost, st));
     MALA_CUDA_TRY(cudaMemcpyAsync(c->host_dos, D, sizeof(double) * nE, cudaMemcpyDeviceToHost, st));
+    MALA_CUDA_TRY(cudaMemcpyAsync(c->host_ints + 8, c->tables.err_d + 1, sizeof(int) * 2, cudaMemcpyDeviceToHost, st));
     MALA_CUDA_TRY(cudaStreamSynchronize(st));
+    MALA_TRY(check_device_flags(c, st));
     if (dos_host) memcpy(dos_host, c->host_dos, sizeof(double) * nE);
     const double* hs = c->host_scalars;
     if (fermi) *fermi = hs[0];
@@ -784,22 +915,18 @@ namespace {
 constexpr size_t kStaticScratchDoubles = size_t(1) << 20;  // 8 MiB
 static __device__ __align__(256) double g_integrate_scratch[kStaticScratchDoubles];
 
-std::mutex g_scratch_mu;
-void* g_scratch_addr[64] = {nullptr};
-
-// Device address of the array on the current device, looked up once per
-// device.  (In host code the array's name is only a host-side stand-in.)
-int scratch_address(int device, double** out) {
-    if (device < 0 || device >= 64) return fail(MALA_ERR_UNSUPPORTED, "device index %d too large", device);
-    std::lock_guard<std::mutex> lk(g_scratch_mu);
-    if (!g_scratch_addr[device]) {
-        void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_integrate_scratch);
-        if (e != cudaSuccess || !p)
-            return fail(MALA_ERR_CUDA, "cudaGetSymbolAddress of the static scratch failed: %s", cudaGetErrorString(e));
-        g_scratch_addr[device] = p;
+// Device address of the array in the current device's context, looked up on
+// every call: the lookup is a host-side query that allocates nothing, and a
+// cached address would go stale after a device reset or in another driver
+// context.  (In host code the array's name is only a host-side stand-in.)
+int scratch_address(double** out) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_integrate_scratch);
+    if (e != cudaSuccess || !p) {
+        cudaGetLastError();
+        return fail(MALA_ERR_CUDA, "cudaGetSymbolAddress of the static scratch failed: %s", cudaGetErrorString(e));
     }
-    *out = static_cast<double*>(g_scratch_addr[device]);
+    *out = static_cast<double*>(p);
     return MALA_OK;
 }
 
@@ -810,10 +937,10 @@ int integrate_noalloc(Ctx* c, const void* ldos, int64_t P, double volume, const 
                       double* ts, mala_precision prec, cudaStream_t st) {
     const int nE = eg->n_E;
     double* scratch = nullptr;
-    MALA_TRY(scratch_address(c->device, &scratch));
+    MALA_TRY(scratch_address(&scratch));
     const int64_t ntile = (P + 127) / 128;
-    const int dens_blocks = (int)std::min<int64_t>(std::max<int64_t>(1, (P + kDensWarps - 1) / kDensWarps),
-                                                   (int64_t)c->num_sms * 16);
+    const bool mixed = prec == MALA_MIXED;
+    const int dens_blocks = density_grid(P, nE, mixed ? 2 : 8, c->num_sms);
     const size_t n_part = std::max<size_t>(dos_sum ? 0 : (size_t)ntile * nE, (size_t)dens_blocks);
     const size_t need = 3 * (size_t)nE + (nE + 1) / 2 + 16 + kFermiStateDoubles + 6 * (size_t)nE + n_part;
     if (need > kStaticScratchDoubles)
@@ -831,7 +958,6 @@ int integrate_noalloc(Ctx* c, const void* ldos, int64_t P, double volume, const 
     double* nsum = scal + 8;
     double* fstate = scal + 16;
     double* part = fstate + kFermiStateDoubles + 6 * (size_t)nE;
-    const bool mixed = prec == MALA_MIXED;
     if (!dos_sum) {
         if (P > 0) {
             if (mixed)
@@ -848,12 +974,13 @@ int integrate_noalloc(Ctx* c, const void* ldos, int64_t P, double volume, const 
     const double dV = volume / (double)(P > 0 ? P : 1);
     launch_fermi(dos_sum, nE, dV, eg, D, w0d, w0f, scal, fstate, st);
     if (P > 0 && density) {
+        int* derr = c->tables.err_d + 2;
         if (mixed)
-            k_density_bf16<<<dens_blocks, kDensWarps * 32, 0, st>>>(static_cast<const __nv_bfloat16*>(ldos), P, nE, w0f,
-                                                                   static_cast<float*>(density), part);
+            launch_density<__nv_bfloat16, float>(static_cast<const __nv_bfloat16*>(ldos), P, nE, w0f,
+                                                 static_cast<float*>(density), part, dens_blocks, derr, st);
         else
-            k_density_f64<<<dens_blocks, kDensWarps * 32, 0, st>>>(static_cast<const double*>(ldos), P, nE, w0d,
-                                                                  static_cast<double*>(density), part);
+            launch_density<double, double>(static_cast<const double*>(ldos), P, nE, w0d, static_cast<double*>(density),
+                                           part, dens_blocks, derr, st);
         k_sum_vec<<<1, 256, 0, st>>>(part, dens_blocks, nsum);
     } else {
         MALA_CUDA_TRY(cudaMemsetAsync(nsum, 0, sizeof(double), st));
@@ -862,7 +989,9 @@ int integrate_noalloc(Ctx* c, const void* ldos, int64_t P, double volume, const 
     // host results: scalars through the context's pinned buffer, D straight into the caller's array
     MALA_CUDA_TRY(cudaMemcpyAsync(c->host_scalars, scal, sizeof(double) * 9, cudaMemcpyDeviceToHost, st));
     if (dos_host) MALA_CUDA_TRY(cudaMemcpyAsync(dos_host, D, sizeof(double) * nE, cudaMemcpyDeviceToHost, st));
+    MALA_CUDA_TRY(cudaMemcpyAsync(c->host_ints + 8, c->tables.err_d + 1, sizeof(int) * 2, cudaMemcpyDeviceToHost, st));
     MALA_CUDA_TRY(cudaStreamSynchronize(st));
+    MALA_TRY(check_device_flags(c, st));
     const double* hs = c->host_scalars;
     if (fermi) *fermi = hs[0];
     if (eb) *eb = hs[1];

@@ -40,23 +40,48 @@ void DevBuf::release() {
     bytes = 0;
 }
 
+bool budget_claim(Ctx* r, size_t n) {
+    if (!r->budget) {
+        r->used += n;
+        return true;
+    }
+    size_t cur = r->used.load();
+    do {
+        if (cur + n > r->budget) return false;
+    } while (!r->used.compare_exchange_weak(cur, cur + n));
+    return true;
+}
+
 int DevBuf::reserve(Ctx* ctx, size_t n) {
     if (n <= bytes && ptr) return MALA_OK;
-    release();
-    owner = ctx;
-    if (n == 0) return MALA_OK;
     Ctx* r = ctx->root();
-    if (r->budget && r->used + n > r->budget)
+    if (owner && owner != ctx) release();
+    owner = ctx;
+    const size_t old = ptr ? bytes : 0;
+    // the bytes beyond the old buffer come first from what admission set aside
+    // for this context, then from the budget; the old buffer's bytes carry over
+    const size_t extra = n > old ? n - old : 0;
+    const size_t from_held = std::min(extra, ctx->held);
+    if (!budget_claim(r, extra - from_held))
         return fail(MALA_ERR_OOM, "workspace of %zu bytes exceeds the HBM budget (%zu of %zu in use)", n,
                     (size_t)r->used, r->budget);
+    ctx->held -= from_held;
+    if (ptr) cudaFree(ptr);
+    ptr = nullptr;
+    bytes = 0;
+    if (n == 0) {
+        r->used -= old;  // nothing kept: the old buffer's bytes go back
+        return MALA_OK;
+    }
     cudaError_t e = cudaMalloc(&ptr, n);
     if (e != cudaSuccess) {
         ptr = nullptr;
         cudaGetLastError();
+        r->used -= old + extra;
         return fail(MALA_ERR_OOM, "cudaMalloc(%zu) failed: %s", n, cudaGetErrorString(e));
     }
     bytes = n;
-    r->used += n;
+    if (n < old) r->used -= old - n;
     return MALA_OK;
 }
 
@@ -299,7 +324,7 @@ int mala_create(mala_ctx** out, int device, size_t hbm_budget_bytes) {
         return fail(MALA_ERR_CUDA, "no CUDA device available: %s", cudaGetErrorString(e));
     }
     if (device < 0 || device >= ndev) return fail(MALA_ERR_INVALID_ARG, "device %d out of range", device);
-    MALA_CUDA_TRY(cudaSetDevice(device));
+    MALA_DEVICE_SCOPE(device);
     cudaDeviceProp prop;
     MALA_CUDA_TRY(cudaGetDeviceProperties(&prop, device));
     if (prop.major < 10) return fail(MALA_ERR_UNSUPPORTED, "device %s (sm_%d%d) is not a Blackwell GPU", prop.name, prop.major, prop.minor);
@@ -326,7 +351,7 @@ int mala_create(mala_ctx** out, int device, size_t hbm_budget_bytes) {
 
 void mala_destroy(mala_ctx* c) {
     if (!c) return;
-    cudaSetDevice(c->device);
+    DeviceScope dev_scope(c->device);
     server_stop(c);
     cudaDeviceSynchronize();
     cublas_release(c);
@@ -387,7 +412,7 @@ int mala_neighbor_lists(mala_ctx* c, const mala_snapshot* snap, double rcut, int
     if (cap < 0 || (cap > 0 && (!atoms_dev || !shifts_dev)) || !counts_dev)
         return fail(MALA_ERR_INVALID_ARG, "bad neighbour-list output arguments");
     std::lock_guard<std::mutex> lk(c->mu);
-    MALA_CUDA_TRY(cudaSetDevice(c->device));
+    MALA_DEVICE_SCOPE(c->device);
     mala_bispectrum_params bp = {0, rcut, 0.99363, 0.0, 1.0, 0, nullptr};
     NbrOut dbg;
     dbg.dbg_atoms = atoms_dev;
@@ -407,7 +432,7 @@ int mala_descriptors(mala_ctx* c, const mala_snapshot* snap, const mala_bispectr
     if (!B_dev) return fail(MALA_ERR_INVALID_ARG, "B output is NULL");
     if (precision != MALA_MIXED && precision != MALA_FP64_PLAIN) return fail(MALA_ERR_INVALID_ARG, "bad precision");
     std::lock_guard<std::mutex> lk(c->mu);
-    MALA_CUDA_TRY(cudaSetDevice(c->device));
+    MALA_DEVICE_SCOPE(c->device);
     return snap_descriptors(c, snap, bp, B_dev, nullptr, precision, as_stream(stream));
 }
 
@@ -420,7 +445,7 @@ int mala_descriptors_batch(mala_ctx* c, int32_t n, const mala_snapshot* snaps, c
     if (!B_dev) return fail(MALA_ERR_INVALID_ARG, "B output is NULL");
     if (precision != MALA_MIXED && precision != MALA_FP64_PLAIN) return fail(MALA_ERR_INVALID_ARG, "bad precision");
     std::lock_guard<std::mutex> lk(c->mu);
-    MALA_CUDA_TRY(cudaSetDevice(c->device));
+    MALA_DEVICE_SCOPE(c->device);
     return snap_descriptors_batch(c, n, snaps, bp, B_dev, precision, as_stream(stream));
 }
 
@@ -433,7 +458,7 @@ int mala_gaussian_descriptors(mala_ctx* c, const mala_snapshot* snap, double rcu
     if (!G_dev) return fail(MALA_ERR_INVALID_ARG, "output is NULL");
     if (precision != MALA_MIXED && precision != MALA_FP64_PLAIN) return fail(MALA_ERR_INVALID_ARG, "bad precision");
     std::lock_guard<std::mutex> lk(c->mu);
-    MALA_CUDA_TRY(cudaSetDevice(c->device));
+    MALA_DEVICE_SCOPE(c->device);
     return snap_gaussian(c, snap, rcut, sigma, G_dev, precision, as_stream(stream));
 }
 
@@ -444,7 +469,7 @@ int mala_expansion_coefficients(mala_ctx* c, const mala_snapshot* snap, const ma
     MALA_TRY(check_bparams(bp));
     if (!u_dev) return fail(MALA_ERR_INVALID_ARG, "u output is NULL");
     std::lock_guard<std::mutex> lk(c->mu);
-    MALA_CUDA_TRY(cudaSetDevice(c->device));
+    MALA_DEVICE_SCOPE(c->device);
     return snap_descriptors(c, snap, bp, nullptr, u_dev, precision, as_stream(stream));
 }
 

@@ -42,9 +42,39 @@ int fail(int code, const char* fmt, ...);
         if (s_ != MALA_OK) return s_; \
     } while (0)
 
+// ---- current device ---------------------------------------------------------
+
+// Makes `dev` the calling thread's current device for the scope of an entry
+// point and makes the caller's previous device current again on return, so a
+// caller working on another device is not silently switched.
+struct DeviceScope {
+    int prev = -1;
+    cudaError_t err = cudaSuccess;
+    explicit DeviceScope(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) {
+            cudaGetLastError();
+            prev = -1;
+        }
+        if (prev != dev) err = cudaSetDevice(dev);
+    }
+    ~DeviceScope() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+    DeviceScope(const DeviceScope&) = delete;
+    DeviceScope& operator=(const DeviceScope&) = delete;
+};
+#define MALA_DEVICE_SCOPE(dev)                    \
+    ::mala::DeviceScope mala_dev_scope_(dev);     \
+    MALA_CUDA_TRY(mala_dev_scope_.err)
+
 // ---- device buffers ---------------------------------------------------------
 
 struct Ctx;
+
+// Claims n bytes of the root context's HBM budget in one atomic step (several
+// serving slots grow their workspaces concurrently); false if they do not fit.
+bool budget_claim(Ctx* root, size_t n);
 
 // A growable device buffer accounted against the context's HBM budget.
 struct DevBuf {
@@ -143,6 +173,9 @@ struct Ctx {
     size_t budget = 0;  // 0 = unlimited
     std::atomic<size_t> used{0};
     Ctx* root() { return parent ? parent : this; }
+    // bytes of the root budget that serving admission set aside for this
+    // context's workspace growth and that DevBuf::reserve has not drawn yet
+    size_t held = 0;
     cudaStream_t stream = nullptr;  // internal work stream for synchronous helpers
     SnapTables tables;
     int num_sms = 0;

@@ -441,7 +441,7 @@ int mala_model_create(mala_ctx* c, const mala_mlp_desc* desc, mala_model** out) 
     if (!c || !out) return fail(MALA_ERR_INVALID_ARG, "NULL argument");
     *out = nullptr;
     MALA_TRY(check_model_desc(desc));
-    MALA_CUDA_TRY(cudaSetDevice(c->device));
+    MALA_DEVICE_SCOPE(c->device);
     auto* m = new mala_model();
     int rc = model_upload(c, desc, m);
     if (rc != MALA_OK) {
@@ -474,7 +474,7 @@ int mala_ldos_forward(mala_ctx* c, const mala_model* m, const void* B_dev, int64
     if (!c || !m || (!B_dev && P > 0) || (!ldos_dev && P > 0) || P < 0) return fail(MALA_ERR_INVALID_ARG, "bad arguments");
     if (precision != MALA_MIXED && precision != MALA_FP64_PLAIN) return fail(MALA_ERR_INVALID_ARG, "bad precision");
     std::lock_guard<std::mutex> lk(c->mu);
-    MALA_CUDA_TRY(cudaSetDevice(c->device));
+    MALA_DEVICE_SCOPE(c->device);
     return mlp_forward(c, m, B_dev, P, ldos_dev, dos_sum_dev, precision, as_stream(stream));
 }
 
@@ -488,7 +488,7 @@ int mala_integrate(mala_ctx* c, const void* ldos_dev, int64_t P, double cell_vol
     if (precision != MALA_MIXED && precision != MALA_FP64_PLAIN) return fail(MALA_ERR_INVALID_ARG, "bad precision");
     if (density_dev && !ldos_dev) return fail(MALA_ERR_INVALID_ARG, "density needs the LDOS");
     std::lock_guard<std::mutex> lk(c->mu);
-    MALA_CUDA_TRY(cudaSetDevice(c->device));
+    MALA_DEVICE_SCOPE(c->device);
     return integrate(c, ldos_dev, P, cell_volume_, eg, dos_sum_dev, density_dev, dos_host, fermi_eV, band_energy_eV,
                      electron_count, entropy_term_eV, precision, as_stream(stream));
 }
@@ -503,7 +503,7 @@ int mala_integrate_noalloc(mala_ctx* c, const void* ldos_dev, int64_t P, double 
     if (precision != MALA_MIXED && precision != MALA_FP64_PLAIN) return fail(MALA_ERR_INVALID_ARG, "bad precision");
     if (density_dev && !ldos_dev) return fail(MALA_ERR_INVALID_ARG, "density needs the LDOS");
     std::lock_guard<std::mutex> lk(c->mu);
-    MALA_CUDA_TRY(cudaSetDevice(c->device));
+    MALA_DEVICE_SCOPE(c->device);
     return integrate_noalloc(c, ldos_dev, P, cell_volume_, eg, dos_sum_dev, density_dev, dos_host, fermi_eV,
                              band_energy_eV, electron_count, entropy_term_eV, precision, as_stream(stream));
 }
@@ -512,7 +512,7 @@ int mala_electron_count(mala_ctx* c, const double* dos_host, const mala_energy_g
     if (!c || !dos_host || !count || !std::isfinite(mu)) return fail(MALA_ERR_INVALID_ARG, "bad arguments");
     MALA_TRY(check_egrid(eg));
     std::lock_guard<std::mutex> lk(c->mu);
-    MALA_CUDA_TRY(cudaSetDevice(c->device));
+    MALA_DEVICE_SCOPE(c->device);
     return electron_count_at(c, dos_host, eg, mu, count, c->stream);
 }
 
@@ -522,7 +522,7 @@ int mala_predict(mala_ctx* c, const mala_snapshot* snap, const mala_bispectrum_p
     memset(res, 0, sizeof(*res));
     MALA_TRY(check_path_args(snap, bp, m, eg, prec));
     std::lock_guard<std::mutex> lk(c->mu);
-    MALA_CUDA_TRY(cudaSetDevice(c->device));
+    MALA_DEVICE_SCOPE(c->device);
     const int64_t P = (int64_t)snap->grid[0] * snap->grid[1] * snap->grid[2];
     const int nB = n_triples(bp->twojmax), nE = eg->n_E;
     const size_t e = prec == MALA_MIXED ? 4 : 8, l = prec == MALA_MIXED ? 2 : 8;
@@ -553,7 +553,7 @@ int mala_predict_batch(mala_ctx* c, int32_t n, const mala_snapshot* snaps, const
         if (egs[i].n_E != egs[0].n_E) return fail(MALA_ERR_INVALID_ARG, "energy grids of a batch need one n_E");
     }
     std::lock_guard<std::mutex> lk(c->mu);
-    MALA_CUDA_TRY(cudaSetDevice(c->device));
+    MALA_DEVICE_SCOPE(c->device);
     std::vector<int64_t> row(n + 1, 0);
     for (int i = 0; i < n; ++i) row[i + 1] = row[i] + (int64_t)snaps[i].grid[0] * snaps[i].grid[1] * snaps[i].grid[2];
     const int64_t P = row[n];
@@ -684,7 +684,7 @@ int mala_band_energy_gradient(mala_ctx* c, const double* dos_host, const mala_en
     if (!c || !dos_host || !grad_host) return fail(MALA_ERR_INVALID_ARG, "NULL argument");
     MALA_TRY(check_egrid(eg));
     std::lock_guard<std::mutex> lk(c->mu);
-    MALA_CUDA_TRY(cudaSetDevice(c->device));
+    MALA_DEVICE_SCOPE(c->device);
     cudaStream_t st = as_stream(stream);
     const int nE = eg->n_E;
     MALA_TRY(c->ws_w.reserve(c, sizeof(double) * 2 * (size_t)nE + 256));
@@ -707,7 +707,7 @@ int mala_ldos_backward(mala_ctx* c, const mala_model* m, const void* B_dev, int6
     if (P < 0) return fail(MALA_ERR_INVALID_ARG, "P < 0");
     if (prec != MALA_MIXED && prec != MALA_FP64_PLAIN) return fail(MALA_ERR_INVALID_ARG, "bad precision");
     std::lock_guard<std::mutex> lk(c->mu);
-    MALA_CUDA_TRY(cudaSetDevice(c->device));
+    MALA_DEVICE_SCOPE(c->device);
     cudaStream_t st = as_stream(stream);
     const int nE = m->dims[m->n_layers];
     MALA_TRY(c->ws_w.reserve(c, sizeof(double) * (size_t)nE + 256));
@@ -726,7 +726,7 @@ int mala_descriptor_forces(mala_ctx* c, const mala_snapshot* snap, const mala_bi
     const int64_t P = (int64_t)snap->grid[0] * snap->grid[1] * snap->grid[2];
     if (P > 0 && !beta_dev) return fail(MALA_ERR_INVALID_ARG, "beta is NULL");
     std::lock_guard<std::mutex> lk(c->mu);
-    MALA_CUDA_TRY(cudaSetDevice(c->device));
+    MALA_DEVICE_SCOPE(c->device);
     cudaStream_t st = as_stream(stream);
     NbrOut nl;
     MALA_TRY(stage_force_descriptors(c, snap, bp, prec, nullptr, &nl, st));
@@ -740,7 +740,7 @@ int mala_band_forces(mala_ctx* c, const mala_snapshot* snap, const mala_bispectr
     memset(res, 0, sizeof(*res));
     MALA_TRY(check_path_args(snap, bp, m, eg, prec));
     std::lock_guard<std::mutex> lk(c->mu);
-    MALA_CUDA_TRY(cudaSetDevice(c->device));
+    MALA_DEVICE_SCOPE(c->device);
     cudaStream_t st = as_stream(stream);
     const int64_t P = (int64_t)snap->grid[0] * snap->grid[1] * snap->grid[2];
     const int nB = n_triples(bp->twojmax), nE = eg->n_E;
@@ -795,7 +795,7 @@ int mala_ace_descriptors(mala_ctx* c, const mala_snapshot* snap, const mala_ace_
     const int64_t P = (int64_t)snap->grid[0] * snap->grid[1] * snap->grid[2];
     if (P > 0 && !D_dev) return fail(MALA_ERR_INVALID_ARG, "output is NULL");
     std::lock_guard<std::mutex> lk(c->mu);
-    MALA_CUDA_TRY(cudaSetDevice(c->device));
+    MALA_DEVICE_SCOPE(c->device);
     cudaStream_t st = as_stream(stream);
     NbrOut nl;
     MALA_TRY(stage_lists_only(c, snap, ap->rcut, ap->n_species, &nl, st));

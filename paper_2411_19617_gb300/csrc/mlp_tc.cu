@@ -597,12 +597,12 @@ int model_upload(Ctx* c, const mala_mlp_desc* d, Model* m) {
     if (m->dims[nl] > 256) m->mixed_ok = false;
     auto dalloc = [&](size_t bytes, void** p) -> int {
         Ctx* r = c->root();
-        if (r->budget && r->used + bytes > r->budget) return fail(MALA_ERR_OOM, "model exceeds the HBM budget");
+        if (!budget_claim(r, bytes)) return fail(MALA_ERR_OOM, "model exceeds the HBM budget");
         if (cudaMalloc(p, bytes) != cudaSuccess) {
             cudaGetLastError();
+            r->used -= bytes;
             return fail(MALA_ERR_OOM, "cudaMalloc for the model failed");
         }
-        r->used += bytes;
         m->bytes += bytes;
         m->allocs.push_back(*p);
         return MALA_OK;

@@ -85,6 +85,26 @@ def zb_flops_per_point(twojmax: int) -> int:
     return 10 * zi_terms_half(twojmax) + 4 * z_half_elements(twojmax)
 
 
+@lru_cache(maxsize=None)
+def zi_terms_full(twojmax: int) -> int:
+    """Coupling terms C C u^{j1} u^{j2} of the full Z (every element (ma, mb) of every
+    triple, every pair (m1a, m1b) whose partners lie inside u^{j2}, no test of the
+    Clebsch-Gordan values): 7,721 at twojmax 6, 121,054 at twojmax 10."""
+    total = 0
+    for (j1, j2, j) in triples(twojmax):
+        d = (j1 + j2 - j) // 2
+        rows = [sum(1 for m1 in range(j1 + 1) if 0 <= m - m1 + d <= j2) for m in range(j + 1)]
+        total += sum(rows) ** 2
+    return total
+
+
+def zb_flops_per_point_full_count(twojmax: int) -> int:
+    """The plainer count: 10 flop per term of the full Z halved by the symmetry of
+    u and Z, plus 4 flop per element of the full Z for compute_bi.  At twojmax 10:
+    121,054 terms -> 605,270 + 4 x 6,832 = 632,598 flop per point."""
+    return 10 * zi_terms_full(twojmax) // 2 + 4 * sum((j + 1) ** 2 for (_, _, j) in triples(twojmax))
+
+
 def ui_flops_per_point(twojmax: int, mean_neighbors: float) -> float:
     return 18.0 * u_half_elements(twojmax) * mean_neighbors
 
@@ -98,8 +118,19 @@ def mlp_flops_per_point(dims) -> int:
     return sum(2 * dims[l] * dims[l + 1] for l in range(len(dims) - 1))
 
 
-# FP32 CUDA-core peak of a GB300: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x SM clock
-GB300_SMS = 152
+def density_bytes(points: int, n_e: int, ldos_bytes: int = 2, out_bytes: int = 4) -> int:
+    """The density pass n(r) = sum_xi w0_xi LDOS(r, xi): the LDOS read once, n written
+    once, the weights read once."""
+    return points * n_e * ldos_bytes + points * out_bytes + n_e * 8
+
+
+def neighbor_bytes(pairs: int, points: int) -> int:
+    """What the neighbour search must write: one record per (point, neighbour) pair
+    (Cayley-Klein a, b as a float4 and w f_c as a float) and a count per point."""
+    return 20 * pairs + 4 * points
+
+
+# FP32 lanes of one Blackwell SM (4 schedulers x 32); the SM count comes from the device
 FP32_LANES_PER_SM = 128
 
 
@@ -179,5 +210,6 @@ def ace_flops(ap, pairs: int, points: int) -> int:
     return per_pair * pairs + per_point * points
 
 
-def fp32_peak_tflops(sm_mhz: float) -> float:
-    return GB300_SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+def fp32_peak_tflops(sm_mhz: float, n_sms: int) -> float:
+    """Nominal FP32 FMA peak: SMs x 128 lanes x 2 flop x clock."""
+    return n_sms * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12

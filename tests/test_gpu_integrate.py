@@ -136,3 +136,40 @@ def test_entropy_term_matches_oracle_across_temperatures(kT):
     assert out["fermi"] == pytest.approx(ref["fermi"], abs=1e-9)
     assert out["entropy_term"] == pytest.approx(ref["entropy_term"], rel=1e-9, abs=1e-13)
     assert out["entropy_term"] <= 0.0
+
+
+@pytest.mark.parametrize("mixed", [True, False])
+@pytest.mark.parametrize("nE,P,row0", [(250, 20011, 1), (250, 3, 3), (11, 9000, 5), (7, 1, 1), (4096, 17, 2),
+                                       (250, 729, 0)])
+def test_density_pass_any_alignment_and_size(mixed, nE, P, row0):
+    """n(r) = sum_xi w0_xi LDOS(r, xi) on row slices that start at any row of a
+    larger buffer (so the LDOS start need not be 16-byte aligned), with tiny,
+    ragged and wide rows: the density equals the oracle's sum with the same
+    weights, element by element."""
+    torch = need_gpu()
+    from paper_2411_19617_gb300 import api
+    eg = wl.EnergyGrid(n_E=nE, e0_eV=-5.0, de_eV=10.0 / (nE - 1))
+    L = _synthetic_ldos(P + row0, eg, seed=P + nE)
+    if mixed:
+        L = _bf16_round(L)
+        full = torch.from_numpy(L.astype(np.float32)).to(torch.bfloat16).cuda()
+    else:
+        full = torch.from_numpy(L).cuda()
+    view = full[row0:]
+    assert view.is_contiguous() and view.shape[0] == P
+    vol = 100.0
+    dV = vol / P
+    Ls = L[row0:]
+    D = oracle.dos(Ls, dV)
+    Ne = oracle.electron_count(D, -5.0 + 0.45 * 10.0, -5.0, eg.de_eV, eg.kT_eV)
+    out = ctx().integrate(view, vol, eg, api.MIXED if mixed else api.FP64_PLAIN, n_electrons=Ne)
+    w0 = oracle.integration_weights(0, -5.0, eg.de_eV, nE, out["fermi"], eg.kT_eV)
+    ref = Ls @ w0
+    got = out["density"].double().cpu().numpy()
+    if mixed:
+        # FP32 weights and sums over BF16 values: relative to the row's sum of |terms|
+        scale = np.abs(Ls) @ np.abs(w0)
+        assert np.max(np.abs(got - ref) / np.maximum(scale, 1e-30)) < 2e-6
+    else:
+        np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-14)
+    assert out["electron_count"] == pytest.approx(Ne, rel=2e-6 if mixed else 1e-9)

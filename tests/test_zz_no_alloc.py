@@ -29,7 +29,8 @@ def _gaussian_ldos(P, eg, seed):
     return L
 
 
-def _call(fn, ctx, ldos, P, vol, eg, ne, dos_sum, dens, precision, stream):
+def _raw_call(fn, ctx, ldos, P, vol, eg, ne, dos_sum, dens, precision, stream):
+    """One call through the C ABI; nothing else touches the device."""
     from paper_2411_19617_gb300 import _lib
     e = _lib.EnergyGrid()
     e.n_E, e.e0_eV, e.de_eV, e.kT_eV, e.n_electrons = eg.n_E, eg.e0_eV, eg.de_eV, eg.kT_eV, ne
@@ -38,7 +39,12 @@ def _call(fn, ctx, ldos, P, vol, eg, ne, dos_sum, dens, precision, stream):
     rc = fn(ctx.h, C.c_void_p(ldos.data_ptr()), P, vol, C.byref(e),
             C.c_void_p(dos_sum.data_ptr()) if dos_sum is not None else None, C.c_void_p(dens.data_ptr()),
             D.ctypes.data_as(C.c_void_p), C.byref(eF), C.byref(Eb), C.byref(Ne), C.byref(TS), precision, stream)
-    return rc, D, eF.value, Eb.value, Ne.value, dens.double().cpu().numpy(), TS.value
+    return rc, D, eF.value, Eb.value, Ne.value, TS.value
+
+
+def _call(fn, ctx, ldos, P, vol, eg, ne, dos_sum, dens, precision, stream):
+    rc, D, eF, Eb, Ne, TS = _raw_call(fn, ctx, ldos, P, vol, eg, ne, dos_sum, dens, precision, stream)
+    return rc, D, eF, Eb, Ne, dens.double().cpu().numpy(), TS
 
 
 @pytest.mark.parametrize("precision", ["mixed", "fp64"])
@@ -49,7 +55,9 @@ def test_noalloc_matches_integrate_twice(precision, with_dos_sum):
         pytest.skip("no CUDA device")
     from paper_2411_19617_gb300 import _lib, api
     lib = _lib.lib()
-    ctx = api.Context(0)
+    ctx = api.Context(0)      # the workspace path (reference results)
+    bare = api.Context(0)     # the no-allocation path: a context that has never reserved a workspace
+    created = bare.device_bytes  # its tables only
     stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
     mixed = precision == "mixed"
     prec = api.MIXED if mixed else api.FP64_PLAIN
@@ -66,9 +74,23 @@ def test_noalloc_matches_integrate_twice(precision, with_dos_sum):
         ref = _call(lib.mala_integrate, ctx, Lt, P, vol, eg, ne, dos_sum, dens_ref, prec, stream)
         assert ref[0] == 0
         rtol = 2e-6 if mixed else 1e-10
-        for _ in range(2):  # two calls in a row share (and reuse) the static array
-            dens = torch.full((P,), float("nan"), dtype=dens_ref.dtype, device="cuda")
-            got = _call(lib.mala_integrate_noalloc, ctx, Lt, P, vol, eg, ne, dos_sum, dens, prec, stream)
+        dens = [torch.full((P,), float("nan"), dtype=dens_ref.dtype, device="cuda") for _ in range(3)]
+        # a first call (any one-time set-up), then the device memory in use is recorded
+        assert _raw_call(lib.mala_integrate_noalloc, bare, Lt, P, vol, eg, ne, dos_sum, dens[0], prec, stream)[0] == 0
+        torch.cuda.synchronize()
+        before = (bare.device_bytes, torch.cuda.mem_get_info()[0])
+        raw = []
+        for k in (1, 2):  # two calls in a row share (and reuse) the static array
+            dens[k].fill_(float("nan"))
+            torch.cuda.synchronize()
+            raw.append(_raw_call(lib.mala_integrate_noalloc, bare, Lt, P, vol, eg, ne, dos_sum, dens[k], prec, stream))
+        torch.cuda.synchronize()
+        # nothing was allocated: neither through the context nor anywhere on the device
+        assert (bare.device_bytes, torch.cuda.mem_get_info()[0]) == before
+        assert bare.device_bytes == created
+        for k in (1, 2):
+            rc, D, eF, Eb, Ne, TS = raw[k - 1]
+            got = (rc, D, eF, Eb, Ne, dens[k].double().cpu().numpy(), TS)
             assert got[0] == 0, lib.mala_last_error()
             np.testing.assert_allclose(got[1], ref[1], rtol=rtol)
             assert got[2] == pytest.approx(ref[2], abs=1e-9)
@@ -76,6 +98,7 @@ def test_noalloc_matches_integrate_twice(precision, with_dos_sum):
             assert got[4] == pytest.approx(ref[4], rel=rtol)
             np.testing.assert_allclose(got[5], ref[5], rtol=rtol, atol=1e-12)
             assert got[6] == pytest.approx(ref[6], rel=rtol)
+    bare.close()
     ctx.close()
 
 
