@@ -811,6 +811,18 @@ int energy_gradient(Ctx* c, const double* dos_sum, double dV, const mala_energy_
     return MALA_OK;
 }
 
+// doubles of the workspace of integrate(): dsum | D | w0d | w0f | scal | fstate | partial rows
+static size_t integrate_doubles(int64_t P, int nE, bool mixed, int num_sms) {
+    const int64_t ntile = (P + 127) / 128;
+    const int dens_blocks = density_grid(P, nE, mixed ? 2 : 8, num_sms);
+    const size_t n_part = std::max<size_t>((size_t)ntile * nE, (size_t)dens_blocks);
+    return 3 * (size_t)nE + (nE + 1) / 2 + 16 + kFermiStateDoubles + 6 * (size_t)nE + n_part;
+}
+
+void integrate_ws_needs(Ctx* c, int64_t P, int nE, mala_precision prec, WsNeeds& out) {
+    out.add(c->ws_red, sizeof(double) * integrate_doubles(P, nE, prec == MALA_MIXED, c->num_sms));
+}
+
 // error flags of the network (err_d[1]) and density (err_d[2]) kernels, read
 // into host_ints[8..9] by the caller's last copy; reset once reported
 static int check_device_flags(Ctx* c, cudaStream_t st) {
@@ -830,9 +842,7 @@ int integrate(Ctx* c, const void* ldos, int64_t P, double volume, const mala_ene
     const int64_t ntile = (P + 127) / 128;
     const bool mixed = prec == MALA_MIXED;
     const int dens_blocks = density_grid(P, nE, mixed ? 2 : 8, c->num_sms);
-    const size_t n_part = std::max<size_t>((size_t)ntile * nE, (size_t)dens_blocks);
-    const size_t doubles = 3 * (size_t)nE + (nE + 1) / 2 + 16 + kFermiStateDoubles + 6 * (size_t)nE + n_part;
-    MALA_TRY(c->ws_red.reserve(c, sizeof(double) * doubles));
+    MALA_TRY(c->ws_red.reserve(c, sizeof(double) * integrate_doubles(P, nE, mixed, c->num_sms)));
     double* dsum = c->ws_red.as<double>();
     double* D = dsum + nE;
     double* w0d = D + nE;

@@ -121,6 +121,54 @@ static cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s
 
 // ---- descriptor step ------------------------------------------------------
 
+// Tiles per chunk of the descriptor step (u half set, neighbour records and
+// counts of a chunk stay below 4 GB) and the workspace sizes of a chunk.
+struct DescSizes {
+    int64_t chunk;
+    size_t u, ab, cw, cnt;
+};
+
+static DescSizes desc_sizes(int64_t tiles, int tj, size_t e, int kmax) {
+    DescSizes d;
+    const int nh = n_half(tj);
+    const size_t per_tile = (size_t)nh * 32 * 2 * e + (size_t)kmax * 32 * (5 * e) + 32 * sizeof(int);
+    const size_t chunk_budget = (size_t)4 << 30;
+    int64_t chunk = (int64_t)(chunk_budget / per_tile);
+    if (chunk < 1) chunk = 1;
+    if (chunk > tiles) chunk = tiles;
+    d.chunk = chunk;
+    // FP32 keeps tiles in pairs: room for an even number of tiles
+    d.u = (size_t)((chunk + 1) & ~int64_t(1)) * nh * 32 * 2 * e;
+    d.ab = (size_t)chunk * kmax * 32 * 4 * e;
+    d.cw = (size_t)chunk * kmax * 32 * e;
+    d.cnt = (size_t)chunk * 32 * sizeof(int);
+    return d;
+}
+
+static int64_t snapshot_tiles(const mala_snapshot* s) {
+    const int64_t tx = (s->grid[0] + kTileX - 1) / kTileX, ty = (s->grid[1] + kTileY - 1) / kTileY,
+                  tz = (s->grid[2] + kTileZ - 1) / kTileZ;
+    return tx * ty * tz;
+}
+
+void descriptors_ws_needs(Ctx* c, int n, const mala_snapshot* const* snaps, const mala_bispectrum_params* bp,
+                          mala_precision prec, WsNeeds& out) {
+    const size_t e = prec == MALA_MIXED ? 4 : 8;
+    size_t staging = 0;
+    int64_t tiles = 0;
+    for (int i = 0; i < n; ++i) {
+        staging += snapshot_ws_bytes(snaps[i], bp, bp->rcut);
+        tiles += snapshot_tiles(snaps[i]);
+    }
+    out.add(c->ws_atoms, staging + 256);
+    out.add(c->ws_batch, sizeof(BatchSnap) * n + 256);
+    const DescSizes d = desc_sizes(tiles, bp->twojmax, e, c->kmax_hint);
+    out.add(c->ws_u, d.u);
+    out.add(c->ws_nbr_ab, d.ab);
+    out.add(c->ws_nbr_c, d.cw);
+    out.add(c->ws_nbr_cnt, d.cnt);
+}
+
 // Run neighbour search + compute_ui + compute_zi/bi over n snapshots in
 // chunks of tiles.  The snapshots' tiles are numbered one after another, so a
 // chunk (and each launch) may hold tiles of several snapshots; B rows are the
@@ -163,16 +211,12 @@ static int run_descriptors(Ctx* c, int nsnap, const mala_snapshot* snaps, const 
     const bool gauss_mode = dbg && dbg->gauss;  // Gaussian descriptors: no neighbour records
     int kmax = gauss_mode ? 0 : c->kmax_hint;
     for (int attempt = 0; attempt < 3; ++attempt) {
-        const size_t per_tile = (size_t)nh * 32 * 2 * sizeof(T) + (size_t)kmax * 32 * (5 * sizeof(T)) + 32 * sizeof(int);
-        const size_t chunk_budget = (size_t)4 << 30;
-        int64_t chunk = (int64_t)(chunk_budget / per_tile);
-        if (chunk < 1) chunk = 1;
-        if (chunk > tiles) chunk = tiles;
-        // FP32 keeps tiles in pairs: room for an even number of tiles
-        MALA_TRY(c->ws_u.reserve(c, (size_t)((chunk + 1) & ~int64_t(1)) * nh * 32 * 2 * sizeof(T)));
-        MALA_TRY(c->ws_nbr_ab.reserve(c, (size_t)chunk * kmax * 32 * 4 * sizeof(T)));
-        MALA_TRY(c->ws_nbr_c.reserve(c, (size_t)chunk * kmax * 32 * sizeof(T)));
-        MALA_TRY(c->ws_nbr_cnt.reserve(c, (size_t)chunk * 32 * sizeof(int)));
+        const DescSizes ds = desc_sizes(tiles, tj, sizeof(T), kmax);
+        const int64_t chunk = ds.chunk;
+        MALA_TRY(c->ws_u.reserve(c, ds.u));
+        MALA_TRY(c->ws_nbr_ab.reserve(c, ds.ab));
+        MALA_TRY(c->ws_nbr_c.reserve(c, ds.cw));
+        MALA_TRY(c->ws_nbr_cnt.reserve(c, ds.cnt));
         NbrOut nb;
         nb.ab = c->ws_nbr_ab.ptr;
         nb.cw = c->ws_nbr_c.ptr;

@@ -90,6 +90,28 @@ struct DevBuf {
     template <class T> T* as() const { return static_cast<T*>(ptr); }
 };
 
+// Device workspace a call will reserve, buffer by buffer: serving admission
+// counts the growth beyond what a slot's buffers already hold.
+struct WsNeeds {
+    std::vector<std::pair<DevBuf*, size_t>> v;
+    void add(DevBuf& b, size_t n) {
+        for (auto& x : v)
+            if (x.first == &b) {
+                x.second = std::max(x.second, n);
+                return;
+            }
+        v.emplace_back(&b, n);
+    }
+    size_t growth() const {
+        size_t g = 0;
+        for (auto& x : v) {
+            const size_t have = x.first->ptr ? x.first->bytes : 0;
+            if (x.second > have) g += x.second - have;
+        }
+        return g;
+    }
+};
+
 // ---- descriptor tables (host-built, uploaded once) -------------------------
 
 struct SnapTables {
@@ -139,8 +161,9 @@ struct Model {
     double slope_d = 0.01;
     int activate_output = 0;
     bool mixed_ok = false;           // shape fits the tensor-core kernel
-    std::vector<int> boxN;           // TMA box rows per layer
-    std::vector<CUtensorMap> maps;   // BF16 weights [Npad][Kpad], 128-byte swizzle
+    std::vector<int> nparts;         // weight chunks (N parts) per layer
+    std::vector<int> prow, pn0;      // [layer][2]: rows and first row of each part
+    std::vector<CUtensorMap> maps;   // [layer][2] BF16 weights [Npad][Kpad], 128-byte swizzle, box = part rows
     std::vector<void*> allocs;
     // MIXED: bf16 weights padded to K multiple of 16 / N multiple of 16, fp32 bias
     std::vector<void*> Wbf;      // device bf16 [Npad][Kpad] per layer
@@ -181,7 +204,7 @@ struct Ctx {
     int num_sms = 0;
     // workspaces of the synchronous path
     DevBuf ws_atoms, ws_batch, ws_bins, ws_nbr_ab, ws_nbr_c, ws_nbr_cnt, ws_u, ws_misc, ws_B, ws_ldos,
-        ws_dens, ws_dos, ws_tile_dos, ws_units, ws_mlp64, ws_red, ws_w;
+        ws_dens, ws_dos, ws_tile_dos, ws_units, ws_mlp64, ws_red, ws_w, ws_mlp_in;
     // workspaces of the force path
     ForceTables ftab;
     DevBuf ws_ftab, ws_force_y, ws_force_aux, ws_force_u, ws_force_nbr, ws_force_beta, ws_force_mlp, ws_force_g,
@@ -318,6 +341,13 @@ __device__ __forceinline__ int batch_find(const BatchSnap* bs, int n, int64_t t)
 // ---- network and integrals ---------------------------------------------------
 
 int model_upload(Ctx* c, const mala_mlp_desc* d, Model* m);
+
+// workspace of the descriptor step for n snapshots (neighbour capacity: the context's hint),
+// of the network over P rows (dos: with the fused DOS partials) and of the integrals of P rows
+void descriptors_ws_needs(Ctx* c, int n, const mala_snapshot* const* snaps, const mala_bispectrum_params* bp,
+                          mala_precision prec, WsNeeds& out);
+void mlp_ws_needs(Ctx* c, const Model* m, int64_t P, bool dos, mala_precision prec, WsNeeds& out);
+void integrate_ws_needs(Ctx* c, int64_t P, int nE, mala_precision prec, WsNeeds& out);
 
 // ---- force path --------------------------------------------------------------
 

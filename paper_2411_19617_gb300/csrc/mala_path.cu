@@ -10,6 +10,8 @@
 // allocates the request's outputs, runs descriptors -> network -> integrals on
 // its stream and marks the request done; requests on different slots run
 // concurrently on the GPU.  Outputs stay on the device until mala_release.
+// Admission claims the outputs and the slot's workspace growth from the budget
+// in one atomic step per request, and an old queue head is never bypassed.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -195,20 +197,44 @@ static bool batchable(const Request* a, const Request* b) {
 
 constexpr int kServeBatchMax = 16;                // requests per batch
 constexpr int64_t kServeBatchPoints = 8000000;    // grid points per batch
+constexpr double kServeBypassS = 0.05;            // how long later requests may pass a queue head that does not fit
+
+// Device workspace a batch would add to a slot: the growth of the slot's
+// buffers (descriptor chunk, network input, integrals) beyond what they hold.
+static size_t batch_ws_growth(Ctx* slot, const std::vector<Request*>& b) {
+    const int n = (int)b.size();
+    std::vector<const mala_snapshot*> snaps(n);
+    int64_t P = 0;
+    for (int i = 0; i < n; ++i) {
+        snaps[i] = &b[i]->snap;
+        P += b[i]->P;
+    }
+    WsNeeds w;
+    descriptors_ws_needs(slot, n, snaps.data(), &b[0]->bp, b[0]->prec, w);
+    mlp_ws_needs(slot, b[0]->model, P, n == 1, b[0]->prec, w);
+    for (const Request* r : b) integrate_ws_needs(slot, r->P, r->eg.n_E, r->prec, w);
+    return w.growth();
+}
 
 static void worker_loop(Server* sv, Ctx* slot) {
     cudaSetDevice(slot->device);
     for (;;) {
         std::vector<Request*> batch;
-        size_t batch_bytes = 0;
+        size_t batch_bytes = 0, ws_grow = 0;
+        bool over_budget = false;
         {
             std::unique_lock<std::mutex> lk(sv->mu);
             for (;;) {
                 if (sv->stop) return;
-                // the oldest queued request whose outputs fit in the budget, then every later
-                // compatible one while the batch still fits (continuous batching)
+                // The oldest queued request whose outputs and workspace growth fit in what the
+                // budget has left, then every later compatible one while the batch still fits
+                // (continuous batching).  The bytes are claimed from the budget one request at
+                // a time; the workspace part is set aside for this slot's buffers.  A queue head
+                // that does not fit may be passed by later requests only for kServeBypassS, after
+                // which nothing is admitted until it fits (no starvation of large snapshots).
                 Ctx* root = sv->root;
                 int64_t pts = 0;
+                const auto now = std::chrono::steady_clock::now();
                 for (auto it = sv->queue.begin(); it != sv->queue.end();) {
                     Request* q = sv->reqs[*it].get();
                     const bool first = batch.empty();
@@ -217,27 +243,42 @@ static void worker_loop(Server* sv, Ctx* slot) {
                         ++it;
                         continue;
                     }
-                    const bool fits = !root->budget || root->used + batch_bytes + q->out_bytes <= root->budget ||
-                                      (first && sv->running == 0);
+                    batch.push_back(q);
+                    const size_t out = batch_bytes + q->out_bytes;
+                    const size_t grow = batch_ws_growth(slot, batch);
+                    const size_t have = batch_bytes + ws_grow, need = out + grow;
+                    bool fits = need <= have || budget_claim(root, need - have);
+                    if (fits && need < have) root->used -= have - need;
                     if (!fits) {
+                        batch.pop_back();
                         if (first) {
+                            if (sv->running == 0) {
+                                // nothing else will free memory: run it alone and report the budget error
+                                batch.push_back(q);
+                                it = sv->queue.erase(it);
+                                over_budget = true;
+                                break;
+                            }
+                            const double age = std::chrono::duration<double>(now - q->t_submit).count();
+                            if (it == sv->queue.begin() && age > kServeBypassS) break;  // the old head goes first
                             ++it;
                             continue;
                         }
                         break;
                     }
-                    batch.push_back(q);
-                    batch_bytes += q->out_bytes;
+                    batch_bytes = out;
+                    ws_grow = grow;
                     pts += q->P;
                     it = sv->queue.erase(it);
                 }
                 if (!batch.empty()) break;
-                sv->cv_work.wait(lk);
+                // woken by submissions, completions and releases; the timeout re-checks the head's age
+                sv->cv_work.wait_for(lk, std::chrono::milliseconds(5));
             }
             for (Request* r : batch) r->state = 1;
             ++sv->running;
-            if (!sv->root->budget || sv->root->used + batch_bytes <= sv->root->budget) sv->root->used += batch_bytes;
-            else batch_bytes = 0;  // over budget: reported below, nothing allocated
+            slot->held = ws_grow;
+            if (over_budget) batch_bytes = 0;  // nothing claimed or allocated: reported below
         }
         int rc = MALA_OK;
         const int n = (int)batch.size();
@@ -286,6 +327,9 @@ static void worker_loop(Server* sv, Ctx* slot) {
             rc = run_path_batch(slot, n, snaps.data(), &r0->bp, r0->model, egs.data(), r0->prec, B, L, D, S, dh.data(),
                                 res.data(), slot->stream);
         }
+        // workspace bytes set aside for this batch and not drawn by the slot's buffers go back
+        sv->root->used -= slot->held;
+        slot->held = 0;
         {
             std::lock_guard<std::mutex> lk(sv->mu);
             const std::string err = rc != MALA_OK ? std::string(mala_last_error()) : std::string();

@@ -2,29 +2,34 @@
 // x_{l+1} = act(W_l x_l + b_l)) on the 5th-generation tensor cores, plus the
 // FP64 path.
 //
-// MIXED path: a persistent kernel, one CTA of 8 warps per SM, walking tiles of
-// 128 grid points (M = 128):
-//   * the descriptors B[P][n_B] (FP32) of a tile are read row by row
-//     (coalesced), standardised ((B - shift) * scale), rounded to BF16 and
-//     written to shared memory in the UMMA K-major layout with the 128-byte
-//     swizzle (the layout TMA produces with SWIZZLE_128B);
-//   * every layer is a chain of tcgen05.mma (kind::f16, BF16 x BF16 -> FP32)
-//     issued by one thread into a tensor-memory accumulator D[128][N] (one TMEM
-//     lane per point); the layer's weights W_l[N][K] stream through two
-//     shared-memory stages in K-blocks of 64 by TMA: block kb+1 is fetched
-//     while the MMAs of block kb run, and the first two blocks of the next
-//     layer (or of the next tile's first layer) are fetched while the
-//     epilogue runs;
-//   * the epilogue reads D with tcgen05.ld (thread = point, the two warps that
-//     share a TMEM lane quarter take alternate 32-column chunks), adds the
-//     bias, applies LeakyReLU on hidden layers and writes the BF16 activations
-//     back to shared memory as the next layer's A operand;
-//   * the last epilogue writes the LDOS in BF16 and, from the same rounded
-//     values, adds the tile's column sums sum_r LDOS(r, xi) to the CTA's FP64
-//     DOS partial; the partials of all CTAs are summed in CTA order afterwards,
-//     so the DOS does not depend on timing.
-// Every wait on an mbarrier is bounded (about one second of clock cycles); on
-// expiry the kernel records an error code, frees its tensor memory and returns.
+// MIXED path: a persistent, warp-specialised kernel, one CTA of ten warps per
+// SM, walking tiles of 128 grid points (M = 128):
+//   * a producer warp streams, by TMA, the tile's standardised BF16
+//     descriptors (written beforehand in a padded [P][8k] layout) into the
+//     activation buffer and every layer's weights W_l[N][K] through a ring of
+//     four shared-memory slots, one "chunk" (a K-block of 64 times one of at
+//     most two N parts of <= 208 rows) per slot, running ahead of the MMAs
+//     across layers and tiles;
+//   * an MMA warp issues the tcgen05.mma chain (kind::f16, BF16 x BF16 -> FP32)
+//     of each layer into one tensor-memory accumulator D[128][N] (a TMEM lane
+//     per point) and releases each slot by tcgen05.commit as soon as its MMAs
+//     have read it;
+//   * eight epilogue warps read D with tcgen05.ld (thread = point; the two
+//     warps that share a TMEM lane quarter take alternate 32-column chunks),
+//     add the bias (held in shared memory), apply LeakyReLU on hidden layers
+//     and write the BF16 activations back as the next layer's A operand in the
+//     UMMA K-major, 128-byte-swizzled layout; the last layer's values go,
+//     rounded to BF16, into a dense [128][N_E] staging tile that one bulk copy
+//     stores to the LDOS, and their column sums over the tile's points (a
+//     transposing butterfly across the warp, then the four lane quarters in a
+//     fixed order, in FP64) go into the CTA's DOS partial; the partials of all
+//     CTAs are summed in CTA order afterwards, so the DOS does not depend on
+//     timing.
+// The next tile's descriptors land (in the activation blocks that the staging
+// tile does not use) while the last epilogue of the current tile runs.  Every
+// wait is bounded (about one second of clock cycles); on expiry the kernel
+// records an error code, raises a shared abort flag that ends every other
+// wait, lets its copies land, frees its tensor memory and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -41,41 +46,59 @@ namespace mala {
 
 namespace {
 
-constexpr int kMlpThreads = 256;
+constexpr int kEpiWarps = 8;
+constexpr int kEpiThreads = kEpiWarps * 32;
+constexpr int kProducerWarp = kEpiWarps;      // TMA issue
+constexpr int kMmaWarp = kEpiWarps + 1;       // tcgen05.mma issue, TMEM owner
+constexpr int kMlpThreads = (kEpiWarps + 2) * 32;
 constexpr int kMaxLayers = 4;
-constexpr int kKBlk = 64;             // K elements per swizzle block (128 bytes of BF16)
-constexpr int kMaxHiddenPad = 448;    // widest K of a hidden activation (7 blocks)
-constexpr int kMaxNPad = 400;         // widest layer output held in one W stage
-constexpr int kHBytes = 128 * kMaxHiddenPad * 2;  // 114688
-constexpr int kStageBytes = kMaxNPad * 128;        // 51200: [N rows][64 K] BF16
-constexpr int kMaxNE = 256;                        // widest output layer
-constexpr int kSmemBytes = kHBytes + 2 * kStageBytes + 1024 /* barriers, tmem slot */ + kMaxNE * 8 /* DOS partial */ +
+constexpr int kKBlk = 64;                     // K elements per swizzle block (128 bytes of BF16)
+constexpr int kHBlocks = 7;
+constexpr int kMaxHiddenPad = kHBlocks * kKBlk;  // widest K of a hidden activation: 448
+constexpr int kBlkBytes = 128 * 128;             // one [128 rows][64] BF16 K-block
+constexpr int kHBytes = kHBlocks * kBlkBytes;    // 114688
+constexpr int kRing = 4;                         // weight slots
+constexpr int kChunkRows = 208;                  // rows of the widest weight chunk
+constexpr int kChunkBytes = kChunkRows * 128;    // 26624
+constexpr int kMaxParts = 2;
+constexpr int kMaxNPad = kMaxParts * kChunkRows; // widest layer output: 416
+constexpr int kMaxNE = 256;                      // widest output layer (staging tile <= 4 K-blocks)
+constexpr int kMaxInBlocks = 2;                  // input K-blocks (descriptor count <= 128)
+constexpr int kQOff = 4 * kBlkBytes;             // column sums of the four lane quarters, behind the staging tile
+constexpr int kMaxBias = kMaxLayers * kMaxNPad;
+constexpr int kSmemBytes = kHBytes + kRing * kChunkBytes + kMaxBias * 4 + kMaxNE * 8 + 256 /* barriers */ +
                            1024 /* alignment */;
+static_assert(kSmemBytes <= 232448, "shared memory of the network kernel");
+static_assert(kQOff + 4 * kMaxNE * 4 <= (kHBlocks - kMaxInBlocks) * kBlkBytes, "quarter sums overlap the input");
 constexpr long long kWaitCycles = 2000000000LL;
 
 struct LayerDev {
-    int K, Kpad, N, Npad, nkb;  // nkb = Kpad / 64
-    int boxN;                   // TMA box rows (Npad split in <= 256-row boxes)
-    int act;                    // apply LeakyReLU
-    const float* bias;          // [Npad]
+    int nkb;            // K-blocks of 64 (the A operand's width / 64)
+    int N, Npad;        // output width, padded to 16
+    int nparts;         // weight chunks per K-block (N parts)
+    int prow[kMaxParts];  // rows of each part (multiples of 16, <= kChunkRows)
+    int pn0[kMaxParts];   // first output column of each part
+    int act;            // apply LeakyReLU
+    int bias_off;       // offset of the layer's bias in the shared bias array
+    const float* bias;  // [Npad]
 };
 
 struct MlpParams {
     int n_layers;
     LayerDev L[kMaxLayers];
     float slope;
-    int nB;                 // descriptor count (K of layer 0)
-    const float* B;         // [P][nB]
-    const float* shift;     // [nB]
-    const float* scale;     // [nB]
+    int nin;                // input K-blocks (layer 0's nkb)
+    int nbias;              // floats of the shared bias array
     __nv_bfloat16* ldos;    // [P][N_E]
+    int bulk_out;           // LDOS 16-byte aligned: full tiles leave by one bulk copy
     double* cta_dos;        // [gridDim.x][N_E] or nullptr
     int64_t P;
     int* err;
 };
 
 struct TMaps {
-    CUtensorMap m[kMaxLayers];
+    CUtensorMap in;                          // standardised BF16 descriptors [P][nin_cols]
+    CUtensorMap w[kMaxLayers][kMaxParts];    // BF16 weights [Npad][Kpad], one map per part height
 };
 
 // ---- PTX wrappers ---------------------------------------------------------
@@ -92,6 +115,10 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
 __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t phase) {
     uint32_t ok;
     asm volatile(
@@ -102,16 +129,27 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t phase) {
     return ok != 0;
 }
 
-// Bounded wait; false (and *err set) if the phase did not complete in time.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase, int* err, int code) {
+// Bounded wait: false if the phase did not complete in time (then *err is set
+// and the abort flag raised) or if another role has raised the abort flag.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase, volatile int* abort_flag, int* err,
+                                          int code) {
     const long long t0 = clock64();
     while (!mbar_try(bar, phase)) {
+        if (*abort_flag) return false;
         if (clock64() - t0 > kWaitCycles) {
             atomicCAS(err, 0, code);
+            *abort_flag = 1;
             return false;
         }
     }
     return true;
+}
+
+// a wait at teardown: for copies still in flight, no abort shortcut
+__device__ __forceinline__ void mbar_drain(uint32_t bar, uint32_t phase) {
+    const long long t0 = clock64();
+    while (!mbar_try(bar, phase))
+        if (clock64() - t0 > kWaitCycles) return;
 }
 
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
@@ -124,6 +162,17 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kEpiThreads) : "memory"); }
+// barrier of the epilogue warps that also ORs a flag over them: the same answer in every thread
+__device__ __forceinline__ bool epi_sync_any(bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.u32 q, %1, 0;\n bar.red.or.pred p, 1, %2, q;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(r)
+        : "r"((uint32_t)v), "n"(kEpiThreads)
+        : "memory");
+    return r != 0;
+}
 
 // Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row
 // groups 1024 bytes apart (SBO), version 1.
@@ -192,13 +241,13 @@ __device__ __forceinline__ void tmem_wait(uint32_t (&r)[32]) {
                  : "memory");
 }
 
-// bias + activation of 32 accumulator columns c0.. (zero beyond the layer's N)
+// bias (shared memory) + activation of 32 accumulator columns c0.. (zero beyond the layer's N)
 __device__ __forceinline__ void bias_act32(const uint32_t (&r)[32], float (&x)[32], int c0, const LayerDev& L,
-                                           float slope) {
+                                           const float* sbias, float slope) {
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
         float4 b = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (c0 + 4 * q < L.Npad) b = __ldg(reinterpret_cast<const float4*>(L.bias) + (c0 / 4 + q));
+        if (c0 + 4 * q < L.Npad) b = *reinterpret_cast<const float4*>(sbias + L.bias_off + c0 + 4 * q);
         const float bb[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
@@ -210,281 +259,288 @@ __device__ __forceinline__ void bias_act32(const uint32_t (&r)[32], float (&x)[3
     }
 }
 
-// Weight pipeline state of the issuing thread.  Stage s holds K-block kb with
-// kb % 2 == s.  full[s] completes when a stage's TMA bytes have landed,
-// free[s] when the MMAs that read it have finished; every completion of either
-// is waited exactly once, in order, before the barrier can complete again.
-struct WPipe {
-    uint32_t full[2], free_[2];
-    uint32_t ph_full[2] = {0, 0}, ph_free[2] = {0, 0};
-    bool pend[2] = {false, false};      // a free[s] completion not yet waited for
-    bool inflight[2] = {false, false};  // a full[s] completion not yet waited for
-};
-
-__device__ __forceinline__ bool wait_full(WPipe& wp, int s, int* err) {
-    const bool ok = mbar_wait(wp.full[s], wp.ph_full[s], err, 2);
-    wp.ph_full[s] ^= 1;
-    wp.inflight[s] = false;
-    return ok;
-}
-
-__device__ __forceinline__ bool load_stage(WPipe& wp, const CUtensorMap* map, const LayerDev& L, int kb,
-                                           unsigned char* sW, int* err) {
-    const int s = kb & 1;
-    if (wp.pend[s]) {
-        if (!mbar_wait(wp.free_[s], wp.ph_free[s], err, 3)) return false;
-        wp.ph_free[s] ^= 1;
-        wp.pend[s] = false;
+// v: this lane's values of 32 columns; returns the sum over the warp's 32
+// lanes of column `lane` (a transposing butterfly: 31 shuffles, fixed order)
+__device__ __forceinline__ float warp_colsum32(float (&v)[32]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < o; ++i) {
+            const float send = up ? v[i] : v[i + o];
+            const float keep = up ? v[i + o] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
     }
-    mbar_expect_tx(wp.full[s], (uint32_t)L.Npad * 128u);
-    wp.inflight[s] = true;
-    for (int n0 = 0; n0 < L.Npad; n0 += L.boxN)
-        tma_load_2d(smem_u32(sW + s * kStageBytes + n0 * 128), map, kb * kKBlk, n0, wp.full[s]);
-    return true;
+    return v[0];
 }
 
 __global__ void __launch_bounds__(kMlpThreads, 1) k_mlp_tc(const __grid_constant__ TMaps maps, MlpParams prm) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    unsigned char* sH = sm;                          // activations, K-blocks of [128][64] BF16
-    unsigned char* sW = sm + kHBytes;                // two weight stages
-    uint64_t* bars = reinterpret_cast<uint64_t*>(sm + kHBytes + 2 * kStageBytes);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 8);
-    double* sDos = reinterpret_cast<double*>(sm + kHBytes + 2 * kStageBytes + 1024);
+    unsigned char* sH = sm;                                  // activations, K-blocks of [128][64] BF16
+    unsigned char* sRing = sm + kHBytes;                     // weight chunks
+    float* sBias = reinterpret_cast<float*>(sRing + kRing * kChunkBytes);
+    double* sDos = reinterpret_cast<double*>(sBias + kMaxBias);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sDos + kMaxNE);
+    // barriers: full[kRing] | empty[kRing] | in_full | in_free | acc_full | epi_done
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2 * kRing + 4);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int quarter = warp & 3, half = warp >> 2;  // TMEM lane quarter, column-chunk parity
     const int64_t ntiles = (prm.P + 127) / 128;
-    const int NE = prm.L[prm.n_layers - 1].N;
-    WPipe wp;
-    wp.full[0] = smem_u32(&bars[0]);
-    wp.full[1] = smem_u32(&bars[1]);
-    wp.free_[0] = smem_u32(&bars[2]);
-    wp.free_[1] = smem_u32(&bars[3]);
-    const uint32_t bar_done = smem_u32(&bars[4]);
+    const int nl = prm.n_layers;
+    const int NE = prm.L[nl - 1].N;
+    auto bar = [&](int i) { return smem_u32(&bars[i]); };
+    const int B_FULL = 0, B_EMPTY = kRing, B_IN_FULL = 2 * kRing, B_IN_FREE = 2 * kRing + 1,
+              B_ACC = 2 * kRing + 2, B_EPI = 2 * kRing + 3;
 
     if (tid == 0) {
-        for (int i = 0; i < 5; ++i) mbar_init(smem_u32(&bars[i]), 1);
+        for (int i = 0; i < 2 * kRing + 3; ++i) mbar_init(bar(i), 1);
+        mbar_init(bar(B_EPI), kEpiWarps);
+        *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        for (int l = 0; l < prm.n_layers; ++l)
-            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&maps.m[l])) : "memory");
     }
-    if (warp == 0) {
+    if (warp == kMmaWarp) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(tslot)));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
+    for (int l = 0; l < nl; ++l)
+        for (int i = tid; i < prm.L[l].Npad; i += kMlpThreads) sBias[prm.L[l].bias_off + i] = __ldg(prm.L[l].bias + i);
     for (int c = tid; c < NE; c += kMlpThreads) sDos[c] = 0.0;
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tslot;
-    const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16);
-    uint32_t ph_done = 0;
-    bool ok = true;
-    if (tid == 0 && (int64_t)blockIdx.x < ntiles) {
-        for (int kb = 0; kb < min(2, prm.L[0].nkb) && ok; ++kb) ok = load_stage(wp, &maps.m[0], prm.L[0], kb, sW, prm.err);
-    }
 
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int64_t row0 = tile * 128;
-        const int nrows = (int)min((int64_t)128, prm.P - row0);
-        // ---- input tile: (B - shift) * scale -> BF16, swizzled, zero-padded ----
-        // warp w takes rows 4w..4w+3 (+32 per pass), lane k = lane + 32 j;
-        // up to 16 loads per thread are in flight before the first store
-        {
-            const int K0pad = prm.L[0].Kpad;
-            const int nch = K0pad / 32;
-            const float* __restrict__ src = prm.B + row0 * prm.nB;
-            for (int rb = warp * 4; rb < 128; rb += 4 * (kMlpThreads / 32)) {
-                for (int j0 = 0; j0 < nch; j0 += 4) {
-                    float v[4][4];
-#pragma unroll
-                    for (int i = 0; i < 4; ++i)
-#pragma unroll
-                        for (int j = 0; j < 4; ++j) {
-                            const int k = lane + 32 * (j0 + j);
-                            v[i][j] = (k < prm.nB && rb + i < nrows) ? __ldg(src + (int64_t)(rb + i) * prm.nB + k) : 0.f;
-                        }
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        if (j0 + j >= nch) break;
-                        const int k = lane + 32 * (j0 + j);
-                        const bool in = k < prm.nB;
-                        const float sh = in ? __ldg(prm.shift + k) : 0.f;
-                        const float sc = in ? __ldg(prm.scale + k) : 0.f;
-#pragma unroll
-                        for (int i = 0; i < 4; ++i)
-                            *reinterpret_cast<__nv_bfloat16*>(sH + (k / kKBlk) * (128 * 128) + swz(rb + i, k % kKBlk)) =
-                                __float2bfloat16_rn((v[i][j] - sh) * sc);
-                    }
-                }
-            }
-            // warm L2 with the next tile's descriptors (a hint; skipped when unaligned)
-            if (tid == 32) {
-                const int64_t nt = tile + gridDim.x;
-                if (nt < ntiles) {
-                    const int64_t nr = min((int64_t)128, prm.P - nt * 128);
-                    const float* nsrc = prm.B + nt * 128 * prm.nB;
-                    const uint32_t bytes = (uint32_t)(nr * prm.nB * 4) & ~15u;
-                    if ((reinterpret_cast<uintptr_t>(nsrc) & 15) == 0 && bytes > 0)
-                        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(nsrc), "r"(bytes) : "memory");
-                }
-            }
-        }
-        fence_proxy_async();
-        tc_fence_before();
-        if (!__syncthreads_and(ok)) {
-            ok = false;
-            break;
-        }
-        tc_fence_after();
-
-        for (int l = 0; l < prm.n_layers; ++l) {
-            const LayerDev& L = prm.L[l];
-            // ---- MMA chain of layer l (one thread issues, the rest wait) ----
-            if (tid == 0) {
-                for (int kb = 0; kb < L.nkb && ok; ++kb) {
-                    const int s = kb & 1;
-                    ok = wait_full(wp, s, prm.err);
+    if (warp == kProducerWarp) {
+        // ---- producer: the next tiles' inputs and the weight chunks, in consumption order ----
+        if (lane == 0) {
+            for (int l = 0; l < nl; ++l)
+                for (int p = 0; p < prm.L[l].nparts; ++p)
+                    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&maps.w[l][p])) : "memory");
+            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&maps.in)) : "memory");
+            uint32_t chunk = 0, in_ph = 0, issued_in = 0;
+            bool ok = true;
+            for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+                if (issued_in > 0) {  // the previous tile's last MMAs have read the activation buffer
+                    ok = mbar_wait(bar(B_IN_FREE), in_ph, abort_flag, prm.err, 5);
+                    in_ph ^= 1;
                     if (!ok) break;
-                    tc_fence_after();
-                    const uint32_t a_base = smem_u32(sH + kb * (128 * 128));
-                    const uint32_t b_base = smem_u32(sW + s * kStageBytes);
-#pragma unroll
-                    for (int k = 0; k < kKBlk / 16; ++k) {
-                        for (int n0 = 0; n0 < L.Npad; n0 += 256) {
-                            const int nn = min(256, L.Npad - n0);
-                            mma_bf16(tmem + (uint32_t)n0, sdesc(a_base + k * 32), sdesc(b_base + n0 * 128 + k * 32),
-                                     idesc_bf16(128, nn), (kb > 0 || k > 0) ? 1u : 0u);
+                }
+                mbar_expect_tx(bar(B_IN_FULL), (uint32_t)prm.nin * kBlkBytes);
+                for (int kb = 0; kb < prm.nin; ++kb)
+                    tma_load_2d(smem_u32(sH + (kHBlocks - prm.nin + kb) * kBlkBytes), &maps.in, kb * kKBlk,
+                                (int)(tile * 128), bar(B_IN_FULL));
+                ++issued_in;
+                for (int l = 0; l < nl && ok; ++l) {
+                    const LayerDev& L = prm.L[l];
+                    for (int kb = 0; kb < L.nkb && ok; ++kb)
+                        for (int p = 0; p < L.nparts; ++p, ++chunk) {
+                            const uint32_t slot = chunk % kRing;
+                            if (chunk >= (uint32_t)kRing) {
+                                ok = mbar_wait(bar(B_EMPTY + slot), ((chunk / kRing) - 1) & 1, abort_flag, prm.err, 3);
+                                if (!ok) break;
+                            }
+                            mbar_expect_tx(bar(B_FULL + slot), (uint32_t)L.prow[p] * 128u);
+                            tma_load_2d(smem_u32(sRing + slot * kChunkBytes), &maps.w[l][p], kb * kKBlk, L.pn0[p],
+                                        bar(B_FULL + slot));
                         }
-                    }
-                    mma_commit(wp.free_[s]);
-                    wp.pend[s] = true;
-                    // block kb+1 goes to the other stage once the MMAs of kb-1 are done
-                    if (kb >= 1 && kb + 1 < L.nkb) {
-                        ok = load_stage(wp, &maps.m[l], L, kb + 1, sW, prm.err);
+                }
+            }
+            // let the copies still in flight land before the CTA can exit
+            for (uint32_t s2 = 0; s2 < (uint32_t)kRing; ++s2) {
+                if (chunk > s2) {
+                    const uint32_t last = chunk - 1 - ((chunk - 1 - s2) % kRing);  // last chunk issued to slot s2
+                    mbar_drain(bar(B_FULL + s2), (last / kRing) & 1);
+                }
+            }
+            if (issued_in > 0) mbar_drain(bar(B_IN_FULL), (issued_in - 1) & 1);
+        }
+    } else if (warp == kMmaWarp) {
+        // ---- MMA issuer ----
+        if (lane == 0) {
+            uint32_t chunk = 0, in_ph = 0, epi_ph = 0;
+            bool ok = true, first = true;
+            for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+                for (int l = 0; l < nl && ok; ++l) {
+                    const LayerDev& L = prm.L[l];
+                    if (l == 0) {
+                        ok = mbar_wait(bar(B_IN_FULL), in_ph, abort_flag, prm.err, 6);
+                        in_ph ^= 1;
                         if (!ok) break;
                     }
-                }
-                mma_commit(bar_done);
-            }
-            const bool mine = mbar_wait(bar_done, ph_done, prm.err, 4);
-            ph_done ^= 1;
-            if (!__syncthreads_and(ok && mine)) {
-                ok = false;
-                break;
-            }
-            tc_fence_after();
-            const bool last = (l == prm.n_layers - 1);
-            // the stages are idle now: fetch the next layer's first blocks during the epilogue
-            if (tid == 0) {
-                const int nl = last ? 0 : l + 1;
-                const bool more = !last || tile + gridDim.x < ntiles;
-                if (more)
-                    for (int kb = 0; kb < min(2, prm.L[nl].nkb) && ok; ++kb)
-                        ok = load_stage(wp, &maps.m[nl], prm.L[nl], kb, sW, prm.err);
-            }
-            // ---- epilogue: TMEM -> registers (thread = point) -> bias/activation ----
-            const int r = quarter * 32 + lane;
-            if (!last) {
-                const int Knext = prm.L[l + 1].Kpad;
-                // this warp's 32-column chunks c0 = half*32 + 64 j; the TMEM read of
-                // chunk j+1 is in flight while chunk j is converted
-                auto store_chunk = [&](const uint32_t (&rr)[32], int c0) {
-                    float x[32];
-                    bias_act32(rr, x, c0, L, prm.slope);
-                    unsigned char* blk = sH + (c0 / kKBlk) * (128 * 128);
+                    if (!first) {  // the previous epilogue has read the accumulator and written this layer's A
+                        ok = mbar_wait(bar(B_EPI), epi_ph, abort_flag, prm.err, 4);
+                        epi_ph ^= 1;
+                        if (!ok) break;
+                    }
+                    first = false;
+                    tc_fence_after();
+                    const int ablk0 = (l == 0) ? kHBlocks - prm.nin : 0;
+                    for (int kb = 0; kb < L.nkb && ok; ++kb)
+                        for (int p = 0; p < L.nparts; ++p, ++chunk) {
+                            const uint32_t slot = chunk % kRing;
+                            ok = mbar_wait(bar(B_FULL + slot), (chunk / kRing) & 1, abort_flag, prm.err, 2);
+                            if (!ok) break;
+                            tc_fence_after();
+                            const uint32_t a_base = smem_u32(sH + (ablk0 + kb) * kBlkBytes);
+                            const uint32_t b_base = smem_u32(sRing + slot * kChunkBytes);
+                            const uint32_t idesc = idesc_bf16(128, L.prow[p]);
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        uint4 w4;
-                        w4.x = pack_bf16(x[8 * q + 0], x[8 * q + 1]);
-                        w4.y = pack_bf16(x[8 * q + 2], x[8 * q + 3]);
-                        w4.z = pack_bf16(x[8 * q + 4], x[8 * q + 5]);
-                        w4.w = pack_bf16(x[8 * q + 6], x[8 * q + 7]);
-                        *reinterpret_cast<uint4*>(blk + swz(r, c0 % kKBlk + 8 * q)) = w4;
-                    }
-                };
-                const int nch = (Knext - half * 32 + 63) / 64;
-                uint32_t ra[32], rb[32];
-                if (nch > 0) {
-                    tmem_issue32(trow + (uint32_t)(half * 32), ra);
-                    tmem_wait(ra);
+                            for (int k = 0; k < kKBlk / 16; ++k)
+                                mma_bf16(tmem + (uint32_t)L.pn0[p], sdesc(a_base + k * 32), sdesc(b_base + k * 32), idesc,
+                                         (kb > 0 || k > 0) ? 1u : 0u);
+                            mma_commit(bar(B_EMPTY + slot));
+                        }
+                    if (!ok) break;
+                    mma_commit(bar(B_ACC));
+                    if (l == nl - 1) mma_commit(bar(B_IN_FREE));
                 }
-                for (int j = 0; j < nch; j += 2) {
-                    const int c0 = half * 32 + 64 * j;
-                    if (j + 1 < nch) tmem_issue32(trow + (uint32_t)(c0 + 64), rb);
-                    store_chunk(ra, c0);
-                    if (j + 1 < nch) {
-                        tmem_wait(rb);
-                        if (j + 2 < nch) tmem_issue32(trow + (uint32_t)(c0 + 128), ra);
-                        store_chunk(rb, c0 + 64);
-                        if (j + 2 < nch) tmem_wait(ra);
-                    }
-                }
-                fence_proxy_async();
-                tc_fence_before();
-                __syncthreads();
-                tc_fence_after();
-            } else {
-                // output: BF16 rows staged in the activation buffer (its MMAs are
-                // done), row stride padded by 16 bytes against bank conflicts
-                __nv_bfloat16* so = reinterpret_cast<__nv_bfloat16*>(sH);
-                const int ldc = (NE + 31) & ~31;
-                const int ldo = ldc + 8;
-                for (int c0 = half * 32; c0 < ldc; c0 += 64) {
-                    uint32_t rr[32];
-                    tmem_issue32(trow + (uint32_t)c0, rr);
-                    tmem_wait(rr);
-                    float x[32];
-                    bias_act32(rr, x, c0, L, prm.slope);
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        uint4 w4;
-                        w4.x = pack_bf16(x[8 * q + 0], x[8 * q + 1]);
-                        w4.y = pack_bf16(x[8 * q + 2], x[8 * q + 3]);
-                        w4.z = pack_bf16(x[8 * q + 4], x[8 * q + 5]);
-                        w4.w = pack_bf16(x[8 * q + 6], x[8 * q + 7]);
-                        *reinterpret_cast<uint4*>(so + r * ldo + c0 + 8 * q) = w4;
-                    }
-                }
-                tc_fence_before();
-                __syncthreads();
-                __nv_bfloat16* dst = prm.ldos + row0 * NE;
-                if ((NE & 1) == 0) {
-                    const int hw = NE / 2;
-                    for (int idx = tid; idx < nrows * hw; idx += kMlpThreads) {
-                        const int rr = idx / hw, c2 = idx - rr * hw;
-                        reinterpret_cast<uint32_t*>(dst)[idx] = *reinterpret_cast<const uint32_t*>(so + rr * ldo + 2 * c2);
-                    }
-                } else {
-                    for (int idx = tid; idx < nrows * NE; idx += kMlpThreads) {
-                        const int rr = idx / NE, c = idx - rr * NE;
-                        dst[idx] = so[rr * ldo + c];
-                    }
-                }
-                if (prm.cta_dos) {
-                    for (int c = tid; c < NE; c += kMlpThreads) {
-                        float sum = 0.f;
-                        for (int rr = 0; rr < nrows; ++rr) sum += __bfloat162float(so[rr * ldo + c]);
-                        sDos[c] += (double)sum;
-                    }
-                }
-                __syncthreads();  // the staging buffer is the next tile's input buffer
             }
         }
-        if (!ok) break;
+    } else {
+        // ---- epilogue warps: TMEM -> registers (thread = point) -> bias/activation -> shared memory ----
+        const int quarter = warp & 3, half = warp >> 2;
+        const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16);
+        const int r = quarter * 32 + lane;
+        float* sQ = reinterpret_cast<float*>(sH + kQOff);  // [4][NE] column sums of the lane quarters
+        __nv_bfloat16* so = reinterpret_cast<__nv_bfloat16*>(sH);
+        uint32_t acc_ph = 0;
+        bool ok = true, store_pending = false;
+        for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+            const int64_t row0 = tile * 128;
+            const int nrows = (int)min((int64_t)128, prm.P - row0);
+            for (int l = 0; l < nl; ++l) {
+                const LayerDev& L = prm.L[l];
+                const bool got = mbar_wait(bar(B_ACC), acc_ph, abort_flag, prm.err, 7);
+                acc_ph ^= 1;
+                tc_fence_after();
+                // before the first writes of a tile: the previous tile's output copy has read the staging tile
+                if (l == 0 && tid == 0 && store_pending) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+                store_pending = false;
+                // one decision for all epilogue warps (none may stop alone: they share named barriers)
+                if (epi_sync_any(!got || *abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                if (l < nl - 1) {
+                    const int Knext = prm.L[l + 1].nkb * kKBlk;
+                    auto store_chunk = [&](const uint32_t (&rr)[32], int c0) {
+                        float x[32];
+                        bias_act32(rr, x, c0, L, sBias, prm.slope);
+                        unsigned char* blk = sH + (c0 / kKBlk) * kBlkBytes;
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            uint4 w4;
+                            w4.x = pack_bf16(x[8 * q + 0], x[8 * q + 1]);
+                            w4.y = pack_bf16(x[8 * q + 2], x[8 * q + 3]);
+                            w4.z = pack_bf16(x[8 * q + 4], x[8 * q + 5]);
+                            w4.w = pack_bf16(x[8 * q + 6], x[8 * q + 7]);
+                            *reinterpret_cast<uint4*>(blk + swz(r, c0 % kKBlk + 8 * q)) = w4;
+                        }
+                    };
+                    // this warp's 32-column chunks c0 = half*32 + 64 j; the TMEM read of
+                    // chunk j+1 is in flight while chunk j is converted
+                    const int nch = (Knext - half * 32 + 63) / 64;
+                    uint32_t ra[32], rb[32];
+                    if (nch > 0) {
+                        tmem_issue32(trow + (uint32_t)(half * 32), ra);
+                        tmem_wait(ra);
+                    }
+                    for (int j = 0; j < nch; j += 2) {
+                        const int c0 = half * 32 + 64 * j;
+                        if (j + 1 < nch) tmem_issue32(trow + (uint32_t)(c0 + 64), rb);
+                        store_chunk(ra, c0);
+                        if (j + 1 < nch) {
+                            tmem_wait(rb);
+                            if (j + 2 < nch) tmem_issue32(trow + (uint32_t)(c0 + 128), ra);
+                            store_chunk(rb, c0 + 64);
+                            if (j + 2 < nch) tmem_wait(ra);
+                        }
+                    }
+                    fence_proxy_async();
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(bar(B_EPI));
+                } else {
+                    // output: BF16 values into the dense staging tile [128][NE] and their column sums
+                    const int ldc = (NE + 31) & ~31;
+                    for (int c0 = half * 32; c0 < ldc; c0 += 64) {
+                        uint32_t rr[32];
+                        tmem_issue32(trow + (uint32_t)c0, rr);
+                        tmem_wait(rr);
+                        float x[32];
+                        bias_act32(rr, x, c0, L, sBias, prm.slope);
+                        __nv_bfloat16* orow = so + (size_t)r * NE;
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) {
+                            const __nv_bfloat16 h = __float2bfloat16_rn(x[i]);
+                            x[i] = (r < nrows && c0 + i < NE) ? __bfloat162float(h) : 0.f;
+                            if (c0 + i < NE) orow[c0 + i] = h;
+                        }
+                        if (prm.cta_dos) {
+                            const float cs = warp_colsum32(x);
+                            if (c0 + lane < NE) sQ[quarter * NE + c0 + lane] = cs;
+                        }
+                    }
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(bar(B_EPI));  // the accumulator has been read
+                    fence_proxy_async();
+                    epi_sync();
+                    if (prm.cta_dos && tid < NE)
+                        sDos[tid] += (((double)sQ[tid] + (double)sQ[NE + tid]) + (double)sQ[2 * NE + tid]) +
+                                     (double)sQ[3 * NE + tid];
+                    __nv_bfloat16* dst = prm.ldos + row0 * NE;
+                    if (prm.bulk_out && nrows == 128) {
+                        if (tid == 0) {
+                            asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst),
+                                         "r"(smem_u32(so)), "r"((uint32_t)(128 * NE * 2))
+                                         : "memory");
+                            asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+                        }
+                        store_pending = true;
+                    } else {
+                        for (int idx = tid; idx < nrows * NE; idx += kEpiThreads) dst[idx] = so[idx];
+                    }
+                }
+            }
+        }
+        if (tid == 0 && store_pending) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+        if (prm.cta_dos)
+            for (int c = tid; c < NE; c += kEpiThreads) prm.cta_dos[(int64_t)blockIdx.x * NE + c] = sDos[c];
     }
-    if (prm.cta_dos)
-        for (int c = tid; c < NE; c += kMlpThreads) prm.cta_dos[(int64_t)blockIdx.x * NE + c] = sDos[c];
-    // after an error: let copies still in flight land before the CTA exits
-    if (tid == 0)
-        for (int s2 = 0; s2 < 2; ++s2)
-            if (wp.inflight[s2]) wait_full(wp, s2, prm.err);
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) {
+    if (warp == kMmaWarp) {
+        __syncwarp();
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
     }
+}
+
+// standardised BF16 copy of the descriptors for the network's input TMA:
+// Bh[p][k] = (B[p][k] - shift[k]) * scale[k] for k < nB, 0 up to the padded width nBh
+__global__ void k_mlp_in(const float* __restrict__ B, int64_t P, int nB, int nBh, const float* __restrict__ shift,
+                         const float* __restrict__ scale, __nv_bfloat16* __restrict__ Bh) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // one 8-column group
+    const int g = nBh / 8;
+    if (i >= P * g) return;
+    const int64_t p = i / g;
+    const int k0 = (int)(i - p * g) * 8;
+    uint32_t w[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        float v[2];
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+            const int k = k0 + 2 * j + t;
+            v[t] = k < nB ? (__ldg(B + p * nB + k) - __ldg(shift + k)) * __ldg(scale + k) : 0.f;
+        }
+        w[j] = pack_bf16(v[0], v[1]);
+    }
+    *reinterpret_cast<uint4*>(Bh + p * nBh + k0) = make_uint4(w[0], w[1], w[2], w[3]);
 }
 
 // ---- FP64 path: plain tiled GEMM + bias + activation per layer -------------
@@ -582,19 +638,29 @@ int model_upload(Ctx* c, const mala_mlp_desc* d, Model* m) {
     m->slope_d = d->leaky_slope;
     m->activate_output = d->activate_output;
     const int nl = d->n_layers;
-    // MIXED layout: K padded to 64 (128-byte swizzle blocks), N padded to 16
+    // MIXED layout: K padded to 64 (128-byte swizzle blocks), N padded to 16 and
+    // cut into at most two parts of <= 208 rows (one ring slot each)
     m->Kpad.resize(nl);
     m->Npad.resize(nl);
-    m->mixed_ok = true;
+    m->nparts.assign(nl, 1);
+    m->prow.assign(2 * nl, 0);
+    m->pn0.assign(2 * nl, 0);
+    m->mixed_ok = nl <= kMaxLayers && m->dims[nl] <= kMaxNE && m->dims[0] <= kMaxInBlocks * kKBlk;
     for (int l = 0; l < nl; ++l) {
         m->Kpad[l] = pad_to(m->dims[l], kKBlk);
         m->Npad[l] = pad_to(m->dims[l + 1], 16);
-        if (l > 0 && m->Kpad[l] > kMaxHiddenPad) m->mixed_ok = false;
         if (m->Kpad[l] > kMaxHiddenPad || m->Npad[l] > kMaxNPad) m->mixed_ok = false;
         if (l + 1 < nl && pad_to(m->dims[l + 1], kKBlk) > kMaxHiddenPad) m->mixed_ok = false;
+        const int units = m->Npad[l] / 16, per = kChunkRows / 16;
+        const int np = std::min(kMaxParts, (units + per - 1) / per);
+        m->nparts[l] = np;
+        for (int p = 0, n0 = 0; p < np; ++p) {
+            const int u = units / np + (p < units % np ? 1 : 0);
+            m->prow[2 * l + p] = 16 * u;
+            m->pn0[2 * l + p] = n0;
+            n0 += 16 * u;
+        }
     }
-    if (nl > kMaxLayers) m->mixed_ok = false;
-    if (m->dims[nl] > 256) m->mixed_ok = false;
     auto dalloc = [&](size_t bytes, void** p) -> int {
         Ctx* r = c->root();
         if (!budget_claim(r, bytes)) return fail(MALA_ERR_OOM, "model exceeds the HBM budget");
@@ -662,23 +728,22 @@ int model_upload(Ctx* c, const mala_mlp_desc* d, Model* m) {
     if (m->mixed_ok) {
         auto enc = get_encode();
         if (!enc) return fail(MALA_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+        m->maps.assign(2 * nl, CUtensorMap{});
         for (int l = 0; l < nl; ++l) {
             const int Kp = m->Kpad[l], Np = m->Npad[l];
-            int boxN = Np;
-            while (boxN > 256) boxN /= 2;  // 400 -> 200
-            boxN = pad_to(boxN, 8);
-            while (Np % boxN) boxN -= 8;
-            m->boxN.push_back(boxN);
-            CUtensorMap map;
-            cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)Np};
-            cuuint64_t strides[1] = {(cuuint64_t)Kp * 2};
-            cuuint32_t box[2] = {(cuuint32_t)kKBlk, (cuuint32_t)boxN};
-            cuuint32_t es[2] = {1, 1};
-            CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, m->Wbf[l], dims, strides, box, es,
-                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-            if (r != CUDA_SUCCESS) return fail(MALA_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d) for layer %d", (int)r, l);
-            m->maps.push_back(map);
+            for (int p = 0; p < m->nparts[l]; ++p) {
+                CUtensorMap map;
+                cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)Np};
+                cuuint64_t strides[1] = {(cuuint64_t)Kp * 2};
+                cuuint32_t box[2] = {(cuuint32_t)kKBlk, (cuuint32_t)m->prow[2 * l + p]};
+                cuuint32_t es[2] = {1, 1};
+                CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, m->Wbf[l], dims, strides, box, es,
+                                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                 CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                if (r != CUDA_SUCCESS)
+                    return fail(MALA_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d) for layer %d", (int)r, l);
+                m->maps[2 * l + p] = map;
+            }
         }
     }
     return MALA_OK;
@@ -694,6 +759,23 @@ void model_free(Model* m) {
 
 // ---- forward ------------------------------------------------------------------
 
+void mlp_ws_needs(Ctx* c, const Model* m, int64_t P, bool dos, mala_precision prec, WsNeeds& out) {
+    const int nl = m->n_layers;
+    const int NE = m->dims[nl];
+    if (P <= 0) return;
+    if (prec == MALA_MIXED) {
+        const int64_t ntiles = (P + 127) / 128;
+        const int grid = (int)std::min<int64_t>(ntiles, std::max(1, c->num_sms));
+        if (dos) out.add(c->ws_tile_dos, sizeof(double) * (size_t)grid * NE);
+        out.add(c->ws_mlp_in, sizeof(__nv_bfloat16) * (size_t)P * pad_to(m->dims[0], 8));
+        return;
+    }
+    int wmax = 0;
+    for (int l = 1; l < nl; ++l) wmax = std::max(wmax, m->dims[l]);
+    out.add(c->ws_mlp64, sizeof(double) * (size_t)P * (size_t)std::max(1, wmax) * 2);
+    if (dos) out.add(c->ws_tile_dos, sizeof(double) * (size_t)((P + 1023) / 1024) * NE);
+}
+
 int mlp_forward(Ctx* c, const Model* m, const void* B, int64_t P, void* ldos, double* dos_sum, mala_precision prec,
                 cudaStream_t st) {
     const int nl = m->n_layers;
@@ -705,42 +787,66 @@ int mlp_forward(Ctx* c, const Model* m, const void* B, int64_t P, void* ldos, do
     if (prec == MALA_MIXED) {
         if (!m->mixed_ok)
             return fail(MALA_ERR_UNSUPPORTED, "network shape outside the tensor-core kernel's limits "
-                                              "(<= %d layers, hidden width <= %d, output <= 256)", kMaxLayers, kMaxHiddenPad);
+                                              "(<= %d layers, input <= %d, hidden width <= %d, output <= %d)",
+                        kMaxLayers, kMaxInBlocks * kKBlk, kMaxNPad, kMaxNE);
         const int64_t ntiles = (P + 127) / 128;
-        int dev = 0, nsm = 0;
-        MALA_CUDA_TRY(cudaGetDevice(&dev));
-        MALA_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-        const int grid = (int)std::min<int64_t>(ntiles, std::max(1, nsm));
+        if (ntiles > (int64_t)INT32_MAX / 2) return fail(MALA_ERR_UNSUPPORTED, "too many grid points for the network");
+        const int grid = (int)std::min<int64_t>(ntiles, std::max(1, c->num_sms));
         double* cta_dos = nullptr;
         if (dos_sum) {
             MALA_TRY(c->ws_tile_dos.reserve(c, sizeof(double) * (size_t)grid * NE));
             cta_dos = c->ws_tile_dos.as<double>();
         }
+        // standardised BF16 input rows, padded to a multiple of 8 (16 bytes) for the input TMA
+        const int nB = m->dims[0];
+        const int nBh = pad_to(nB, 8);
+        MALA_TRY(c->ws_mlp_in.reserve(c, sizeof(__nv_bfloat16) * (size_t)P * nBh));
+        __nv_bfloat16* Bh = c->ws_mlp_in.as<__nv_bfloat16>();
+        {
+            const int64_t groups = P * (nBh / 8);
+            MALA_PROF(c, "k_mlp_in", st,
+                      (k_mlp_in<<<(unsigned)((groups + 255) / 256), 256, 0, st>>>(static_cast<const float*>(B), P, nB, nBh,
+                                                                                  m->in_shift, m->in_scale, Bh)));
+        }
+        auto enc = get_encode();
+        if (!enc) return fail(MALA_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
         TMaps maps;
         memset(&maps, 0, sizeof(maps));
+        {
+            cuuint64_t dims[2] = {(cuuint64_t)nBh, (cuuint64_t)P};
+            cuuint64_t strides[1] = {(cuuint64_t)nBh * 2};
+            cuuint32_t box[2] = {(cuuint32_t)kKBlk, 128u};
+            cuuint32_t es[2] = {1, 1};
+            CUresult r = enc(&maps.in, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, Bh, dims, strides, box, es,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS) return fail(MALA_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d) for the input", (int)r);
+        }
         MlpParams prm;
         memset(&prm, 0, sizeof(prm));
         prm.n_layers = nl;
+        int boff = 0;
         for (int l = 0; l < nl; ++l) {
-            maps.m[l] = m->maps[l];
             LayerDev& L = prm.L[l];
-            L.K = m->dims[l];
-            L.Kpad = m->Kpad[l];
+            L.nkb = m->Kpad[l] / kKBlk;
             L.N = m->dims[l + 1];
             L.Npad = m->Npad[l];
-            L.nkb = L.Kpad / kKBlk;
-            L.boxN = m->boxN[l];
+            L.nparts = m->nparts[l];
+            for (int p = 0; p < L.nparts; ++p) {
+                L.prow[p] = m->prow[2 * l + p];
+                L.pn0[p] = m->pn0[2 * l + p];
+                maps.w[l][p] = m->maps[2 * l + p];
+            }
             L.act = (l < nl - 1) || m->activate_output;
+            L.bias_off = boff;
             L.bias = m->bias[l];
+            boff += L.Npad;
         }
-        // hidden layers feed the next layer with K = Npad rounded to 64
-        for (int l = 0; l + 1 < nl; ++l) prm.L[l + 1].Kpad = pad_to(m->dims[l + 1], kKBlk), prm.L[l + 1].nkb = prm.L[l + 1].Kpad / kKBlk;
+        prm.nbias = boff;
         prm.slope = m->leaky_slope;
-        prm.nB = m->dims[0];
-        prm.B = static_cast<const float*>(B);
-        prm.shift = m->in_shift;
-        prm.scale = m->in_scale;
+        prm.nin = m->Kpad[0] / kKBlk;
         prm.ldos = static_cast<__nv_bfloat16*>(ldos);
+        prm.bulk_out = (reinterpret_cast<uintptr_t>(ldos) & 15) == 0;
         prm.cta_dos = cta_dos;
         prm.P = P;
         prm.err = c->tables.err_d + 1;
