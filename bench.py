@@ -48,15 +48,23 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--serve-requests", type=int, default=16,
-                    help="requests of the serving comparison (0 skips it)")
-    ap.add_argument("--serve-max-atoms", type=int, default=512,
-                    help="atom-count cap of the serving sample (bounds the FP64 arm's time)")
+    ap.add_argument("--serve-requests", type=int, default=2000,
+                    help="requests of the serving trace (Poisson arrivals at 200/s; 0 skips the serving leg)")
+    ap.add_argument("--serve-util-requests", type=int, default=300,
+                    help="requests of the serving run at about 70%% utilisation")
+    ap.add_argument("--serve-fp64-requests", type=int, default=24,
+                    help="leading requests of the trace served by the plain FP64 path and, for the same "
+                         "schedule, by the served mixed path")
+    ap.add_argument("--workload-calls", type=int, default=2,
+                    help="timed calls of the boron-cluster batch, Be slab and small FP64 legs (0 skips them)")
     ap.add_argument("--forces-calls", type=int, default=3,
                     help="timed calls of the band-energy forces leg (0 skips it)")
     ap.add_argument("--ace-calls", type=int, default=3, help="timed calls of the ACE descriptor leg (0 skips it)")
     ap.add_argument("--gauss-calls", type=int, default=3,
                     help="timed calls of the Gaussian descriptor leg (0 skips it)")
+    ap.add_argument("--grid", type=int, default=0,
+                    help="points per axis of the workload's grid (0: the workload's own 90; smaller grids are "
+                         "for profiler captures, never for the bench line)")
     return ap.parse_args()
 
 
@@ -125,9 +133,12 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # workload
 
-def setup_workload(ctx, api, wl, torch):
+def setup_workload(ctx, api, wl, torch, grid=0):
     snaps, bp, mlp, eg, _ = wl.config(2)
     snap = snaps[0]
+    if grid:
+        snap = wl.Snapshot(pos=snap.pos, species=snap.species, cell=snap.cell, grid=(grid, grid, grid),
+                           periodic=snap.periodic)
     # input standardisation from the descriptors of this snapshot (model set-up)
     B = ctx.descriptors(snap, bp, api.MIXED).double()
     mlp = wl.with_input_scaling(mlp, B.mean(0).cpu().numpy(), 1.0 / (B.std(0).cpu().numpy() + 1e-12))
@@ -146,57 +157,226 @@ def pct(v, q):
     return v[k]
 
 
-def serving_compare(ctx, api, wl, model, bp, eg, n_req, nmax):
-    """The same Poisson arrival schedule served two ways: MIXED requests through
-    mala_submit/mala_poll (continuous batching over the serving slots) and the
-    plain FP64 path one snapshot at a time (mala_predict, FP64_PLAIN).  Latency
-    is completion minus arrival, queueing included."""
-    trace = wl.serving_trace(n_req, rate_per_s=200.0, seed=5, nmin=32, nmax=nmax)
-    # a reachable electron count per request: N(mu = 0) of its own (MIXED) DOS, untimed
-    ne = []
-    for rq in trace:
+def _serve(ctx, api, trace, bp, model, eg, nes, time_scale=1.0):
+    """Replay an arrival schedule through mala_submit/mala_poll (continuous batching over the
+    serving slots): every request is submitted at its arrival time, completed tickets are read
+    and released at once.  Latency = completion - arrival, queueing included."""
+    lat, status, pending, i = [], [], {}, 0
+    t0 = time.perf_counter()
+    while i < len(trace) or pending:
+        now = time.perf_counter() - t0
+        while i < len(trace) and trace[i].arrival_s * time_scale <= now:
+            tk = ctx.submit(trace[i].snapshot, bp, model, eg, api.MIXED, n_electrons=nes[i])
+            pending[tk] = trace[i].arrival_s * time_scale
+            i += 1
+        for tk in list(pending):
+            st = ctx.poll_status(tk)
+            if st != 1:
+                lat.append(time.perf_counter() - t0 - pending.pop(tk))
+                status.append(st)
+                ctx.release(tk)
+        time.sleep(0.0002)
+    return lat, status, time.perf_counter() - t0
+
+
+def _plain_fp64(ctx, api, trace, bp, model, eg, nes):
+    """The same schedule through the plain FP64 path, one snapshot at a time."""
+    lat, status = [], []
+    t0 = time.perf_counter()
+    for i, rq in enumerate(trace):
+        wait = rq.arrival_s - (time.perf_counter() - t0)
+        if wait > 0:
+            time.sleep(wait)
+        r = ctx.predict(rq.snapshot, bp, model, eg, api.FP64_PLAIN, n_electrons=nes[i], raise_on_bracket=False)
+        status.append(r["status"])
+        lat.append(time.perf_counter() - t0 - rq.arrival_s)
+    return lat, status, time.perf_counter() - t0
+
+
+def serving_leg(ctx, api, wl, mlp, bp, eg, n_req, n_util, n_fp64):
+    """The serving trace (Poisson arrivals at 200/s; Al or Be bulk, 32..2048 atoms log-uniform,
+    0.2 A spacing; network 91-400-400-250) served with mixed precision, at full size and at a
+    rate giving about 70% utilisation, and its leading requests served by the plain FP64 path
+    one snapshot at a time beside the served mixed path on the same schedule."""
+    trace = wl.serving_trace(n_req, rate_per_s=200.0, seed=5)
+    model = api.Model(ctx, mlp)
+    # a reachable electron count per request: N(mu = 0) per unit volume of a calibration snapshot
+    # of each material (untimed), times the request's volume
+    per_vol = {}
+    for mat in ("Al", "Be"):
+        rq = next((r for r in trace if r.material == mat), None)
+        if rq is None:
+            continue
         r = ctx.predict(rq.snapshot, bp, model, eg, api.MIXED, n_electrons=0.0, raise_on_bracket=False)
-        ne.append(ctx.electron_count(r["dos"], eg, 0.0))
-    pts = [rq.snapshot.n_points for rq in trace]
-    ctx.predict(trace[0].snapshot, bp, model, eg, api.FP64_PLAIN, n_electrons=ne[0])  # warm the FP64 path
+        per_vol[mat] = ctx.electron_count(r["dos"], eg, 0.0) / rq.snapshot.volume
+    nes = [per_vol[r.material] * r.snapshot.volume for r in trace]
+    pts = [r.snapshot.n_points for r in trace]
 
-    def served():
-        lat, pending, i = [], {}, 0
-        t0 = time.perf_counter()
-        while i < len(trace) or pending:
-            now = time.perf_counter() - t0
-            while i < len(trace) and trace[i].arrival_s <= now:
-                tk = ctx.submit(trace[i].snapshot, bp, model, eg, api.MIXED, n_electrons=ne[i])
-                pending[tk] = trace[i].arrival_s
-                i += 1
-            for tk in list(pending):
-                if ctx.poll(tk) is not None:
-                    lat.append(time.perf_counter() - t0 - pending.pop(tk))
-                    ctx.release(tk)
-            time.sleep(0.0002)
-        return lat, time.perf_counter() - t0
+    def summary(lat, status, span, n):
+        ok = [l for l, st in zip(lat, status) if st in (0, -4)]
+        return {"requests": n, "p50_ms": 1e3 * pct(lat, 50), "p99_ms": 1e3 * pct(lat, 99), "max_ms": 1e3 * max(lat),
+                "points_per_s": sum(pts[:n]) / span, "wall_s": span,
+                "unreachable_electron_count": int(sum(1 for st in status if st == -4)),
+                "failed": int(sum(1 for st in status if st not in (0, -4))), "completed": len(ok)}
 
-    def plain():
-        lat = []
-        t0 = time.perf_counter()
-        for i, rq in enumerate(trace):
-            wait = rq.arrival_s - (time.perf_counter() - t0)
-            if wait > 0:
-                time.sleep(wait)
-            ctx.predict(rq.snapshot, bp, model, eg, api.FP64_PLAIN, n_electrons=ne[i])
-            lat.append(time.perf_counter() - t0 - rq.arrival_s)
-        return lat, time.perf_counter() - t0
+    out = {"trace": "Poisson arrivals at 200/s (seed 5), Al or Be (p = 1/2) at bulk density, N log-uniform in "
+                    "[32, 2048] atoms, 0.2 A grid spacing; twojmax 10, network 91-400-400-250, 250 energies",
+           "grid_points": int(sum(pts))}
+    lat, st, span = _serve(ctx, api, trace, bp, model, eg, nes)
+    out["served_mixed_200_per_s"] = summary(lat, st, span, len(trace))
+    capacity = len(trace) / span  # requests/s the saturated run sustained
+    rate = 0.7 * capacity
+    if n_util > 0:
+        sub = trace[:n_util]
+        lat, st, span = _serve(ctx, api, sub, bp, model, eg, nes, time_scale=200.0 / rate)
+        out["served_mixed_70pct_util"] = dict(summary(lat, st, span, len(sub)), rate_per_s=rate,
+                                              note="arrival times of the trace scaled to 70% of the saturated "
+                                                   "run's request throughput")
+    if n_fp64 > 0:
+        sub = trace[:n_fp64]
+        ctx.predict(sub[0].snapshot, bp, model, eg, api.FP64_PLAIN, n_electrons=nes[0], raise_on_bracket=False)
+        lat, st, span = _serve(ctx, api, sub, bp, model, eg, nes)
+        out["subset_served_mixed"] = summary(lat, st, span, len(sub))
+        lat, st, span = _plain_fp64(ctx, api, sub, bp, model, eg, nes)
+        out["subset_plain_fp64_single"] = summary(lat, st, span, len(sub))
+        out["subset"] = f"the first {len(sub)} requests of the trace, same arrival times, both arms"
+    model.close()
+    return out
 
-    def summary(lat, span):
-        return {"p50_ms": 1e3 * pct(lat, 50), "p99_ms": 1e3 * pct(lat, 99), "max_ms": 1e3 * max(lat),
-                "points_per_s": sum(pts) / span}
 
-    lm, sm = served()
-    lp, sp = plain()
-    return {"requests": len(trace), "grid_points": int(sum(pts)),
-            "trace": f"Poisson arrivals at 200/s (seed 5), Al or Be bulk at 0.2 A spacing, N log-uniform in "
-                     f"[32, {nmax}]; twojmax 10, MLP 91-400-400-250, 250 energies",
-            "served_mixed": summary(lm, sm), "plain_fp64_single": summary(lp, sp)}
+def _kern(ctx, names):
+    out = {}
+    for k in names:
+        t, n = ctx.profile_get(k)
+        out[k] = {"ms": t, "launches": n}
+    return out
+
+
+def _leg_roofs(kern, roofline, P, pairs, twojmax, dims, n_e, fp32_peak, tensor_peak, hbm, fp64=False):
+    """Rooflines of one call: algorithmic work of the call over the kernels' summed event time."""
+    def ent(name, bound, work, peak, unit):
+        t = kern[name]["ms"] / 1e3
+        scale = 1e12 if unit == "TFLOP/s" else 1e9
+        ach = work / t / scale if t > 0 else 0.0
+        return {"bound": bound, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak if peak else None,
+                "work": work}
+    r = {"k_zb": ent("k_zb", "alu", roofline.zb_flops_per_point(twojmax) * P, fp32_peak, "TFLOP/s"),
+         "k_ui": ent("k_ui", "alu", roofline.ui_flops_per_point(twojmax, 1.0) * pairs, fp32_peak, "TFLOP/s"),
+         "k_mlp": ent("k_mlp", "alu" if fp64 else "tensor", roofline.mlp_flops_per_point(dims) * P, tensor_peak,
+                      "TFLOP/s"),
+         "k_density": ent("k_density", "hbm", roofline.density_bytes(P, n_e, 8 if fp64 else 2, 8 if fp64 else 4), hbm,
+                          "GB/s")}
+    return r
+
+
+def _timed_calls(torch, calls, fn):
+    fn()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(calls):
+        fn()
+    ev1.record()
+    torch.cuda.synchronize()
+    return ev0.elapsed_time(ev1) / calls
+
+
+def _pairs(ctx, snaps, rcut):
+    return int(sum(int(ctx.neighbor_lists(s, rcut, cap=0)[0].sum().item()) for s in snaps))
+
+
+KERNELS = ("k_neighbors", "k_ui", "k_zb", "k_mlp_in", "k_mlp", "k_dos_reduce", "k_sum_rows", "k_fermi", "k_density")
+
+
+def workload_legs(ctx, api, wl, roofline, torch, calls, fp32_peak, fp64_peak, bf16_peak, hbm):
+    """The paper-shaped workloads besides the default one, each through the public path:
+    64 boron clusters in one mala_predict_batch, the Be slab with a stacking fault (streamed in
+    chunks of tiles), and the small Al workload on the plain FP64 path."""
+    out = {}
+    # -- 64 boron clusters (8..96 atoms, 18 A box, 90^3 each), one batched call --
+    try:
+        snaps, bp, mlp, eg, _ = wl.config(3)
+        B = ctx.descriptors_batch(snaps, bp, api.MIXED).double()
+        mlp = wl.with_input_scaling(mlp, B.mean(0).cpu().numpy(), 1.0 / (B.std(0).cpu().numpy() + 1e-12))
+        del B
+        model = api.Model(ctx, mlp)
+        first = ctx.predict_batch(snaps, bp, model, eg, api.MIXED, n_electrons=[0.0] * len(snaps),
+                                  raise_on_bracket=False)
+        nes = [ctx.electron_count(r["dos"], eg, 0.0) for r in first]
+        P = sum(s.n_points for s in snaps)
+        ms = _timed_calls(torch, calls, lambda: ctx.predict_batch(snaps, bp, model, eg, api.MIXED, n_electrons=nes,
+                                                                  raise_on_bracket=False))
+        ctx.profile(True)
+        res = ctx.predict_batch(snaps, bp, model, eg, api.MIXED, n_electrons=nes, raise_on_bracket=False)
+        kern = _kern(ctx, KERNELS)
+        ctx.profile(False)
+        pairs = _pairs(ctx, snaps, bp.rcut)
+        out["boron_clusters"] = {
+            "workload": "64 boron clusters, N ~ U{8..96} (seed 3), compact growth, 18 A periodic box, 90^3 each; "
+                        "twojmax 10, network 91-400-400-11, 11 energies; one mala_predict_batch",
+            "grid_points": P, "ms_per_call": ms, "grid_points_per_s": P / (ms / 1e3), "neighbour_pairs": pairs,
+            "unreachable_electron_count": int(sum(1 for r in res if r["status"] == -4)), "kernels": kern,
+            "rooflines": _leg_roofs(kern, roofline, P, pairs, bp.twojmax, mlp.dims, eg.n_E, fp32_peak, bf16_peak, hbm)}
+        model.close()
+    except Exception as e:  # reported, never costs the bench line
+        out["boron_clusters"] = {"error": f"{type(e).__name__}: {e}"}
+    # -- Be slab with a stacking fault: 16384 atoms, 183 x 317 x 336 grid --
+    try:
+        snaps, bp, mlp, eg, _ = wl.config(4)
+        snap = snaps[0]
+        B = ctx.descriptors(snap, bp, api.MIXED)
+        mean = B.double().mean(0).cpu().numpy()
+        std = B.double().std(0).cpu().numpy()
+        del B
+        mlp = wl.with_input_scaling(mlp, mean, 1.0 / (std + 1e-12))
+        model = api.Model(ctx, mlp)
+        r = ctx.predict(snap, bp, model, eg, api.MIXED, n_electrons=0.0, raise_on_bracket=False)
+        ne = ctx.electron_count(r["dos"], eg, 0.0)
+        P = snap.n_points
+        ms = _timed_calls(torch, calls, lambda: ctx.predict(snap, bp, model, eg, api.MIXED, n_electrons=ne))
+        ctx.profile(True)
+        ctx.predict(snap, bp, model, eg, api.MIXED, n_electrons=ne)
+        kern = _kern(ctx, KERNELS)
+        ctx.profile(False)
+        pairs = _pairs(ctx, [snap], bp.rcut)
+        out["be_slab"] = {
+            "workload": "hcp Be 16x16x16 orthohexagonal (16384 atoms) with one stacking fault, 10 A vacuum, "
+                        f"grid {snap.grid[0]}x{snap.grid[1]}x{snap.grid[2]}; twojmax 10, rcut 4.5 A, "
+                        "network 91-400-400-11, 11 energies; one mala_predict",
+            "grid_points": P, "ms_per_call": ms, "grid_points_per_s": P / (ms / 1e3), "neighbour_pairs": pairs,
+            "kernels": kern,
+            "rooflines": _leg_roofs(kern, roofline, P, pairs, bp.twojmax, mlp.dims, eg.n_E, fp32_peak, bf16_peak, hbm)}
+        model.close()
+    except Exception as e:
+        out["be_slab"] = {"error": f"{type(e).__name__}: {e}"}
+    # -- small Al on the plain FP64 path --
+    try:
+        snaps, bp, mlp, eg, _ = wl.config(1)
+        snap = snaps[0]
+        B = ctx.descriptors(snap, bp, api.FP64_PLAIN)
+        mlp = wl.with_input_scaling(mlp, B.mean(0).cpu().numpy(), 1.0 / (B.std(0).cpu().numpy() + 1e-12))
+        model = api.Model(ctx, mlp)
+        r = ctx.predict(snap, bp, model, eg, api.FP64_PLAIN, n_electrons=0.0, raise_on_bracket=False)
+        ne = ctx.electron_count(r["dos"], eg, 0.0)
+        P = snap.n_points
+        ms = _timed_calls(torch, max(calls, 5), lambda: ctx.predict(snap, bp, model, eg, api.FP64_PLAIN,
+                                                                    n_electrons=ne))
+        ctx.profile(True)
+        ctx.predict(snap, bp, model, eg, api.FP64_PLAIN, n_electrons=ne)
+        kern = _kern(ctx, KERNELS)
+        ctx.profile(False)
+        pairs = _pairs(ctx, [snap], bp.rcut)
+        out["al_small_fp64"] = {
+            "workload": "Al fcc 2x2x2 (32 atoms, jitter N(0,0.1 A)), 18^3 grid, twojmax 6, network 30-100-100-11, "
+                        "11 energies; plain FP64 path (mala_predict, MALA_FP64_PLAIN)",
+            "grid_points": P, "ms_per_call": ms, "grid_points_per_s": P / (ms / 1e3), "neighbour_pairs": pairs,
+            "kernels": kern,
+            "rooflines": _leg_roofs(kern, roofline, P, pairs, bp.twojmax, mlp.dims, eg.n_E, fp64_peak, fp64_peak, hbm,
+                                    fp64=True)}
+        model.close()
+    except Exception as e:
+        out["al_small_fp64"] = {"error": f"{type(e).__name__}: {e}"}
+    return out
 
 
 def forces_leg(ctx, api, roofline, model, snap, bp, eg, ne, calls, peak_tflops):
@@ -483,7 +663,7 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     ctx = api.Context(local)
-    snap, bp, mlp, model, eg, ne = setup_workload(ctx, api, wl, torch)
+    snap, bp, mlp, model, eg, ne = setup_workload(ctx, api, wl, torch, args.grid)
     P = snap.n_points
     pairs = int(ctx.neighbor_lists(snap, bp.rcut, cap=0)[0].sum().item())  # (point, neighbour) pairs
     stream = torch.cuda.current_stream()
@@ -558,7 +738,7 @@ def run_ours(args):
     peaks, peak_src = load_peaks()
     n_sms = int(props.multi_processor_count)
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    fp32_scalar, fp32_packed = ctx.measure_fp32_peak()
+    fp32_scalar, fp32_packed, fp64_peak = ctx.measure_peaks()
     fp32_peak = max(fp32_scalar, fp32_packed)
     fp32 = (fp32_peak, f"measured FMA chains on every SM (scalar {fp32_scalar:.1f}, packed FP32x2 {fp32_packed:.1f} "
                        f"TFLOP/s; the larger); nominal {n_sms} SMs x 128 lanes x 2 flop x {sm_max:.0f} MHz = "
@@ -576,7 +756,19 @@ def run_ours(args):
             derr = descriptor_error(ctx.descriptors(snap, bp, api.MIXED), keep["points"], keep["B"])
         serving = None
         if world == 1 and args.serve_requests > 0:
-            serving = serving_compare(ctx, api, wl, model, bp, eg, args.serve_requests, args.serve_max_atoms)
+            try:
+                smlp = wl.config(5)[2]
+                smlp = wl.MLP(dims=smlp.dims, W=smlp.W, b=smlp.b, leaky_slope=smlp.leaky_slope,
+                              in_shift=mlp.in_shift, in_scale=mlp.in_scale)
+                serving = serving_leg(ctx, api, wl, smlp, bp, eg, args.serve_requests, args.serve_util_requests,
+                                      args.serve_fp64_requests)
+            except Exception as e:  # reported, never costs the bench line
+                serving = {"error": f"{type(e).__name__}: {e}"}
+        workloads = None
+        if world == 1 and args.workload_calls > 0:
+            workloads = workload_legs(ctx, api, wl, roofline, torch, args.workload_calls, fp32_peak, fp64_peak,
+                                      float(peaks.get("bf16_tflops_sustained", 1700.0)),
+                                      float(peaks.get("hbm_gbs", 6800.0)))
         forces = None
         if world == 1 and args.forces_calls > 0:
             forces = forces_leg(ctx, api, roofline, model, snap, bp, eg, ne, args.forces_calls, fp32_peak)
@@ -594,10 +786,12 @@ def run_ours(args):
                            "f64 Fermi level and energy reductions",
                            "l2": "working set larger than L2 (u: 1.5 GB, neighbour records 0.9 GB, LDOS 0.36 GB)",
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-                "roofline": roof, "rooflines": roofs, "fp32_peak_tflops": {"scalar": fp32_scalar,
-                                                                           "packed": fp32_packed, "sms": n_sms},
+                "roofline": roof, "rooflines": roofs,
+                "measured_peaks_tflops": {"fp32_scalar": fp32_scalar, "fp32_packed": fp32_packed, "fp64": fp64_peak,
+                                          "sms": n_sms},
                 "cpu_baseline": cpu, "descriptor_error": derr, "e2e": e2e, "gpu_launches": int(launches),
-                "clocks": clk, "kernels": kernels, "serving": serving, "forces": forces, "ace": ace_res, "gaussian": gauss_res,
+                "clocks": clk, "kernels": kernels, "serving": serving, "workloads": workloads, "forces": forces,
+                "ace": ace_res, "gaussian": gauss_res,
                 "fermi_eV": r["fermi"], "band_energy_eV": r["band_energy"], "entropy_term_eV": r["entropy_term"]}
         print(json.dumps(line), flush=True)
     if dist:

@@ -114,6 +114,8 @@ typedef struct {
     const void* density_dev;     /* device [P] (float for MIXED, double for FP64_PLAIN) */
     double submit_to_done_s;     /* serving latency (mala_poll only) */
     double entropy_term_eV;      /* -tau S_s, Eqs. (electronicentropyDOS), (KSfreeenergy) */
+    double gpu_start_ms;         /* served requests: device-clock interval of the batch that carried it, */
+    double gpu_end_ms;           /* ms since the server started (CUDA events on the slot's stream); else 0 */
 } mala_result;
 
 /* ---- context ------------------------------------------------------------ */
@@ -139,13 +141,14 @@ size_t mala_device_bytes(const mala_ctx* ctx);
 int mala_profile(mala_ctx* ctx, int enable);
 int mala_profile_get(mala_ctx* ctx, const char* kernel, double* total_ms, int64_t* launches);
 
-/* The FP32 CUDA-core peak of the context's device, measured (no counterpart
- * in the paper: it is the denominator of the descriptor kernels' roofline
+/* The CUDA-core peaks of the context's device, measured (no counterpart in
+ * the paper: they are the denominators of the descriptor kernels' roofline
  * fractions).  Independent fused multiply-add chains on every SM, timed by
  * CUDA events on the context's stream, best of three after a warm-up run, an
- * FMA counted as two FLOP: *scalar_tflops with scalar FMAs, *packed_tflops
- * with packed FP32x2 FMAs (either may be NULL).  Synchronous; about 10 ms. */
-int mala_measure_fp32_peak(mala_ctx* ctx, double* scalar_tflops, double* packed_tflops);
+ * FMA counted as two FLOP: FP32 with scalar FMAs, FP32 with packed FP32x2
+ * FMAs, FP64 (any output may be NULL).  Synchronous; about 20 ms. */
+int mala_measure_peaks(mala_ctx* ctx, double* fp32_scalar_tflops, double* fp32_packed_tflops,
+                       double* fp64_tflops);
 
 /* ---- network ---------------------------------------------------------- */
 

@@ -57,7 +57,8 @@ class Result(C.Structure):
     _fields_ = [("status", C.c_int32), ("n_B", C.c_int32), ("n_E", C.c_int32), ("n_points", C.c_int64),
                 ("fermi_eV", C.c_double), ("band_energy_eV", C.c_double), ("electron_count", C.c_double),
                 ("dos", C.POINTER(C.c_double)), ("B_dev", C.c_void_p), ("ldos_dev", C.c_void_p),
-                ("density_dev", C.c_void_p), ("submit_to_done_s", C.c_double), ("entropy_term_eV", C.c_double)]
+                ("density_dev", C.c_void_p), ("submit_to_done_s", C.c_double), ("entropy_term_eV", C.c_double),
+                ("gpu_start_ms", C.c_double), ("gpu_end_ms", C.c_double)]
 
 
 # name -> (restype, argtypes); every function declared in include/mala.h
@@ -69,7 +70,8 @@ PROTOTYPES = {
     "mala_device_bytes": (C.c_size_t, [C.c_void_p]),
     "mala_profile": (C.c_int, [C.c_void_p, C.c_int]),
     "mala_profile_get": (C.c_int, [C.c_void_p, C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
-    "mala_measure_fp32_peak": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "mala_measure_peaks": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                     C.POINTER(C.c_double)]),
     "mala_model_create": (C.c_int, [C.c_void_p, C.POINTER(MLPDesc), C.POINTER(C.c_void_p)]),
     "mala_model_destroy": (None, [C.c_void_p]),
     "mala_neighbor_lists": (C.c_int, [C.c_void_p, C.POINTER(Snapshot), C.c_double, C.c_int32, C.c_void_p,

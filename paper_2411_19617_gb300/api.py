@@ -171,7 +171,8 @@ def _result_dict(r: "_lib.Result", precision: int):
     out = {"status": int(r.status), "fermi": float(r.fermi_eV), "band_energy": float(r.band_energy_eV),
            "electron_count": float(r.electron_count), "entropy_term": float(r.entropy_term_eV),
            "n_points": int(r.n_points), "n_B": int(r.n_B),
-           "n_E": int(r.n_E), "latency_s": float(r.submit_to_done_s)}
+           "n_E": int(r.n_E), "latency_s": float(r.submit_to_done_s),
+           "gpu_interval_ms": (float(r.gpu_start_ms), float(r.gpu_end_ms))}
     out["dos"] = np.ctypeslib.as_array(r.dos, shape=(r.n_E,)).copy() if r.dos else None
     fdt = torch.float32 if precision == MIXED else torch.float64
     ldt = torch.bfloat16 if precision == MIXED else torch.float64
@@ -216,11 +217,11 @@ class Context:
         check(lib().mala_profile_get(self.h, kernel.encode(), C.byref(ms), C.byref(n)), "mala_profile_get")
         return float(ms.value), int(n.value)
 
-    def measure_fp32_peak(self):
-        """(scalar, packed FP32x2) FMA throughput of the device in TFLOP/s, measured."""
-        a, b = C.c_double(0.0), C.c_double(0.0)
-        check(lib().mala_measure_fp32_peak(self.h, C.byref(a), C.byref(b)), "mala_measure_fp32_peak")
-        return float(a.value), float(b.value)
+    def measure_peaks(self):
+        """(FP32 scalar, FP32 packed FP32x2, FP64) FMA throughput of the device in TFLOP/s, measured."""
+        a, b, d = C.c_double(0.0), C.c_double(0.0), C.c_double(0.0)
+        check(lib().mala_measure_peaks(self.h, C.byref(a), C.byref(b), C.byref(d)), "mala_measure_peaks")
+        return float(a.value), float(b.value), float(d.value)
 
     # ---- one step at a time --------------------------------------------
 
@@ -460,6 +461,11 @@ class Context:
             return None
         check(rc, "mala_poll")
         return _result_dict(r, precision)
+
+    def poll_status(self, ticket: int) -> int:
+        """The request's status without raising: 1 (MALA_PENDING) while queued or running,
+        0 when done, a negative error code when it failed."""
+        return int(lib().mala_poll(self.h, C.c_uint64(ticket), None))
 
     def wait(self, ticket: int, timeout_s: float = 60.0, precision: int = MIXED):
         r = _lib.Result()

@@ -504,12 +504,27 @@ constexpr long long kDensWaitCycles = 2000000000LL;        // about one second
 struct DensPlan {
     int rows;   // rows per tile
     int G;      // lanes per row (power of two <= 32)
+    int wpl;    // BF16 pairs per lane in the register path (0: shared-memory weights)
 };
 
+constexpr int kDensMaxWpl = 16;  // weights held in registers: at most 16 BF16 pairs per lane
+
+// BF16 rows of even length: a lane takes every G-th 4-byte pair of its row with
+// its weights in registers; otherwise lanes take every G-th element, weights in
+// shared memory.
 inline DensPlan dens_plan(int nE, int elem_bytes) {
     DensPlan d;
     int G = 1;
-    while (G < 32 && G * 8 < nE) G *= 2;  // about 8 or more energies per lane
+    d.wpl = 0;
+    if (elem_bytes == 2 && (nE & 1) == 0) {
+        const int nw = nE / 2;
+        while (G < 32 && (nw + G - 1) / G > kDensMaxWpl) G *= 2;
+        if ((nw + G - 1) / G <= kDensMaxWpl) d.wpl = (nw + G - 1) / G;
+    }
+    if (!d.wpl) {
+        G = 1;
+        while (G < 32 && G * 8 < nE) G *= 2;  // about 8 or more energies per lane
+    }
     const int rb = nE * elem_bytes;
     int rows = std::max(1, kDensTileBytes / rb);
     const int pass = kDensThreads / G;     // rows one pass over the CTA's threads covers
@@ -560,7 +575,7 @@ __device__ __forceinline__ void dens_range(const unsigned char* L, int64_t P, in
 // TL: LDOS element (BF16 or FP64), TW: arithmetic and output type (float or double)
 template <class TL, class TW>
 __global__ void __launch_bounds__(kDensThreads) k_density(const TL* __restrict__ Lg, int64_t P, int nE, int R, int G,
-                                                          const TW* __restrict__ w0, TW* __restrict__ n,
+                                                          int wpl, const TW* __restrict__ w0, TW* __restrict__ n,
                                                           double* __restrict__ part, int* __restrict__ err) {
     extern __shared__ __align__(128) unsigned char dsm[];
     unsigned char* stage = dsm;
@@ -574,6 +589,18 @@ __global__ void __launch_bounds__(kDensThreads) k_density(const TL* __restrict__
     const int tid = threadIdx.x, lane = tid & 31;
     const int g = tid & (G - 1), grp = tid / G, ngrp = kDensThreads / G;
     for (int i = tid; i < nE; i += kDensThreads) sw[i] = w0[i];
+    // register path: this lane's weights, pairs g, g + G, ... of the row
+    float wr[2 * kDensMaxWpl];
+    const bool regs = sizeof(TL) == 2 && wpl > 0 && (reinterpret_cast<uintptr_t>(Lg) & 3) == 0;
+    if (regs) {
+#pragma unroll
+        for (int k = 0; k < kDensMaxWpl; ++k) {
+            const int q = g + k * G;
+            const bool in = k < wpl && 2 * q < nE;
+            wr[2 * k] = in ? (float)w0[2 * q] : 0.f;
+            wr[2 * k + 1] = in ? (float)w0[2 * q + 1] : 0.f;
+        }
+    }
     if (tid == 0) {
         for (int s2 = 0; s2 < kDensStages; ++s2)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"((uint32_t)__cvta_generic_to_shared(&bars[s2])));
@@ -623,11 +650,31 @@ __global__ void __launch_bounds__(kDensThreads) k_density(const TL* __restrict__
             TW s = TW(0);
             if (r < nr) {
                 const unsigned char* row = base + (size_t)r * rb;
-                for (int c = g; c < nE; c += G) {
-                    TW v;
-                    if constexpr (sizeof(TL) == 2) v = dens_val<TL>(row + 2 * c);
-                    else v = *reinterpret_cast<const double*>(row + 8 * c);
-                    s = fma(v, sw[c], s);
+                if (regs) {
+                    // all of the lane's pairs loaded first (independent 4-byte loads), then two FMA chains
+                    const uint32_t* row32 = reinterpret_cast<const uint32_t*>(row);
+                    const int nw = nE >> 1;
+                    uint32_t v[kDensMaxWpl];
+#pragma unroll
+                    for (int k = 0; k < kDensMaxWpl; ++k) {
+                        const int q = g + k * G;
+                        v[k] = (k < wpl && q < nw) ? row32[q] : 0u;
+                    }
+                    float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+                    for (int k = 0; k < kDensMaxWpl; ++k) {
+                        const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&v[k]));
+                        s0 = fmaf(f.x, wr[2 * k], s0);
+                        s1 = fmaf(f.y, wr[2 * k + 1], s1);
+                    }
+                    s = (TW)(s0 + s1);
+                } else {
+                    for (int c = g; c < nE; c += G) {
+                        TW v;
+                        if constexpr (sizeof(TL) == 2) v = dens_val<TL>(row + 2 * c);
+                        else v = *reinterpret_cast<const double*>(row + 8 * c);
+                        s = fma(v, sw[c], s);
+                    }
                 }
             }
             for (int o = G >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
@@ -672,7 +719,7 @@ void launch_density(const TL* L, int64_t P, int nE, const TW* w0, TW* n, double*
     const DensPlan d = dens_plan(nE, (int)sizeof(TL));
     const size_t smem = dens_smem_bytes(nE, (int)sizeof(TW));
     cudaFuncSetAttribute(k_density<TL, TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_density<TL, TW><<<grid, kDensThreads, smem, st>>>(L, P, nE, d.rows, d.G, w0, n, part, err);
+    k_density<TL, TW><<<grid, kDensThreads, smem, st>>>(L, P, nE, d.rows, d.G, d.wpl, w0, n, part, err);
 }
 
 // CTAs of the density pass: one per SM at most, never more than the tiles

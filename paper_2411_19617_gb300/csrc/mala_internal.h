@@ -102,6 +102,11 @@ struct WsNeeds {
             }
         v.emplace_back(&b, n);
     }
+    size_t total() const {
+        size_t t = 0;
+        for (auto& x : v) t += x.second;
+        return t;
+    }
     size_t growth() const {
         size_t g = 0;
         for (auto& x : v) {

@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -183,6 +184,9 @@ struct Server {
     uint64_t next_ticket = 1;
     bool stop = false;
     int running = 0;
+    std::vector<char> busy;          // per slot: a batch is running on it
+    size_t out_live = 0;             // bytes of batch outputs allocated and not yet released
+    cudaEvent_t t0 = nullptr;        // device-clock origin of the batches' intervals
 };
 
 // requests that may share one batch: same network, precision, bispectrum setting and n_E
@@ -199,9 +203,28 @@ constexpr int kServeBatchMax = 16;                // requests per batch
 constexpr int64_t kServeBatchPoints = 8000000;    // grid points per batch
 constexpr double kServeBypassS = 0.05;            // how long later requests may pass a queue head that does not fit
 
+// the path's workspaces of a serving slot
+static std::array<DevBuf*, 17> slot_buffers(Ctx* s) {
+    return {&s->ws_atoms, &s->ws_batch, &s->ws_bins, &s->ws_nbr_ab, &s->ws_nbr_c, &s->ws_nbr_cnt, &s->ws_u,
+            &s->ws_misc, &s->ws_B, &s->ws_ldos, &s->ws_dens, &s->ws_dos, &s->ws_tile_dos, &s->ws_mlp64,
+            &s->ws_red, &s->ws_w, &s->ws_mlp_in};
+}
+
+// an idle slot's workspaces, returned to the budget
+static void release_workspaces(Ctx* s) {
+    for (DevBuf* b : slot_buffers(s)) b->release();
+}
+
+static size_t workspace_bytes(Ctx* s) {
+    size_t t = 0;
+    for (DevBuf* b : slot_buffers(s)) t += b->ptr ? b->bytes : 0;
+    return t;
+}
+
 // Device workspace a batch would add to a slot: the growth of the slot's
-// buffers (descriptor chunk, network input, integrals) beyond what they hold.
-static size_t batch_ws_growth(Ctx* slot, const std::vector<Request*>& b) {
+// buffers (descriptor chunk, network input, integrals) beyond what they hold
+// (or, with total, all of it).
+static size_t batch_ws_growth(Ctx* slot, const std::vector<Request*>& b, bool total = false) {
     const int n = (int)b.size();
     std::vector<const mala_snapshot*> snaps(n);
     int64_t P = 0;
@@ -213,10 +236,10 @@ static size_t batch_ws_growth(Ctx* slot, const std::vector<Request*>& b) {
     descriptors_ws_needs(slot, n, snaps.data(), &b[0]->bp, b[0]->prec, w);
     mlp_ws_needs(slot, b[0]->model, P, n == 1, b[0]->prec, w);
     for (const Request* r : b) integrate_ws_needs(slot, r->P, r->eg.n_E, r->prec, w);
-    return w.growth();
+    return total ? w.total() : w.growth();
 }
 
-static void worker_loop(Server* sv, Ctx* slot) {
+static void worker_loop(Server* sv, Ctx* slot, int idx) {
     cudaSetDevice(slot->device);
     for (;;) {
         std::vector<Request*> batch;
@@ -249,14 +272,42 @@ static void worker_loop(Server* sv, Ctx* slot) {
                     const size_t have = batch_bytes + ws_grow, need = out + grow;
                     bool fits = need <= have || budget_claim(root, need - have);
                     if (fits && need < have) root->used -= have - need;
+                    if (!fits && first && (sv->running == 0 || it == sv->queue.begin())) {
+                        // workspaces that idle slots keep from earlier batches may be what blocks the
+                        // head: release them (the slots regrow them on their next batch) and try again
+                        const double age = std::chrono::duration<double>(now - q->t_submit).count();
+                        if (sv->running == 0 || age > kServeBypassS) {
+                            for (size_t j = 0; j < sv->slots.size(); ++j)
+                                if ((int)j != idx && !sv->busy[j]) release_workspaces(sv->slots[j].get());
+                            const size_t grow2 = batch_ws_growth(slot, batch);
+                            fits = budget_claim(root, q->out_bytes + grow2);
+                            if (fits) {
+                                batch_bytes = q->out_bytes;
+                                ws_grow = grow2;
+                                pts += q->P;
+                                it = sv->queue.erase(it);
+                                continue;
+                            }
+                        }
+                    }
                     if (!fits) {
                         batch.pop_back();
                         if (first) {
                             if (sv->running == 0) {
-                                // nothing else will free memory: run it alone and report the budget error
-                                batch.push_back(q);
-                                it = sv->queue.erase(it);
-                                over_budget = true;
+                                // Nothing runs.  Outputs still held by finished requests come back when
+                                // they are released and workspaces when slots are trimmed; what remains
+                                // is memory the server cannot free.  A request that cannot fit even
+                                // then is run alone to report the budget error; otherwise it waits.
+                                size_t ws = 0;
+                                for (auto& sl : sv->slots) ws += workspace_bytes(sl.get());
+                                const size_t floor = root->used - std::min<size_t>(root->used, sv->out_live + ws);
+                                std::vector<Request*> alone{q};
+                                const size_t ever = q->out_bytes + batch_ws_growth(slot, alone, true);
+                                if (root->budget && floor + ever > root->budget) {
+                                    batch.push_back(q);
+                                    it = sv->queue.erase(it);
+                                    over_budget = true;
+                                }
                                 break;
                             }
                             const double age = std::chrono::duration<double>(now - q->t_submit).count();
@@ -277,8 +328,10 @@ static void worker_loop(Server* sv, Ctx* slot) {
             }
             for (Request* r : batch) r->state = 1;
             ++sv->running;
+            sv->busy[idx] = 1;
             slot->held = ws_grow;
             if (over_budget) batch_bytes = 0;  // nothing claimed or allocated: reported below
+            sv->out_live += batch_bytes;
         }
         int rc = MALA_OK;
         const int n = (int)batch.size();
@@ -324,8 +377,24 @@ static void worker_loop(Server* sv, Ctx* slot) {
                 res[i] = &r->res;
             }
             std::lock_guard<std::mutex> lk(slot->mu);
+            cudaEvent_t ea = nullptr, eb = nullptr;
+            const bool timed = sv->t0 && cudaEventCreate(&ea) == cudaSuccess && cudaEventCreate(&eb) == cudaSuccess;
+            if (timed) cudaEventRecord(ea, slot->stream);
             rc = run_path_batch(slot, n, snaps.data(), &r0->bp, r0->model, egs.data(), r0->prec, B, L, D, S, dh.data(),
                                 res.data(), slot->stream);
+            if (timed) {
+                cudaEventRecord(eb, slot->stream);
+                float a = 0.f, b = 0.f;
+                if (cudaEventSynchronize(eb) == cudaSuccess && cudaEventElapsedTime(&a, sv->t0, ea) == cudaSuccess &&
+                    cudaEventElapsedTime(&b, sv->t0, eb) == cudaSuccess)
+                    for (mala_result* rr : res) {
+                        rr->gpu_start_ms = a;
+                        rr->gpu_end_ms = b;
+                    }
+                cudaGetLastError();
+            }
+            if (ea) cudaEventDestroy(ea);
+            if (eb) cudaEventDestroy(eb);
         }
         // workspace bytes set aside for this batch and not drawn by the slot's buffers go back
         sv->root->used -= slot->held;
@@ -347,6 +416,7 @@ static void worker_loop(Server* sv, Ctx* slot) {
                 r->state = 2;
             }
             --sv->running;
+            sv->busy[idx] = 0;
         }
         sv->cv_done.notify_all();
         sv->cv_work.notify_all();
@@ -374,7 +444,10 @@ static int server_start(Ctx* c) {
         }
         sv->slots.push_back(std::move(s));
     }
-    for (auto& s : sv->slots) sv->workers.emplace_back(worker_loop, sv, s.get());
+    sv->busy.assign(sv->slots.size(), 0);
+    if (cudaEventCreate(&sv->t0) == cudaSuccess) cudaEventRecord(sv->t0, c->stream);
+    else sv->t0 = nullptr;
+    for (size_t i = 0; i < sv->slots.size(); ++i) sv->workers.emplace_back(worker_loop, sv, sv->slots[i].get(), (int)i);
     c->server = sv;
     return MALA_OK;
 }
@@ -397,6 +470,7 @@ void server_stop(Ctx* c) {
         c->used -= ob->bytes;
         delete ob;
     }
+    if (sv->t0) cudaEventDestroy(sv->t0);
     for (auto& s : sv->slots) {
         cudaStreamSynchronize(s->stream);
         cudaStreamDestroy(s->stream);
@@ -715,6 +789,7 @@ int mala_release(mala_ctx* c, uint64_t ticket) {
         if (r->out && --r->out->refs == 0) {
             if (r->out->ptr) cudaFree(r->out->ptr);
             c->used -= r->out->bytes;
+            sv->out_live -= r->out->bytes;
             delete r->out;
         }
         r->out = nullptr;

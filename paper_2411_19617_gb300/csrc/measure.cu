@@ -1,11 +1,13 @@
-// measure.cu -- the FP32 CUDA-core peak that the descriptor kernels' roofline
-// fractions are taken against, measured on the device the context runs on.
+// measure.cu -- the FP32 and FP64 CUDA-core peaks that the descriptor
+// kernels' roofline fractions are taken against, measured on the device the
+// context runs on.
 //
 // Every thread runs independent chains of fused multiply-adds (eight scalar
-// chains, or eight chains of packed FP32x2 FMAs): enough independent work per
-// scheduler to hide the pipe latency, nothing else in the loop.  The grid is a
-// multiple of the SM count.  Time by CUDA events on the context's stream; the
-// best of a few repetitions is returned, in FLOP/s with an FMA counted as two.
+// FP32 chains, eight chains of packed FP32x2 FMAs, or eight FP64 chains):
+// enough independent work per scheduler to hide the pipe latency, nothing else
+// in the loop.  The grid is a multiple of the SM count.  Time by CUDA events on
+// the context's stream; the best of a few repetitions is returned, in FLOP/s
+// with an FMA counted as two.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -49,12 +51,28 @@ __global__ void __launch_bounds__(kFmaThreads) k_fma_packed(float a, float b, fl
     if (s == 1234.5f) sink[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
+constexpr int kFmaIters64 = 1024;  // FP64 runs at a small fraction of the FP32 rate
+
+__global__ void __launch_bounds__(kFmaThreads) k_fma_f64(double a, double b, double* __restrict__ sink) {
+    double x[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) x[i] = b * (double)(threadIdx.x + i);
+    for (int it = 0; it < kFmaIters64; ++it) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) x[i] = fma(x[i], a, b);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) s += x[i];
+    if (s == 1234.5) sink[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
 }  // namespace
 
-int measure_fp32_peak(Ctx* c, double* scalar_tflops, double* packed_tflops) {
+int measure_peaks(Ctx* c, double* scalar_tflops, double* packed_tflops, double* fp64_tflops) {
     const int blocks = std::max(1, c->num_sms) * kFmaBlocksPerSm;
     const cudaStream_t st = c->stream;
-    MALA_TRY(c->ws_misc.reserve(c, sizeof(float) * (size_t)blocks * kFmaThreads));
+    MALA_TRY(c->ws_misc.reserve(c, sizeof(double) * (size_t)blocks * kFmaThreads));
     float* sink = c->ws_misc.as<float>();
     cudaEvent_t e0, e1;
     MALA_CUDA_TRY(cudaEventCreate(&e0));
@@ -62,15 +80,16 @@ int measure_fp32_peak(Ctx* c, double* scalar_tflops, double* packed_tflops) {
         cudaEventDestroy(e0);
         return fail(MALA_ERR_CUDA, "cudaEventCreate failed");
     }
-    double best[2] = {0.0, 0.0};
+    double best[3] = {0.0, 0.0, 0.0};
     int rc = MALA_OK;
-    for (int kind = 0; kind < 2 && rc == MALA_OK; ++kind) {
-        const double fma_per_thread = (double)kFmaIters * 8.0 * (kind ? 2.0 : 1.0);
+    for (int kind = 0; kind < 3 && rc == MALA_OK; ++kind) {
+        const double fma_per_thread = kind == 2 ? (double)kFmaIters64 * 8.0 : (double)kFmaIters * 8.0 * (kind ? 2.0 : 1.0);
         const double flop = 2.0 * fma_per_thread * (double)blocks * kFmaThreads;
         for (int rep = 0; rep < 4; ++rep) {  // the first repetition warms clocks and caches
             cudaEventRecord(e0, st);
             if (kind == 0) k_fma_scalar<<<blocks, kFmaThreads, 0, st>>>(0.999999f, 1e-7f, sink);
-            else k_fma_packed<<<blocks, kFmaThreads, 0, st>>>(0.999999f, 1e-7f, sink);
+            else if (kind == 1) k_fma_packed<<<blocks, kFmaThreads, 0, st>>>(0.999999f, 1e-7f, sink);
+            else k_fma_f64<<<blocks, kFmaThreads, 0, st>>>(0.999999999, 1e-12, reinterpret_cast<double*>(sink));
             cudaEventRecord(e1, st);
             cudaError_t e = cudaEventSynchronize(e1);
             if (e == cudaSuccess) e = cudaGetLastError();
@@ -87,6 +106,7 @@ int measure_fp32_peak(Ctx* c, double* scalar_tflops, double* packed_tflops) {
     cudaEventDestroy(e1);
     if (scalar_tflops) *scalar_tflops = best[0];
     if (packed_tflops) *packed_tflops = best[1];
+    if (fp64_tflops) *fp64_tflops = best[2];
     return rc;
 }
 
@@ -96,9 +116,10 @@ using namespace mala;
 
 struct mala_ctx : public mala::Ctx {};
 
-extern "C" int mala_measure_fp32_peak(mala_ctx* c, double* scalar_tflops, double* packed_tflops) {
+extern "C" int mala_measure_peaks(mala_ctx* c, double* fp32_scalar_tflops, double* fp32_packed_tflops,
+                                  double* fp64_tflops) {
     if (!c) return fail(MALA_ERR_INVALID_ARG, "context is NULL");
     std::lock_guard<std::mutex> lk(c->mu);
     MALA_DEVICE_SCOPE(c->device);
-    return measure_fp32_peak(c, scalar_tflops, packed_tflops);
+    return measure_peaks(c, fp32_scalar_tflops, fp32_packed_tflops, fp64_tflops);
 }

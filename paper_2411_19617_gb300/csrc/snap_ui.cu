@@ -18,6 +18,10 @@
 // enough that their sums and Kahan compensations stay in registers; each
 // segment loops over the lane's neighbours, rebuilding its column from the
 // seed, and accumulates c_k * coefficient with compensated (Kahan) summation.
+// FP32 takes the neighbours two at a time: both column chains run packed in
+// FP32x2 pairs (one FFMA2 does a step of both), and the two weighted terms of
+// an element are added in one rounding before the compensated add, which
+// halves the compensation work per neighbour.
 // The normalisation N and the self term are applied once at the end.  Output:
 // the half set of u (rows ma < J/2, plus the middle row's columns <= J/2 for
 // even J).  FP64: [tile][element][lane] (re, im).  FP32: tiles in pairs,
@@ -120,6 +124,31 @@ __device__ __forceinline__ void mul_linear(T (&vr)[kTJMax + 1], T (&vi)[kTJMax +
     }
 }
 
+// the same for a pair of coefficient vectors (two neighbours) in FP32x2:
+// v <- (alpha xi + beta eta) v per neighbour, nali = -ali and nbei = -bei
+__device__ __forceinline__ void mul_linear2(float2 (&vr)[kTJMax + 1], float2 (&vi)[kTJMax + 1], int n, float2 alr,
+                                            float2 ali, float2 nali, float2 ber, float2 bei, float2 nbei) {
+#pragma unroll
+    for (int i = kTJMax; i >= 0; --i) {
+        if (i <= n) {
+            float2 nr, ni;
+            if (i < n) {
+                nr = __ffma2_rn(nali, vi[i], __fmul2_rn(alr, vr[i]));
+                ni = __ffma2_rn(ali, vr[i], __fmul2_rn(alr, vi[i]));
+                if (i > 0) {
+                    nr = __ffma2_rn(nbei, vi[i - 1], __ffma2_rn(ber, vr[i - 1], nr));
+                    ni = __ffma2_rn(bei, vr[i - 1], __ffma2_rn(ber, vi[i - 1], ni));
+                }
+            } else {
+                nr = __ffma2_rn(nbei, vi[i - 1], __fmul2_rn(ber, vr[i - 1]));
+                ni = __ffma2_rn(bei, vr[i - 1], __fmul2_rn(ber, vi[i - 1]));
+            }
+            vr[i] = nr;
+            vi[i] = ni;
+        }
+    }
+}
+
 template <class T>
 __device__ __forceinline__ void kahan_add(T& s, T& c, T x) {
     const T y = x - c;
@@ -164,6 +193,52 @@ __device__ __forceinline__ void ui_segment(const typename AB4<T>::type* __restri
 #pragma unroll
     for (int e = 0; e < NE; ++e) sr[e] = si[e] = cr[e] = ci[e] = T(0);
 
+    if constexpr (sizeof(T) == 4) {
+        // FP32: two neighbours per step; their column chains run packed in FP32x2
+        // pairs, and the two weighted terms of an element are added (one rounding)
+        // before the compensated add to the sum
+        float4 abn0, abn1;
+        float cn0, cn1;
+        load_nbr<float>(ab_t, cw_t, 0, cnt, lane, abn0, cn0);
+        load_nbr<float>(ab_t, cw_t, 1, cnt, lane, abn1, cn1);
+        for (int k = 0; k < kwarp; k += 2) {
+            const float4 a0 = abn0, a1 = abn1;
+            const float2 c2 = make_float2(cn0, cn1);
+            load_nbr<float>(ab_t, cw_t, k + 2, cnt, lane, abn0, cn0);  // prefetch the next pair
+            load_nbr<float>(ab_t, cw_t, k + 3, cnt, lane, abn1, cn1);
+            // linear forms per neighbour: L1 = conj(a) xi - conj(b) eta, L2 = b xi + a eta
+            const float2 l1ar = make_float2(a0.x, a1.x), l1ai = make_float2(-a0.y, -a1.y);
+            const float2 l1br = make_float2(-a0.z, -a1.z), l1bi = make_float2(a0.w, a1.w);
+            const float2 l2ar = make_float2(a0.z, a1.z), l2ai = make_float2(a0.w, a1.w);
+            const float2 l2br = make_float2(a0.x, a1.x), l2bi = make_float2(a0.y, a1.y);
+            const float2 nl1ai = make_float2(a0.y, a1.y), nl1bi = make_float2(-a0.w, -a1.w);
+            const float2 nl2ai = make_float2(-a0.w, -a1.w), nl2bi = make_float2(-a0.y, -a1.y);
+            float2 vr[kTJMax + 1], vi[kTJMax + 1];
+            vr[0] = make_float2(1.f, 1.f);
+            vi[0] = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int st = 0; st < MB; ++st) {
+                mul_linear2(vr, vi, 2 * st + 1, l1ar, l1ai, nl1ai, l1br, l1bi, nl1bi);
+                mul_linear2(vr, vi, 2 * st + 2, l2ar, l2ai, nl2ai, l2br, l2bi, nl2bi);
+            }
+#pragma unroll
+            for (int J = 2 * MB; J <= L1; ++J) {
+                if (J > 2 * MB) mul_linear2(vr, vi, J, l1ar, l1ai, nl1ai, l1br, l1bi, nl1bi);
+                if (J >= L0) {
+                    const int off = seg_offset(MB, L0, J);
+                    const int ne = seg_level_elems(MB, J);
+#pragma unroll
+                    for (int i = 0; i < kTJMax + 1; ++i) {
+                        if (i < ne) {
+                            const float2 xr = __fmul2_rn(c2, vr[i]), xi = __fmul2_rn(c2, vi[i]);
+                            kahan_add(sr[off + i], cr[off + i], xr.x + xr.y);
+                            kahan_add(si[off + i], ci[off + i], xi.x + xi.y);
+                        }
+                    }
+                }
+            }
+        }
+    } else {
     typename AB4<T>::type abn;
     T cn;
     load_nbr<T>(ab_t, cw_t, 0, cnt, lane, abn, cn);
@@ -198,6 +273,7 @@ __device__ __forceinline__ void ui_segment(const typename AB4<T>::type* __restri
                 }
             }
         }
+    }
     }
     if (!store) return;
     // normalise, map to the half set, add the self term, store

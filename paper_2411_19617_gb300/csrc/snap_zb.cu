@@ -161,6 +161,11 @@ int upload_cg_tables(Ctx* c) {
                                 // coefficients of a term flip together; keep m1a <= m2a, count
                                 // m1a < m2a twice (bit 8)
                                 if (j1 == j2 && m1a > m2a) continue;
+                                // a unit whose row coefficient C(j1 m1a j2 m2a | j ma) vanishes adds
+                                // nothing: Racah's sum has accidental zeros (e.g. <1 0 1 0 | 1 0>),
+                                // ~1e-16 in floating point against >= 1.8e-2 for every true nonzero
+                                // coefficient up to twojmax 10
+                                if (std::fabs(tab[cg_offset(j1, j2, j) + ma * (j1 + 1) + m1a]) < 1e-10) continue;
                                 const int twice = (j1 == j2 && m1a < m2a) ? 1 : 0;
                                 units.push_back((unsigned short)(ma | (m1a << 4) | (twice << 8)));
                             }
