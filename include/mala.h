@@ -141,6 +141,23 @@ size_t mala_device_bytes(const mala_ctx* ctx);
 int mala_profile(mala_ctx* ctx, int enable);
 int mala_profile_get(mala_ctx* ctx, const char* kernel, double* total_ms, int64_t* launches);
 
+/* Tile-shape tuning (no counterpart in the paper, whose descriptor code runs
+ * with fixed shapes).  mode 1, the default: the first MALA_MIXED descriptor
+ * pass for a new key (twojmax, neighbour capacity in bands of 8, grid points
+ * in powers of two) times every compiled variant of compute_ui (segment length
+ * x warps per CTA) and of compute_zi/bi (warps per CTA) on that pass's own
+ * data and keeps the fastest for the context and its serving slots; later
+ * passes with the key use it.  mode 0: the default variants.  mode 2: the
+ * variants ui_variant and zb_variant for every pass (testing).  Every variant
+ * adds the same terms in the same order, so all give the same bits.  Modes 0
+ * and 2 forget earlier choices. */
+int mala_set_tuning(mala_ctx* ctx, int mode, int ui_variant, int zb_variant);
+/* Numbers of compiled compute_ui and compute_zi/bi variants (host only). */
+int mala_tuning_variants(int32_t* n_ui, int32_t* n_zb);
+/* The choices made so far, one line per key with every variant's time, as
+ * NUL-terminated text in buf (truncated to len bytes). */
+int mala_tuning_report(mala_ctx* ctx, char* buf, size_t len);
+
 /* The CUDA-core peaks of the context's device, measured (no counterpart in
  * the paper: they are the denominators of the descriptor kernels' roofline
  * fractions).  Independent fused multiply-add chains on every SM, timed by

@@ -72,6 +72,9 @@ PROTOTYPES = {
     "mala_profile_get": (C.c_int, [C.c_void_p, C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "mala_measure_peaks": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                      C.POINTER(C.c_double)]),
+    "mala_set_tuning": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int]),
+    "mala_tuning_variants": (C.c_int, [C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "mala_tuning_report": (C.c_int, [C.c_void_p, C.c_char_p, C.c_size_t]),
     "mala_model_create": (C.c_int, [C.c_void_p, C.POINTER(MLPDesc), C.POINTER(C.c_void_p)]),
     "mala_model_destroy": (None, [C.c_void_p]),
     "mala_neighbor_lists": (C.c_int, [C.c_void_p, C.POINTER(Snapshot), C.c_double, C.c_int32, C.c_void_p,

@@ -29,6 +29,13 @@ def _stream_ptr(stream=None):
     return C.c_void_p(s.cuda_stream)
 
 
+def tuning_variants():
+    """(compute_ui variants, compute_zi/bi variants) compiled into the library."""
+    a, b = C.c_int32(0), C.c_int32(0)
+    check(lib().mala_tuning_variants(C.byref(a), C.byref(b)), "mala_tuning_variants")
+    return int(a.value), int(b.value)
+
+
 def n_descriptors(twojmax: int) -> int:
     return (twojmax + 2) * (twojmax + 3) * (twojmax + 4) // 24
 
@@ -216,6 +223,15 @@ class Context:
         ms, n = C.c_double(0.0), C.c_int64(0)
         check(lib().mala_profile_get(self.h, kernel.encode(), C.byref(ms), C.byref(n)), "mala_profile_get")
         return float(ms.value), int(n.value)
+
+    def set_tuning(self, mode: int, ui_variant: int = 0, zb_variant: int = 0):
+        """0: default kernel shapes, 1: autotune per key (default), 2: force the given variants."""
+        check(lib().mala_set_tuning(self.h, int(mode), int(ui_variant), int(zb_variant)), "mala_set_tuning")
+
+    def tuning_report(self) -> str:
+        buf = C.create_string_buffer(8192)
+        check(lib().mala_tuning_report(self.h, buf, len(buf)), "mala_tuning_report")
+        return buf.value.decode()
 
     def measure_peaks(self):
         """(FP32 scalar, FP32 packed FP32x2, FP64) FMA throughput of the device in TFLOP/s, measured."""

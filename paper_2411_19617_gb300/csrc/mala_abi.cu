@@ -121,6 +121,40 @@ static cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s
 
 // ---- descriptor step ------------------------------------------------------
 
+// ---- tile-shape tuning ---------------------------------------------------
+
+// (twojmax, neighbour capacity in bands of 8, grid points in powers of two)
+static uint64_t tune_key(int tj, int kmax, int64_t points) {
+    int lg = 0;
+    while (lg < 62 && (int64_t(1) << (lg + 1)) <= points) ++lg;
+    return (uint64_t)tj | ((uint64_t)((kmax + 7) / 8) << 8) | ((uint64_t)lg << 24);
+}
+
+// one timed launch of each variant (CUDA events on the stream; the pass's
+// first kernel launches are already queued before it)
+template <class F>
+static int time_variants(int n, float* ms, cudaStream_t st, F&& launch) {
+    cudaEvent_t e[5];
+    for (int i = 0; i <= n; ++i) MALA_CUDA_TRY(cudaEventCreate(&e[i]));
+    cudaEventRecord(e[0], st);
+    for (int v = 0; v < n; ++v) {
+        launch(v);
+        cudaEventRecord(e[v + 1], st);
+    }
+    cudaError_t err = cudaEventSynchronize(e[n]);
+    for (int v = 0; v < n && err == cudaSuccess; ++v) err = cudaEventElapsedTime(&ms[v], e[v], e[v + 1]);
+    for (int i = 0; i <= n; ++i) cudaEventDestroy(e[i]);
+    if (err != cudaSuccess) return fail(MALA_ERR_CUDA, "variant timing failed: %s", cudaGetErrorString(err));
+    return MALA_OK;
+}
+
+static int best_variant(const float* ms, int n) {
+    int b = 0;
+    for (int v = 1; v < n; ++v)
+        if (ms[v] < ms[b]) b = v;
+    return b;
+}
+
 // Tiles per chunk of the descriptor step (u half set, neighbour records and
 // counts of a chunk stay below 4 GB) and the workspace sizes of a chunk.
 struct DescSizes {
@@ -231,6 +265,27 @@ static int run_descriptors(Ctx* c, int nsnap, const mala_snapshot* snaps, const 
             nb.gauss_inv2s2 = dbg->gauss_inv2s2;
         }
         for (int i = 0; i < nsnap; ++i) MALA_CUDA_TRY(cudaMemsetAsync(hb[i].sd.maxcnt, 0, sizeof(int), st));
+        // the kernel shapes of this pass: tuned per key, the defaults, or forced
+        int v_ui = 0, v_zb = 0;
+        bool tune_now = false;
+        uint64_t key = 0;
+        Ctx* rt = c->root();
+        if (sizeof(T) == 4 && !gauss_mode && B) {
+            std::lock_guard<std::mutex> lk(rt->tune_mu);
+            if (rt->tune_mode == 2) {
+                v_ui = rt->force_ui;
+                v_zb = rt->force_zb;
+            } else if (rt->tune_mode == 1) {
+                key = tune_key(tj, kmax, rows);
+                auto it = rt->tune.find(key);
+                if (it != rt->tune.end()) {
+                    v_ui = it->second.ui;
+                    v_zb = it->second.zb;
+                } else {
+                    tune_now = true;
+                }
+            }
+        }
         for (int64_t t0 = 0; t0 < tiles; t0 += chunk) {
             const int64_t nt = (tiles - t0) < chunk ? (tiles - t0) : chunk;
             if (sizeof(T) == 4)
@@ -240,8 +295,29 @@ static int run_descriptors(Ctx* c, int nsnap, const mala_snapshot* snaps, const 
                           launch_neighbors_f64(bs, nsnap, bp->rcut, bp->rfac0, bp->rmin0, t0, nt, nb, st));
             if (B || u_full) {
                 T* uh = c->ws_u.as<T>();
-                MALA_PROF(c, "k_ui", st, launch_ui<T>(tj, nb, bp->wself, nt, uh, st));
-                if (B) MALA_PROF(c, "k_zb", st, launch_zb<T>(c, tj, uh, bs, nsnap, t0, nt, nb.cnt, bp->wself, B, st));
+                if (tune_now) {
+                    // every variant on this chunk's own data (they give the same bits), the fastest kept
+                    TuneEntry e;
+                    MALA_TRY(time_variants(ui_variant_count(true), e.ui_ms, st, [&](int v) {
+                        launch_ui<T>(tj, nb, bp->wself, nt, uh, st, v);
+                    }));
+                    e.ui = best_variant(e.ui_ms, ui_variant_count(true));
+                    launch_ui<T>(tj, nb, bp->wself, nt, uh, st, e.ui);
+                    MALA_TRY(time_variants(zb_variant_count(), e.zb_ms, st, [&](int v) {
+                        launch_zb<T>(c, tj, uh, bs, nsnap, t0, nt, nb.cnt, bp->wself, B, st, v);
+                    }));
+                    e.zb = best_variant(e.zb_ms, zb_variant_count());
+                    v_ui = e.ui;
+                    v_zb = e.zb;
+                    tune_now = false;
+                    std::lock_guard<std::mutex> lk(rt->tune_mu);
+                    rt->tune[key] = e;
+                } else {
+                    MALA_PROF(c, "k_ui", st, launch_ui<T>(tj, nb, bp->wself, nt, uh, st, v_ui));
+                    if (B)
+                        MALA_PROF(c, "k_zb", st,
+                                  launch_zb<T>(c, tj, uh, bs, nsnap, t0, nt, nb.cnt, bp->wself, B, st, v_zb));
+                }
                 if (u_full) MALA_PROF(c, "k_u_expand", st, launch_u_expand<T>(tj, uh, hb[0].sd.g, t0, nt, u_full, st));
             }
         }
@@ -445,6 +521,53 @@ int mala_profile_get(mala_ctx* c, const char* kernel, double* total_ms, int64_t*
     auto it = c->prof.total.find(kernel);
     if (total_ms) *total_ms = it == c->prof.total.end() ? 0.0 : it->second.first;
     if (launches) *launches = it == c->prof.total.end() ? 0 : it->second.second;
+    return MALA_OK;
+}
+
+int mala_set_tuning(mala_ctx* c, int mode, int ui_variant, int zb_variant) {
+    if (!c) return fail(MALA_ERR_INVALID_ARG, "context is NULL");
+    if (mode < 0 || mode > 2) return fail(MALA_ERR_INVALID_ARG, "tuning mode %d is not 0, 1 or 2", mode);
+    if (mode == 2 && (ui_variant < 0 || ui_variant >= ui_variant_count(true) || zb_variant < 0 ||
+                      zb_variant >= zb_variant_count()))
+        return fail(MALA_ERR_INVALID_ARG, "variant (%d, %d) outside [0, %d) x [0, %d)", ui_variant, zb_variant,
+                    ui_variant_count(true), zb_variant_count());
+    std::lock_guard<std::mutex> lk(c->tune_mu);
+    c->tune_mode = mode;
+    c->force_ui = mode == 2 ? ui_variant : 0;
+    c->force_zb = mode == 2 ? zb_variant : 0;
+    if (mode != 1) c->tune.clear();
+    return MALA_OK;
+}
+
+int mala_tuning_variants(int32_t* n_ui, int32_t* n_zb) {
+    if (n_ui) *n_ui = ui_variant_count(true);
+    if (n_zb) *n_zb = zb_variant_count();
+    return MALA_OK;
+}
+
+int mala_tuning_report(mala_ctx* c, char* buf, size_t len) {
+    if (!c || !buf || len == 0) return fail(MALA_ERR_INVALID_ARG, "bad arguments");
+    std::string out;
+    std::lock_guard<std::mutex> lk(c->tune_mu);
+    char line[512];
+    for (auto& kv : c->tune) {
+        const uint64_t k = kv.first;
+        const TuneEntry& e = kv.second;
+        int seg = 0, warps = 0;
+        ui_variant_shape(e.ui, &seg, &warps);
+        int n = snprintf(line, sizeof(line), "twojmax=%d kmax<=%d points~2^%d: compute_ui seg %d x %d warps (",
+                         (int)(k & 0xff), (int)(((k >> 8) & 0xffff) * 8), (int)(k >> 24), seg, warps);
+        for (int v = 0; v < ui_variant_count(true); ++v) {
+            ui_variant_shape(v, &seg, &warps);
+            n += snprintf(line + n, sizeof(line) - n, "%s%dx%d %.3f ms", v ? ", " : "", seg, warps, e.ui_ms[v]);
+        }
+        n += snprintf(line + n, sizeof(line) - n, "), compute_zi/bi %d warps (", zb_variant_warps(e.zb));
+        for (int v = 0; v < zb_variant_count(); ++v)
+            n += snprintf(line + n, sizeof(line) - n, "%s%d %.3f ms", v ? ", " : "", zb_variant_warps(v), e.zb_ms[v]);
+        snprintf(line + n, sizeof(line) - n, ")\n");
+        out += line;
+    }
+    snprintf(buf, len, "%s", out.c_str());
     return MALA_OK;
 }
 

@@ -170,9 +170,9 @@ struct Model {
     std::vector<int> prow, pn0;      // [layer][2]: rows and first row of each part
     std::vector<CUtensorMap> maps;   // [layer][2] BF16 weights [Npad][Kpad], 128-byte swizzle, box = part rows
     std::vector<void*> allocs;
-    // MIXED: bf16 weights padded to K multiple of 16 / N multiple of 16, fp32 bias
-    std::vector<void*> Wbf;      // device bf16 [Npad][Kpad] per layer
-    std::vector<float*> bias;    // device fp32 [Npad]
+    // MIXED: bf16 weights [Npad][Kpad] per layer, N padded to 16, K + 2 padded to 64;
+    // columns K and K + 1 hold the bias as a BF16 (high, low) pair
+    std::vector<void*> Wbf;
     std::vector<int> Kpad, Npad;
     float* in_shift = nullptr;   // device fp32 [dims[0]] (0 if absent)
     float* in_scale = nullptr;   // device fp32 [dims[0]] (1 if absent)
@@ -188,6 +188,13 @@ struct ForceTables {
     int tj = -1;
     int ncoup = 0, list_len = 0, nh = 0;
     size_t off[10] = {0};
+};
+
+// Tile-shape tuning: per key (twojmax, neighbour-capacity band, grid-size band)
+// the compute_ui and compute_zi/bi variants chosen, with the times that chose them.
+struct TuneEntry {
+    int ui = 0, zb = 0;
+    float ui_ms[4] = {0, 0, 0, 0}, zb_ms[4] = {0, 0, 0, 0};
 };
 
 struct SnapStage;  // per-call staging of one snapshot (atoms, bins, neighbours)
@@ -226,6 +233,11 @@ struct Ctx {
     std::mutex prof_mu;
     Prof prof;
     int kmax_hint = 64;             // neighbour capacity that sufficed last time
+    // tile-shape tuning (the root context's state serves its serving slots too)
+    int tune_mode = 1;              // 0 defaults, 1 autotune, 2 forced variants
+    int force_ui = 0, force_zb = 0;
+    std::mutex tune_mu;
+    std::map<uint64_t, TuneEntry> tune;
     // serving
     struct Server* server = nullptr;
     // networks created on this context; mala_destroy frees their device memory
@@ -300,20 +312,33 @@ void launch_neighbors(const BatchSnap* bs, int nsnap, double rcut, double rfac0,
 void launch_neighbors_f64(const BatchSnap* bs, int nsnap, double rcut, double rfac0, double rmin0, int64_t tile0,
                           int64_t ntiles, const NbrOut& out, cudaStream_t st);
 
-// u half storage [tile][n_half][32] complex
+// u half storage [tile][n_half][32] complex; variant: a compiled (segment length,
+// warps per CTA) shape of the FP32 kernel (0 = default), ignored for FP64
 template <class T>
-void launch_ui(int twojmax, const NbrOut& nb, double wself, int64_t ntiles, T* u_half, cudaStream_t st);
+void launch_ui(int twojmax, const NbrOut& nb, double wself, int64_t ntiles, T* u_half, cudaStream_t st,
+               int variant = 0);
+int ui_variant_count(bool fp32);
+void ui_variant_shape(int v, int* seg, int* warps);
 
-// nbr_cnt: the chunk's neighbour counts [tile][32]; wself: the self-term weight
+// nbr_cnt: the chunk's neighbour counts [tile][32]; wself: the self-term weight;
+// variant: the FP32 kernel's warps-per-CTA shape (0 = default), ignored for FP64
 template <class T>
 void launch_zb(Ctx* c, int twojmax, const T* u_half, const BatchSnap* bs, int nsnap, int64_t tile0, int64_t ntiles,
-               const int* nbr_cnt, double wself, T* B, cudaStream_t st);
+               const int* nbr_cnt, double wself, T* B, cudaStream_t st, int variant = 0);
 template <>
 void launch_zb<float>(Ctx* c, int twojmax, const float* u_half, const BatchSnap* bs, int nsnap, int64_t tile0,
-                      int64_t ntiles, const int* nbr_cnt, double wself, float* B, cudaStream_t st);
+                      int64_t ntiles, const int* nbr_cnt, double wself, float* B, cudaStream_t st, int variant);
 template <>
 void launch_zb<double>(Ctx* c, int twojmax, const double* u_half, const BatchSnap* bs, int nsnap, int64_t tile0,
-                       int64_t ntiles, const int* nbr_cnt, double wself, double* B, cudaStream_t st);
+                       int64_t ntiles, const int* nbr_cnt, double wself, double* B, cudaStream_t st, int variant);
+int zb_variant_count();
+int zb_variant_warps(int v);
+// the alternate-warp-count FP32 kernel (its own translation unit) and its constant tables
+constexpr int kZbWarpsAlt = 12;
+void launch_zb_alt(Ctx* c, int twojmax, const float* u_half, const BatchSnap* bs, int nsnap, int64_t tile0,
+                   int64_t ntiles, const int* nbr_cnt, double wself, float* B, cudaStream_t st);
+int upload_zb_alt_cg(const float2* cg2, int bytes);
+int upload_zb_alt_jp1(const float* jp1, int bytes, int offset);
 
 template <class T>
 void launch_u_expand(int twojmax, const T* u_half, const SnapGeom& g, int64_t tile0, int64_t ntiles,

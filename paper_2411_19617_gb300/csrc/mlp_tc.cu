@@ -61,34 +61,35 @@ constexpr int kRing = 4;                         // weight slots
 constexpr int kChunkRows = 208;                  // rows of the widest weight chunk
 constexpr int kChunkBytes = kChunkRows * 128;    // 26624
 constexpr int kMaxParts = 2;
-constexpr int kMaxNPad = kMaxParts * kChunkRows; // widest layer output: 416
+constexpr int kMaxNPad = 400;                    // widest layer output (two parts, cut at a K-block boundary)
 constexpr int kMaxNE = 256;                      // widest output layer (staging tile <= 4 K-blocks)
-constexpr int kMaxInBlocks = 2;                  // input K-blocks (descriptor count <= 128)
+constexpr int kMaxInBlocks = 2;                  // input K-blocks (descriptor count + 2 <= 128)
 constexpr int kQOff = 4 * kBlkBytes;             // column sums of the four lane quarters, behind the staging tile
-constexpr int kMaxBias = kMaxLayers * kMaxNPad;
-constexpr int kSmemBytes = kHBytes + kRing * kChunkBytes + kMaxBias * 4 + kMaxNE * 8 + 256 /* barriers */ +
-                           1024 /* alignment */;
+constexpr int kSmemBytes = kHBytes + kRing * kChunkBytes + kMaxNE * 8 + 256 /* barriers */ + 1024 /* alignment */;
 static_assert(kSmemBytes <= 232448, "shared memory of the network kernel");
 static_assert(kQOff + 4 * kMaxNE * 4 <= (kHBlocks - kMaxInBlocks) * kBlkBytes, "quarter sums overlap the input");
 constexpr long long kWaitCycles = 2000000000LL;
 
+// The bias rides in the MMA: the A operand of every layer carries two
+// constant-one columns right after its K real columns, and the weights carry
+// the bias there as a BF16 pair (b_hi = bf16(b), b_lo = bf16(b - b_hi)), so the
+// FP32 accumulator already holds W x + b (to about 2^-16 of b).
+
 struct LayerDev {
-    int nkb;            // K-blocks of 64 (the A operand's width / 64)
-    int N, Npad;        // output width, padded to 16
-    int nparts;         // weight chunks per K-block (N parts)
+    int nkb;              // K-blocks of 64 (the A operand's width / 64)
+    int N, Npad;          // output width, padded to 16
+    int nparts;           // N parts (one commit each; part boundaries on K-block boundaries)
     int prow[kMaxParts];  // rows of each part (multiples of 16, <= kChunkRows)
-    int pn0[kMaxParts];   // first output column of each part
-    int act;            // apply LeakyReLU
-    int bias_off;       // offset of the layer's bias in the shared bias array
-    const float* bias;  // [Npad]
+    int pn0[kMaxParts];   // first output column of each part (multiples of 64)
+    int act;              // apply LeakyReLU
 };
 
 struct MlpParams {
     int n_layers;
     LayerDev L[kMaxLayers];
     float slope;
+    int slope_max;          // 0 <= slope <= 1: LeakyReLU as max(t, slope t)
     int nin;                // input K-blocks (layer 0's nkb)
-    int nbias;              // floats of the shared bias array
     __nv_bfloat16* ldos;    // [P][N_E]
     int bulk_out;           // LDOS 16-byte aligned: full tiles leave by one bulk copy
     double* cta_dos;        // [gridDim.x][N_E] or nullptr
@@ -97,7 +98,7 @@ struct MlpParams {
 };
 
 struct TMaps {
-    CUtensorMap in;                          // standardised BF16 descriptors [P][nin_cols]
+    CUtensorMap in;                          // standardised BF16 descriptors [P][nin_cols] (+ the ones columns)
     CUtensorMap w[kMaxLayers][kMaxParts];    // BF16 weights [Npad][Kpad], one map per part height
 };
 
@@ -230,6 +231,34 @@ __device__ __forceinline__ void tmem_issue32(uint32_t taddr, uint32_t (&r)[32]) 
         : "r"(taddr + 16u));
 }
 
+// tcgen05.st of 16 registers into 16 consecutive columns of the warp's lane
+// quarter, then the wait for it; and the matching 16-column read
+__device__ __forceinline__ void tmem_park16(uint32_t taddr, const uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
+        "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+        : "memory");
+}
+__device__ __forceinline__ void tmem_park1(uint32_t taddr, uint32_t v) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x1.b32 [%0], {%1};" ::"r"(taddr), "r"(v) : "memory");
+}
+__device__ __forceinline__ void tmem_park_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tmem_unpark17(uint32_t taddr, uint32_t (&r)[16], uint32_t& v) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(v) : "r"(taddr + 16u));
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]),
+                   "+r"(v)
+                 :
+                 : "memory");
+}
+
 __device__ __forceinline__ void tmem_wait(uint32_t (&r)[32]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;"
                  : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
@@ -241,20 +270,25 @@ __device__ __forceinline__ void tmem_wait(uint32_t (&r)[32]) {
                  : "memory");
 }
 
-// bias (shared memory) + activation of 32 accumulator columns c0.. (zero beyond the layer's N)
-__device__ __forceinline__ void bias_act32(const uint32_t (&r)[32], float (&x)[32], int c0, const LayerDev& L,
-                                           const float* sbias, float slope) {
+// activation of 32 accumulator columns c0.. (bias already inside): columns
+// beyond the layer's N become the constant-one columns of the next layer's
+// bias (N and N + 1) or zero
+__device__ __forceinline__ void act32(const uint32_t (&r)[32], float (&x)[32], int c0, const LayerDev& L, float slope,
+                                      bool slope_max, bool ones) {
+    if (c0 + 32 <= L.N) {
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        float4 b = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (c0 + 4 * q < L.Npad) b = *reinterpret_cast<const float4*>(sbias + L.bias_off + c0 + 4 * q);
-        const float bb[4] = {b.x, b.y, b.z, b.w};
+        for (int i = 0; i < 32; ++i) {
+            float t = __uint_as_float(r[i]);
+            if (L.act) t = slope_max ? fmaxf(t, slope * t) : (t > 0.f ? t : slope * t);
+            x[i] = t;
+        }
+    } else {
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int c = c0 + 4 * q + i;
-            float t = (c < L.N) ? __uint_as_float(r[4 * q + i]) + bb[i] : 0.f;
-            if (L.act) t = t > 0.f ? t : slope * t;
-            x[4 * q + i] = t;
+        for (int i = 0; i < 32; ++i) {
+            const int c = c0 + i;
+            float t = __uint_as_float(r[i]);
+            if (L.act) t = slope_max ? fmaxf(t, slope * t) : (t > 0.f ? t : slope * t);
+            x[i] = c < L.N ? t : ((ones && (c == L.N || c == L.N + 1)) ? 1.f : 0.f);
         }
     }
 }
@@ -276,28 +310,35 @@ __device__ __forceinline__ float warp_colsum32(float (&v)[32]) {
     return v[0];
 }
 
+// A-operand K-block kb of layer l (l > 0) is written by the part of layer
+// l - 1 that holds its first column (part boundaries sit on K-block
+// boundaries; the padding blocks belong to the last part)
+__device__ __forceinline__ int part_of_col(const LayerDev& L, int col) {
+    return (L.nparts > 1 && col >= L.pn0[1]) ? 1 : 0;
+}
+
 __global__ void __launch_bounds__(kMlpThreads, 1) k_mlp_tc(const __grid_constant__ TMaps maps, MlpParams prm) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     unsigned char* sH = sm;                                  // activations, K-blocks of [128][64] BF16
     unsigned char* sRing = sm + kHBytes;                     // weight chunks
-    float* sBias = reinterpret_cast<float*>(sRing + kRing * kChunkBytes);
-    double* sDos = reinterpret_cast<double*>(sBias + kMaxBias);
+    double* sDos = reinterpret_cast<double*>(sRing + kRing * kChunkBytes);
     uint64_t* bars = reinterpret_cast<uint64_t*>(sDos + kMaxNE);
-    // barriers: full[kRing] | empty[kRing] | in_full | in_free | acc_full | epi_done
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2 * kRing + 4);
+    // barriers: full[kRing] | empty[kRing] | in_full | in_free | acc[2] | epi[2]
+    constexpr int B_FULL = 0, B_EMPTY = kRing, B_IN_FULL = 2 * kRing, B_IN_FREE = 2 * kRing + 1,
+                  B_ACC = 2 * kRing + 2, B_EPI = 2 * kRing + 4, NBARS = 2 * kRing + 6;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + NBARS);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t ntiles = (prm.P + 127) / 128;
     const int nl = prm.n_layers;
     const int NE = prm.L[nl - 1].N;
     auto bar = [&](int i) { return smem_u32(&bars[i]); };
-    const int B_FULL = 0, B_EMPTY = kRing, B_IN_FULL = 2 * kRing, B_IN_FREE = 2 * kRing + 1,
-              B_ACC = 2 * kRing + 2, B_EPI = 2 * kRing + 3;
 
     if (tid == 0) {
-        for (int i = 0; i < 2 * kRing + 3; ++i) mbar_init(bar(i), 1);
+        for (int i = 0; i < B_EPI; ++i) mbar_init(bar(i), 1);
         mbar_init(bar(B_EPI), kEpiWarps);
+        mbar_init(bar(B_EPI + 1), kEpiWarps);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -305,8 +346,6 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_mlp_tc(const __grid_constant
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(tslot)));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
-    for (int l = 0; l < nl; ++l)
-        for (int i = tid; i < prm.L[l].Npad; i += kMlpThreads) sBias[prm.L[l].bias_off + i] = __ldg(prm.L[l].bias + i);
     for (int c = tid; c < NE; c += kMlpThreads) sDos[c] = 0.0;
     tc_fence_before();
     __syncthreads();
@@ -314,7 +353,8 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_mlp_tc(const __grid_constant
     const uint32_t tmem = *tslot;
 
     if (warp == kProducerWarp) {
-        // ---- producer: the next tiles' inputs and the weight chunks, in consumption order ----
+        // ---- producer: the next tiles' inputs and the weight chunks, in consumption order
+        //      (per layer: part-major, K-blocks within a part) ----
         if (lane == 0) {
             for (int l = 0; l < nl; ++l)
                 for (int p = 0; p < prm.L[l].nparts; ++p)
@@ -335,8 +375,8 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_mlp_tc(const __grid_constant
                 ++issued_in;
                 for (int l = 0; l < nl && ok; ++l) {
                     const LayerDev& L = prm.L[l];
-                    for (int kb = 0; kb < L.nkb && ok; ++kb)
-                        for (int p = 0; p < L.nparts; ++p, ++chunk) {
+                    for (int p = 0; p < L.nparts && ok; ++p)
+                        for (int kb = 0; kb < L.nkb; ++kb, ++chunk) {
                             const uint32_t slot = chunk % kRing;
                             if (chunk >= (uint32_t)kRing) {
                                 ok = mbar_wait(bar(B_EMPTY + slot), ((chunk / kRing) - 1) & 1, abort_flag, prm.err, 3);
@@ -358,28 +398,51 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_mlp_tc(const __grid_constant
             if (issued_in > 0) mbar_drain(bar(B_IN_FULL), (issued_in - 1) & 1);
         }
     } else if (warp == kMmaWarp) {
-        // ---- MMA issuer ----
+        // ---- MMA issuer: a part's K-blocks, then its commit; every A block and
+        //      TMEM column waits only for the epilogue part that produces or reads it ----
         if (lane == 0) {
-            uint32_t chunk = 0, in_ph = 0, epi_ph = 0;
+            uint32_t chunk = 0, in_ph = 0, epi_ph = 0;  // epi_ph: bit q = phase of epilogue barrier q
             bool ok = true, first = true;
+            auto wait_epi = [&](int q) {
+                ok = mbar_wait(bar(B_EPI + q), (epi_ph >> q) & 1u, abort_flag, prm.err, 4);
+                epi_ph ^= 1u << q;
+                tc_fence_after();
+            };
             for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
                 for (int l = 0; l < nl && ok; ++l) {
                     const LayerDev& L = prm.L[l];
+                    const LayerDev& Lp = prm.L[l == 0 ? nl - 1 : l - 1];  // the layer whose epilogue comes before
+                    uint32_t waited = 0;  // parts of that epilogue waited for in this layer
                     if (l == 0) {
                         ok = mbar_wait(bar(B_IN_FULL), in_ph, abort_flag, prm.err, 6);
                         in_ph ^= 1;
-                        if (!ok) break;
-                    }
-                    if (!first) {  // the previous epilogue has read the accumulator and written this layer's A
-                        ok = mbar_wait(bar(B_EPI), epi_ph, abort_flag, prm.err, 4);
-                        epi_ph ^= 1;
+                        tc_fence_after();
+                        // the previous tile's last epilogue must have read every accumulator column
+                        if (!first)
+                            for (int q = 0; q < Lp.nparts && ok; ++q) wait_epi(q);
+                        waited = 3u;
                         if (!ok) break;
                     }
                     first = false;
-                    tc_fence_after();
                     const int ablk0 = (l == 0) ? kHBlocks - prm.nin : 0;
-                    for (int kb = 0; kb < L.nkb && ok; ++kb)
-                        for (int p = 0; p < L.nparts; ++p, ++chunk) {
+                    for (int p = 0; p < L.nparts && ok; ++p) {
+                        // TMEM columns of this part: every part of the previous epilogue reading them
+                        for (int q = 0; q < Lp.nparts && ok; ++q) {
+                            const int q0 = Lp.pn0[q], q1 = (q + 1 < Lp.nparts) ? Lp.pn0[q + 1] : (1 << 30);
+                            if (!(waited >> q & 1) && q0 < L.pn0[p] + L.prow[p] && L.pn0[p] < q1) {
+                                wait_epi(q);
+                                waited |= 1u << q;
+                            }
+                        }
+                        for (int kb = 0; kb < L.nkb && ok; ++kb, ++chunk) {
+                            if (l > 0) {  // the A block's producer part
+                                const int q = part_of_col(Lp, kb * kKBlk);
+                                if (!(waited >> q & 1)) {
+                                    wait_epi(q);
+                                    waited |= 1u << q;
+                                    if (!ok) break;
+                                }
+                            }
                             const uint32_t slot = chunk % kRing;
                             ok = mbar_wait(bar(B_FULL + slot), (chunk / kRing) & 1, abort_flag, prm.err, 2);
                             if (!ok) break;
@@ -393,101 +456,143 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_mlp_tc(const __grid_constant
                                          (kb > 0 || k > 0) ? 1u : 0u);
                             mma_commit(bar(B_EMPTY + slot));
                         }
+                        if (!ok) break;
+                        mma_commit(bar(B_ACC + p));
+                    }
                     if (!ok) break;
-                    mma_commit(bar(B_ACC));
+                    // every part of the previous epilogue has been waited for (all A blocks are read)
+                    for (int q = 0; q < Lp.nparts && ok && l > 0; ++q)
+                        if (!(waited >> q & 1)) wait_epi(q);
                     if (l == nl - 1) mma_commit(bar(B_IN_FREE));
                 }
             }
         }
     } else {
-        // ---- epilogue warps: TMEM -> registers (thread = point) -> bias/activation -> shared memory ----
+        // ---- epilogue warps: TMEM -> registers (thread = point) -> activation -> shared memory ----
         const int quarter = warp & 3, half = warp >> 2;
         const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16);
         const int r = quarter * 32 + lane;
         float* sQ = reinterpret_cast<float*>(sH + kQOff);  // [4][NE] column sums of the lane quarters
         __nv_bfloat16* so = reinterpret_cast<__nv_bfloat16*>(sH);
-        uint32_t acc_ph = 0;
+        const bool smax = prm.slope_max != 0;
+        uint32_t acc_ph = 0;  // bit p = phase of accumulator barrier p
         bool ok = true, store_pending = false;
+        // one 32-column chunk c0 of this thread's row: activation, then into the next
+        // layer's A block (swizzled) or, for the last layer, into the staging row with
+        // the chunk's column sums over the warp's rows (returned for lane c)
+        auto chunk_vals = [&](const uint32_t (&rr)[32], int c0, const LayerDev& L, bool last, int nrows,
+                              uint32_t (&pk)[16], float& cs) {
+            float x[32];
+            act32(rr, x, c0, L, prm.slope, smax, !last);
+#pragma unroll
+            for (int q = 0; q < 16; ++q) pk[q] = pack_bf16(x[2 * q], x[2 * q + 1]);
+            if (last && prm.cta_dos) {
+                // column sums of the rounded values of the tile's real rows and columns
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&pk[q]));
+                    x[2 * q] = (r < nrows && c0 + 2 * q < NE) ? f.x : 0.f;
+                    x[2 * q + 1] = (r < nrows && c0 + 2 * q + 1 < NE) ? f.y : 0.f;
+                }
+                cs = warp_colsum32(x);
+            }
+        };
+        auto chunk_store = [&](const uint32_t (&pk)[16], float cs, int c0, bool last) {
+            if (!last) {
+                unsigned char* blk = sH + (c0 / kKBlk) * kBlkBytes;
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    *reinterpret_cast<uint4*>(blk + swz(r, c0 % kKBlk + 8 * q)) =
+                        make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+            } else {
+                __nv_bfloat16* orow = so + (size_t)r * NE;
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    const __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162*>(&pk[q]);
+                    if (c0 + 2 * q < NE) orow[c0 + 2 * q] = h.x;
+                    if (c0 + 2 * q + 1 < NE) orow[c0 + 2 * q + 1] = h.y;
+                }
+                if (prm.cta_dos && c0 + lane < NE) sQ[quarter * NE + c0 + lane] = cs;
+            }
+        };
         for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
             const int64_t row0 = tile * 128;
             const int nrows = (int)min((int64_t)128, prm.P - row0);
-            for (int l = 0; l < nl; ++l) {
+            for (int l = 0; l < nl && ok; ++l) {
                 const LayerDev& L = prm.L[l];
-                const bool got = mbar_wait(bar(B_ACC), acc_ph, abort_flag, prm.err, 7);
-                acc_ph ^= 1;
-                tc_fence_after();
-                // before the first writes of a tile: the previous tile's output copy has read the staging tile
-                if (l == 0 && tid == 0 && store_pending) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
-                store_pending = false;
-                // one decision for all epilogue warps (none may stop alone: they share named barriers)
-                if (epi_sync_any(!got || *abort_flag)) {
-                    ok = false;
-                    break;
+                const bool last = l == nl - 1;
+                const int cend = last ? ((NE + 31) & ~31) : prm.L[l + 1].nkb * kKBlk;
+                bool acc1_taken = false;  // the second part's accumulator barrier already waited for
+                for (int p = 0; p < L.nparts; ++p) {
+                    bool got = true;
+                    if (!(p == 1 && acc1_taken)) {
+                        got = mbar_wait(bar(B_ACC + p), (acc_ph >> p) & 1u, abort_flag, prm.err, 7);
+                        acc_ph ^= 1u << p;
+                        tc_fence_after();
+                    }
+                    // before the first writes of a tile: the previous tile's output copy has read the staging tile
+                    if (l == 0 && p == 0 && tid == 0 && store_pending)
+                        asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+                    if (l == 0 && p == 0) store_pending = false;
+                    // one decision for all epilogue warps (none may stop alone: they share named barriers)
+                    if (epi_sync_any(!got || *abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    const int cb = L.pn0[p];
+                    const int ce = (p + 1 < L.nparts) ? L.pn0[p + 1] : cend;
+                    const int nch = (ce - cb - half * 32 + 63) / 64;  // this warp's chunks: cb + half*32 + 64 j
+                    // the layer's A blocks: the input blocks for layer 0, all of them afterwards
+                    const bool park = p == 0 && L.nparts == 2 && (l > 0 || L.pn0[1] / kKBlk > kHBlocks - prm.nin);
+                    if (park) {
+                        // The second part's MMAs still read the activations this part overwrites: while
+                        // they run, convert this part's chunks and park the packed results (and column
+                        // sums) in the chunks' own, already read, accumulator columns; store them to
+                        // shared memory once every MMA of the layer is done.
+                        for (int j = 0; j < nch; ++j) {
+                            const int c0 = cb + half * 32 + 64 * j;
+                            uint32_t rr[32], pk[16];
+                            float cs = 0.f;
+                            tmem_issue32(trow + (uint32_t)c0, rr);
+                            tmem_wait(rr);
+                            chunk_vals(rr, c0, L, last, nrows, pk, cs);
+                            tmem_park16(trow + (uint32_t)c0, pk);
+                            tmem_park1(trow + (uint32_t)(c0 + 16), __float_as_uint(cs));
+                        }
+                        tmem_park_wait();
+                        got = mbar_wait(bar(B_ACC + 1), (acc_ph >> 1) & 1u, abort_flag, prm.err, 7);
+                        acc_ph ^= 2u;
+                        acc1_taken = true;
+                        tc_fence_after();
+                        if (epi_sync_any(!got || *abort_flag)) {
+                            ok = false;
+                            break;
+                        }
+                        for (int j = 0; j < nch; ++j) {
+                            const int c0 = cb + half * 32 + 64 * j;
+                            uint32_t pk[16], csu;
+                            tmem_unpark17(trow + (uint32_t)c0, pk, csu);
+                            chunk_store(pk, __uint_as_float(csu), c0, last);
+                        }
+                    } else {
+                        for (int j = 0; j < nch; ++j) {
+                            const int c0 = cb + half * 32 + 64 * j;
+                            uint32_t rr[32], pk[16];
+                            float cs = 0.f;
+                            tmem_issue32(trow + (uint32_t)c0, rr);
+                            tmem_wait(rr);
+                            chunk_vals(rr, c0, L, last, nrows, pk, cs);
+                            chunk_store(pk, cs, c0, last);
+                        }
+                    }
+                    // this part of the accumulator has been read and its outputs written
+                    fence_proxy_async();
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(bar(B_EPI + p));
                 }
-                if (l < nl - 1) {
-                    const int Knext = prm.L[l + 1].nkb * kKBlk;
-                    auto store_chunk = [&](const uint32_t (&rr)[32], int c0) {
-                        float x[32];
-                        bias_act32(rr, x, c0, L, sBias, prm.slope);
-                        unsigned char* blk = sH + (c0 / kKBlk) * kBlkBytes;
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            uint4 w4;
-                            w4.x = pack_bf16(x[8 * q + 0], x[8 * q + 1]);
-                            w4.y = pack_bf16(x[8 * q + 2], x[8 * q + 3]);
-                            w4.z = pack_bf16(x[8 * q + 4], x[8 * q + 5]);
-                            w4.w = pack_bf16(x[8 * q + 6], x[8 * q + 7]);
-                            *reinterpret_cast<uint4*>(blk + swz(r, c0 % kKBlk + 8 * q)) = w4;
-                        }
-                    };
-                    // this warp's 32-column chunks c0 = half*32 + 64 j; the TMEM read of
-                    // chunk j+1 is in flight while chunk j is converted
-                    const int nch = (Knext - half * 32 + 63) / 64;
-                    uint32_t ra[32], rb[32];
-                    if (nch > 0) {
-                        tmem_issue32(trow + (uint32_t)(half * 32), ra);
-                        tmem_wait(ra);
-                    }
-                    for (int j = 0; j < nch; j += 2) {
-                        const int c0 = half * 32 + 64 * j;
-                        if (j + 1 < nch) tmem_issue32(trow + (uint32_t)(c0 + 64), rb);
-                        store_chunk(ra, c0);
-                        if (j + 1 < nch) {
-                            tmem_wait(rb);
-                            if (j + 2 < nch) tmem_issue32(trow + (uint32_t)(c0 + 128), ra);
-                            store_chunk(rb, c0 + 64);
-                            if (j + 2 < nch) tmem_wait(ra);
-                        }
-                    }
-                    fence_proxy_async();
-                    tc_fence_before();
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(bar(B_EPI));
-                } else {
-                    // output: BF16 values into the dense staging tile [128][NE] and their column sums
-                    const int ldc = (NE + 31) & ~31;
-                    for (int c0 = half * 32; c0 < ldc; c0 += 64) {
-                        uint32_t rr[32];
-                        tmem_issue32(trow + (uint32_t)c0, rr);
-                        tmem_wait(rr);
-                        float x[32];
-                        bias_act32(rr, x, c0, L, sBias, prm.slope);
-                        __nv_bfloat16* orow = so + (size_t)r * NE;
-#pragma unroll
-                        for (int i = 0; i < 32; ++i) {
-                            const __nv_bfloat16 h = __float2bfloat16_rn(x[i]);
-                            x[i] = (r < nrows && c0 + i < NE) ? __bfloat162float(h) : 0.f;
-                            if (c0 + i < NE) orow[c0 + i] = h;
-                        }
-                        if (prm.cta_dos) {
-                            const float cs = warp_colsum32(x);
-                            if (c0 + lane < NE) sQ[quarter * NE + c0 + lane] = cs;
-                        }
-                    }
-                    tc_fence_before();
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(bar(B_EPI));  // the accumulator has been read
-                    fence_proxy_async();
+                if (!ok) break;
+                if (last) {
                     epi_sync();
                     if (prm.cta_dos && tid < NE)
                         sDos[tid] += (((double)sQ[tid] + (double)sQ[NE + tid]) + (double)sQ[2 * NE + tid]) +
@@ -521,7 +626,8 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_mlp_tc(const __grid_constant
 }
 
 // standardised BF16 copy of the descriptors for the network's input TMA:
-// Bh[p][k] = (B[p][k] - shift[k]) * scale[k] for k < nB, 0 up to the padded width nBh
+// Bh[p][k] = (B[p][k] - shift[k]) * scale[k] for k < nB, 1 at k = nB and nB + 1
+// (the bias columns), 0 up to the padded width nBh
 __global__ void k_mlp_in(const float* __restrict__ B, int64_t P, int nB, int nBh, const float* __restrict__ shift,
                          const float* __restrict__ scale, __nv_bfloat16* __restrict__ Bh) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // one 8-column group
@@ -536,7 +642,7 @@ __global__ void k_mlp_in(const float* __restrict__ B, int64_t P, int nB, int nBh
 #pragma unroll
         for (int t = 0; t < 2; ++t) {
             const int k = k0 + 2 * j + t;
-            v[t] = k < nB ? (__ldg(B + p * nB + k) - __ldg(shift + k)) * __ldg(scale + k) : 0.f;
+            v[t] = k < nB ? (__ldg(B + p * nB + k) - __ldg(shift + k)) * __ldg(scale + k) : (k < nB + 2 ? 1.f : 0.f);
         }
         w[j] = pack_bf16(v[0], v[1]);
     }
@@ -638,27 +744,30 @@ int model_upload(Ctx* c, const mala_mlp_desc* d, Model* m) {
     m->slope_d = d->leaky_slope;
     m->activate_output = d->activate_output;
     const int nl = d->n_layers;
-    // MIXED layout: K padded to 64 (128-byte swizzle blocks), N padded to 16 and
-    // cut into at most two parts of <= 208 rows (one ring slot each)
+    // MIXED layout: K + 2 (the two bias columns) padded to 64 (128-byte swizzle
+    // blocks), N padded to 16 and cut into at most two parts of <= 208 rows at a
+    // K-block boundary (one ring slot and one commit each)
     m->Kpad.resize(nl);
     m->Npad.resize(nl);
     m->nparts.assign(nl, 1);
     m->prow.assign(2 * nl, 0);
     m->pn0.assign(2 * nl, 0);
-    m->mixed_ok = nl <= kMaxLayers && m->dims[nl] <= kMaxNE && m->dims[0] <= kMaxInBlocks * kKBlk;
+    m->mixed_ok = nl <= kMaxLayers && m->dims[nl] <= kMaxNE;
     for (int l = 0; l < nl; ++l) {
-        m->Kpad[l] = pad_to(m->dims[l], kKBlk);
+        m->Kpad[l] = pad_to(m->dims[l] + 2, kKBlk);
         m->Npad[l] = pad_to(m->dims[l + 1], 16);
-        if (m->Kpad[l] > kMaxHiddenPad || m->Npad[l] > kMaxNPad) m->mixed_ok = false;
-        if (l + 1 < nl && pad_to(m->dims[l + 1], kKBlk) > kMaxHiddenPad) m->mixed_ok = false;
-        const int units = m->Npad[l] / 16, per = kChunkRows / 16;
-        const int np = std::min(kMaxParts, (units + per - 1) / per);
-        m->nparts[l] = np;
-        for (int p = 0, n0 = 0; p < np; ++p) {
-            const int u = units / np + (p < units % np ? 1 : 0);
-            m->prow[2 * l + p] = 16 * u;
-            m->pn0[2 * l + p] = n0;
-            n0 += 16 * u;
+        const int Np = m->Npad[l];
+        if ((l == 0 && m->Kpad[l] > kMaxInBlocks * kKBlk) || m->Kpad[l] > kMaxHiddenPad || Np > kMaxNPad)
+            m->mixed_ok = false;
+        if (Np <= kChunkRows) {
+            m->prow[2 * l] = Np;
+        } else {
+            const int p0 = std::max(kKBlk * ((Np - kChunkRows + kKBlk - 1) / kKBlk), kKBlk * (Np / (2 * kKBlk)));
+            if (p0 > kChunkRows || Np - p0 > kChunkRows) m->mixed_ok = false;
+            m->nparts[l] = 2;
+            m->prow[2 * l] = p0;
+            m->prow[2 * l + 1] = Np - p0;
+            m->pn0[2 * l + 1] = p0;
         }
     }
     auto dalloc = [&](size_t bytes, void** p) -> int {
@@ -685,22 +794,21 @@ int model_upload(Ctx* c, const mala_mlp_desc* d, Model* m) {
         m->Wd.push_back((double*)pw);
         m->bd.push_back((double*)pb);
         if (!m->mixed_ok) continue;
-        // BF16 [Npad][Kpad], FP32 bias [Npad]
+        // BF16 [Npad][Kpad]; the bias as a BF16 pair in columns K and K + 1, which
+        // meet the constant-one columns of the A operand
         const int Kp = m->Kpad[l], Np = m->Npad[l];
         std::vector<__nv_bfloat16> w((size_t)Np * Kp, __float2bfloat16(0.f));
-        std::vector<float> bb(Np, 0.f);
         for (int n = 0; n < N; ++n) {
             for (int k = 0; k < K; ++k) w[(size_t)n * Kp + k] = __float2bfloat16((float)d->W[l][(size_t)n * K + k]);
-            bb[n] = (float)d->b[l][n];
+            const double b = d->b[l][n];
+            const __nv_bfloat16 hi = __float2bfloat16((float)b);
+            w[(size_t)n * Kp + K] = hi;
+            w[(size_t)n * Kp + K + 1] = __float2bfloat16((float)(b - (double)__bfloat162float(hi)));
         }
         void* pwb = nullptr;
-        void* pbb = nullptr;
         MALA_TRY(dalloc(sizeof(__nv_bfloat16) * w.size(), &pwb));
-        MALA_TRY(dalloc(sizeof(float) * bb.size(), &pbb));
         MALA_CUDA_TRY(cudaMemcpy(pwb, w.data(), sizeof(__nv_bfloat16) * w.size(), cudaMemcpyHostToDevice));
-        MALA_CUDA_TRY(cudaMemcpy(pbb, bb.data(), sizeof(float) * bb.size(), cudaMemcpyHostToDevice));
         m->Wbf.push_back(pwb);
-        m->bias.push_back((float*)pbb);
     }
     // input standardisation (identity when absent)
     const int n0 = m->dims[0];
@@ -767,7 +875,7 @@ void mlp_ws_needs(Ctx* c, const Model* m, int64_t P, bool dos, mala_precision pr
         const int64_t ntiles = (P + 127) / 128;
         const int grid = (int)std::min<int64_t>(ntiles, std::max(1, c->num_sms));
         if (dos) out.add(c->ws_tile_dos, sizeof(double) * (size_t)grid * NE);
-        out.add(c->ws_mlp_in, sizeof(__nv_bfloat16) * (size_t)P * pad_to(m->dims[0], 8));
+        out.add(c->ws_mlp_in, sizeof(__nv_bfloat16) * (size_t)P * pad_to(m->dims[0] + 2, 8));
         return;
     }
     int wmax = 0;
@@ -788,7 +896,7 @@ int mlp_forward(Ctx* c, const Model* m, const void* B, int64_t P, void* ldos, do
         if (!m->mixed_ok)
             return fail(MALA_ERR_UNSUPPORTED, "network shape outside the tensor-core kernel's limits "
                                               "(<= %d layers, input <= %d, hidden width <= %d, output <= %d)",
-                        kMaxLayers, kMaxInBlocks * kKBlk, kMaxNPad, kMaxNE);
+                        kMaxLayers, kMaxInBlocks * kKBlk - 2, kMaxNPad, kMaxNE);
         const int64_t ntiles = (P + 127) / 128;
         if (ntiles > (int64_t)INT32_MAX / 2) return fail(MALA_ERR_UNSUPPORTED, "too many grid points for the network");
         const int grid = (int)std::min<int64_t>(ntiles, std::max(1, c->num_sms));
@@ -799,7 +907,7 @@ int mlp_forward(Ctx* c, const Model* m, const void* B, int64_t P, void* ldos, do
         }
         // standardised BF16 input rows, padded to a multiple of 8 (16 bytes) for the input TMA
         const int nB = m->dims[0];
-        const int nBh = pad_to(nB, 8);
+        const int nBh = pad_to(nB + 2, 8);  // + the two bias columns
         MALA_TRY(c->ws_mlp_in.reserve(c, sizeof(__nv_bfloat16) * (size_t)P * nBh));
         __nv_bfloat16* Bh = c->ws_mlp_in.as<__nv_bfloat16>();
         {
@@ -825,7 +933,6 @@ int mlp_forward(Ctx* c, const Model* m, const void* B, int64_t P, void* ldos, do
         MlpParams prm;
         memset(&prm, 0, sizeof(prm));
         prm.n_layers = nl;
-        int boff = 0;
         for (int l = 0; l < nl; ++l) {
             LayerDev& L = prm.L[l];
             L.nkb = m->Kpad[l] / kKBlk;
@@ -838,12 +945,9 @@ int mlp_forward(Ctx* c, const Model* m, const void* B, int64_t P, void* ldos, do
                 maps.w[l][p] = m->maps[2 * l + p];
             }
             L.act = (l < nl - 1) || m->activate_output;
-            L.bias_off = boff;
-            L.bias = m->bias[l];
-            boff += L.Npad;
         }
-        prm.nbias = boff;
         prm.slope = m->leaky_slope;
+        prm.slope_max = (m->leaky_slope >= 0.f && m->leaky_slope <= 1.f) ? 1 : 0;
         prm.nin = m->Kpad[0] / kKBlk;
         prm.ldos = static_cast<__nv_bfloat16*>(ldos);
         prm.bulk_out = (reinterpret_cast<uintptr_t>(ldos) & 15) == 0;

@@ -47,11 +47,19 @@ template <class T> __device__ __forceinline__ T unorm_at(int idx);
 template <> __device__ __forceinline__ float unorm_at<float>(int idx) { return c_unorm_f[idx]; }
 template <> __device__ __forceinline__ double unorm_at<double>(int idx) { return c_unorm_d[idx]; }
 
-// FP32: sums + compensations of up to 36 complex numbers (144 registers) per segment, with 8 warps
-// per CTA so each thread may hold 255 registers: fewer, longer segments re-walk the column chains
-// less often (measured 13% faster than 24-element segments at 12 warps)
-constexpr int kSegElemsF32 = 36;
+// FP32 variants (segment elements, warps per CTA): sums + compensations of up to SEG complex
+// numbers per segment live in registers, so longer segments (fewer chain re-walks) need fewer
+// warps per CTA (255 registers a thread at 8 warps, 168 at 12; the register file is split over
+// the four schedulers, so 10 warps get no more than 12).  Which one is fastest depends
+// on the neighbour count; the tuner times them on the data.  Every variant adds every element's
+// terms in the same order, so all give the same bits.
+struct UiVariant {
+    int seg, warps;
+};
+constexpr UiVariant kUiVariantsF32[] = {{36, 8}, {30, 8}, {20, 12}};
+constexpr int kNumUiVariantsF32 = 3;
 constexpr int kSegElemsF64 = 10;
+constexpr int kUiWarpsF64 = 6;
 
 struct Seg {
     int mb, l0, l1;
@@ -89,8 +97,8 @@ __host__ __device__ constexpr SegPlan make_plan(int tj, int emax) {
     return p;
 }
 
-template <class T, int TJ> struct Plan {
-    static constexpr SegPlan value = make_plan(TJ, sizeof(T) == 4 ? kSegElemsF32 : kSegElemsF64);
+template <int TJ, int SEG> struct Plan {
+    static constexpr SegPlan value = make_plan(TJ, SEG);
 };
 
 template <class T> struct C2;
@@ -308,25 +316,21 @@ __device__ __forceinline__ void ui_segment(const typename AB4<T>::type* __restri
 
 // All warps of the block run the same segment between barriers, so the SM
 // fetches one segment's code at a time.
-template <class T, int TJ, int I>
+template <class T, int TJ, int SEG, int I>
 __device__ __forceinline__ void run_segments(const typename AB4<T>::type* ab_t, const T* cw_t, int cnt, int kwarp,
                                              int lane, T wself, bool store, typename C2<T>::type* uo, int h) {
-    if constexpr (I < Plan<T, TJ>::value.n) {
-        constexpr Seg sg = Plan<T, TJ>::value.s[I];
+    if constexpr (I < Plan<TJ, SEG>::value.n) {
+        constexpr Seg sg = Plan<TJ, SEG>::value.s[I];
         ui_segment<T, TJ, sg.mb, sg.l0, sg.l1>(ab_t, cw_t, cnt, kwarp, lane, wself, store, uo, h);
         __syncthreads();
-        run_segments<T, TJ, I + 1>(ab_t, cw_t, cnt, kwarp, lane, wself, store, uo, h);
+        run_segments<T, TJ, SEG, I + 1>(ab_t, cw_t, cnt, kwarp, lane, wself, store, uo, h);
     }
 }
 
-template <class T> struct UiWarps { static constexpr int value = 8; };
-template <> struct UiWarps<double> { static constexpr int value = 6; };
-
-template <class T, int TJ>
-__global__ void __launch_bounds__(UiWarps<T>::value * 32, 1)
+template <class T, int TJ, int SEG, int W>
+__global__ void __launch_bounds__(W * 32, 1)
     k_ui(const typename AB4<T>::type* __restrict__ ab, const T* __restrict__ cw, const int* __restrict__ cnt,
          int kmax, T wself, int64_t ntiles, typename C2<T>::type* __restrict__ u) {
-    constexpr int W = UiWarps<T>::value;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t tl = (int64_t)blockIdx.x * W + warp;
     const bool live = tl < ntiles;
@@ -337,7 +341,7 @@ __global__ void __launch_bounds__(UiWarps<T>::value * 32, 1)
     const T* cw_t = cw + (size_t)tls * kmax * 32;
     // FP64: one block per tile; FP32: one block of two float2 per element and lane per tile pair
     auto* uo = (sizeof(T) == 8) ? u + (size_t)tls * n_half(TJ) * 32 : u + (size_t)(tls >> 1) * n_half(TJ) * 32 * 2;
-    run_segments<T, TJ, 0>(ab_t, cw_t, n, kw, lane, wself, live, uo, (int)(tls & 1));
+    run_segments<T, TJ, SEG, 0>(ab_t, cw_t, n, kw, lane, wself, live, uo, (int)(tls & 1));
 }
 
 // half set -> full (J+1)^2 blocks per point, point-major (for tests / the ABI)
@@ -385,13 +389,24 @@ __global__ void k_u_expand(int tj, const typename C2<T>::type* __restrict__ uh, 
     }
 }
 
-template <class T, int TJ>
-void launch_ui_tj(const NbrOut& nb, double wself, int64_t ntiles, T* u_half, cudaStream_t st) {
-    constexpr int W = UiWarps<T>::value;
+template <class T, int TJ, int SEG, int W>
+void launch_ui_v(const NbrOut& nb, double wself, int64_t ntiles, T* u_half, cudaStream_t st) {
     const unsigned blocks = (unsigned)((ntiles + W - 1) / W);
-    k_ui<T, TJ><<<blocks, W * 32, 0, st>>>(reinterpret_cast<const typename AB4<T>::type*>(nb.ab),
-                                                  reinterpret_cast<const T*>(nb.cw), nb.cnt, nb.kmax, (T)wself,
-                                                  ntiles, reinterpret_cast<typename C2<T>::type*>(u_half));
+    k_ui<T, TJ, SEG, W><<<blocks, W * 32, 0, st>>>(reinterpret_cast<const typename AB4<T>::type*>(nb.ab),
+                                                   reinterpret_cast<const T*>(nb.cw), nb.cnt, nb.kmax, (T)wself,
+                                                   ntiles, reinterpret_cast<typename C2<T>::type*>(u_half));
+}
+
+template <class T, int TJ>
+void launch_ui_tj(const NbrOut& nb, double wself, int64_t ntiles, T* u_half, int variant, cudaStream_t st) {
+    if constexpr (sizeof(T) == 8) {
+        launch_ui_v<T, TJ, kSegElemsF64, kUiWarpsF64>(nb, wself, ntiles, u_half, st);
+    } else {
+        constexpr UiVariant v0 = kUiVariantsF32[0], v1 = kUiVariantsF32[1], v2 = kUiVariantsF32[2];
+        if (variant == 1) launch_ui_v<T, TJ, v1.seg, v1.warps>(nb, wself, ntiles, u_half, st);
+        else if (variant == 2) launch_ui_v<T, TJ, v2.seg, v2.warps>(nb, wself, ntiles, u_half, st);
+        else launch_ui_v<T, TJ, v0.seg, v0.warps>(nb, wself, ntiles, u_half, st);
+    }
 }
 
 }  // namespace
@@ -413,8 +428,16 @@ int upload_ui_tables() {
     return MALA_OK;
 }
 
+int ui_variant_count(bool fp32) { return fp32 ? kNumUiVariantsF32 : 1; }
+
+void ui_variant_shape(int v, int* seg, int* warps) {
+    const UiVariant u = kUiVariantsF32[(v >= 0 && v < kNumUiVariantsF32) ? v : 0];
+    *seg = u.seg;
+    *warps = u.warps;
+}
+
 template <class T>
-void launch_ui(int twojmax, const NbrOut& nb, double wself, int64_t ntiles, T* u_half, cudaStream_t st) {
+void launch_ui(int twojmax, const NbrOut& nb, double wself, int64_t ntiles, T* u_half, cudaStream_t st, int variant) {
     if (ntiles <= 0) return;
     if (sizeof(T) == 4 && (ntiles & 1)) {
         // odd tile count: the B half of the last pair holds no tile; keep it finite (zero)
@@ -422,12 +445,12 @@ void launch_ui(int twojmax, const NbrOut& nb, double wself, int64_t ntiles, T* u
         cudaMemsetAsync(u_half + (size_t)(ntiles >> 1) * pair_floats, 0, pair_floats * sizeof(float), st);
     }
     switch (twojmax) {
-        case 0: launch_ui_tj<T, 0>(nb, wself, ntiles, u_half, st); break;
-        case 2: launch_ui_tj<T, 2>(nb, wself, ntiles, u_half, st); break;
-        case 4: launch_ui_tj<T, 4>(nb, wself, ntiles, u_half, st); break;
-        case 6: launch_ui_tj<T, 6>(nb, wself, ntiles, u_half, st); break;
-        case 8: launch_ui_tj<T, 8>(nb, wself, ntiles, u_half, st); break;
-        case 10: launch_ui_tj<T, 10>(nb, wself, ntiles, u_half, st); break;
+        case 0: launch_ui_tj<T, 0>(nb, wself, ntiles, u_half, variant, st); break;
+        case 2: launch_ui_tj<T, 2>(nb, wself, ntiles, u_half, variant, st); break;
+        case 4: launch_ui_tj<T, 4>(nb, wself, ntiles, u_half, variant, st); break;
+        case 6: launch_ui_tj<T, 6>(nb, wself, ntiles, u_half, variant, st); break;
+        case 8: launch_ui_tj<T, 8>(nb, wself, ntiles, u_half, variant, st); break;
+        case 10: launch_ui_tj<T, 10>(nb, wself, ntiles, u_half, variant, st); break;
         default: break;
     }
 }
@@ -440,8 +463,8 @@ void launch_u_expand(int twojmax, const T* u_half, const SnapGeom& g, int64_t ti
                                                     g, tile0, ntiles, u_full);
 }
 
-template void launch_ui<float>(int, const NbrOut&, double, int64_t, float*, cudaStream_t);
-template void launch_ui<double>(int, const NbrOut&, double, int64_t, double*, cudaStream_t);
+template void launch_ui<float>(int, const NbrOut&, double, int64_t, float*, cudaStream_t, int);
+template void launch_ui<double>(int, const NbrOut&, double, int64_t, double*, cudaStream_t, int);
 template void launch_u_expand<float>(int, const float*, const SnapGeom&, int64_t, int64_t, float*, cudaStream_t);
 template void launch_u_expand<double>(int, const double*, const SnapGeom&, int64_t, int64_t, double*, cudaStream_t);
 

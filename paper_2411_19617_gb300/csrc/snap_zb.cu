@@ -103,6 +103,7 @@ int upload_cg_tables(Ctx* c) {
             }
     c->tables.cg = tab;
     MALA_CUDA_TRY(cudaMemcpyToSymbol(c_cg2, tabf.data(), sizeof(float2) * kCgSize));
+    MALA_TRY(upload_zb_alt_cg(tabf.data(), (int)(sizeof(float2) * kCgSize)));
 
     MALA_TRY(c->ws_misc.reserve(c, sizeof(double) * kCgSize));
     c->tables.cg_d = c->ws_misc.as<double>();
@@ -184,6 +185,7 @@ int upload_cg_tables(Ctx* c) {
                     for (int j = 0; j <= tj; ++j)
                         if (triple_ok(j1, j2, j, tj)) jp1[col++] = (float)(j + 1);
             MALA_CUDA_TRY(cudaMemcpyToSymbol(c_zb_jp1, jp1, sizeof(jp1), sizeof(jp1) * (tj / 2)));
+            MALA_TRY(upload_zb_alt_jp1(jp1, (int)sizeof(jp1), (int)(sizeof(jp1) * (tj / 2))));
         }
         c->tables.tri_n[tj / 2] = lid;
     }
@@ -200,20 +202,17 @@ int upload_cg_tables(Ctx* c) {
     return MALA_OK;
 }
 
+// variants of the FP32 kernel (warps per CTA); index 0 is the default
+constexpr int kZbVariantWarps[] = {kZbUWarps, kZbWarpsAlt};
+
+int zb_variant_count() { return 2; }
+int zb_variant_warps(int v) { return kZbVariantWarps[(v == 1) ? 1 : 0]; }
+
 template <>
 void launch_zb<float>(Ctx* c, int twojmax, const float* u_half, const BatchSnap* bs, int nsnap, int64_t tile0,
-                      int64_t ntiles, const int* nbr_cnt, double wself, float* B, cudaStream_t st) {
-    if (ntiles <= 0) return;
-    const size_t smem = sizeof(float4) * (size_t)n_half(twojmax) * 32 +
-                        sizeof(long long) * (size_t)n_triples(twojmax) * 64 + 2 * sizeof(uint64_t) + 64 * sizeof(long long);
-    cudaFuncSetAttribute(k_zb_units, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    const int k = twojmax / 2;
-    const int64_t npairs = (ntiles + 1) / 2;
-    const int grid = (int)std::min<int64_t>(npairs, std::max(1, c->num_sms));
-    k_zb_units<<<(unsigned)grid, kZbUWarps * 32, smem, st>>>(
-        twojmax, reinterpret_cast<const float4*>(u_half), bs, nsnap, tile0, ntiles, c->tables.tri_d + c->tables.tri_off[k],
-        c->tables.tri_n[k], c->tables.units_d + c->tables.unit_off[k], nbr_cnt, (float)(wself * wself * wself), B,
-        c->tables.err_d);
+                      int64_t ntiles, const int* nbr_cnt, double wself, float* B, cudaStream_t st, int variant) {
+    if (variant == 1) launch_zb_alt(c, twojmax, u_half, bs, nsnap, tile0, ntiles, nbr_cnt, wself, B, st);
+    else zb_units_launch<kZbUWarps>(c, twojmax, u_half, bs, nsnap, tile0, ntiles, nbr_cnt, wself, B, st);
 }
 
 }  // namespace mala

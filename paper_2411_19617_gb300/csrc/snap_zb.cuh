@@ -4,6 +4,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "mala_internal.h"
@@ -227,7 +228,7 @@ __global__ void __launch_bounds__(kZbWarps * 32)
 // sums meet in 64-bit fixed point (2^-32) through shared-memory atomics:
 // integer addition is associative, so B does not depend on the warp order.
 
-constexpr int kZbUWarps = 16;
+constexpr int kZbUWarps = 16;                // default warps per CTA (the tuner may pick another variant)
 constexpr float kFixLimit = 1.0e9f;          // |partial| bound that keeps 16 partials inside int64
 
 __device__ __forceinline__ float4 lds4(uint32_t addr) {
@@ -375,11 +376,11 @@ __device__ __forceinline__ float2 unit_pairs(uint32_t sbase, int ma, int m1a, fl
     return make_float2(s * (2.f * acc.x + accm.x), s * (2.f * acc.y + accm.y));
 }
 
-// this warp's units (ma | m1a << 4 | twice << 8) of one triple, starting at `first`
-template <int J1, int J2, int J>
+// this warp's units (ma | m1a << 4 | twice << 8) of one triple, starting at `first`, every W-th
+template <int J1, int J2, int J, int W>
 __device__ __forceinline__ float2 triple_units(uint32_t su, const unsigned short* __restrict__ ul, int n, int first) {
     float2 acc = make_float2(0.f, 0.f);
-    for (int i = first; i < n; i += kZbUWarps) {
+    for (int i = first; i < n; i += W) {
         const int e = ul[i];
         const float2 r = unit_pairs<J1, J2, J>(su, e & 0xf, (e >> 4) & 0xf, (e & 0x100) ? 2.f : 1.f);
         acc.x += r.x;
@@ -388,14 +389,14 @@ __device__ __forceinline__ float2 triple_units(uint32_t su, const unsigned short
     return acc;
 }
 
-template <int LO, int HI>
+template <int LO, int HI, int W>
 __device__ __forceinline__ float2 triple_dispatch(int id, uint32_t su, const unsigned short* ul, int n, int first) {
     if constexpr (HI - LO == 1) {
-        return triple_units<triple_field(LO, 0), triple_field(LO, 1), triple_field(LO, 2)>(su, ul, n, first);
+        return triple_units<triple_field(LO, 0), triple_field(LO, 1), triple_field(LO, 2), W>(su, ul, n, first);
     } else {
         constexpr int MIDI = (LO + HI) / 2;
-        if (id < MIDI) return triple_dispatch<LO, MIDI>(id, su, ul, n, first);
-        return triple_dispatch<MIDI, HI>(id, su, ul, n, first);
+        if (id < MIDI) return triple_dispatch<LO, MIDI, W>(id, su, ul, n, first);
+        return triple_dispatch<MIDI, HI, W>(id, su, ul, n, first);
     }
 }
 
@@ -447,7 +448,9 @@ __device__ __forceinline__ void zb_fetch(uint32_t dst, const void* src, uint32_t
 // (128 KB at twojmax 10) comes in by one bulk copy; the next pair's block is
 // meanwhile pulled into L2, so the copy reads L2 rather than HBM.
 // tri: per triple of this twojmax, int4 (global id, first unit, unit count, output column)
-__global__ void __launch_bounds__(kZbUWarps * 32, 1)
+// W: warps per CTA; units are dealt round-robin, so every W gives the same bits
+template <int W>
+__global__ void __launch_bounds__(W * 32, 1)
     k_zb_units(int tj, const float4* __restrict__ u, const BatchSnap* __restrict__ batch, int nsnap, int64_t tile0,
                int64_t ntiles,
                const int4* __restrict__ tri, int ntri, const unsigned short* __restrict__ units,
@@ -501,9 +504,9 @@ __global__ void __launch_bounds__(kZbUWarps * 32, 1)
         const uint32_t su = sbuf0 + (uint32_t)lane * 16u;
         for (int t = 0; t < ntri && !vacuum; ++t) {
             const int4 d = __ldg(tri + t);  // (gid, start, count, column)
-            const int first = ((warp - d.y) % kZbUWarps + kZbUWarps) % kZbUWarps;
+            const int first = ((warp - d.y) % W + W) % W;
             if (first >= d.z) continue;
-            const float2 acc = triple_dispatch<0, n_triples(kTJMax)>(d.x, su, units + d.y, d.z, first);
+            const float2 acc = triple_dispatch<0, n_triples(kTJMax), W>(d.x, su, units + d.y, d.z, first);
             const bool ok = fabsf(acc.x) < kFixLimit && fabsf(acc.y) < kFixLimit;
             bad |= !ok;
             atomicAdd(&sacc[d.w * 64 + lane], (unsigned long long)(ok ? to_fixed(acc.x) : 0ll));
@@ -546,7 +549,7 @@ __global__ void __launch_bounds__(kZbUWarps * 32, 1)
             }
         }
         __syncthreads();
-        for (int pl = warp; pl < 64; pl += kZbUWarps) {
+        for (int pl = warp; pl < 64; pl += W) {
             const long long q = spix[pl];
             if (q < 0) continue;
             for (int t = lane; t < nB; t += 32) B[(size_t)q * nB + t] = out[pl * ldo + t];
@@ -563,6 +566,23 @@ __global__ void __launch_bounds__(kZbUWarps * 32, 1)
 
 }  // namespace
 
+
+// the FP32 units kernel with W warps per CTA, persistent over tile pairs (one CTA per SM)
+template <int W>
+inline void zb_units_launch(Ctx* c, int twojmax, const float* u_half, const BatchSnap* bs, int nsnap, int64_t tile0,
+                            int64_t ntiles, const int* nbr_cnt, double wself, float* B, cudaStream_t st) {
+    if (ntiles <= 0) return;
+    const size_t smem = sizeof(float4) * (size_t)n_half(twojmax) * 32 +
+                        sizeof(long long) * (size_t)n_triples(twojmax) * 64 + 2 * sizeof(uint64_t) + 64 * sizeof(long long);
+    cudaFuncSetAttribute(k_zb_units<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int k = twojmax / 2;
+    const int64_t npairs = (ntiles + 1) / 2;
+    const int grid = (int)std::min<int64_t>(npairs, std::max(1, c->num_sms));
+    k_zb_units<W><<<(unsigned)grid, W * 32, smem, st>>>(
+        twojmax, reinterpret_cast<const float4*>(u_half), bs, nsnap, tile0, ntiles, c->tables.tri_d + c->tables.tri_off[k],
+        c->tables.tri_n[k], c->tables.units_d + c->tables.unit_off[k], nbr_cnt, (float)(wself * wself * wself), B,
+        c->tables.err_d);
+}
 
 template <class T>
 inline void zb_launch_impl(const void*, int twojmax, const T* u_half, const BatchSnap* bs, int nsnap,

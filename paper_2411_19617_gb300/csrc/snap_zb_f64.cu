@@ -12,7 +12,7 @@ int upload_zb_lists_f64(const int* lists, int bytes) {
 
 template <>
 void launch_zb<double>(Ctx* c, int twojmax, const double* u_half, const BatchSnap* bs, int nsnap, int64_t tile0,
-                       int64_t ntiles, const int*, double, double* B, cudaStream_t st) {
+                       int64_t ntiles, const int*, double, double* B, cudaStream_t st, int) {
     if (ntiles <= 0) return;
     cudaFuncSetAttribute(k_zb<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     zb_launch_impl<double>(nullptr, twojmax, u_half, bs, nsnap, tile0, ntiles, c->tables.cg_d, B, st);

@@ -71,3 +71,10 @@ def test_force_bindings_check_dtype_and_shape_before_the_library():
         ctx.descriptor_forces(snap, bp, torch.zeros((63, 14), dtype=torch.float32), api.MIXED)
     with pytest.raises(ValueError, match="CUDA"):
         ctx.descriptor_forces(snap, bp, torch.zeros((64, 14), dtype=torch.float32), api.MIXED)
+
+
+def test_tuning_variant_counts_host_only():
+    from paper_2411_19617_gb300 import api, build
+    build.build()
+    n_ui, n_zb = api.tuning_variants()
+    assert n_ui == 3 and n_zb == 2

@@ -145,7 +145,11 @@ def test_slots_overlap_on_the_device():
                                             np.full(91, 10.0), np.full(91, 0.05)))
     rng = np.random.default_rng(3)
     snaps = [wl.bulk_snapshot("Al", 256, rng, spacing=0.2) for _ in range(4)]
-    ts = [c.submit(s, bp, mA if i % 2 == 0 else mB, eg, api.MIXED, n_electrons=0.0) for i, s in enumerate(snaps)]
+    models = [mA if i % 2 == 0 else mB for i in range(4)]
+    # reachable electron counts: N(mu = 0) of each request's own DOS
+    nes = [c.electron_count(c.predict(s, bp, m, eg, api.MIXED, n_electrons=0.0, raise_on_bracket=False)["dos"],
+                            eg, 0.0) for s, m in zip(snaps, models)]
+    ts = [c.submit(s, bp, m, eg, api.MIXED, n_electrons=ne) for s, m, ne in zip(snaps, models, nes)]
     iv = []
     for t in ts:
         r = c.wait(t, timeout_s=120.0)
