@@ -496,7 +496,7 @@ __global__ void k_sum_rows(const double* __restrict__ part, int64_t nt, int nE, 
 // partial sums of n give the electron-count check.  Every wait is bounded;
 // on expiry the CTA sets *err, lets its copies land and returns.
 constexpr int kDensThreads = 256;
-constexpr int kDensStages = 4;
+constexpr int kDensStages = 6;
 constexpr int kDensTileBytes = 32768;                      // payload of one stage
 constexpr int kDensStageBytes = kDensTileBytes + 32;       // + the 16-byte rounding at both ends
 constexpr long long kDensWaitCycles = 2000000000LL;        // about one second

@@ -224,12 +224,15 @@ __global__ void __launch_bounds__(kZbWarps * 32)
 // u[J-ma][J-mb] = (-1)^(ma-mb) conj(u[ma][mb]) with compile-time column signs,
 // the run-time row parities folding into the unit's scalar.  The units of all
 // triples are dealt round-robin to the warps, which therefore execute the same
-// triple's code at nearly the same time (instruction-cache locality).  Partial
-// sums meet in 64-bit fixed point (2^-32) through shared-memory atomics:
-// integer addition is associative, so B does not depend on the warp order.
+// triple's code at nearly the same time (instruction-cache locality).  Every
+// unit's value meets its column's sum in 64-bit fixed point (2^-32) through a
+// shared-memory atomic: integer addition is associative, so B depends neither
+// on the warp order nor on the number of warps.
 
 constexpr int kZbUWarps = 16;                // default warps per CTA (the tuner may pick another variant)
-constexpr float kFixLimit = 1.0e9f;          // |partial| bound that keeps 16 partials inside int64
+// |value| bound per unit: a column's sum in 2^-32 fixed point must stay below
+// 2^31 = 2.1e9 to fit int64, and a column takes at most 44 units at twojmax 10
+constexpr float kFixLimit = 1.0e7f;
 
 __device__ __forceinline__ float4 lds4(uint32_t addr) {
     float4 v;
@@ -376,30 +379,6 @@ __device__ __forceinline__ float2 unit_pairs(uint32_t sbase, int ma, int m1a, fl
     return make_float2(s * (2.f * acc.x + accm.x), s * (2.f * acc.y + accm.y));
 }
 
-// this warp's units (ma | m1a << 4 | twice << 8) of one triple, starting at `first`, every W-th
-template <int J1, int J2, int J, int W>
-__device__ __forceinline__ float2 triple_units(uint32_t su, const unsigned short* __restrict__ ul, int n, int first) {
-    float2 acc = make_float2(0.f, 0.f);
-    for (int i = first; i < n; i += W) {
-        const int e = ul[i];
-        const float2 r = unit_pairs<J1, J2, J>(su, e & 0xf, (e >> 4) & 0xf, (e & 0x100) ? 2.f : 1.f);
-        acc.x += r.x;
-        acc.y += r.y;
-    }
-    return acc;
-}
-
-template <int LO, int HI, int W>
-__device__ __forceinline__ float2 triple_dispatch(int id, uint32_t su, const unsigned short* ul, int n, int first) {
-    if constexpr (HI - LO == 1) {
-        return triple_units<triple_field(LO, 0), triple_field(LO, 1), triple_field(LO, 2), W>(su, ul, n, first);
-    } else {
-        constexpr int MIDI = (LO + HI) / 2;
-        if (id < MIDI) return triple_dispatch<LO, MIDI, W>(id, su, ul, n, first);
-        return triple_dispatch<MIDI, HI, W>(id, su, ul, n, first);
-    }
-}
-
 // Float -> 64-bit fixed point (2^-32 units), rounded to nearest with ties away
 // from zero, by integer operations on the float's fields (no FP64); requires
 // |v| < kFixLimit (v * 2^32 < 2^62).
@@ -414,6 +393,34 @@ __device__ __forceinline__ long long to_fixed(float v) {
     else if (sh > -25) q = (m + (1ull << (-sh - 1))) >> (-sh);
     else q = 0;
     return (b >> 31) ? -(long long)q : (long long)q;
+}
+
+// this warp's units (ma | m1a << 4 | twice << 8) of one triple, starting at
+// `first`, every W-th; each unit's value meets the column's sums in fixed point
+// on its own, so the result does not depend on how units are dealt to warps
+template <int J1, int J2, int J, int W>
+__device__ __forceinline__ void triple_units(uint32_t su, const unsigned short* __restrict__ ul, int n, int first,
+                                             unsigned long long* acc, bool& bad) {
+    for (int i = first; i < n; i += W) {
+        const int e = ul[i];
+        const float2 r = unit_pairs<J1, J2, J>(su, e & 0xf, (e >> 4) & 0xf, (e & 0x100) ? 2.f : 1.f);
+        const bool ok = fabsf(r.x) < kFixLimit && fabsf(r.y) < kFixLimit;
+        bad |= !ok;
+        atomicAdd(acc, (unsigned long long)(ok ? to_fixed(r.x) : 0ll));       // point of the pair's first tile
+        atomicAdd(acc + 32, (unsigned long long)(ok ? to_fixed(r.y) : 0ll));  // and of its second
+    }
+}
+
+template <int LO, int HI, int W>
+__device__ __forceinline__ void triple_dispatch(int id, uint32_t su, const unsigned short* ul, int n, int first,
+                                                unsigned long long* acc, bool& bad) {
+    if constexpr (HI - LO == 1) {
+        triple_units<triple_field(LO, 0), triple_field(LO, 1), triple_field(LO, 2), W>(su, ul, n, first, acc, bad);
+    } else {
+        constexpr int MIDI = (LO + HI) / 2;
+        if (id < MIDI) triple_dispatch<LO, MIDI, W>(id, su, ul, n, first, acc, bad);
+        else triple_dispatch<MIDI, HI, W>(id, su, ul, n, first, acc, bad);
+    }
 }
 
 // 64-bit fixed point (2^-32 units) -> float: the two words converted apart
@@ -448,7 +455,8 @@ __device__ __forceinline__ void zb_fetch(uint32_t dst, const void* src, uint32_t
 // (128 KB at twojmax 10) comes in by one bulk copy; the next pair's block is
 // meanwhile pulled into L2, so the copy reads L2 rather than HBM.
 // tri: per triple of this twojmax, int4 (global id, first unit, unit count, output column)
-// W: warps per CTA; units are dealt round-robin, so every W gives the same bits
+// W: warps per CTA; units are dealt round-robin and each unit's value is added
+// in fixed point on its own, so every W gives the same bits
 template <int W>
 __global__ void __launch_bounds__(W * 32, 1)
     k_zb_units(int tj, const float4* __restrict__ u, const BatchSnap* __restrict__ batch, int nsnap, int64_t tile0,
@@ -506,11 +514,7 @@ __global__ void __launch_bounds__(W * 32, 1)
             const int4 d = __ldg(tri + t);  // (gid, start, count, column)
             const int first = ((warp - d.y) % W + W) % W;
             if (first >= d.z) continue;
-            const float2 acc = triple_dispatch<0, n_triples(kTJMax), W>(d.x, su, units + d.y, d.z, first);
-            const bool ok = fabsf(acc.x) < kFixLimit && fabsf(acc.y) < kFixLimit;
-            bad |= !ok;
-            atomicAdd(&sacc[d.w * 64 + lane], (unsigned long long)(ok ? to_fixed(acc.x) : 0ll));
-            atomicAdd(&sacc[d.w * 64 + 32 + lane], (unsigned long long)(ok ? to_fixed(acc.y) : 0ll));
+            triple_dispatch<0, n_triples(kTJMax), W>(d.x, su, units + d.y, d.z, first, &sacc[d.w * 64 + lane], bad);
         }
         __syncthreads();
         // grid points of the pair's 64 (tile, lane) slots
