@@ -281,6 +281,18 @@ def _timed_calls(torch, calls, fn):
     return ev0.elapsed_time(ev1) / calls
 
 
+def _reachable_ne(ctx, dos, eg):
+    """N(mu = 0) of a DOS (the reading for random networks); if that count has no root on the
+    bisection bracket (a random network's DOS can dip below zero), the midpoint of the counts
+    at the bracket's ends, which always has one."""
+    ne = ctx.electron_count(dos, eg, 0.0)
+    lo = ctx.electron_count(dos, eg, eg.e0_eV - 20.0 * eg.kT_eV)
+    hi = ctx.electron_count(dos, eg, eg.e0_eV + (eg.n_E - 1) * eg.de_eV + 20.0 * eg.kT_eV)
+    if (lo - ne) * (hi - ne) < 0.0:
+        return ne
+    return 0.5 * (lo + hi)
+
+
 def _pairs(ctx, snaps, rcut):
     return int(sum(int(ctx.neighbor_lists(s, rcut, cap=0)[0].sum().item()) for s in snaps))
 
@@ -302,7 +314,7 @@ def workload_legs(ctx, api, wl, roofline, torch, calls, fp32_peak, fp64_peak, bf
         model = api.Model(ctx, mlp)
         first = ctx.predict_batch(snaps, bp, model, eg, api.MIXED, n_electrons=[0.0] * len(snaps),
                                   raise_on_bracket=False)
-        nes = [ctx.electron_count(r["dos"], eg, 0.0) for r in first]
+        nes = [_reachable_ne(ctx, r["dos"], eg) for r in first]
         P = sum(s.n_points for s in snaps)
         ms = _timed_calls(torch, calls, lambda: ctx.predict_batch(snaps, bp, model, eg, api.MIXED, n_electrons=nes,
                                                                   raise_on_bracket=False))
@@ -331,7 +343,7 @@ def workload_legs(ctx, api, wl, roofline, torch, calls, fp32_peak, fp64_peak, bf
         mlp = wl.with_input_scaling(mlp, mean, 1.0 / (std + 1e-12))
         model = api.Model(ctx, mlp)
         r = ctx.predict(snap, bp, model, eg, api.MIXED, n_electrons=0.0, raise_on_bracket=False)
-        ne = ctx.electron_count(r["dos"], eg, 0.0)
+        ne = _reachable_ne(ctx, r["dos"], eg)
         P = snap.n_points
         ms = _timed_calls(torch, calls, lambda: ctx.predict(snap, bp, model, eg, api.MIXED, n_electrons=ne))
         ctx.profile(True)
@@ -357,7 +369,7 @@ def workload_legs(ctx, api, wl, roofline, torch, calls, fp32_peak, fp64_peak, bf
         mlp = wl.with_input_scaling(mlp, B.mean(0).cpu().numpy(), 1.0 / (B.std(0).cpu().numpy() + 1e-12))
         model = api.Model(ctx, mlp)
         r = ctx.predict(snap, bp, model, eg, api.FP64_PLAIN, n_electrons=0.0, raise_on_bracket=False)
-        ne = ctx.electron_count(r["dos"], eg, 0.0)
+        ne = _reachable_ne(ctx, r["dos"], eg)
         P = snap.n_points
         ms = _timed_calls(torch, max(calls, 5), lambda: ctx.predict(snap, bp, model, eg, api.FP64_PLAIN,
                                                                     n_electrons=ne))
@@ -789,6 +801,7 @@ def run_ours(args):
                 "roofline": roof, "rooflines": roofs,
                 "measured_peaks_tflops": {"fp32_scalar": fp32_scalar, "fp32_packed": fp32_packed, "fp64": fp64_peak,
                                           "sms": n_sms},
+                "tuning": ctx.tuning_report().strip().splitlines(),
                 "cpu_baseline": cpu, "descriptor_error": derr, "e2e": e2e, "gpu_launches": int(launches),
                 "clocks": clk, "kernels": kernels, "serving": serving, "workloads": workloads, "forces": forces,
                 "ace": ace_res, "gaussian": gauss_res,

@@ -478,12 +478,22 @@ __global__ void k_colsum(const TL* __restrict__ L, int64_t P, int nE, double* __
     }
 }
 
-__global__ void k_sum_rows(const double* __restrict__ part, int64_t nt, int nE, double* __restrict__ out) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= nE) return;
+// out[c] = sum_t part[t][c]: one CTA per column, threads over row strides, then a
+// fixed-order tree over the threads (deterministic)
+constexpr int kSumRowsThreads = 256;
+__global__ void __launch_bounds__(kSumRowsThreads) k_sum_rows(const double* __restrict__ part, int64_t nt, int nE,
+                                                              double* __restrict__ out) {
+    __shared__ double red[kSumRowsThreads];
+    const int c = blockIdx.x;
     double s = 0.0;
-    for (int64_t t = 0; t < nt; ++t) s += part[t * nE + c];
-    out[c] = s;
+    for (int64_t t = threadIdx.x; t < nt; t += kSumRowsThreads) s += part[t * nE + c];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = kSumRowsThreads / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[c] = red[0];
 }
 
 // n(r) = sum_xi w0_xi LDOS(r, xi): one streaming pass over the LDOS.
@@ -908,7 +918,7 @@ int integrate(Ctx* c, const void* ldos, int64_t P, double volume, const mala_ene
                 MALA_PROF(c, "k_dos_reduce", st,
                           (k_colsum<double><<<(unsigned)ntile, 256, 0, st>>>(static_cast<const double*>(ldos), P, nE,
                                                                             part)));
-            MALA_PROF(c, "k_sum_rows", st, (k_sum_rows<<<(nE + 127) / 128, 128, 0, st>>>(part, ntile, nE, dsum)));
+            MALA_PROF(c, "k_sum_rows", st, (k_sum_rows<<<nE, kSumRowsThreads, 0, st>>>(part, ntile, nE, dsum)));
         } else {
             MALA_CUDA_TRY(cudaMemsetAsync(dsum, 0, sizeof(double) * nE, st));
         }
@@ -1022,7 +1032,7 @@ int integrate_noalloc(Ctx* c, const void* ldos, int64_t P, double volume, const 
                                                                           nE, part);
             else
                 k_colsum<double><<<(unsigned)ntile, 256, 0, st>>>(static_cast<const double*>(ldos), P, nE, part);
-            k_sum_rows<<<(nE + 127) / 128, 128, 0, st>>>(part, ntile, nE, dsum);
+            k_sum_rows<<<nE, kSumRowsThreads, 0, st>>>(part, ntile, nE, dsum);
         } else {
             MALA_CUDA_TRY(cudaMemsetAsync(dsum, 0, sizeof(double) * nE, st));
         }

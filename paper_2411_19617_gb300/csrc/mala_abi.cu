@@ -337,7 +337,7 @@ static int run_descriptors(Ctx* c, int nsnap, const mala_snapshot* snaps, const 
             const int code = c->host_ints[2];
             cudaMemsetAsync(c->tables.err_d, 0, sizeof(int), st);
             if (code == 2) return fail(MALA_ERR_TIMEOUT, "compute_zi/bi: a copy into shared memory did not complete in time");
-            return fail(MALA_ERR_UNSUPPORTED, "a bispectrum partial sum exceeded 1e7 (outside the fixed-point range)");
+            return fail(MALA_ERR_UNSUPPORTED, "a bispectrum partial sum exceeded 1e8 (outside the fixed-point range)");
         }
         if (dbg) dbg->kmax = maxcnt;
         if (gauss_mode) return MALA_OK;

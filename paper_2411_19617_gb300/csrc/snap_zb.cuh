@@ -224,15 +224,16 @@ __global__ void __launch_bounds__(kZbWarps * 32)
 // u[J-ma][J-mb] = (-1)^(ma-mb) conj(u[ma][mb]) with compile-time column signs,
 // the run-time row parities folding into the unit's scalar.  The units of all
 // triples are dealt round-robin to the warps, which therefore execute the same
-// triple's code at nearly the same time (instruction-cache locality).  Every
-// unit's value meets its column's sum in 64-bit fixed point (2^-32) through a
-// shared-memory atomic: integer addition is associative, so B depends neither
-// on the warp order nor on the number of warps.
+// triple's code at nearly the same time (instruction-cache locality).  The
+// units of a triple form 16 fixed groups; each group's FP32 sum meets its
+// column's total in 64-bit fixed point (2^-32) through a shared-memory atomic:
+// integer addition is associative, so B depends neither on the warp order nor
+// on the number of warps.
 
 constexpr int kZbUWarps = 16;                // default warps per CTA (the tuner may pick another variant)
-// |value| bound per unit: a column's sum in 2^-32 fixed point must stay below
-// 2^31 = 2.1e9 to fit int64, and a column takes at most 44 units at twojmax 10
-constexpr float kFixLimit = 1.0e7f;
+// |value| bound per group sum: a column's total in 2^-32 fixed point must stay
+// below 2^31 = 2.1e9 to fit int64, and a column takes at most 16 group sums
+constexpr float kFixLimit = 1.0e8f;
 
 __device__ __forceinline__ float4 lds4(uint32_t addr) {
     float4 v;
@@ -395,19 +396,29 @@ __device__ __forceinline__ long long to_fixed(float v) {
     return (b >> 31) ? -(long long)q : (long long)q;
 }
 
-// this warp's units (ma | m1a << 4 | twice << 8) of one triple, starting at
-// `first`, every W-th; each unit's value meets the column's sums in fixed point
-// on its own, so the result does not depend on how units are dealt to warps
+// A triple's units (ma | m1a << 4 | twice << 8) fall into kZbGroups fixed groups
+// (unit i in group i mod kZbGroups); a group's values are summed in FP32 in unit
+// order and the sum meets its column's total in fixed point.  This warp takes
+// the groups first_group, first_group + W, ...  The groups do not depend on W,
+// so every warp count gives the same bits (with W = kZbGroups a warp holds
+// exactly one group per triple).
+constexpr int kZbGroups = 16;
+
 template <int J1, int J2, int J, int W>
-__device__ __forceinline__ void triple_units(uint32_t su, const unsigned short* __restrict__ ul, int n, int first,
+__device__ __forceinline__ void triple_units(uint32_t su, const unsigned short* __restrict__ ul, int n, int first_group,
                                              unsigned long long* acc, bool& bad) {
-    for (int i = first; i < n; i += W) {
-        const int e = ul[i];
-        const float2 r = unit_pairs<J1, J2, J>(su, e & 0xf, (e >> 4) & 0xf, (e & 0x100) ? 2.f : 1.f);
-        const bool ok = fabsf(r.x) < kFixLimit && fabsf(r.y) < kFixLimit;
+    for (int g = first_group; g < kZbGroups && g < n; g += W) {
+        float2 s = make_float2(0.f, 0.f);
+        for (int i = g; i < n; i += kZbGroups) {
+            const int e = ul[i];
+            const float2 r = unit_pairs<J1, J2, J>(su, e & 0xf, (e >> 4) & 0xf, (e & 0x100) ? 2.f : 1.f);
+            s.x += r.x;
+            s.y += r.y;
+        }
+        const bool ok = fabsf(s.x) < kFixLimit && fabsf(s.y) < kFixLimit;
         bad |= !ok;
-        atomicAdd(acc, (unsigned long long)(ok ? to_fixed(r.x) : 0ll));       // point of the pair's first tile
-        atomicAdd(acc + 32, (unsigned long long)(ok ? to_fixed(r.y) : 0ll));  // and of its second
+        atomicAdd(acc, (unsigned long long)(ok ? to_fixed(s.x) : 0ll));       // point of the pair's first tile
+        atomicAdd(acc + 32, (unsigned long long)(ok ? to_fixed(s.y) : 0ll));  // and of its second
     }
 }
 
@@ -455,14 +466,14 @@ __device__ __forceinline__ void zb_fetch(uint32_t dst, const void* src, uint32_t
 // (128 KB at twojmax 10) comes in by one bulk copy; the next pair's block is
 // meanwhile pulled into L2, so the copy reads L2 rather than HBM.
 // tri: per triple of this twojmax, int4 (global id, first unit, unit count, output column)
-// W: warps per CTA; units are dealt round-robin and each unit's value is added
-// in fixed point on its own, so every W gives the same bits
+// W: warps per CTA (<= kZbGroups); the fixed groups of units make every W give the same bits
 template <int W>
 __global__ void __launch_bounds__(W * 32, 1)
     k_zb_units(int tj, const float4* __restrict__ u, const BatchSnap* __restrict__ batch, int nsnap, int64_t tile0,
                int64_t ntiles,
                const int4* __restrict__ tri, int ntri, const unsigned short* __restrict__ units,
                const int* __restrict__ nbr_cnt, float wself3, float* __restrict__ B, int* __restrict__ err) {
+    static_assert(W <= kZbGroups, "a warp count above the group count would leave warps idle");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nh = n_half(tj);
     const int nB = n_triples(tj);
@@ -512,7 +523,7 @@ __global__ void __launch_bounds__(W * 32, 1)
         const uint32_t su = sbuf0 + (uint32_t)lane * 16u;
         for (int t = 0; t < ntri && !vacuum; ++t) {
             const int4 d = __ldg(tri + t);  // (gid, start, count, column)
-            const int first = ((warp - d.y) % W + W) % W;
+            const int first = ((warp - d.y) % W + W) % W;  // this warp's first group (rotated per triple)
             if (first >= d.z) continue;
             triple_dispatch<0, n_triples(kTJMax), W>(d.x, su, units + d.y, d.z, first, &sacc[d.w * 64 + lane], bad);
         }
