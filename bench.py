@@ -410,8 +410,8 @@ def forces_leg(ctx, api, roofline, model, snap, bp, eg, ne, calls, peak_tflops):
     ctx.profile(True)
     ctx.band_forces(snap, bp, model, eg, api.MIXED, n_electrons=ne)
     kern = {}
-    for k in ("k_neighbors", "k_ui", "k_u_expand", "k_zb", "k_mlp", "k_fermi", "k_egrad", "k_bwd_elementwise", "k_yi",
-              "k_force"):
+    for k in ("k_neighbors", "k_ui", "k_u_expand", "k_zb", "k_mlp_in", "k_mlp", "k_fermi", "k_egrad", "k_gemm_rows",
+              "k_bwd_elementwise", "k_yi", "k_force"):
         t, n = ctx.profile_get(k)
         kern[k] = {"ms": t, "launches": n}
     ctx.profile(False)

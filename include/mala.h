@@ -286,7 +286,8 @@ int mala_electron_count(mala_ctx* ctx, const double* dos_host, const mala_energy
  * right to left as the paper prescribes: a vector per grid point, the
  * network's backward pass, then the descriptor adjoint.  Each factor has its
  * own entry point.  MALA_MIXED: FP32 descriptors and u, FP32 backward pass
- * (cuBLAS SGEMM for the dense products), FP32 adjoint, forces summed per atom
+ * (the library's own register-tiled GEMM for the dense products), FP32
+ * adjoint, forces summed per atom
  * in 2^-40 fixed point (order-independent).  MALA_FP64_PLAIN: the same in
  * FP64.  Synchronous; forces_host is [n_atoms][3] doubles in eV/Angstrom. */
 

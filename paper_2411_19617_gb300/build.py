@@ -65,7 +65,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     newest = max(os.path.getmtime(o) for o in objs)
     if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < newest:
         tmp = LIB + f".tmp{os.getpid()}"
-        cmd = [_nvcc(), *ARCH, "-shared", "-o", tmp, *sorted(objs), "-lcudart", "-lcublas"]
+        cmd = [_nvcc(), *ARCH, "-shared", "-o", tmp, *sorted(objs), "-lcudart"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -723,18 +723,96 @@ __global__ void __launch_bounds__(kDensThreads) k_density(const TL* __restrict__
     }
 }
 
+// BF16 rows of even length: direct loads instead of staged tiles.  A group of
+// G lanes takes a row; every lane issues its (up to kDensMaxWpl) 4-byte pairs of
+// the row back to back (streaming loads, read once), then one FMA chain pair
+// with the weights from shared memory (one broadcast 8-byte read per pair) and
+// a shuffle reduction over the group.  At most 42 registers a thread let 6 CTAs
+// of 256 threads share an SM, about 100 KB of loads in flight per SM.
+constexpr int kDensDirectCtasPerSm = 6;
+
+__global__ void __launch_bounds__(kDensThreads, kDensDirectCtasPerSm)
+    k_density_direct(const __nv_bfloat16* __restrict__ L, int64_t P, int nE, int G, int wpl,
+                     const float* __restrict__ w0, float* __restrict__ n, double* __restrict__ part) {
+    extern __shared__ __align__(16) float swd[];  // [nE] weights, then the CTA's partial sums
+    double* sred = reinterpret_cast<double*>(swd + ((nE + 3) & ~3));
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int g = tid & (G - 1), grp = tid / G, ngrp = kDensThreads / G;
+    const int nw = nE >> 1;
+    for (int i = tid; i < nE; i += kDensThreads) swd[i] = w0[i];
+    __syncthreads();
+    const float2* sw2 = reinterpret_cast<const float2*>(swd);
+    double acc = 0.0;
+    const int64_t stride = (int64_t)gridDim.x * ngrp;
+    for (int64_t rb = (int64_t)blockIdx.x * ngrp; rb < P; rb += stride) {  // uniform over the CTA
+        const int64_t r = rb + grp;
+        float s0 = 0.f, s1 = 0.f;
+        if (r < P) {
+            const uint32_t* row32 = reinterpret_cast<const uint32_t*>(L + r * nE);
+            uint32_t v[kDensMaxWpl];
+#pragma unroll
+            for (int k = 0; k < kDensMaxWpl; ++k) {
+                const int q = g + k * G;
+                v[k] = (k < wpl && q < nw) ? __ldcs(row32 + q) : 0u;
+            }
+#pragma unroll
+            for (int k = 0; k < kDensMaxWpl; ++k) {
+                const int q = g + k * G;
+                if (k < wpl && q < nw) {
+                    const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&v[k]));
+                    const float2 w = sw2[q];
+                    s0 = fmaf(f.x, w.x, s0);
+                    s1 = fmaf(f.y, w.y, s1);
+                }
+            }
+        }
+        float s = s0 + s1;
+        for (int o = G >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (r < P && g == 0) {
+            n[r] = s;
+            acc += (double)s;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) sred[tid >> 5] = acc;
+    __syncthreads();
+    if (tid == 0) {
+        double t = 0.0;
+        for (int w = 0; w < kDensThreads / 32; ++w) t += sred[w];
+        part[blockIdx.x] = t;
+    }
+}
+
+// the direct path applies: BF16, an even row length whose pairs fit the registers, 4-byte aligned rows
+inline bool density_direct(int nE, int elem_bytes) {
+    return elem_bytes == 2 && dens_plan(nE, elem_bytes).wpl > 0;
+}
+
 template <class TL, class TW>
 void launch_density(const TL* L, int64_t P, int nE, const TW* w0, TW* n, double* part, int grid, int* err,
                     cudaStream_t st) {
     const DensPlan d = dens_plan(nE, (int)sizeof(TL));
+    if constexpr (sizeof(TL) == 2) {
+        if (density_direct(nE, 2) && (reinterpret_cast<uintptr_t>(L) & 3) == 0) {
+            const size_t smem = sizeof(float) * (size_t)((nE + 3) & ~3) + sizeof(double) * (kDensThreads / 32);
+            k_density_direct<<<grid, kDensThreads, smem, st>>>(L, P, nE, d.G, d.wpl, w0, n, part);
+            return;
+        }
+    }
     const size_t smem = dens_smem_bytes(nE, (int)sizeof(TW));
     cudaFuncSetAttribute(k_density<TL, TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_density<TL, TW><<<grid, kDensThreads, smem, st>>>(L, P, nE, d.rows, d.G, d.wpl, w0, n, part, err);
 }
 
-// CTAs of the density pass: one per SM at most, never more than the tiles
+// CTAs of the density pass (the partial-sum rows it writes): the direct path
+// runs kDensDirectCtasPerSm per SM, the staged path one per SM, never more
+// than there are row groups or tiles
 inline int density_grid(int64_t P, int nE, int elem_bytes, int num_sms) {
     const DensPlan d = dens_plan(nE, elem_bytes);
+    if (density_direct(nE, elem_bytes)) {
+        const int64_t groups = (P + kDensThreads / d.G - 1) / (kDensThreads / d.G);
+        return (int)std::max<int64_t>(1, std::min<int64_t>(groups, (int64_t)std::max(1, num_sms) * kDensDirectCtasPerSm));
+    }
     const int64_t ntiles = (P + d.rows - 1) / d.rows;
     return (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, std::max(1, num_sms)));
 }

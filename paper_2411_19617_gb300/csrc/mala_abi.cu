@@ -474,7 +474,6 @@ void mala_destroy(mala_ctx* c) {
     DeviceScope dev_scope(c->device);
     server_stop(c);
     cudaDeviceSynchronize();
-    cublas_release(c);
     {
         // networks outliving their context keep only their host object
         std::lock_guard<std::mutex> lk(c->models_mu);

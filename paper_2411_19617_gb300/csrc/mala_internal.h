@@ -221,7 +221,6 @@ struct Ctx {
     ForceTables ftab;
     DevBuf ws_ftab, ws_force_y, ws_force_aux, ws_force_u, ws_force_nbr, ws_force_beta, ws_force_mlp, ws_force_g,
         ws_force_bt, ws_ace;
-    void* cublas = nullptr;  // cuBLAS handle of the network's backward GEMMs (created on first use)
     double* host_dos = nullptr;     // pinned [max N_E]
     size_t host_dos_len = 0;
     double* host_scalars = nullptr; // pinned small buffer
@@ -334,7 +333,7 @@ void launch_zb<double>(Ctx* c, int twojmax, const double* u_half, const BatchSna
 int zb_variant_count();
 int zb_variant_warps(int v);
 // the alternate-warp-count FP32 kernel (its own translation unit) and its constant tables
-constexpr int kZbWarpsAlt = 12;
+constexpr int kZbWarpsAlt = 8;
 void launch_zb_alt(Ctx* c, int twojmax, const float* u_half, const BatchSnap* bs, int nsnap, int64_t tile0,
                    int64_t ntiles, const int* nbr_cnt, double wself, float* B, cudaStream_t st);
 int upload_zb_alt_cg(const float2* cg2, int bytes);
@@ -392,7 +391,6 @@ int descriptor_adjoint(Ctx* c, const SnapDev& sd, const mala_snapshot* snap, con
 // beta[P][n_B] = sum_e v[e] dLDOS[p][e]/dB[p][:] (v device [n_E]); float for MIXED, double for FP64_PLAIN
 int mlp_backward(Ctx* c, const Model* m, const void* B, int64_t P, const double* v_dev, void* beta,
                  mala_precision prec, cudaStream_t st);
-void cublas_release(Ctx* c);
 // ACE descriptors (ace.cu): parameter check, column count, descriptors from a staged snapshot and its
 // complete neighbour lists (nl.dbg_*), out: [P][n_desc] float (MIXED) or double
 int check_ace_params(const mala_ace_params* ap);

@@ -10,10 +10,10 @@
 // recomputed (the forward pass of the LDOS keeps none), then
 //     delta_l = g_l (.) sigma'(z_l),  g_{l-1} = delta_l W_l,
 // with sigma'(z) read from the sign of h = sigma(z) (LeakyReLU keeps the sign),
-// and beta = g_0 (.) scale.  The dense products run as cuBLAS GEMMs (FP32 for
-// MALA_MIXED, FP64 for MALA_FP64_PLAIN); bias, activation, masks and the input
-// scaling are the elementwise kernels below.
-#include <cublas_v2.h>
+// and beta = g_0 (.) scale.  The dense products run in the register-tiled GEMM
+// below (FP32 for MALA_MIXED, FP64 for MALA_FP64_PLAIN, in the precision of the
+// chain's tests); bias, activation, masks and the input scaling are the
+// elementwise kernels below.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -87,31 +87,102 @@ unsigned ew_blocks(Ctx* c, int64_t n) {
     return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)c->num_sms * 32));
 }
 
-// C[P][N] (row-major) = X[P][K] W^T (W [N][K] row-major), or with trans_w = false C[P][N] = X[P][K] W (W [K][N])
-cublasStatus_t gemm_rows(cublasHandle_t h, bool trans_w, int64_t P, int N, int K, const float* W, const float* X,
-                         float* Cm) {
-    const float one = 1.f, zero = 0.f;
-    return cublasSgemm(h, trans_w ? CUBLAS_OP_T : CUBLAS_OP_N, CUBLAS_OP_N, N, (int)P, K, &one, W, trans_w ? K : N, X,
-                       K, &zero, Cm, N);
+// ---- row GEMM: C[P][N] = X[P][K] op(W), op(W) = W^T (W [N][K]) or W (W [K][N]) ----
+//
+// A CTA of 256 threads (16 x 16) computes a BM x BN tile of C, each thread a
+// contiguous TM x TN block (rows ty*TM.., columns tx*TN..), so a step of k
+// reads its operands as 16-byte vectors from shared memory.  K advances in
+// steps of BK: X as [BK][BM + pad] (the pad spreads the transposing stores over
+// the banks and keeps rows 16-byte aligned), op(W) as [BK][BN].  Every output
+// is one FMA chain over k in order, accumulated in T.
+template <class T> struct GemmShape;
+template <> struct GemmShape<float> { static constexpr int BM = 128, BN = 64, BK = 16, PAD = 4; };
+template <> struct GemmShape<double> { static constexpr int BM = 64, BN = 64, BK = 16, PAD = 2; };
+
+template <class T, bool TRANS>
+__global__ void __launch_bounds__(256) k_gemm_rows(const T* __restrict__ X, const T* __restrict__ W, int64_t P, int N,
+                                                   int K, T* __restrict__ Cm) {
+    constexpr int BM = GemmShape<T>::BM, BN = GemmShape<T>::BN, BK = GemmShape<T>::BK, PAD = GemmShape<T>::PAD;
+    constexpr int TM = BM / 16, TN = BN / 16;
+    constexpr int VEC = 16 / sizeof(T);  // elements per 16-byte vector
+    __shared__ __align__(16) T xs[BK][BM + PAD];
+    __shared__ __align__(16) T ws[BK][BN];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int64_t m0 = (int64_t)blockIdx.x * BM;
+    const int n0 = blockIdx.y * BN;
+    T acc[TM][TN];
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
+    for (int k0 = 0; k0 < K; k0 += BK) {
+        // X tile: rows m0.., columns k0..k0+BK (consecutive threads along k: coalesced rows)
+        for (int idx = threadIdx.x; idx < BM * BK; idx += 256) {
+            const int r = idx / BK, kk = idx - r * BK;
+            const int64_t m = m0 + r;
+            const int k = k0 + kk;
+            xs[kk][r] = (m < P && k < K) ? X[m * K + k] : T(0);
+        }
+        // op(W) tile: [BK][BN]
+        for (int idx = threadIdx.x; idx < BN * BK; idx += 256) {
+            int kk, c;
+            if (TRANS) {  // W [N][K]: consecutive threads along k
+                c = idx / BK;
+                kk = idx - c * BK;
+            } else {      // W [K][N]: consecutive threads along n
+                kk = idx / BN;
+                c = idx - kk * BN;
+            }
+            const int k = k0 + kk, n = n0 + c;
+            T v = T(0);
+            if (k < K && n < N) v = TRANS ? W[(size_t)n * K + k] : W[(size_t)k * N + n];
+            ws[kk][c] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            T a[TM], b[TN];
+#pragma unroll
+            for (int i = 0; i < TM; i += VEC)
+                *reinterpret_cast<uint4*>(&a[i]) = *reinterpret_cast<const uint4*>(&xs[kk][ty * TM + i]);
+#pragma unroll
+            for (int j = 0; j < TN; j += VEC)
+                *reinterpret_cast<uint4*>(&b[j]) = *reinterpret_cast<const uint4*>(&ws[kk][tx * TN + j]);
+#pragma unroll
+            for (int i = 0; i < TM; ++i)
+#pragma unroll
+                for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < TM; ++i) {
+        const int64_t m = m0 + ty * TM + i;
+        if (m >= P) continue;
+#pragma unroll
+        for (int j = 0; j < TN; ++j) {
+            const int n = n0 + tx * TN + j;
+            if (n < N) Cm[m * N + n] = acc[i][j];
+        }
+    }
 }
-cublasStatus_t gemm_rows(cublasHandle_t h, bool trans_w, int64_t P, int N, int K, const double* W, const double* X,
-                         double* Cm) {
-    const double one = 1.0, zero = 0.0;
-    return cublasDgemm(h, trans_w ? CUBLAS_OP_T : CUBLAS_OP_N, CUBLAS_OP_N, N, (int)P, K, &one, W, trans_w ? K : N, X,
-                       K, &zero, Cm, N);
+
+template <class T>
+int gemm_rows(bool trans_w, int64_t P, int N, int K, const T* W, const T* X, T* Cm, cudaStream_t st) {
+    constexpr int BM = GemmShape<T>::BM, BN = GemmShape<T>::BN;
+    const int64_t gx = (P + BM - 1) / BM;
+    if (gx > 0x7fffffff) return fail(MALA_ERR_UNSUPPORTED, "too many rows for the backward GEMM");
+    const dim3 grid((unsigned)gx, (unsigned)((N + BN - 1) / BN));
+    if (trans_w) k_gemm_rows<T, true><<<grid, 256, 0, st>>>(X, W, P, N, K, Cm);
+    else k_gemm_rows<T, false><<<grid, 256, 0, st>>>(X, W, P, N, K, Cm);
+    MALA_CUDA_TRY(cudaGetLastError());
+    return MALA_OK;
 }
 
 template <class T>
 int backward_impl(Ctx* c, const Model* m, const T* B, int64_t P, const double* v_dev, T* beta, cudaStream_t st) {
     const int nl = m->n_layers;
     const std::vector<int>& d = m->dims;
-    if (!c->cublas) {
-        cublasHandle_t h = nullptr;
-        if (cublasCreate(&h) != CUBLAS_STATUS_SUCCESS) return fail(MALA_ERR_CUDA, "cublasCreate failed");
-        c->cublas = h;
-    }
-    cublasHandle_t h = static_cast<cublasHandle_t>(c->cublas);
-    if (cublasSetStream(h, st) != CUBLAS_STATUS_SUCCESS) return fail(MALA_ERR_CUDA, "cublasSetStream failed");
     // parameters in T: W_l [d_{l+1}][d_l], b_l, shift, scale; then the vector u
     size_t npar = 2 * (size_t)d[0];
     for (int l = 0; l < nl; ++l) npar += (size_t)d[l] * d[l + 1] + d[l + 1];
@@ -170,8 +241,7 @@ int backward_impl(Ctx* c, const Model* m, const T* B, int64_t P, const double* v
     MALA_PROF(c, "k_bwd_elementwise", st,
               (k_in_std<T><<<ew_blocks(c, P * d[0]), 256, 0, st>>>(B, P, d[0], shift, scale, H[0])));
     for (int l = 0; l + 1 < nl; ++l) {
-        if (gemm_rows(h, true, P, d[l + 1], d[l], W[l], H[l], H[l + 1]) != CUBLAS_STATUS_SUCCESS)
-            return fail(MALA_ERR_CUDA, "cuBLAS GEMM (layer %d forward) failed", l);
+        MALA_PROF(c, "k_gemm_rows", st, MALA_TRY(gemm_rows<T>(true, P, d[l + 1], d[l], W[l], H[l], H[l + 1], st)));
         MALA_PROF(c, "k_bwd_elementwise", st,
                   (k_bias_act<T><<<ew_blocks(c, P * d[l + 1]), 256, 0, st>>>(H[l + 1], P, d[l + 1], bb[l], slope, 1)));
     }
@@ -181,15 +251,13 @@ int backward_impl(Ctx* c, const Model* m, const T* B, int64_t P, const double* v
         k_vec_wt<T><<<(d[nl - 1] + 127) / 128, 128, 0, st>>>(m->Wd[nl - 1], v_dev, d[nl], d[nl - 1], u);
         vec = true;
     } else {
-        if (gemm_rows(h, true, P, d[nl], d[nl - 1], W[nl - 1], H[nl - 1], Zo) != CUBLAS_STATUS_SUCCESS)
-            return fail(MALA_ERR_CUDA, "cuBLAS GEMM (output layer) failed");
+        MALA_PROF(c, "k_gemm_rows", st, MALA_TRY(gemm_rows<T>(true, P, d[nl], d[nl - 1], W[nl - 1], H[nl - 1], Zo, st)));
         MALA_PROF(c, "k_bwd_elementwise", st,
                   (k_bias_act<T><<<ew_blocks(c, P * d[nl]), 256, 0, st>>>(Zo, P, d[nl], bb[nl - 1], slope, 1)));
         k_cvt<T><<<ew_blocks(c, d[nl]), 256, 0, st>>>(v_dev, d[nl], u);
         MALA_PROF(c, "k_bwd_elementwise", st,
                   (k_mask<T><<<ew_blocks(c, P * d[nl]), 256, 0, st>>>(Zo, u, Zo, P, d[nl], slope)));
-        if (gemm_rows(h, false, P, d[nl - 1], d[nl], W[nl - 1], Zo, Gb[cur]) != CUBLAS_STATUS_SUCCESS)
-            return fail(MALA_ERR_CUDA, "cuBLAS GEMM (output layer backward) failed");
+        MALA_PROF(c, "k_gemm_rows", st, MALA_TRY(gemm_rows<T>(false, P, d[nl - 1], d[nl], W[nl - 1], Zo, Gb[cur], st)));
     }
     for (int l = nl - 1; l >= 1; --l) {
         // delta = dE/dH_l (.) sigma'(z) (H_l = sigma(z) is layer l-1's output), then dE/dH_{l-1} = delta W_{l-1}
@@ -197,8 +265,8 @@ int backward_impl(Ctx* c, const Model* m, const T* B, int64_t P, const double* v
                   (k_mask<T><<<ew_blocks(c, P * d[l]), 256, 0, st>>>(Gb[cur], vec ? u : nullptr, H[l], P, d[l],
                                                                      slope)));
         vec = false;
-        if (gemm_rows(h, false, P, d[l - 1], d[l], W[l - 1], Gb[cur], Gb[cur ^ 1]) != CUBLAS_STATUS_SUCCESS)
-            return fail(MALA_ERR_CUDA, "cuBLAS GEMM (layer %d backward) failed", l - 1);
+        MALA_PROF(c, "k_gemm_rows", st,
+                  MALA_TRY(gemm_rows<T>(false, P, d[l - 1], d[l], W[l - 1], Gb[cur], Gb[cur ^ 1], st)));
         cur ^= 1;
     }
     T* G = Gb[cur];
@@ -217,9 +285,6 @@ int mlp_backward(Ctx* c, const Model* m, const void* B, int64_t P, const double*
     return backward_impl<double>(c, m, static_cast<const double*>(B), P, v_dev, static_cast<double*>(beta), st);
 }
 
-void cublas_release(Ctx* c) {
-    if (c->cublas) cublasDestroy(static_cast<cublasHandle_t>(c->cublas));
-    c->cublas = nullptr;
-}
+
 
 }  // namespace mala

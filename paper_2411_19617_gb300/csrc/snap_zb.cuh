@@ -398,39 +398,33 @@ __device__ __forceinline__ long long to_fixed(float v) {
 
 // A triple's units (ma | m1a << 4 | twice << 8) fall into kZbGroups fixed groups
 // (unit i in group i mod kZbGroups); a group's values are summed in FP32 in unit
-// order and the sum meets its column's total in fixed point.  This warp takes
-// the groups first_group, first_group + W, ...  The groups do not depend on W,
+// order and the sum meets its column's total in fixed point.  A warp takes the
+// groups first, first + W, ... of a triple.  The groups do not depend on W,
 // so every warp count gives the same bits (with W = kZbGroups a warp holds
 // exactly one group per triple).
 constexpr int kZbGroups = 16;
 
-template <int J1, int J2, int J, int W>
-__device__ __forceinline__ void triple_units(uint32_t su, const unsigned short* __restrict__ ul, int n, int first_group,
-                                             unsigned long long* acc, bool& bad) {
-    for (int g = first_group; g < kZbGroups && g < n; g += W) {
-        float2 s = make_float2(0.f, 0.f);
-        for (int i = g; i < n; i += kZbGroups) {
-            const int e = ul[i];
-            const float2 r = unit_pairs<J1, J2, J>(su, e & 0xf, (e >> 4) & 0xf, (e & 0x100) ? 2.f : 1.f);
-            s.x += r.x;
-            s.y += r.y;
-        }
-        const bool ok = fabsf(s.x) < kFixLimit && fabsf(s.y) < kFixLimit;
-        bad |= !ok;
-        atomicAdd(acc, (unsigned long long)(ok ? to_fixed(s.x) : 0ll));       // point of the pair's first tile
-        atomicAdd(acc + 32, (unsigned long long)(ok ? to_fixed(s.y) : 0ll));  // and of its second
+// the FP32 sum of one group g of a triple's units: units g, g + kZbGroups, ...
+template <int J1, int J2, int J>
+__device__ __forceinline__ float2 group_sum(uint32_t su, const unsigned short* __restrict__ ul, int n, int g) {
+    float2 s = make_float2(0.f, 0.f);
+    for (int i = g; i < n; i += kZbGroups) {
+        const int e = ul[i];
+        const float2 r = unit_pairs<J1, J2, J>(su, e & 0xf, (e >> 4) & 0xf, (e & 0x100) ? 2.f : 1.f);
+        s.x += r.x;
+        s.y += r.y;
     }
+    return s;
 }
 
-template <int LO, int HI, int W>
-__device__ __forceinline__ void triple_dispatch(int id, uint32_t su, const unsigned short* ul, int n, int first,
-                                                unsigned long long* acc, bool& bad) {
+template <int LO, int HI>
+__device__ __forceinline__ float2 group_dispatch(int id, uint32_t su, const unsigned short* ul, int n, int g) {
     if constexpr (HI - LO == 1) {
-        triple_units<triple_field(LO, 0), triple_field(LO, 1), triple_field(LO, 2), W>(su, ul, n, first, acc, bad);
+        return group_sum<triple_field(LO, 0), triple_field(LO, 1), triple_field(LO, 2)>(su, ul, n, g);
     } else {
         constexpr int MIDI = (LO + HI) / 2;
-        if (id < MIDI) triple_dispatch<LO, MIDI, W>(id, su, ul, n, first, acc, bad);
-        else triple_dispatch<MIDI, HI, W>(id, su, ul, n, first, acc, bad);
+        if (id < MIDI) return group_dispatch<LO, MIDI>(id, su, ul, n, g);
+        return group_dispatch<MIDI, HI>(id, su, ul, n, g);
     }
 }
 
@@ -523,9 +517,14 @@ __global__ void __launch_bounds__(W * 32, 1)
         const uint32_t su = sbuf0 + (uint32_t)lane * 16u;
         for (int t = 0; t < ntri && !vacuum; ++t) {
             const int4 d = __ldg(tri + t);  // (gid, start, count, column)
-            const int first = ((warp - d.y) % W + W) % W;  // this warp's first group (rotated per triple)
-            if (first >= d.z) continue;
-            triple_dispatch<0, n_triples(kTJMax), W>(d.x, su, units + d.y, d.z, first, &sacc[d.w * 64 + lane], bad);
+            // this warp's groups: first, first + W, ... (rotated per triple for balance)
+            for (int g = ((warp - d.y) % W + W) % W; g < kZbGroups && g < d.z; g += W) {
+                const float2 gs = group_dispatch<0, n_triples(kTJMax)>(d.x, su, units + d.y, d.z, g);
+                const bool ok = fabsf(gs.x) < kFixLimit && fabsf(gs.y) < kFixLimit;
+                bad |= !ok;
+                atomicAdd(&sacc[d.w * 64 + lane], (unsigned long long)(ok ? to_fixed(gs.x) : 0ll));       // first tile
+                atomicAdd(&sacc[d.w * 64 + 32 + lane], (unsigned long long)(ok ? to_fixed(gs.y) : 0ll));  // second tile
+            }
         }
         __syncthreads();
         // grid points of the pair's 64 (tile, lane) slots
