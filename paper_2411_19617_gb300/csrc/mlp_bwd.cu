@@ -92,9 +92,11 @@ unsigned ew_blocks(Ctx* c, int64_t n) {
 // A CTA of 256 threads (16 x 16) computes a BM x BN tile of C, each thread a
 // contiguous TM x TN block (rows ty*TM.., columns tx*TN..), so a step of k
 // reads its operands as 16-byte vectors from shared memory.  K advances in
-// steps of BK: X as [BK][BM + pad] (the pad spreads the transposing stores over
-// the banks and keeps rows 16-byte aligned), op(W) as [BK][BN].  Every output
-// is one FMA chain over k in order, accumulated in T.
+// steps of BK through two shared-memory buffers: X as [BK][BM + pad] (the pad
+// spreads the transposing stores over the banks and keeps rows 16-byte
+// aligned), op(W) as [BK][BN]; the next step's tile is loaded into registers
+// while the current one is multiplied.  Every output is one FMA chain over k in
+// order, accumulated in T.
 template <class T> struct GemmShape;
 template <> struct GemmShape<float> { static constexpr int BM = 128, BN = 64, BK = 16, PAD = 4; };
 template <> struct GemmShape<double> { static constexpr int BM = 64, BN = 64, BK = 16, PAD = 2; };
@@ -104,9 +106,10 @@ __global__ void __launch_bounds__(256) k_gemm_rows(const T* __restrict__ X, cons
                                                    int K, T* __restrict__ Cm) {
     constexpr int BM = GemmShape<T>::BM, BN = GemmShape<T>::BN, BK = GemmShape<T>::BK, PAD = GemmShape<T>::PAD;
     constexpr int TM = BM / 16, TN = BN / 16;
-    constexpr int VEC = 16 / sizeof(T);  // elements per 16-byte vector
-    __shared__ __align__(16) T xs[BK][BM + PAD];
-    __shared__ __align__(16) T ws[BK][BN];
+    constexpr int VEC = 16 / sizeof(T);          // elements per 16-byte vector
+    constexpr int XL = BM * BK / 256, WL = BN * BK / 256;  // tile elements a thread loads
+    __shared__ __align__(16) T xs[2][BK][BM + PAD];
+    __shared__ __align__(16) T ws[2][BK][BN];
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     const int64_t m0 = (int64_t)blockIdx.x * BM;
     const int n0 = blockIdx.y * BN;
@@ -115,16 +118,20 @@ __global__ void __launch_bounds__(256) k_gemm_rows(const T* __restrict__ X, cons
     for (int i = 0; i < TM; ++i)
 #pragma unroll
         for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
-    for (int k0 = 0; k0 < K; k0 += BK) {
-        // X tile: rows m0.., columns k0..k0+BK (consecutive threads along k: coalesced rows)
-        for (int idx = threadIdx.x; idx < BM * BK; idx += 256) {
+    // the next K-tile travels global -> registers while the current one is multiplied
+    T xr[XL], wr[WL];
+    auto load = [&](int k0) {
+#pragma unroll
+        for (int u = 0; u < XL; ++u) {  // X rows m0.., columns k0..k0+BK: consecutive threads along k
+            const int idx = threadIdx.x + 256 * u;
             const int r = idx / BK, kk = idx - r * BK;
             const int64_t m = m0 + r;
             const int k = k0 + kk;
-            xs[kk][r] = (m < P && k < K) ? X[m * K + k] : T(0);
+            xr[u] = (m < P && k < K) ? X[m * K + k] : T(0);
         }
-        // op(W) tile: [BK][BN]
-        for (int idx = threadIdx.x; idx < BN * BK; idx += 256) {
+#pragma unroll
+        for (int u = 0; u < WL; ++u) {
+            const int idx = threadIdx.x + 256 * u;
             int kk, c;
             if (TRANS) {  // W [N][K]: consecutive threads along k
                 c = idx / BK;
@@ -134,25 +141,53 @@ __global__ void __launch_bounds__(256) k_gemm_rows(const T* __restrict__ X, cons
                 c = idx - kk * BN;
             }
             const int k = k0 + kk, n = n0 + c;
-            T v = T(0);
-            if (k < K && n < N) v = TRANS ? W[(size_t)n * K + k] : W[(size_t)k * N + n];
-            ws[kk][c] = v;
+            wr[u] = (k < K && n < N) ? (TRANS ? W[(size_t)n * K + k] : W[(size_t)k * N + n]) : T(0);
         }
-        __syncthreads();
+    };
+    auto store = [&](int b) {
+#pragma unroll
+        for (int u = 0; u < XL; ++u) {
+            const int idx = threadIdx.x + 256 * u;
+            const int r = idx / BK, kk = idx - r * BK;
+            xs[b][kk][r] = xr[u];
+        }
+#pragma unroll
+        for (int u = 0; u < WL; ++u) {
+            const int idx = threadIdx.x + 256 * u;
+            int kk, c;
+            if (TRANS) {
+                c = idx / BK;
+                kk = idx - c * BK;
+            } else {
+                kk = idx / BN;
+                c = idx - kk * BN;
+            }
+            ws[b][kk][c] = wr[u];
+        }
+    };
+    const int ntile = (K + BK - 1) / BK;
+    load(0);
+    store(0);
+    __syncthreads();
+    for (int t = 0; t < ntile; ++t) {
+        const int b = t & 1;
+        if (t + 1 < ntile) load((t + 1) * BK);
 #pragma unroll
         for (int kk = 0; kk < BK; ++kk) {
-            T a[TM], b[TN];
+            T a[TM], bv[TN];
 #pragma unroll
             for (int i = 0; i < TM; i += VEC)
-                *reinterpret_cast<uint4*>(&a[i]) = *reinterpret_cast<const uint4*>(&xs[kk][ty * TM + i]);
+                *reinterpret_cast<uint4*>(&a[i]) = *reinterpret_cast<const uint4*>(&xs[b][kk][ty * TM + i]);
 #pragma unroll
             for (int j = 0; j < TN; j += VEC)
-                *reinterpret_cast<uint4*>(&b[j]) = *reinterpret_cast<const uint4*>(&ws[kk][tx * TN + j]);
+                *reinterpret_cast<uint4*>(&bv[j]) = *reinterpret_cast<const uint4*>(&ws[b][kk][tx * TN + j]);
 #pragma unroll
             for (int i = 0; i < TM; ++i)
 #pragma unroll
-                for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+                for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], bv[j], acc[i][j]);
         }
+        // the other buffer was last read before the previous barrier
+        if (t + 1 < ntile) store(b ^ 1);
         __syncthreads();
     }
 #pragma unroll
