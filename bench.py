@@ -419,7 +419,7 @@ def forces_leg(ctx, api, roofline, model, snap, bp, eg, ne, calls, peak_tflops):
     fo_f = roofline.force_flops_per_pair(bp.twojmax) * pairs
     roof = {}
     for name, flops in (("k_yi", yi_f), ("k_force", fo_f)):
-        t = kern[name]["ms"] / max(kern[name]["launches"], 1)
+        t = kern[name]["ms"]  # one call's launches together do the call's work (k_yi: one launch per coupling group)
         ach = flops / (t / 1e3) / 1e12 if t > 0 else 0.0
         roof[name] = {"bound": "alu", "achieved": ach, "peak": peak_tflops, "unit": "TFLOP/s",
                       "frac": ach / peak_tflops, "flops": flops}
@@ -512,7 +512,7 @@ def load_peaks():
 
 # source files whose text decides each kernel's DRAM traffic (hashed against the ncu capture)
 KERNEL_SOURCES = {
-    "k_zb": ("snap_zb.cu", "snap_zb.cuh", "snap_common.cuh"),
+    "k_zb": ("snap_zb.cu", "snap_zb.cuh", "snap_pairs.cuh", "snap_common.cuh"),
     "k_ui": ("snap_ui.cu", "snap_common.cuh"),
     "k_mlp": ("mlp_tc.cu",),
     "k_density": ("integrate.cu",),

@@ -257,7 +257,7 @@ int mala_integrate(mala_ctx* ctx, const void* ldos_dev, int64_t P, double cell_v
  * static device array of MALA_NOALLOC_SCRATCH_BYTES that each GPU loading the
  * library holds until the process exits.  Limit: 9.5 n_E + 296 + max(
  * ceil(P/128) n_E [only when dos_sum_dev is NULL], the CTAs of the density
- * pass [at most one per SM]) doubles must fit in the array; larger sizes
+ * pass [at most six per SM]) doubles must fit in the array; larger sizes
  * return MALA_ERR_UNSUPPORTED with the numbers in the message.  Every call
  * looks up the array's device address in the current context (a host-side
  * query, no allocation); make the first call on a device before any stream

@@ -281,7 +281,10 @@ static int run_descriptors(Ctx* c, int nsnap, const mala_snapshot* snaps, const 
                 if (it != rt->tune.end()) {
                     v_ui = it->second.ui;
                     v_zb = it->second.zb;
-                } else {
+                } else if (!c->parent) {
+                    // only a synchronous call tunes: a serving slot shares the GPU with the other slots,
+                    // so its timings would rank the variants by what else happened to run; slots take
+                    // the defaults until a synchronous call has tuned the key
                     tune_now = true;
                 }
             }

@@ -190,6 +190,13 @@ struct ForceTables {
     size_t off[10] = {0};
 };
 
+// launch plan of the FP32 Y step (units per row and warp) for one twojmax, in Ctx::ws_yplan
+struct YiPlanState {
+    int tj = -1;
+    int row0[4] = {0, 0, 0, 0}, nrows[4] = {0, 0, 0, 0};
+    size_t off[5] = {0, 0, 0, 0, 0};  // rows, off, units, be_t, be_f in ws_yplan
+};
+
 // Tile-shape tuning: per key (twojmax, neighbour-capacity band, grid-size band)
 // the compute_ui and compute_zi/bi variants chosen, with the times that chose them.
 struct TuneEntry {
@@ -219,6 +226,8 @@ struct Ctx {
         ws_dens, ws_dos, ws_tile_dos, ws_units, ws_mlp64, ws_red, ws_w, ws_mlp_in;
     // workspaces of the force path
     ForceTables ftab;
+    YiPlanState yplan;
+    DevBuf ws_yplan;
     DevBuf ws_ftab, ws_force_y, ws_force_aux, ws_force_u, ws_force_nbr, ws_force_beta, ws_force_mlp, ws_force_g,
         ws_force_bt, ws_ace;
     double* host_dos = nullptr;     // pinned [max N_E]
@@ -384,6 +393,8 @@ double clebsch_gordan(int j1, int m1, int j2, int m2, int j, int m);  // twice-u
 // descriptors with the full u and neighbour lists of one snapshot (nl.dbg_* outputs set by the caller)
 int snap_descriptors_full(Ctx* c, const mala_snapshot* snap, const mala_bispectrum_params* bp, void* B,
                           void* u_full, NbrOut* nl, mala_precision prec, cudaStream_t st);
+// FP32 Y step of the descriptor adjoint: y[p] = conj(Y) N over the full set (snap_yi.cu)
+int yi_units(Ctx* c, int tj, const float* u_full, const float* beta, int nB, int64_t P, float* y, cudaStream_t st);
 // F_host[n_atoms][3] = -sum_r sum_j beta[r][j] dB(r, j)/dR from the staged snapshot sd
 template <class T>
 int descriptor_adjoint(Ctx* c, const SnapDev& sd, const mala_snapshot* snap, const mala_bispectrum_params* bp,

@@ -12,10 +12,11 @@
 //     Y^J = sum_t beta_t ( [J = j] Z^j_{j1 j2} + [J = j1] (j+1)/(j1+1) Z^{j1}_{j j2}
 //                         + [J = j2] (j+1)/(j2+1) Z^{j2}_{j j1} ),
 // and Z^c_{ab} = Z^c_{ba}.  Y keeps u's symmetry Y[J-ma][J-mb] = (-1)^(ma-mb) conj(Y[ma][mb]),
-// so the half set is contracted and the rest mirrored.  One CTA holds the full
-// u of 32 grid points (16 in FP64) in shared memory, lane = point; a warp walks
-// a list of Y elements, each a list of couplings, each a list of
-// (C C, u^a index, u^b index) terms built on the host.  Output per point:
+// so the half set is contracted and the rest mirrored.  FP32: units with the
+// couplings compiled in (snap_yi.cu).  FP64 (k_yi here): one CTA holds the full
+// u of 16 grid points in shared memory, lane = point; a warp walks a list of Y
+// elements, each a list of couplings, each a list of (C C, u^a index, u^b
+// index) terms built on the host.  Output per point:
 // y_{J,mb}[ma] = conj(Y^J[ma][mb]) N(J, ma, mb) over the full set, the form
 // the force step contracts with.
 //
@@ -62,12 +63,7 @@ template <class T> struct YTerm {
 
 // N(J, ma, mb) = sqrt((J-ma)! ma! / ((J-mb)! mb!)), [J][ma][mb]
 __constant__ double c_fnorm_d[(kTJMax + 1) * (kTJMax + 1) * (kTJMax + 1)];
-__constant__ float c_fnorm_f[(kTJMax + 1) * (kTJMax + 1) * (kTJMax + 1)];
-template <class T> __device__ __forceinline__ T fnorm(int J, int ma, int mb);
-template <> __device__ __forceinline__ float fnorm<float>(int J, int ma, int mb) {
-    return c_fnorm_f[(J * (kTJMax + 1) + ma) * (kTJMax + 1) + mb];
-}
-template <> __device__ __forceinline__ double fnorm<double>(int J, int ma, int mb) {
+__device__ __forceinline__ double fnorm(int J, int ma, int mb) {
     return c_fnorm_d[(J * (kTJMax + 1) + ma) * (kTJMax + 1) + mb];
 }
 
@@ -79,17 +75,13 @@ struct YiTab {
     const int* grp_off;     // [nh + 1] groups of each half element
     const int* grp_cpl;     // coupling of each group
     const int* term_off;    // [ngrp + 1]
-    const YTerm<float>* terms_f;
     const YTerm<double>* terms_d;
     const int4* elem;       // half element: J, ma, mb, full index
     const short* warp_list; // [kYiWarps][list_len], -1 padded
 };
 
-template <class T> __device__ __forceinline__ const YTerm<T>* terms_of(const YiTab& t);
-template <> __device__ __forceinline__ const YTerm<float>* terms_of<float>(const YiTab& t) { return t.terms_f; }
-template <> __device__ __forceinline__ const YTerm<double>* terms_of<double>(const YiTab& t) { return t.terms_d; }
 
-template <class T> constexpr int yi_points() { return sizeof(T) == 4 ? 32 : 16; }
+template <class T> constexpr int yi_points() { return 16; }  // FP64 only
 
 template <class T>
 __global__ void __launch_bounds__(kYiWarps * 32) k_yi(int tj, const T* __restrict__ u_full, const T* __restrict__ beta,
@@ -127,7 +119,7 @@ __global__ void __launch_bounds__(kYiWarps * 32) k_yi(int tj, const T* __restric
     const int pt = lane % NP, sub = lane / NP;
     const int64_t p = p0 + pt;
     const short* wl = tab.warp_list + (size_t)warp * tab.list_len;
-    const YTerm<T>* terms = terms_of<T>(tab);
+    const YTerm<T>* terms = tab.terms_d;
     for (int i = sub; i < tab.list_len; i += 32 / NP) {
         const int h = wl[i];
         if (h < 0) break;
@@ -165,7 +157,7 @@ __global__ void __launch_bounds__(kYiWarps * 32) k_yi(int tj, const T* __restric
         if (p < P) {
             const int4 el = tab.elem[h];
             const int J = el.x, ma = el.y, mb = el.z;
-            const T nrm = fnorm<T>(J, ma, mb);  // N is the same at the mirrored element
+            const T nrm = fnorm(J, ma, mb);  // N is the same at the mirrored element
             T* o = y_out + (size_t)p * nf * 2;
             o[2 * el.w] = yr * nrm;  // conj(Y) N
             o[2 * el.w + 1] = -yi * nrm;
@@ -364,7 +356,6 @@ __global__ void k_fix_to_double(const unsigned long long* __restrict__ F_fix, in
 struct HostYiTab {
     std::vector<int> cpl_off, ent_t, grp_off, grp_cpl, term_off;
     std::vector<double> ent_f;
-    std::vector<YTerm<float>> tf;
     std::vector<YTerm<double>> td;
     std::vector<int4> elem;
     std::vector<short> wl;
@@ -429,7 +420,6 @@ void build_yi_tab(int tj, HostYiTab& H) {
                             const int ia = full_off(a) + m1a * (a + 1) + m1b;
                             const int ib = full_off(b) + ((m2 + b) / 2) * (b + 1) + (m2p + b) / 2;
                             H.td.push_back(YTerm<double>{c1 * c2, (unsigned short)ia, (unsigned short)ib});
-                            H.tf.push_back(YTerm<float>{(float)(c1 * c2), (unsigned short)ia, (unsigned short)ib});
                         }
                     }
                     if (H.td.size() == before) continue;
@@ -471,8 +461,8 @@ int ensure_yi_tab(Ctx* c, int tj, YiTab* out) {
             {H.cpl_off.data(), H.cpl_off.size() * sizeof(int)}, {H.ent_t.data(), H.ent_t.size() * sizeof(int)},
             {H.ent_f.data(), H.ent_f.size() * sizeof(double)},  {H.grp_off.data(), H.grp_off.size() * sizeof(int)},
             {H.grp_cpl.data(), H.grp_cpl.size() * sizeof(int)}, {H.term_off.data(), H.term_off.size() * sizeof(int)},
-            {H.tf.data(), H.tf.size() * sizeof(YTerm<float>)}, {H.td.data(), H.td.size() * sizeof(YTerm<double>)},
-            {H.elem.data(), H.elem.size() * sizeof(int4)},     {H.wl.data(), H.wl.size() * sizeof(short)}};
+            {H.td.data(), H.td.size() * sizeof(YTerm<double>)}, {H.elem.data(), H.elem.size() * sizeof(int4)},
+            {H.wl.data(), H.wl.size() * sizeof(short)}};
         std::vector<size_t> off;
         size_t total = 0;
         for (auto& p : parts) {
@@ -484,7 +474,7 @@ int ensure_yi_tab(Ctx* c, int tj, YiTab* out) {
             if (parts[i].second) memcpy(blob.data() + off[i], parts[i].first, parts[i].second);
         MALA_TRY(c->ws_ftab.reserve(c, total + 256));
         MALA_CUDA_TRY(cudaMemcpy(c->ws_ftab.ptr, blob.data(), total, cudaMemcpyHostToDevice));
-        for (int i = 0; i < 10; ++i) F.off[i] = off[i];
+        for (int i = 0; i < 9; ++i) F.off[i] = off[i];
         F.ncoup = H.ncoup;
         F.list_len = H.list_len;
         F.nh = (int)H.elem.size();
@@ -499,10 +489,9 @@ int ensure_yi_tab(Ctx* c, int tj, YiTab* out) {
     out->grp_off = reinterpret_cast<const int*>(b + F.off[3]);
     out->grp_cpl = reinterpret_cast<const int*>(b + F.off[4]);
     out->term_off = reinterpret_cast<const int*>(b + F.off[5]);
-    out->terms_f = reinterpret_cast<const YTerm<float>*>(b + F.off[6]);
-    out->terms_d = reinterpret_cast<const YTerm<double>*>(b + F.off[7]);
-    out->elem = reinterpret_cast<const int4*>(b + F.off[8]);
-    out->warp_list = reinterpret_cast<const short*>(b + F.off[9]);
+    out->terms_d = reinterpret_cast<const YTerm<double>*>(b + F.off[6]);
+    out->elem = reinterpret_cast<const int4*>(b + F.off[7]);
+    out->warp_list = reinterpret_cast<const short*>(b + F.off[8]);
     return MALA_OK;
 }
 
@@ -512,16 +501,13 @@ int ensure_fnorm(int device) {
     if (device >= 0 && device < 64 && g_fnorm_ready[device]) return MALA_OK;
     constexpr int n = (kTJMax + 1) * (kTJMax + 1) * (kTJMax + 1);
     std::vector<double> d(n, 0.0);
-    std::vector<float> f(n, 0.f);
     for (int J = 0; J <= kTJMax; ++J)
         for (int a = 0; a <= J; ++a)
             for (int b = 0; b <= J; ++b) {
                 const double v = std::sqrt(fact_d(J - a) * fact_d(a) / (fact_d(J - b) * fact_d(b)));
                 d[(J * (kTJMax + 1) + a) * (kTJMax + 1) + b] = v;
-                f[(J * (kTJMax + 1) + a) * (kTJMax + 1) + b] = (float)v;
             }
     MALA_CUDA_TRY(cudaMemcpyToSymbol(c_fnorm_d, d.data(), sizeof(double) * n));
-    MALA_CUDA_TRY(cudaMemcpyToSymbol(c_fnorm_f, f.data(), sizeof(float) * n));
     if (device >= 0 && device < 64) g_fnorm_ready[device] = true;
     return MALA_OK;
 }
@@ -546,8 +532,6 @@ int descriptor_adjoint(Ctx* c, const SnapDev& sd, const mala_snapshot* snap, con
     const int64_t P = sd.g.P;
     const int nf = n_full(tj), nB = n_triples(tj), na = sd.g.n_atoms;
     MALA_TRY(ensure_fnorm(c->device));
-    YiTab tab;
-    MALA_TRY(ensure_yi_tab(c, tj, &tab));
     // Y, then per-atom weights, fixed-point sums, error flag
     MALA_TRY(c->ws_force_y.reserve(c, sizeof(T) * 2 * (size_t)nf * (size_t)std::max<int64_t>(P, 1)));
     const size_t aux = sizeof(double) * na + sizeof(unsigned long long) * 3 * (size_t)na + sizeof(double) * 3 * na + 512;
@@ -561,13 +545,21 @@ int descriptor_adjoint(Ctx* c, const SnapDev& sd, const mala_snapshot* snap, con
     if (na > 0) MALA_CUDA_TRY(cudaMemsetAsync(F_fix, 0, sizeof(unsigned long long) * 3 * na, st));
     MALA_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
     if (P > 0) {
-        constexpr int NP = yi_points<T>();
-        const size_t smem_yi = sizeof(typename Cx<T>::type) * (size_t)nf * NP + sizeof(T) * (size_t)tab.ncoup * NP;
-        cudaFuncSetAttribute(k_yi<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_yi);
-        MALA_PROF(c, "k_yi", st,
-                  (k_yi<T><<<(unsigned)((P + NP - 1) / NP), kYiWarps * 32, smem_yi, st>>>(tj, u_full, beta, nB, P,
-                                                                                          tab, y)));
-        MALA_CUDA_TRY(cudaGetLastError());
+        if constexpr (sizeof(T) == 4) {
+            // FP32: units with compiled couplings, two points per lane (snap_yi.cu)
+            MALA_TRY(yi_units(c, tj, u_full, beta, nB, P, y, st));
+        } else {
+            YiTab tab;
+            MALA_TRY(ensure_yi_tab(c, tj, &tab));
+            constexpr int NP = yi_points<T>();
+            const size_t smem_yi =
+                sizeof(typename Cx<T>::type) * (size_t)nf * NP + sizeof(T) * (size_t)tab.ncoup * NP;
+            cudaFuncSetAttribute(k_yi<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_yi);
+            MALA_PROF(c, "k_yi", st,
+                      (k_yi<T><<<(unsigned)((P + NP - 1) / NP), kYiWarps * 32, smem_yi, st>>>(tj, u_full, beta, nB,
+                                                                                              P, tab, y)));
+            MALA_CUDA_TRY(cudaGetLastError());
+        }
         ForceGeom g;
         g.wpos = sd.wpos;
         g.gcoord = sd.gcoord;

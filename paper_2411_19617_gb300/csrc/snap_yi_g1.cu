@@ -1,0 +1,11 @@
+// snap_yi_g1.cu -- unit kernel of coupling group 1 of the FP32 Y step
+// (snap_yi.cuh); the group's couplings are those whose coupled momentum c is
+// in yi_mask(1).
+#include "snap_yi.cuh"
+
+namespace mala {
+
+int yi_upload_g1(const float* cg, int n, const float* fnorm) { return yi_upload<yi_mask(1)>(cg, n, fnorm); }
+int yi_launch_g1(const YiLaunch& a) { return yi_launch<yi_mask(1)>(a); }
+
+}  // namespace mala

@@ -1,0 +1,11 @@
+// snap_yi_g3.cu -- unit kernel of coupling group 3 of the FP32 Y step
+// (snap_yi.cuh); the group's couplings are those whose coupled momentum c is
+// in yi_mask(3).
+#include "snap_yi.cuh"
+
+namespace mala {
+
+int yi_upload_g3(const float* cg, int n, const float* fnorm) { return yi_upload<yi_mask(3)>(cg, n, fnorm); }
+int yi_launch_g3(const YiLaunch& a) { return yi_launch<yi_mask(3)>(a); }
+
+}  // namespace mala
