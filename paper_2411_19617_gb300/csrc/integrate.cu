@@ -783,6 +783,165 @@ __global__ void __launch_bounds__(kDensThreads, kDensDirectCtasPerSm)
     }
 }
 
+// Tiled BF16 density pass.  A tile is R whole rows whose bytes start on a
+// 16-byte boundary (R = 8 / gcd(n_E, 8), so R n_E is a multiple of 8 and the
+// tile a whole number of 16-byte chunks of 8 energies); a warp reads a tile as
+// 16-byte loads, chunk j by lane j mod 32.  Every lane meets its chunks at the
+// same offsets in every tile, so their weights and the row each chunk starts
+// in are fixed per lane and kept in registers.  A chunk meets at most two rows
+// (n_E >= 8): the energies in its first row are weighted from registers, the
+// few past that row's end (three lanes per tile at n_E = 250) from the cached
+// weight array, each part goes to its own row, and the per-row sums meet by
+// warp shuffles.  The warp loads the next tile before it reduces the current
+// one.  Rows before the first aligned tile and after the last whole tile go
+// through warp 0 of CTA 0, element by element.  One CTA of 512 threads per SM.
+constexpr int kDensTileThreads = 512;
+constexpr int kDensTileWarps = kDensTileThreads / 32;
+
+inline int dens_tile_rows(int nE) {
+    int g = 8;
+    while (nE % g) g >>= 1;  // gcd(nE, 8)
+    return 8 / g;
+}
+
+template <int R, int K>
+__global__ void __launch_bounds__(kDensTileThreads, 1)
+    k_density_tiled(const __nv_bfloat16* __restrict__ L, int64_t P, int nE, int64_t head, int64_t ntile,
+                    const float* __restrict__ w0, float* __restrict__ n, double* __restrict__ part) {
+    __shared__ double sred[kDensTileWarps];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int C = R * nE / 8;  // chunks per tile, at most 32 K
+    float w[K][8];
+    int ra[K], bnd[K];
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+        const int j = lane + 32 * i;
+        const int e0 = 8 * j;
+        ra[i] = e0 / nE;
+        bnd[i] = (ra[i] + 1) * nE - e0;  // energies of the chunk in row ra (>= 8: all of them)
+#pragma unroll
+        for (int k = 0; k < 8; ++k)  // the weights of the energies in row ra (0 past its end)
+            w[i][k] = (j < C && k < bnd[i]) ? __ldg(w0 + e0 + k - nE * ra[i]) : 0.f;
+    }
+    const uint4* T = reinterpret_cast<const uint4*>(L + head * nE);
+    const int64_t wid = (int64_t)blockIdx.x * kDensTileWarps + warp;
+    const int64_t nwarp = (int64_t)gridDim.x * kDensTileWarps;
+    double dacc = 0.0;
+    uint4 cur[K], nxt[K];
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+        const int j = lane + 32 * i;
+        cur[i] = (wid < ntile && j < C) ? __ldcs(T + wid * C + j) : make_uint4(0u, 0u, 0u, 0u);
+    }
+    for (int64_t t = wid; t < ntile; t += nwarp) {
+        const int64_t tn = t + nwarp;
+#pragma unroll
+        for (int i = 0; i < K; ++i) {
+            const int j = lane + 32 * i;
+            nxt[i] = (tn < ntile && j < C) ? __ldcs(T + tn * C + j) : make_uint4(0u, 0u, 0u, 0u);
+        }
+        float acc[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc[r] = 0.f;
+#pragma unroll
+        for (int i = 0; i < K; ++i) {
+            const uint32_t q[4] = {cur[i].x, cur[i].y, cur[i].z, cur[i].w};
+            float f[8];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float2 p = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&q[k]));
+                f[2 * k] = p.x;
+                f[2 * k + 1] = p.y;
+            }
+            float lo = 0.f, hi = 0.f;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) lo = fmaf(f[k], w[i][k], lo);
+            if (bnd[i] < 8) {  // the chunk runs into the next row (a few lanes per tile)
+                const int c1 = 8 * (lane + 32 * i) - (ra[i] + 1) * nE;  // its column there (< 0 before it)
+#pragma unroll
+                for (int k = 0; k < 8; ++k)
+                    if (k >= bnd[i]) hi = fmaf(f[k], __ldg(w0 + c1 + k), hi);
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r) acc[r] += (r == ra[i] ? lo : 0.f) + (r == ra[i] + 1 ? hi : 0.f);
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
+        float s = acc[0];
+#pragma unroll
+        for (int r = 1; r < R; ++r) s = lane == r ? acc[r] : s;
+        if (lane < R) {
+            n[head + t * R + lane] = s;
+            dacc += (double)s;
+        }
+#pragma unroll
+        for (int i = 0; i < K; ++i) cur[i] = nxt[i];
+    }
+    if (blockIdx.x == 0 && warp == 0) {
+        // the rows outside the whole tiles
+        const int64_t tail0 = head + ntile * R;
+        for (int64_t r = 0; r < P; ++r) {
+            if (r == head) r = tail0;
+            if (r >= P) break;
+            float s = 0.f;
+            for (int e = lane; e < nE; e += 32) s = fmaf(__bfloat162float(L[r * nE + e]), __ldg(w0 + e), s);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0) {
+                n[r] = s;
+                dacc += (double)s;
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dacc += __shfl_xor_sync(0xffffffffu, dacc, o);
+    if (lane == 0) sred[warp] = dacc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tsum = 0.0;
+        for (int k = 0; k < kDensTileWarps; ++k) tsum += sred[k];
+        part[blockIdx.x] = tsum;
+    }
+}
+
+// the tiled path applies: BF16, n_E >= 8 and a tile of at most 128 chunks (4 per lane)
+inline bool density_tiled(int nE, int elem_bytes) {
+    return elem_bytes == 2 && nE >= 8 && dens_tile_rows(nE) * nE <= 1024;
+}
+
+template <int R>
+void launch_density_tiled_r(const __nv_bfloat16* L, int64_t P, int nE, int64_t head, int64_t ntile, const float* w0,
+                            float* n, double* part, int grid, cudaStream_t st) {
+    const int K = (R * nE / 8 + 31) / 32;
+    if (K <= 1) k_density_tiled<R, 1><<<grid, kDensTileThreads, 0, st>>>(L, P, nE, head, ntile, w0, n, part);
+    else if (K == 2) k_density_tiled<R, 2><<<grid, kDensTileThreads, 0, st>>>(L, P, nE, head, ntile, w0, n, part);
+    else if (K == 3) k_density_tiled<R, 3><<<grid, kDensTileThreads, 0, st>>>(L, P, nE, head, ntile, w0, n, part);
+    else k_density_tiled<R, 4><<<grid, kDensTileThreads, 0, st>>>(L, P, nE, head, ntile, w0, n, part);
+}
+
+// false when no row of L starts on a 16-byte boundary within the first tile (then the other paths run)
+inline bool launch_density_tiled(const __nv_bfloat16* L, int64_t P, int nE, const float* w0, float* n, double* part,
+                                 int grid, cudaStream_t st) {
+    const int R = dens_tile_rows(nE);
+    int64_t head = -1;
+    for (int r = 0; r < R && r <= P; ++r)
+        if ((reinterpret_cast<uintptr_t>(L + (int64_t)r * nE) & 15) == 0) {
+            head = r;
+            break;
+        }
+    if (head < 0) return false;
+    const int64_t ntile = P > head ? (P - head) / R : 0;
+    switch (R) {
+        case 1: launch_density_tiled_r<1>(L, P, nE, head, ntile, w0, n, part, grid, st); break;
+        case 2: launch_density_tiled_r<2>(L, P, nE, head, ntile, w0, n, part, grid, st); break;
+        case 4: launch_density_tiled_r<4>(L, P, nE, head, ntile, w0, n, part, grid, st); break;
+        default: launch_density_tiled_r<8>(L, P, nE, head, ntile, w0, n, part, grid, st); break;
+    }
+    return true;
+}
+
 // the direct path applies: BF16, an even row length whose pairs fit the registers, 4-byte aligned rows
 inline bool density_direct(int nE, int elem_bytes) {
     return elem_bytes == 2 && dens_plan(nE, elem_bytes).wpl > 0;
@@ -792,6 +951,9 @@ template <class TL, class TW>
 void launch_density(const TL* L, int64_t P, int nE, const TW* w0, TW* n, double* part, int grid, int* err,
                     cudaStream_t st) {
     const DensPlan d = dens_plan(nE, (int)sizeof(TL));
+    if constexpr (sizeof(TL) == 2 && sizeof(TW) == 4) {
+        if (density_tiled(nE, 2) && launch_density_tiled(L, P, nE, w0, n, part, grid, st)) return;
+    }
     if constexpr (sizeof(TL) == 2) {
         if (density_direct(nE, 2) && (reinterpret_cast<uintptr_t>(L) & 3) == 0) {
             const size_t smem = sizeof(float) * (size_t)((nE + 3) & ~3) + sizeof(double) * (kDensThreads / 32);
@@ -804,10 +966,16 @@ void launch_density(const TL* L, int64_t P, int nE, const TW* w0, TW* n, double*
     k_density<TL, TW><<<grid, kDensThreads, smem, st>>>(L, P, nE, d.rows, d.G, d.wpl, w0, n, part, err);
 }
 
-// CTAs of the density pass (the partial-sum rows it writes): the direct path
-// runs kDensDirectCtasPerSm per SM, the staged path one per SM, never more
-// than there are row groups or tiles
+// CTAs of the density pass (the partial-sum rows it writes): the tiled path
+// runs one per SM, the direct path kDensDirectCtasPerSm per SM, the staged path
+// one per SM, never more than there are row groups or tiles (any count works
+// for every path: the kernels stride over the CTAs)
 inline int density_grid(int64_t P, int nE, int elem_bytes, int num_sms) {
+    if (density_tiled(nE, elem_bytes)) {  // one CTA per SM, at most one per kDensTileWarps tiles
+        const int64_t tiles = P / dens_tile_rows(nE);
+        return (int)std::max<int64_t>(1, std::min<int64_t>((tiles + kDensTileWarps - 1) / kDensTileWarps,
+                                                           (int64_t)std::max(1, num_sms)));
+    }
     const DensPlan d = dens_plan(nE, elem_bytes);
     if (density_direct(nE, elem_bytes)) {
         const int64_t groups = (P + kDensThreads / d.G - 1) / (kDensThreads / d.G);

@@ -140,7 +140,7 @@ def test_entropy_term_matches_oracle_across_temperatures(kT):
 
 @pytest.mark.parametrize("mixed", [True, False])
 @pytest.mark.parametrize("nE,P,row0", [(250, 20011, 1), (250, 3, 3), (11, 9000, 5), (7, 1, 1), (4096, 17, 2),
-                                       (250, 729, 0)])
+                                       (250, 729, 0), (300, 5003, 2), (1000, 999, 1), (64, 4097, 3), (8, 100, 7)])
 def test_density_pass_any_alignment_and_size(mixed, nE, P, row0):
     """n(r) = sum_xi w0_xi LDOS(r, xi) on row slices that start at any row of a
     larger buffer (so the LDOS start need not be 16-byte aligned), with tiny,
