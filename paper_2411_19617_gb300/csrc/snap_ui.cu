@@ -17,7 +17,9 @@
 // are split into "segments" (one column chain over a range of levels) small
 // enough that their sums and Kahan compensations stay in registers; each
 // segment loops over the lane's neighbours, rebuilding its column from the
-// seed, and accumulates c_k * coefficient with compensated (Kahan) summation.
+// seed, and accumulates c_k * coefficient with compensated (Kahan) summation;
+// the chain starts from c_k instead of 1 (the recursion is linear), so every
+// coefficient arrives already weighted.
 // FP32 takes the neighbours two at a time: both column chains run packed in
 // FP32x2 pairs (one FFMA2 does a step of both), and the two weighted terms of
 // an element are added in one rounding before the compensated add, which
@@ -221,8 +223,9 @@ __device__ __forceinline__ void ui_segment(const typename AB4<T>::type* __restri
             const float2 l2br = make_float2(a0.x, a1.x), l2bi = make_float2(a0.y, a1.y);
             const float2 nl1ai = make_float2(a0.y, a1.y), nl1bi = make_float2(-a0.w, -a1.w);
             const float2 nl2ai = make_float2(-a0.w, -a1.w), nl2bi = make_float2(-a0.y, -a1.y);
+            // the chain starts from the neighbour's weight: every level comes out scaled by c
             float2 vr[kTJMax + 1], vi[kTJMax + 1];
-            vr[0] = make_float2(1.f, 1.f);
+            vr[0] = c2;
             vi[0] = make_float2(0.f, 0.f);
 #pragma unroll
             for (int st = 0; st < MB; ++st) {
@@ -238,9 +241,8 @@ __device__ __forceinline__ void ui_segment(const typename AB4<T>::type* __restri
 #pragma unroll
                     for (int i = 0; i < kTJMax + 1; ++i) {
                         if (i < ne) {
-                            const float2 xr = __fmul2_rn(c2, vr[i]), xi = __fmul2_rn(c2, vi[i]);
-                            kahan_add(sr[off + i], cr[off + i], xr.x + xr.y);
-                            kahan_add(si[off + i], ci[off + i], xi.x + xi.y);
+                            kahan_add(sr[off + i], cr[off + i], vr[i].x + vr[i].y);
+                            kahan_add(si[off + i], ci[off + i], vi[i].x + vi[i].y);
                         }
                     }
                 }
@@ -258,7 +260,7 @@ __device__ __forceinline__ void ui_segment(const typename AB4<T>::type* __restri
         const T l1ar = ab.x, l1ai = -ab.y, l1br = -ab.z, l1bi = ab.w;
         const T l2ar = ab.z, l2ai = ab.w, l2br = ab.x, l2bi = ab.y;
         T vr[kTJMax + 1], vi[kTJMax + 1];
-        vr[0] = T(1);
+        vr[0] = c;  // the chain starts from the neighbour's weight: every level comes out scaled by c
         vi[0] = T(0);
         // seed: (L1 L2)^MB at level 2 MB
 #pragma unroll
@@ -275,8 +277,8 @@ __device__ __forceinline__ void ui_segment(const typename AB4<T>::type* __restri
 #pragma unroll
                 for (int i = 0; i < kTJMax + 1; ++i) {
                     if (i < ne) {
-                        kahan_add(sr[off + i], cr[off + i], c * vr[i]);
-                        kahan_add(si[off + i], ci[off + i], c * vi[i]);
+                        kahan_add(sr[off + i], cr[off + i], vr[i]);
+                        kahan_add(si[off + i], ci[off + i], vi[i]);
                     }
                 }
             }
