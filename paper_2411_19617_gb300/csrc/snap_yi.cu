@@ -18,7 +18,7 @@ namespace mala {
 
 namespace {
 
-using UploadFn = int (*)(const float*, int, const float*);
+using UploadFn = int (*)(const float*, int, const int*, const float*);
 using LaunchFn = int (*)(const YiLaunch&);
 constexpr UploadFn kUpload[kYiGroups] = {yi_upload_g0, yi_upload_g1, yi_upload_g2, yi_upload_g3};
 constexpr LaunchFn kLaunch[kYiGroups] = {yi_launch_g0, yi_launch_g1, yi_launch_g2, yi_launch_g3};
@@ -34,6 +34,9 @@ double ycg_value(int c, int a, int b, int r, int m1a) {
 std::mutex g_upload_mu;
 bool g_uploaded[64] = {false};
 
+// Per group: the full blocks of its couplings, [m][m1] over a and (a != b) [m][m2] over b
+// (C(b m2, a m1 | c m) = (-1)^((a + b - c)/2) C(a m1, b m2 | c m)), and per coupling
+// {a, b, offset of the (a, b) block, offset of the (b, a) block}.
 int ensure_yi_tables(int device) {
     std::lock_guard<std::mutex> lk(g_upload_mu);
     if (device >= 0 && device < 64 && g_uploaded[device]) return MALA_OK;
@@ -46,30 +49,35 @@ int ensure_yi_tables(int device) {
     for (int g = 0; g < kYiGroups; ++g) {
         const unsigned mask = yi_mask(g);
         std::vector<float> tab;
+        std::vector<int> info(4 * (size_t)kNCouplings, -1);
         for (int c = 0; c <= kTJMax; ++c) {
             if (!((mask >> c) & 1u)) continue;
             for (int i = 0; i < n_couplings(c); ++i) {
                 const int a = coupling_field(c, i, 0), b = coupling_field(c, i, 1);
-                for (int r = 0; 2 * r <= c; ++r)
-                    for (int m1a = 0; m1a <= a; ++m1a) tab.push_back((float)ycg_value(c, a, b, r, m1a));
+                const int k = coupling_base(c) + i;
+                info[4 * k] = a;
+                info[4 * k + 1] = b;
+                info[4 * k + 2] = (int)tab.size();
+                for (int m = 0; m <= c; ++m)
+                    for (int m1a = 0; m1a <= a; ++m1a) tab.push_back((float)ycg_value(c, a, b, m, m1a));
+                if (a != b) {
+                    const double sg = (((a + b - c) / 2) & 1) ? -1.0 : 1.0;
+                    const int d = (a + b - c) / 2;
+                    info[4 * k + 3] = (int)tab.size();
+                    for (int m = 0; m <= c; ++m)
+                        for (int m2a = 0; m2a <= b; ++m2a) {
+                            const int m1a = m - m2a + d;  // the partner in u^a
+                            tab.push_back(m1a < 0 || m1a > a ? 0.f : (float)(sg * ycg_value(c, a, b, m, m1a)));
+                        }
+                } else {
+                    info[4 * k + 3] = info[4 * k + 2];
+                }
             }
         }
-        MALA_TRY(kUpload[g](tab.data(), (int)tab.size(), fn.data()));
+        MALA_TRY(kUpload[g](tab.data(), (int)tab.size(), info.data(), fn.data()));
     }
     if (device >= 0 && device < 64) g_uploaded[device] = true;
     return MALA_OK;
-}
-
-// complex multiply-adds of one unit with NCOL columns
-int unit_terms(int a, int b, int c, int ncol) {
-    const int d = (a + b - c) / 2;
-    int n = 0;
-    for (int mb = 0; mb < ncol; ++mb)
-        for (int m1b = 0; m1b <= a; ++m1b) {
-            const int m2b = mb - m1b + d;
-            if (m2b >= 0 && m2b <= b) ++n;
-        }
-    return n;
 }
 
 struct HostPlan {
@@ -123,8 +131,13 @@ void build_plan(int tj, HostPlan& H) {
                         const int m2a = ma - m1a + d;
                         if (m2a < 0 || m2a > b) continue;
                         if (std::fabs(ycg_value(c, a, b, ma, m1a)) < 1e-10) continue;
-                        us.push_back((unsigned short)(i | (m1a << 6)));
-                        cost.push_back(6.0 * unit_terms(a, b, c, ncol) + 3.0 * ncol + 2.0 * (a + b + 2) + 12.0);
+                        // the shorter row in registers when the longer one lies at or below its
+                        // middle (it is then read from shared memory), else the other way round
+                        const int swap = (2 * m1a <= a) ? 1 : 0;
+                        const int R = swap ? b : a;
+                        us.push_back((unsigned short)(i | (m1a << 6) | (swap << 10)));
+                        cost.push_back(12.0 * (R + 1) * ((ncol + 1) / 2) + 4.0 * (R + 2) * ((ncol + 1) / 2) +
+                                       2.0 * (R + 1) + 24.0);
                     }
                 }
                 std::vector<int> order(us.size());

@@ -20,7 +20,7 @@
 
 namespace mala {
 
-constexpr int kYuWarps = 12;            // warps per CTA of the unit kernels
+constexpr int kYuWarps = 16;            // warps per CTA of the unit kernels
 constexpr int kYuPts = 64;              // grid points per CTA: two per lane
 constexpr int kYuMaxCols = kTJMax + 1;  // columns of a Y row
 
@@ -55,13 +55,21 @@ __host__ __device__ constexpr int coupling_base(int c) {
 }
 constexpr int kNCouplings = coupling_base(kTJMax + 1);
 
-// Clebsch-Gordan block of a coupling: rows r = 0..c/2 (coupled projection
-// 2r - c), columns m1 = 0..a; rows above c/2 follow from
-// C(a -m1, b -m2 | c -m) = (-1)^((a + b - c)/2) C(a m1, b m2 | c m).
-__host__ __device__ constexpr int ycg_block(int c, int a) { return (c / 2 + 1) * (a + 1); }
+// Shared-memory layout of u the unit kernels read: for every J the rows
+// ma <= J/2 in full (J + 1 elements each, the middle row too), row (J, ma) at
+// frow_off(J) + ma (J + 1); rows above the middle follow from
+// u[J-ma][J-mb] = (-1)^(ma-mb) conj(u[ma][mb]).
+__host__ __device__ constexpr int frow_off(int J) {
+    int o = 0;
+    for (int k = 0; k < J; ++k) o += (k / 2 + 1) * (k + 1);
+    return o;
+}
+__host__ __device__ constexpr int n_frows(int tj) { return frow_off(tj + 1); }
 
-// The couplings are split by c over four translation units (code size and
-// compile time); each holds the blocks of its couplings, c ascending.
+// The couplings are split by c over four translation units (one launch each);
+// each holds, in constant memory, the full Clebsch-Gordan blocks of its
+// couplings in both orientations: [m][m1] (rows m = 0..c, columns over a) and,
+// for a != b, the block of (c; b, a), [m][m2] with columns over b.
 constexpr int kYiGroups = 4;
 __host__ __device__ constexpr unsigned yi_mask(int g) {
     return g == 0 ? ((1u << 10) | (1u << 3) | (1u << 1))
@@ -69,30 +77,13 @@ __host__ __device__ constexpr unsigned yi_mask(int g) {
          : g == 2 ? ((1u << 6) | (1u << 7))
                   : ((1u << 4) | (1u << 9) | (1u << 2));
 }
-__host__ __device__ constexpr int ycg_offset(unsigned mask, int c, int i) {
-    int off = 0;
-    for (int k = 0; k <= kTJMax; ++k) {
-        if (!((mask >> k) & 1u)) continue;
-        for (int j = 0; j < n_couplings(k); ++j) {
-            if (k == c && j == i) return off;
-            off += ycg_block(k, coupling_field(k, j, 0));
-        }
-    }
-    return -1;
-}
-__host__ __device__ constexpr int ycg_size(unsigned mask) {
-    int off = 0;
-    for (int k = 0; k <= kTJMax; ++k) {
-        if (!((mask >> k) & 1u)) continue;
-        for (int j = 0; j < n_couplings(k); ++j) off += ycg_block(k, coupling_field(k, j, 0));
-    }
-    return off;
-}
-constexpr int kYcgCap = 1792;  // pairs; every group's table fits
+constexpr int kYcgCap = 4736;  // pairs; every group's blocks fit, with room for a read one row past the last
 
 // Work of one launch (one group), in device memory.  Row r of the launch is
 // (c, ma) = rows[row0 + r]; warp w takes units off[(row0 + r) * (kYuWarps + 1) + w]
-// up to the next offset; a unit is (coupling index within c) | m1a << 6.
+// up to the next offset; a unit is (coupling index within c) | m1a << 6 |
+// s << 10, s = 1 when the u^b row is the one held in registers (the u^a row is
+// then read from shared memory), s = 0 the other way round.
 struct YiPlan {
     const int2* rows;
     const int* off;
@@ -102,9 +93,9 @@ struct YiPlan {
     int row0, nrows;
 };
 
-// dynamic shared memory of a unit kernel: u half set, beta, the warps' partial rows
-inline size_t yi_units_smem(int tj, int nB) {
-    return (size_t)n_half(tj) * 512 + (size_t)nB * 256 + (size_t)kYuWarps * kYuMaxCols * 512;
+// dynamic shared memory of a unit kernel: u rows and the warps' partial rows
+inline size_t yi_units_smem(int tj, int) {
+    return (size_t)n_frows(tj) * 512 + (size_t)kYuWarps * kYuMaxCols * 512;
 }
 
 struct YiLaunch {
@@ -118,11 +109,12 @@ struct YiLaunch {
     cudaStream_t st;
 };
 
-// per group g: the table upload and the launch (snap_yi_g<g>.cu)
-int yi_upload_g0(const float* cg, int n, const float* fnorm);
-int yi_upload_g1(const float* cg, int n, const float* fnorm);
-int yi_upload_g2(const float* cg, int n, const float* fnorm);
-int yi_upload_g3(const float* cg, int n, const float* fnorm);
+// per group g: the table upload (blocks, per-coupling info {a, b, offset of the
+// (a, b) block, offset of the (b, a) block}, N) and the launch (snap_yi_g<g>.cu)
+int yi_upload_g0(const float* cg, int n, const int* info, const float* fnorm);
+int yi_upload_g1(const float* cg, int n, const int* info, const float* fnorm);
+int yi_upload_g2(const float* cg, int n, const int* info, const float* fnorm);
+int yi_upload_g3(const float* cg, int n, const int* info, const float* fnorm);
 int yi_launch_g0(const YiLaunch& a);
 int yi_launch_g1(const YiLaunch& a);
 int yi_launch_g2(const YiLaunch& a);

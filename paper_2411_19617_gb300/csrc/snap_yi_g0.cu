@@ -5,7 +5,9 @@
 
 namespace mala {
 
-int yi_upload_g0(const float* cg, int n, const float* fnorm) { return yi_upload<yi_mask(0)>(cg, n, fnorm); }
+int yi_upload_g0(const float* cg, int n, const int* info, const float* fnorm) {
+    return yi_upload<yi_mask(0)>(cg, n, info, fnorm);
+}
 int yi_launch_g0(const YiLaunch& a) { return yi_launch<yi_mask(0)>(a); }
 
 }  // namespace mala

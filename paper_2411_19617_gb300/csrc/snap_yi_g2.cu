@@ -5,7 +5,9 @@
 
 namespace mala {
 
-int yi_upload_g2(const float* cg, int n, const float* fnorm) { return yi_upload<yi_mask(2)>(cg, n, fnorm); }
+int yi_upload_g2(const float* cg, int n, const int* info, const float* fnorm) {
+    return yi_upload<yi_mask(2)>(cg, n, info, fnorm);
+}
 int yi_launch_g2(const YiLaunch& a) { return yi_launch<yi_mask(2)>(a); }
 
 }  // namespace mala

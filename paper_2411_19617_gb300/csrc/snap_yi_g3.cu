@@ -5,7 +5,9 @@
 
 namespace mala {
 
-int yi_upload_g3(const float* cg, int n, const float* fnorm) { return yi_upload<yi_mask(3)>(cg, n, fnorm); }
+int yi_upload_g3(const float* cg, int n, const int* info, const float* fnorm) {
+    return yi_upload<yi_mask(3)>(cg, n, info, fnorm);
+}
 int yi_launch_g3(const YiLaunch& a) { return yi_launch<yi_mask(3)>(a); }
 
 }  // namespace mala
