@@ -181,10 +181,24 @@ __global__ void __launch_bounds__(256) k_gemm_rows(const T* __restrict__ X, cons
 #pragma unroll
             for (int j = 0; j < TN; j += VEC)
                 *reinterpret_cast<uint4*>(&bv[j]) = *reinterpret_cast<const uint4*>(&ws[b][kk][tx * TN + j]);
+            if constexpr (sizeof(T) == 4) {
+                // rows in pairs: one packed FP32x2 FMA per (row pair, column), each half the same
+                // fused multiply-add as the scalar form (same bits), half the issue slots
 #pragma unroll
-            for (int i = 0; i < TM; ++i)
+                for (int i = 0; i < TM; i += 2)
 #pragma unroll
-                for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], bv[j], acc[i][j]);
+                    for (int j = 0; j < TN; ++j) {
+                        const float2 r = __ffma2_rn(make_float2(a[i], a[i + 1]), make_float2(bv[j], bv[j]),
+                                                    make_float2(acc[i][j], acc[i + 1][j]));
+                        acc[i][j] = r.x;
+                        acc[i + 1][j] = r.y;
+                    }
+            } else {
+#pragma unroll
+                for (int i = 0; i < TM; ++i)
+#pragma unroll
+                    for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], bv[j], acc[i][j]);
+            }
         }
         // the other buffer was last read before the previous barrier
         if (t + 1 < ntile) store(b ^ 1);
