@@ -55,12 +55,6 @@ namespace {
 // full_off(J) = sum_{k<J} (k+1)^2 in closed form
 __device__ __forceinline__ int full_off_cf(int J) { return J * (J + 1) * (2 * J + 1) / 6; }
 
-__device__ __forceinline__ float2 lds2(uint32_t addr) {
-    float2 v;
-    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(addr));
-    return v;
-}
-
 __device__ __forceinline__ void sts4(uint32_t addr, float4 v) {
     asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
                  : "memory");

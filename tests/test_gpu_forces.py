@@ -91,7 +91,9 @@ def _model_with_output_activation(c, mlp):
 
 
 @pytest.mark.parametrize("precision,tj,grid", [("fp64", 4, 8), ("fp64", 6, (7, 5, 6)), ("mixed", 6, 8),
-                                               ("mixed", 10, (9, 7, 5)), ("fp64", 10, 5)])
+                                               ("mixed", 10, (9, 7, 5)), ("fp64", 10, 5), ("mixed", 0, 5),
+                                               ("mixed", 2, (7, 6, 5)), ("mixed", 4, (3, 11, 4)),
+                                               ("mixed", 8, (6, 5, 7))])
 def test_descriptor_forces_match_oracle(precision, tj, grid):
     torch = need_gpu()
     from paper_2411_19617_gb300 import api
