@@ -209,6 +209,79 @@ __device__ __forceinline__ void lin_mul(T (&vr)[N], T (&vi)[N], int n, T l0r, T 
     }
 }
 
+// The chain walk of k_force, one level at a time: level J of column chain cc
+// (the chain index at run time, the level's code compiled once per J), so
+// the code a neighbour runs is the eleven level bodies rather than all 66
+// (chain, level) pairs unrolled, and stays in the instruction cache.
+template <class T> struct GSums {
+    T G0, Gar, Gai, Gbr, Gbi;
+};
+
+template <class T, int TJ, int J>
+__device__ __forceinline__ void force_level(const typename Cx<T>::type* __restrict__ ys, int cc, T (&pr)[TJ + 1],
+                                            T (&pim)[TJ + 1], T al0r, T al0i, T al1r, T al1i, GSums<T>& gs) {
+    using C = typename Cx<T>::type;
+    constexpr int o = full_off(J);
+    T s0 = T(0);
+#pragma unroll
+    for (int k2 = 0; k2 <= J; ++k2) {
+        const C yv = ys[o + k2 * (J + 1) + cc];
+        s0 += yv.x * pr[k2] - yv.y * pim[k2];
+    }
+    gs.G0 += s0;
+    if constexpr (J < TJ) {
+        constexpr int o1 = full_off(J + 1);
+        T a0r = T(0), a0i = T(0), a1r = T(0), a1i = T(0), b0r = T(0), b0i = T(0), b1r = T(0), b1i = T(0);
+#pragma unroll
+        for (int k2 = 0; k2 <= J; ++k2) {
+            const C ya0 = ys[o1 + k2 * (J + 2) + cc];
+            const C ya1 = ys[o1 + (k2 + 1) * (J + 2) + cc];
+            const C yb0 = ys[o1 + k2 * (J + 2) + cc + 1];
+            const C yb1 = ys[o1 + (k2 + 1) * (J + 2) + cc + 1];
+            const T xr = pr[k2], xi = pim[k2];
+            a0r += ya0.x * xr - ya0.y * xi;
+            a0i += ya0.x * xi + ya0.y * xr;
+            a1r += ya1.x * xr - ya1.y * xi;
+            a1i += ya1.x * xi + ya1.y * xr;
+            b0r += yb0.x * xr - yb0.y * xi;
+            b0i += yb0.x * xi + yb0.y * xr;
+            b1r += yb1.x * xr - yb1.y * xi;
+            b1i += yb1.x * xi + yb1.y * xr;
+        }
+        const T fa = T(J + 1 - cc), fb = T(cc + 1);
+        gs.Gar += fa * a0r + fb * b1r;
+        gs.Gai += fa * a0i - fb * b1i;
+        gs.Gbr += -fa * a1r + fb * b0r;
+        gs.Gbi += -fa * a1i - fb * b0i;
+        lin_mul<T, TJ + 1>(pr, pim, J + 1, al0r, al0i, al1r, al1i);  // level J: J + 1 coefficients
+    }
+}
+
+template <class T, int TJ, int LO, int HI>
+__device__ __forceinline__ void force_level_at(int J, const typename Cx<T>::type* ys, int cc, T (&pr)[TJ + 1],
+                                               T (&pim)[TJ + 1], T al0r, T al0i, T al1r, T al1i, GSums<T>& gs) {
+    if constexpr (HI - LO == 1) {
+        force_level<T, TJ, LO>(ys, cc, pr, pim, al0r, al0i, al1r, al1i, gs);
+    } else {
+        constexpr int MID = (LO + HI) / 2;
+        if (J < MID) force_level_at<T, TJ, LO, MID>(J, ys, cc, pr, pim, al0r, al0i, al1r, al1i, gs);
+        else force_level_at<T, TJ, MID, HI>(J, ys, cc, pr, pim, al0r, al0i, al1r, al1i, gs);
+    }
+}
+
+// beta^cc from beta^(cc-1) (cc coefficients -> cc + 1), cc >= 1 at run time
+template <class T, int TJ, int LO, int HI>
+__device__ __forceinline__ void beta_step_at(int cc, T (&dr)[TJ + 1], T (&di)[TJ + 1], T be0r, T be0i, T be1r,
+                                             T be1i) {
+    if constexpr (HI - LO == 1) {
+        lin_mul<T, TJ + 1>(dr, di, LO, be0r, be0i, be1r, be1i);
+    } else {
+        constexpr int MID = (LO + HI) / 2;
+        if (cc < MID) beta_step_at<T, TJ, LO, MID>(cc, dr, di, be0r, be0i, be1r, be1i);
+        else beta_step_at<T, TJ, MID, HI>(cc, dr, di, be0r, be0i, be1r, be1i);
+    }
+}
+
 template <class T, int TJ>
 __global__ void __launch_bounds__(kForceWarps * 32) k_force(const T* __restrict__ y_all, int64_t P, int cap,
                                                             const int* __restrict__ cnt, const int* __restrict__ atoms,
@@ -269,7 +342,7 @@ __global__ void __launch_bounds__(kForceWarps * 32) k_force(const T* __restrict_
             // linear forms: alpha = (ar - i ai) xi + (-br + i bi) eta, beta = (br + i bi) xi + (ar + i ai) eta
             const T al0r = ar, al0i = -ai, al1r = -br, al1i = bi;
             const T be0r = br, be0i = bi, be1r = ar, be1i = ai;
-            T G0 = T(0), Gar = T(0), Gai = T(0), Gbr = T(0), Gbi = T(0);
+            GSums<T> gs{T(0), T(0), T(0), T(0), T(0)};
             T dr_[TJ + 1], di_[TJ + 1];
 #pragma unroll
             for (int i = 0; i <= TJ; ++i) {
@@ -277,54 +350,19 @@ __global__ void __launch_bounds__(kForceWarps * 32) k_force(const T* __restrict_
                 di_[i] = T(0);
             }
             dr_[0] = T(1);
-#pragma unroll
             for (int cc = 0; cc <= TJ; ++cc) {
-                if (cc > 0) lin_mul<T, TJ + 1>(dr_, di_, cc, be0r, be0i, be1r, be1i);  // beta^(cc-1) has cc coefficients
+                // beta^(cc-1) has cc coefficients
+                if (cc > 0) beta_step_at<T, TJ, 1, TJ + 1>(cc, dr_, di_, be0r, be0i, be1r, be1i);
                 T pr[TJ + 1], pim[TJ + 1];
 #pragma unroll
                 for (int i = 0; i <= TJ; ++i) {
                     pr[i] = dr_[i];
                     pim[i] = di_[i];
                 }
-#pragma unroll
-                for (int J = cc; J <= TJ; ++J) {
-                    const int o = full_off(J);
-                    T s0 = T(0);
-#pragma unroll
-                    for (int k2 = 0; k2 <= J; ++k2) {
-                        const C yv = ys[o + k2 * (J + 1) + cc];
-                        s0 += yv.x * pr[k2] - yv.y * pim[k2];
-                    }
-                    G0 += s0;
-                    if (J < TJ) {
-                        const int o1 = full_off(J + 1);
-                        T a0r = T(0), a0i = T(0), a1r = T(0), a1i = T(0), b0r = T(0), b0i = T(0), b1r = T(0),
-                          b1i = T(0);
-#pragma unroll
-                        for (int k2 = 0; k2 <= J; ++k2) {
-                            const C ya0 = ys[o1 + k2 * (J + 2) + cc];
-                            const C ya1 = ys[o1 + (k2 + 1) * (J + 2) + cc];
-                            const C yb0 = ys[o1 + k2 * (J + 2) + cc + 1];
-                            const C yb1 = ys[o1 + (k2 + 1) * (J + 2) + cc + 1];
-                            const T xr = pr[k2], xi = pim[k2];
-                            a0r += ya0.x * xr - ya0.y * xi;
-                            a0i += ya0.x * xi + ya0.y * xr;
-                            a1r += ya1.x * xr - ya1.y * xi;
-                            a1i += ya1.x * xi + ya1.y * xr;
-                            b0r += yb0.x * xr - yb0.y * xi;
-                            b0i += yb0.x * xi + yb0.y * xr;
-                            b1r += yb1.x * xr - yb1.y * xi;
-                            b1i += yb1.x * xi + yb1.y * xr;
-                        }
-                        const T fa = T(J + 1 - cc), fb = T(cc + 1);
-                        Gar += fa * a0r + fb * b1r;
-                        Gai += fa * a0i - fb * b1i;
-                        Gbr += -fa * a1r + fb * b0r;
-                        Gbi += -fa * a1i - fb * b0i;
-                        lin_mul<T, TJ + 1>(pr, pim, J + 1, al0r, al0i, al1r, al1i);  // level J: J + 1 coefficients
-                    }
-                }
+                for (int J = cc; J <= TJ; ++J)
+                    force_level_at<T, TJ, 0, TJ + 1>(J, ys, cc, pr, pim, al0r, al0i, al1r, al1i, gs);
             }
+            const T G0 = gs.G0, Gar = gs.Gar, Gai = gs.Gai, Gbr = gs.Gbr, Gbi = gs.Gbi;
             // chain rule to the offset d
             const T ir = T(1) / r;
             const T dsdr = (co * rfac0 * K * r - so) * ir * ir;
