@@ -15,9 +15,10 @@
 // N = 3: sum <l1 m1 l2 m2|l3 M><l3 M l3 -M|0 0> A_{c1 l1 m1} A_{c2 l2 m2} A_{c3 l3 -M}.
 //
 // Mapping: one warp per grid point (persistent).  Lanes take neighbours; each
-// lane evaluates R_n and Y_l^m of its neighbour, and a butterfly reduction over
-// the warp (fixed order: deterministic) adds each A element into the warp's
-// shared-memory copy of A.  The lanes then take descriptor columns and contract
+// lane evaluates R_n and Y_l^m of its neighbour, and for every (species, n) a
+// reduce-scatter over the warp (fixed order: deterministic) leaves lane l with
+// the batch's sum of value l of a chunk of 16 (l, m) elements (re, im), which
+// it adds into the warp's shared-memory copy of A.  The lanes then take descriptor columns and contract
 // A with host-built coefficient lists; each row is written coalesced.
 #include <cuda_runtime.h>
 
@@ -92,8 +93,28 @@ __host__ __device__ inline size_t ace_table_bytes(int n_desc, int n_coef) {
     return ace_coef_bytes(n_coef) + (((size_t)n_desc * sizeof(AceCol) + 15) & ~size_t(15));
 }
 
+// Reduce-scatter over the warp: each lane holds N values (N a multiple of 32);
+// after log2(32) halving steps lane l holds the warp sums of values
+// (N/32) l .. (N/32) l + N/32 - 1 in v[0 .. N/32 - 1].  A step exchanges half of
+// the live values with the partner lane (lane ^ mask): the lane whose mask bit
+// is set keeps the upper half.  The order of the additions is fixed.
+template <class T, int N, int H>
+__device__ __forceinline__ void reduce_scatter(T (&v)[N], int lane) {
+    if constexpr (H >= N / 32) {
+        constexpr int mask = 32 * H / N;
+        const bool up = (lane & mask) != 0;
+#pragma unroll
+        for (int i = 0; i < H; ++i) {
+            const T send = up ? v[i] : v[i + H];
+            const T keep = up ? v[i + H] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, mask);
+        }
+        reduce_scatter<T, N, H / 2>(v, lane);
+    }
+}
+
 template <class T>
-__global__ void __launch_bounds__(kAceWarps * 32) k_ace(AceArgs g, T* __restrict__ out) {
+__global__ void __launch_bounds__(kAceWarps * 32, 3) k_ace(AceArgs g, T* __restrict__ out) {
     using C = typename Cx<T>::type;
     extern __shared__ __align__(16) unsigned char smem_ace[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -193,21 +214,23 @@ __global__ void __launch_bounds__(kAceWarps * 32) k_ace(AceArgs g, T* __restrict
                     }
                     const T rn = mine ? tn * fc : T(0);
                     const int base = (s * g.nmax + nn) * g.n_lm;
+                    // the (l, m) elements in chunks of 16: v holds (re, im) of chunk element e at 2e, 2e + 1;
+                    // after the reduce-scatter lane l holds the warp sum of value l of the chunk
 #pragma unroll
-                    for (int l = 0; l <= kAceLMax; ++l) {
-                        if (l > g.lmax) break;
+                    for (int c0 = 0; c0 < kAceLM; c0 += 16) {
+                        if (c0 >= g.n_lm) break;
+                        T v[32];
 #pragma unroll
-                        for (int m = 0; m <= l; ++m) {
-                            T vr = rn * yr[lm_index(l, m)], vi = rn * yi[lm_index(l, m)];
-#pragma unroll
-                            for (int o = 16; o > 0; o >>= 1) {
-                                vr += __shfl_xor_sync(0xffffffffu, vr, o);
-                                vi += __shfl_xor_sync(0xffffffffu, vi, o);
-                            }
-                            if (lane == 0) {
-                                A[base + lm_index(l, m)].x += vr;
-                                A[base + lm_index(l, m)].y += vi;
-                            }
+                        for (int e = 0; e < 16; ++e) {
+                            const int lm = c0 + e < kAceLM ? c0 + e : 0;
+                            v[2 * e] = c0 + e < kAceLM ? rn * yr[lm] : T(0);
+                            v[2 * e + 1] = c0 + e < kAceLM ? rn * yi[lm] : T(0);
+                        }
+                        reduce_scatter<T, 32, 16>(v, lane);
+                        const int lm = c0 + (lane >> 1);
+                        if (lm < g.n_lm) {
+                            if (lane & 1) A[base + lm].y += v[0];
+                            else A[base + lm].x += v[0];
                         }
                     }
                 }
