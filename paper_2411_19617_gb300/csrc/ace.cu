@@ -113,8 +113,10 @@ __device__ __forceinline__ void reduce_scatter(T (&v)[N], int lane) {
     }
 }
 
-template <class T>
+// LMX: the largest l the kernel evaluates (4, 6 or 8, at least lmax)
+template <class T, int LMX>
 __global__ void __launch_bounds__(kAceWarps * 32, 3) k_ace(AceArgs g, T* __restrict__ out) {
+    constexpr int NLM = (LMX + 1) * (LMX + 2) / 2;
     using C = typename Cx<T>::type;
     extern __shared__ __align__(16) unsigned char smem_ace[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -170,12 +172,12 @@ __global__ void __launch_bounds__(kAceWarps * 32, 3) k_ace(AceArgs g, T* __restr
                 fc = T(0.5) * (T(1) + cp);
             }
             // Y_l^m (m >= 0) of the lane's neighbour
-            T yr[kAceLM], yi[kAceLM];
+            T yr[NLM], yi[NLM];
             {
                 T pmm = T(1);             // Ptilde_m^m
                 T er = T(1), ei = T(0);   // (x + i y)^m
 #pragma unroll
-                for (int m = 0; m <= kAceLMax; ++m) {
+                for (int m = 0; m <= LMX; ++m) {
                     if (m > 0) {
                         pmm *= -T(2 * m - 1);
                         const T nr = er * ux - ei * uy, ni = er * uy + ei * ux;
@@ -184,11 +186,17 @@ __global__ void __launch_bounds__(kAceWarps * 32, 3) k_ace(AceArgs g, T* __restr
                     }
                     T p2 = T(0), p1 = pmm;
 #pragma unroll
-                    for (int l = m; l <= kAceLMax; ++l) {
+                    for (int l = m; l <= LMX; ++l) {
                         T pl;
-                        if (l == m) pl = pmm;
-                        else if (l == m + 1) pl = T(2 * m + 1) * uz * pmm;
-                        else pl = (T(2 * l - 1) * uz * p1 - T(l + m - 1) * p2) / T(l - m);
+                        if (l == m) {
+                            pl = pmm;
+                        } else if (l == m + 1) {
+                            pl = T(2 * m + 1) * uz * pmm;
+                        } else {
+                            // (l - m) P_l = (2l - 1) z P_{l-1} - (l + m - 1) P_{l-2}, the ratios as constants
+                            const T ca = T((2.0 * l - 1.0) / (double)(l - m)), cb = T((l + m - 1.0) / (double)(l - m));
+                            pl = ca * uz * p1 - cb * p2;
+                        }
                         if (l > m) {
                             p2 = p1;
                             p1 = pl;
@@ -217,14 +225,14 @@ __global__ void __launch_bounds__(kAceWarps * 32, 3) k_ace(AceArgs g, T* __restr
                     // the (l, m) elements in chunks of 16: v holds (re, im) of chunk element e at 2e, 2e + 1;
                     // after the reduce-scatter lane l holds the warp sum of value l of the chunk
 #pragma unroll
-                    for (int c0 = 0; c0 < kAceLM; c0 += 16) {
+                    for (int c0 = 0; c0 < NLM; c0 += 16) {
                         if (c0 >= g.n_lm) break;
                         T v[32];
 #pragma unroll
                         for (int e = 0; e < 16; ++e) {
-                            const int lm = c0 + e < kAceLM ? c0 + e : 0;
-                            v[2 * e] = c0 + e < kAceLM ? rn * yr[lm] : T(0);
-                            v[2 * e + 1] = c0 + e < kAceLM ? rn * yi[lm] : T(0);
+                            const int lm = c0 + e < NLM ? c0 + e : 0;
+                            v[2 * e] = c0 + e < NLM ? rn * yr[lm] : T(0);
+                            v[2 * e + 1] = c0 + e < NLM ? rn * yi[lm] : T(0);
                         }
                         reduce_scatter<T, 32, 16>(v, lane);
                         const int lm = c0 + (lane >> 1);
@@ -269,6 +277,21 @@ __global__ void __launch_bounds__(kAceWarps * 32, 3) k_ace(AceArgs g, T* __restr
 }
 
 }  // namespace
+
+// the kernel compiled for the smallest supported l range that covers lmax
+template <class T>
+static void launch_ace(int lmax, int grid, size_t smem, const AceArgs& g, T* out, cudaStream_t st) {
+    if (lmax <= 4) {
+        cudaFuncSetAttribute(k_ace<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_ace<T, 4><<<grid, kAceWarps * 32, smem, st>>>(g, out);
+    } else if (lmax <= 6) {
+        cudaFuncSetAttribute(k_ace<T, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_ace<T, 6><<<grid, kAceWarps * 32, smem, st>>>(g, out);
+    } else {
+        cudaFuncSetAttribute(k_ace<T, kAceLMax>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_ace<T, kAceLMax><<<grid, kAceWarps * 32, smem, st>>>(g, out);
+    }
+}
 
 // columns in the order of the documented enumeration; returns the count
 static int ace_columns(const mala_ace_params* ap, std::vector<AceCol>* cols, std::vector<AceCoef>* coefs) {
@@ -411,12 +434,10 @@ int ace_from_lists(Ctx* c, const SnapDev& sd, const mala_snapshot* snap, const m
         const size_t tb = g.stage ? ace_table_bytes(nd, g.n_coef) : 0;
         if (prec == MALA_MIXED) {
             const size_t smem = tb + sizeof(float2) * (size_t)g.nA * kAceWarps;
-            cudaFuncSetAttribute(k_ace<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            MALA_PROF(c, "k_ace", st, (k_ace<float><<<grid, kAceWarps * 32, smem, st>>>(g, static_cast<float*>(out))));
+            MALA_PROF(c, "k_ace", st, (launch_ace<float>(lmax, grid, smem, g, static_cast<float*>(out), st)));
         } else {
             const size_t smem = tb + sizeof(double2) * (size_t)g.nA * kAceWarps;
-            cudaFuncSetAttribute(k_ace<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            MALA_PROF(c, "k_ace", st, (k_ace<double><<<grid, kAceWarps * 32, smem, st>>>(g, static_cast<double*>(out))));
+            MALA_PROF(c, "k_ace", st, (launch_ace<double>(lmax, grid, smem, g, static_cast<double*>(out), st)));
         }
         MALA_CUDA_TRY(cudaGetLastError());
     }
