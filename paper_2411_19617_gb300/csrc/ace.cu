@@ -48,9 +48,13 @@ template <> struct Cx<double> { using type = double2; };
 struct AceCol {
     int kind, a1, a2, a3, l1, l2, l3, c_off, c_cnt;
 };
+// one term of an N = 3 column: A1[i1] A2[i2] A3[i3] (each conjugated when its bit of
+// cj is set: A_{l,-m} = (-1)^m conj(A_{l,m})) times c, the (-1)^m signs folded into c;
+// i = lm_index(l, |m|) within the channel's block; cf = c rounded to FP32 on the host
 struct AceCoef {
     double c;
-    int m1, m2;
+    float cf;
+    short i1, i2, i3, cj;
 };
 
 struct AceArgs {
@@ -264,10 +268,15 @@ __global__ void __launch_bounds__(kAceWarps * 32, 3) k_ace(AceArgs g, T* __restr
             } else {
                 for (int q = cl.c_off; q < cl.c_off + cl.c_cnt; ++q) {
                     const AceCoef cf = coefs[q];
-                    const C x = a_at<T>(A, cl.a1, cl.l1, cf.m1), y = a_at<T>(A, cl.a2, cl.l2, cf.m2);
-                    const C z = a_at<T>(A, cl.a3, cl.l3, -(cf.m1 + cf.m2));
+                    C x = A[cl.a1 + cf.i1], y = A[cl.a2 + cf.i2], z = A[cl.a3 + cf.i3];
+                    if (cf.cj & 1) x.y = -x.y;
+                    if (cf.cj & 2) y.y = -y.y;
+                    if (cf.cj & 4) z.y = -z.y;
                     const T pr = x.x * y.x - x.y * y.y, pi_ = x.x * y.y + x.y * y.x;
-                    v += (T)cf.c * (pr * z.x - pi_ * z.y);
+                    T cv;
+                    if constexpr (sizeof(T) == 4) cv = cf.cf;
+                    else cv = cf.c;
+                    v += cv * (pr * z.x - pi_ * z.y);
                 }
             }
             o[d] = v;
@@ -330,7 +339,22 @@ static int ace_columns(const mala_ace_params* ap, std::vector<AceCol>* cols, std
                     if (M < -l3 || M > l3) continue;
                     const double c = clebsch_gordan(2 * l1, 2 * m1, 2 * l2, 2 * m2, 2 * l3, 2 * M) *
                                      clebsch_gordan(2 * l3, 2 * M, 2 * l3, -2 * M, 0, 0);
-                    if (c != 0.0) cf.push_back(AceCoef{c, m1, m2});
+                    if (c != 0.0) {
+                        // A_{l,m} for m < 0 is (-1)^m conj(A_{l,|m|}): the sign goes into c, the conjugation into cj
+                        const int ms[3] = {m1, m2, -M};
+                        const int ls[3] = {l1, l2, l3};
+                        double cc = c;
+                        short idx[3], cj = 0;
+                        for (int f = 0; f < 3; ++f) {
+                            const int am = ms[f] < 0 ? -ms[f] : ms[f];
+                            idx[f] = (short)(ls[f] * (ls[f] + 1) / 2 + am);
+                            if (ms[f] < 0) {
+                                cj |= (short)(1 << f);
+                                if (am & 1) cc = -cc;
+                            }
+                        }
+                        cf.push_back(AceCoef{cc, (float)cc, idx[0], idx[1], idx[2], cj});
+                    }
                 }
             lists[2 * key + 1] = (int)cf.size() - lists[2 * key];
         }
