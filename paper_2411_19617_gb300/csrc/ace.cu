@@ -81,17 +81,6 @@ __device__ __forceinline__ int lm_index(int l, int m) { return l * (l + 1) / 2 +
 // N_lm = sqrt((2l+1)/(4 pi) (l-m)!/(l+m)!) by (l, m >= 0) index, every compiled l
 __constant__ double c_ace_ynorm[kAceLM];
 
-template <class T>
-__device__ __forceinline__ typename Cx<T>::type a_at(const typename Cx<T>::type* A, int base, int l, int m) {
-    typename Cx<T>::type v = A[base + lm_index(l, m < 0 ? -m : m)];
-    if (m < 0) {
-        const T s = (m & 1) ? T(-1) : T(1);
-        v.x = s * v.x;
-        v.y = -s * v.y;
-    }
-    return v;
-}
-
 __host__ __device__ inline size_t ace_coef_bytes(int n_coef) { return ((size_t)n_coef * sizeof(AceCoef) + 15) & ~size_t(15); }
 __host__ __device__ inline size_t ace_table_bytes(int n_desc, int n_coef) {
     return ace_coef_bytes(n_coef) + (((size_t)n_desc * sizeof(AceCol) + 15) & ~size_t(15));
@@ -258,13 +247,17 @@ __global__ void __launch_bounds__(kAceWarps * 32, 3) k_ace(AceArgs g, T* __restr
             if (cl.kind == 1) {
                 v = A[cl.a1].x;
             } else if (cl.kind == 2) {
-                const int l = cl.l1;
-                const T inv = T(1) / sqrt(T(2 * l + 1));
-                for (int m = -l; m <= l; ++m) {
-                    const C x = a_at<T>(A, cl.a1, l, m), y = a_at<T>(A, cl.a2, l, -m);
-                    const T cg = (((l - m) & 1) ? -inv : inv);  // <l m l -m | 0 0>
-                    v += cg * (x.x * y.x - x.y * y.y);
+                // sum_m <l m l -m|0 0> Re(A1_m A2_-m) with A_-m = (-1)^m conj(A_m) and <l m l -m|0 0> =
+                // (-1)^(l-m)/sqrt(2l+1): (-1)^l/sqrt(2l+1) (Re(A1_0 A2_0) + 2 sum_{m>0} Re(A1_m conj(A2_m)))
+                const int l = cl.l1, b0 = l * (l + 1) / 2;
+                const C x0 = A[cl.a1 + b0], y0 = A[cl.a2 + b0];
+                T s2 = T(0);
+                for (int m = 1; m <= l; ++m) {
+                    const C x = A[cl.a1 + b0 + m], y = A[cl.a2 + b0 + m];
+                    s2 += x.x * y.x + x.y * y.y;
                 }
+                const T inv = ((l & 1) ? -T(1) : T(1)) / sqrt(T(2 * l + 1));
+                v = inv * ((x0.x * y0.x - x0.y * y0.y) + T(2) * s2);
             } else {
                 for (int q = cl.c_off; q < cl.c_off + cl.c_cnt; ++q) {
                     const AceCoef cf = coefs[q];
