@@ -44,9 +44,10 @@ template <class T> struct Cx;
 template <> struct Cx<float> { using type = float2; };
 template <> struct Cx<double> { using type = double2; };
 
-// descriptor column: kind 1, 2, 3; channel bases into A (mu n block * n_lm); l values; coefficient list
+// descriptor column: kind 1, 2, 3; channel bases into A (mu n block * n_lm); l values; coefficient
+// list; d: its place in the output row (the kernel takes the columns in descending order of cost)
 struct AceCol {
-    int kind, a1, a2, a3, l1, l2, l3, c_off, c_cnt;
+    int kind, a1, a2, a3, l1, l2, l3, c_off, c_cnt, d;
 };
 // one term of an N = 3 column: A1[i1] A2[i2] A3[i3] (each conjugated when its bit of
 // cj is set: A_{l,-m} = (-1)^m conj(A_{l,m})) times c, the (-1)^m signs folded into c;
@@ -80,6 +81,11 @@ __device__ __forceinline__ int lm_index(int l, int m) { return l * (l + 1) / 2 +
 
 // N_lm = sqrt((2l+1)/(4 pi) (l-m)!/(l+m)!) by (l, m >= 0) index, every compiled l
 __constant__ double c_ace_ynorm[kAceLM];
+__constant__ float c_ace_ynormf[kAceLM];  // the same rounded to FP32
+
+template <class T> __device__ __forceinline__ T ace_ynorm(int i);
+template <> __device__ __forceinline__ float ace_ynorm<float>(int i) { return c_ace_ynormf[i]; }
+template <> __device__ __forceinline__ double ace_ynorm<double>(int i) { return c_ace_ynorm[i]; }
 
 __host__ __device__ inline size_t ace_coef_bytes(int n_coef) { return ((size_t)n_coef * sizeof(AceCoef) + 15) & ~size_t(15); }
 __host__ __device__ inline size_t ace_table_bytes(int n_desc, int n_coef) {
@@ -106,25 +112,25 @@ __device__ __forceinline__ void reduce_scatter(T (&v)[N], int lane) {
     }
 }
 
-// LMX: the largest l the kernel evaluates (4, 6 or 8, at least lmax)
-template <class T, int LMX>
+// LMX: the largest l the kernel evaluates (4, 6 or 8, at least lmax); STAGE: the column and
+// coefficient tables are copied into shared memory (else read from global memory)
+template <class T, int LMX, bool STAGE>
 __global__ void __launch_bounds__(kAceWarps * 32, 3) k_ace(AceArgs g, T* __restrict__ out) {
     constexpr int NLM = (LMX + 1) * (LMX + 2) / 2;
     using C = typename Cx<T>::type;
     extern __shared__ __align__(16) unsigned char smem_ace[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // shared memory: [coefficients][columns] (when staged) | A of each warp
-    const size_t tab_bytes = g.stage ? ace_table_bytes(g.n_desc, g.n_coef) : 0;
-    const AceCoef* coefs = g.coefs;
-    const AceCol* cols = g.cols;
-    if (g.stage) {
+    const size_t tab_bytes = STAGE ? ace_table_bytes(g.n_desc, g.n_coef) : 0;
+    // the pointers are fixed per instantiation, so staged tables are read by shared-memory loads
+    const AceCoef* coefs = STAGE ? reinterpret_cast<const AceCoef*>(smem_ace) : g.coefs;
+    const AceCol* cols = STAGE ? reinterpret_cast<const AceCol*>(smem_ace + ace_coef_bytes(g.n_coef)) : g.cols;
+    if constexpr (STAGE) {
         AceCoef* sc = reinterpret_cast<AceCoef*>(smem_ace);
         AceCol* scl = reinterpret_cast<AceCol*>(smem_ace + ace_coef_bytes(g.n_coef));
         for (int i = threadIdx.x; i < g.n_coef; i += blockDim.x) sc[i] = g.coefs[i];
         for (int i = threadIdx.x; i < g.n_desc; i += blockDim.x) scl[i] = g.cols[i];
         __syncthreads();
-        coefs = sc;
-        cols = scl;
     }
     C* A = reinterpret_cast<C*>(smem_ace + tab_bytes) + (size_t)warp * g.nA;
     for (int64_t p = (int64_t)blockIdx.x * kAceWarps + warp; p < g.P; p += (int64_t)gridDim.x * kAceWarps) {
@@ -194,7 +200,7 @@ __global__ void __launch_bounds__(kAceWarps * 32, 3) k_ace(AceArgs g, T* __restr
                             p2 = p1;
                             p1 = pl;
                         }
-                        const T nrm = (T)c_ace_ynorm[lm_index(l, m)] * (center && l > 0 ? T(0) : T(1));
+                        const T nrm = ace_ynorm<T>(lm_index(l, m)) * (center && l > 0 ? T(0) : T(1));
                         yr[lm_index(l, m)] = nrm * pl * er;
                         yi[lm_index(l, m)] = nrm * pl * ei;
                     }
@@ -272,7 +278,7 @@ __global__ void __launch_bounds__(kAceWarps * 32, 3) k_ace(AceArgs g, T* __restr
                     v += cv * (pr * z.x - pi_ * z.y);
                 }
             }
-            o[d] = v;
+            o[cl.d] = v;
         }
         __syncwarp();
     }
@@ -280,19 +286,24 @@ __global__ void __launch_bounds__(kAceWarps * 32, 3) k_ace(AceArgs g, T* __restr
 
 }  // namespace
 
+// the kernel with the table path the arguments ask for
+template <class T, int LMX>
+static void launch_ace_l(int grid, size_t smem, const AceArgs& g, T* out, cudaStream_t st) {
+    if (g.stage) {
+        cudaFuncSetAttribute(k_ace<T, LMX, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_ace<T, LMX, true><<<grid, kAceWarps * 32, smem, st>>>(g, out);
+    } else {
+        cudaFuncSetAttribute(k_ace<T, LMX, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_ace<T, LMX, false><<<grid, kAceWarps * 32, smem, st>>>(g, out);
+    }
+}
+
 // the kernel compiled for the smallest supported l range that covers lmax
 template <class T>
 static void launch_ace(int lmax, int grid, size_t smem, const AceArgs& g, T* out, cudaStream_t st) {
-    if (lmax <= 4) {
-        cudaFuncSetAttribute(k_ace<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_ace<T, 4><<<grid, kAceWarps * 32, smem, st>>>(g, out);
-    } else if (lmax <= 6) {
-        cudaFuncSetAttribute(k_ace<T, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_ace<T, 6><<<grid, kAceWarps * 32, smem, st>>>(g, out);
-    } else {
-        cudaFuncSetAttribute(k_ace<T, kAceLMax>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_ace<T, kAceLMax><<<grid, kAceWarps * 32, smem, st>>>(g, out);
-    }
+    if (lmax <= 4) launch_ace_l<T, 4>(grid, smem, g, out, st);
+    else if (lmax <= 6) launch_ace_l<T, 6>(grid, smem, g, out, st);
+    else launch_ace_l<T, kAceLMax>(grid, smem, g, out, st);
 }
 
 // columns in the order of the documented enumeration; returns the count
@@ -305,7 +316,7 @@ static int ace_columns(const mala_ace_params* ap, std::vector<AceCol>* cols, std
     std::vector<AceCol> cl;
     std::vector<AceCoef> cf;
     for (int mu = 0; mu < ns; ++mu)
-        for (int n = 0; n < ap->nmax1; ++n) cl.push_back(AceCol{1, base(mu, n), 0, 0, 0, 0, 0, 0, 0});
+        for (int n = 0; n < ap->nmax1; ++n) cl.push_back(AceCol{1, base(mu, n), 0, 0, 0, 0, 0, 0, 0, 0});
     std::vector<std::pair<int, int>> ch2;
     for (int mu = 0; mu < ns; ++mu)
         for (int n = 0; n < ap->nmax2; ++n) ch2.push_back({mu, n});
@@ -313,7 +324,7 @@ static int ace_columns(const mala_ace_params* ap, std::vector<AceCol>* cols, std
         for (size_t j = i; j < ch2.size(); ++j)
             for (int l = 0; l <= ap->lmax2; ++l)
                 cl.push_back(AceCol{2, base(ch2[i].first, ch2[i].second), base(ch2[j].first, ch2[j].second), 0, l, l,
-                                    0, 0, 0});
+                                    0, 0, 0, 0});
     struct Ch3 {
         int mu, n, l;
     };
@@ -362,8 +373,9 @@ static int ace_columns(const mala_ace_params* ap, std::vector<AceCol>* cols, std
                 int off = 0, cnt = 0;
                 coef_list(l1, l2, l3, &off, &cnt);
                 cl.push_back(AceCol{3, base(ch3[i].mu, ch3[i].n), base(ch3[j].mu, ch3[j].n), base(ch3[k].mu, ch3[k].n),
-                                    l1, l2, l3, off, cnt});
+                                    l1, l2, l3, off, cnt, 0});
             }
+    for (size_t i = 0; i < cl.size(); ++i) cl[i].d = (int)i;
     if (cols) *cols = cl;
     if (coefs) *coefs = cf;
     return (int)cl.size();
@@ -393,6 +405,10 @@ int ace_from_lists(Ctx* c, const SnapDev& sd, const mala_snapshot* snap, const m
     std::vector<AceCol> cols;
     std::vector<AceCoef> coefs;
     const int nd = ace_columns(ap, &cols, &coefs);
+    // a warp takes 32 columns at a time and waits for its costliest: order them by cost (terms,
+    // an N = 3 term about twice an N = 2 one), so that the columns taken together cost about the same
+    auto cost = [](const AceCol& x) { return x.kind == 3 ? 2 * x.c_cnt : x.kind == 2 ? x.l1 + 1 : 1; };
+    std::stable_sort(cols.begin(), cols.end(), [&](const AceCol& x, const AceCol& y) { return cost(x) > cost(y); });
     const int nmax = std::max(ap->nmax1, std::max(ap->nmax2, ap->nmax3));
     const int lmax = std::max(ap->lmax2, ap->lmax3);
     const int nlm = (lmax + 1) * (lmax + 2) / 2;
@@ -417,7 +433,9 @@ int ace_from_lists(Ctx* c, const SnapDev& sd, const mala_snapshot* snap, const m
     // the tables are host vectors of this call: copy synchronously before they go out of scope
     if (!cols.empty()) MALA_CUDA_TRY(cudaMemcpyAsync(d_cols, cols.data(), sizeof(AceCol) * cols.size(), cudaMemcpyHostToDevice, st));
     if (!coefs.empty()) MALA_CUDA_TRY(cudaMemcpyAsync(d_coef, coefs.data(), sizeof(AceCoef) * coefs.size(), cudaMemcpyHostToDevice, st));
+    std::vector<float> ynf(yn.begin(), yn.end());
     MALA_CUDA_TRY(cudaMemcpyToSymbolAsync(c_ace_ynorm, yn.data(), sizeof(double) * kAceLM, 0, cudaMemcpyHostToDevice, st));
+    MALA_CUDA_TRY(cudaMemcpyToSymbolAsync(c_ace_ynormf, ynf.data(), sizeof(float) * kAceLM, 0, cudaMemcpyHostToDevice, st));
     if (na > 0 && snap->species)
         MALA_CUDA_TRY(cudaMemcpyAsync(d_sp, snap->species, sizeof(int) * na, cudaMemcpyHostToDevice, st));
     AceArgs g;
