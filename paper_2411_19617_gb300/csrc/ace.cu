@@ -44,18 +44,17 @@ template <class T> struct Cx;
 template <> struct Cx<float> { using type = float2; };
 template <> struct Cx<double> { using type = double2; };
 
-// descriptor column: kind 1, 2, 3; channel bases into A (mu n block * n_lm); l values; coefficient
+// descriptor column: kind 1, 2, 3; channel bases into A (mu n block * n_lmf); l values; coefficient
 // list; d: its place in the output row (the kernel takes the columns in descending order of cost)
 struct AceCol {
     int kind, a1, a2, a3, l1, l2, l3, c_off, c_cnt, d;
 };
-// one term of an N = 3 column: A1[i1] A2[i2] A3[i3] (each conjugated when its bit of
-// cj is set: A_{l,-m} = (-1)^m conj(A_{l,m})) times c, the (-1)^m signs folded into c;
-// i = lm_index(l, |m|) within the channel's block; cf = c rounded to FP32 on the host
+// one term of an N = 3 column: c A1[i1] A2[i2] A3[i3], i = lm_full(l, m) within the channel's
+// block (m of either sign), packed as i1 | i2 << 10 | i3 << 20; cf = c rounded to FP32 on the host
 struct AceCoef {
     double c;
     float cf;
-    short i1, i2, i3, cj;
+    uint32_t idx;
 };
 
 struct AceArgs {
@@ -70,7 +69,10 @@ struct AceArgs {
     int n_atoms, grid[3];
     double L[3];
     double rcut;
-    int lmax, nmax, n_species, n_lm, nA, n_desc;
+    int lmax, nmax, n_species;
+    int n_lm;   // (l, m >= 0) elements of a channel: the elements the neighbour sums produce
+    int n_lmf;  // (l, m) elements of a channel, m of either sign: its block in A
+    int nA, n_desc;
     const AceCol* cols;
     const AceCoef* coefs;
     int stage;            // column and coefficient tables copied into shared memory
@@ -78,6 +80,14 @@ struct AceArgs {
 };
 
 __device__ __forceinline__ int lm_index(int l, int m) { return l * (l + 1) / 2 + m; }
+__host__ __device__ __forceinline__ int lm_full(int l, int m) { return l * l + l + m; }  // -l <= m <= l
+
+// (l, m) of the m >= 0 element with index h = lm_index(l, m)
+__device__ __forceinline__ int2 lm_of(int h) {
+    int l = 0;
+    while ((l + 1) * (l + 2) / 2 <= h) ++l;
+    return make_int2(l, h - l * (l + 1) / 2);
+}
 
 // N_lm = sqrt((2l+1)/(4 pi) (l-m)!/(l+m)!) by (l, m >= 0) index, every compiled l
 __constant__ double c_ace_ynorm[kAceLM];
@@ -133,6 +143,15 @@ __global__ void __launch_bounds__(kAceWarps * 32, 3) k_ace(AceArgs g, T* __restr
         __syncthreads();
     }
     C* A = reinterpret_cast<C*>(smem_ace + tab_bytes) + (size_t)warp * g.nA;
+    // the block index of the m >= 0 element this lane adds in each chunk of 16 (see below), and of
+    // the elements h = lane, lane + 32 it mirrors to m < 0 (m = 0: nothing to mirror)
+    int fchunk[(NLM + 15) / 16];
+#pragma unroll
+    for (int c = 0; c < (NLM + 15) / 16; ++c) {
+        const int2 lm = lm_of(16 * c + (lane >> 1));
+        fchunk[c] = lm_full(lm.x, lm.y);
+    }
+    const int2 mir0 = lm_of(lane), mir1 = lm_of(lane + 32);
     for (int64_t p = (int64_t)blockIdx.x * kAceWarps + warp; p < g.P; p += (int64_t)gridDim.x * kAceWarps) {
         for (int e = lane; e < g.nA; e += 32) {
             A[e].x = T(0);
@@ -220,7 +239,7 @@ __global__ void __launch_bounds__(kAceWarps * 32, 3) k_ace(AceArgs g, T* __restr
                         t1 = tn;
                     }
                     const T rn = mine ? tn * fc : T(0);
-                    const int base = (s * g.nmax + nn) * g.n_lm;
+                    const int base = (s * g.nmax + nn) * g.n_lmf;
                     // the (l, m) elements in chunks of 16: v holds (re, im) of chunk element e at 2e, 2e + 1;
                     // after the reduce-scatter lane l holds the warp sum of value l of the chunk
 #pragma unroll
@@ -234,15 +253,28 @@ __global__ void __launch_bounds__(kAceWarps * 32, 3) k_ace(AceArgs g, T* __restr
                             v[2 * e + 1] = c0 + e < NLM ? rn * yi[lm] : T(0);
                         }
                         reduce_scatter<T, 32, 16>(v, lane);
-                        const int lm = c0 + (lane >> 1);
-                        if (lm < g.n_lm) {
-                            if (lane & 1) A[base + lm].y += v[0];
-                            else A[base + lm].x += v[0];
+                        if (c0 + (lane >> 1) < g.n_lm) {
+                            const int f = base + fchunk[c0 / 16];
+                            if (lane & 1) A[f].y += v[0];
+                            else A[f].x += v[0];
                         }
                     }
                 }
             }
             __syncwarp();
+        }
+        __syncwarp();
+        // A_{l,-m} = (-1)^m conj(A_{l,m}), so that the invariants index A by (l, m) of either sign
+        for (int ch = 0; ch < g.n_species * g.nmax; ++ch) {
+            C* Ac = A + ch * g.n_lmf;
+            if (lane < g.n_lm && mir0.y > 0) {
+                const C a = Ac[lm_full(mir0.x, mir0.y)];
+                Ac[lm_full(mir0.x, -mir0.y)] = (mir0.y & 1) ? C{-a.x, a.y} : C{a.x, -a.y};
+            }
+            if (lane + 32 < g.n_lm && mir1.y > 0) {
+                const C a = Ac[lm_full(mir1.x, mir1.y)];
+                Ac[lm_full(mir1.x, -mir1.y)] = (mir1.y & 1) ? C{-a.x, a.y} : C{a.x, -a.y};
+            }
         }
         __syncwarp();
         // invariants
@@ -255,7 +287,7 @@ __global__ void __launch_bounds__(kAceWarps * 32, 3) k_ace(AceArgs g, T* __restr
             } else if (cl.kind == 2) {
                 // sum_m <l m l -m|0 0> Re(A1_m A2_-m) with A_-m = (-1)^m conj(A_m) and <l m l -m|0 0> =
                 // (-1)^(l-m)/sqrt(2l+1): (-1)^l/sqrt(2l+1) (Re(A1_0 A2_0) + 2 sum_{m>0} Re(A1_m conj(A2_m)))
-                const int l = cl.l1, b0 = l * (l + 1) / 2;
+                const int l = cl.l1, b0 = lm_full(l, 0);
                 const C x0 = A[cl.a1 + b0], y0 = A[cl.a2 + b0];
                 T s2 = T(0);
                 for (int m = 1; m <= l; ++m) {
@@ -267,10 +299,8 @@ __global__ void __launch_bounds__(kAceWarps * 32, 3) k_ace(AceArgs g, T* __restr
             } else {
                 for (int q = cl.c_off; q < cl.c_off + cl.c_cnt; ++q) {
                     const AceCoef cf = coefs[q];
-                    C x = A[cl.a1 + cf.i1], y = A[cl.a2 + cf.i2], z = A[cl.a3 + cf.i3];
-                    if (cf.cj & 1) x.y = -x.y;
-                    if (cf.cj & 2) y.y = -y.y;
-                    if (cf.cj & 4) z.y = -z.y;
+                    const C x = A[cl.a1 + (cf.idx & 1023u)], y = A[cl.a2 + ((cf.idx >> 10) & 1023u)],
+                            z = A[cl.a3 + (cf.idx >> 20)];
                     const T pr = x.x * y.x - x.y * y.y, pi_ = x.x * y.y + x.y * y.x;
                     T cv;
                     if constexpr (sizeof(T) == 4) cv = cf.cf;
@@ -311,8 +341,8 @@ static int ace_columns(const mala_ace_params* ap, std::vector<AceCol>* cols, std
     const int ns = ap->n_species;
     const int nmax = std::max(ap->nmax1, std::max(ap->nmax2, ap->nmax3));
     const int lmax = std::max(ap->lmax2, ap->lmax3);
-    const int nlm = (lmax + 1) * (lmax + 2) / 2;
-    auto base = [&](int mu, int n) { return (mu * nmax + n) * nlm; };
+    const int nlmf = (lmax + 1) * (lmax + 1);
+    auto base = [&](int mu, int n) { return (mu * nmax + n) * nlmf; };
     std::vector<AceCol> cl;
     std::vector<AceCoef> cf;
     for (int mu = 0; mu < ns; ++mu)
@@ -344,20 +374,9 @@ static int ace_columns(const mala_ace_params* ap, std::vector<AceCol>* cols, std
                     const double c = clebsch_gordan(2 * l1, 2 * m1, 2 * l2, 2 * m2, 2 * l3, 2 * M) *
                                      clebsch_gordan(2 * l3, 2 * M, 2 * l3, -2 * M, 0, 0);
                     if (c != 0.0) {
-                        // A_{l,m} for m < 0 is (-1)^m conj(A_{l,|m|}): the sign goes into c, the conjugation into cj
-                        const int ms[3] = {m1, m2, -M};
-                        const int ls[3] = {l1, l2, l3};
-                        double cc = c;
-                        short idx[3], cj = 0;
-                        for (int f = 0; f < 3; ++f) {
-                            const int am = ms[f] < 0 ? -ms[f] : ms[f];
-                            idx[f] = (short)(ls[f] * (ls[f] + 1) / 2 + am);
-                            if (ms[f] < 0) {
-                                cj |= (short)(1 << f);
-                                if (am & 1) cc = -cc;
-                            }
-                        }
-                        cf.push_back(AceCoef{cc, (float)cc, idx[0], idx[1], idx[2], cj});
+                        const uint32_t idx = (uint32_t)lm_full(l1, m1) | (uint32_t)lm_full(l2, m2) << 10 |
+                                             (uint32_t)lm_full(l3, -M) << 20;
+                        cf.push_back(AceCoef{c, (float)c, idx});
                     }
                 }
             lists[2 * key + 1] = (int)cf.size() - lists[2 * key];
@@ -407,8 +426,11 @@ int ace_from_lists(Ctx* c, const SnapDev& sd, const mala_snapshot* snap, const m
     const int nd = ace_columns(ap, &cols, &coefs);
     // a warp takes 32 columns at a time and waits for its costliest: order them by cost (terms,
     // an N = 3 term about twice an N = 2 one), so that the columns taken together cost about the same
+    // (columns of equal cost by coefficient list, so that lanes taken together read the same terms)
     auto cost = [](const AceCol& x) { return x.kind == 3 ? 2 * x.c_cnt : x.kind == 2 ? x.l1 + 1 : 1; };
-    std::stable_sort(cols.begin(), cols.end(), [&](const AceCol& x, const AceCol& y) { return cost(x) > cost(y); });
+    std::stable_sort(cols.begin(), cols.end(), [&](const AceCol& x, const AceCol& y) {
+        return cost(x) != cost(y) ? cost(x) > cost(y) : x.c_off < y.c_off;
+    });
     const int nmax = std::max(ap->nmax1, std::max(ap->nmax2, ap->nmax3));
     const int lmax = std::max(ap->lmax2, ap->lmax3);
     const int nlm = (lmax + 1) * (lmax + 2) / 2;
@@ -457,7 +479,8 @@ int ace_from_lists(Ctx* c, const SnapDev& sd, const mala_snapshot* snap, const m
     g.nmax = nmax;
     g.n_species = ap->n_species;
     g.n_lm = nlm;
-    g.nA = ap->n_species * nmax * nlm;
+    g.n_lmf = (lmax + 1) * (lmax + 1);
+    g.nA = ap->n_species * nmax * g.n_lmf;
     g.n_desc = nd;
     g.cols = d_cols;
     g.coefs = d_coef;
