@@ -373,10 +373,15 @@ static int ace_columns(const mala_ace_params* ap, std::vector<AceCol>* cols, std
                     if (M < -l3 || M > l3) continue;
                     const double c = clebsch_gordan(2 * l1, 2 * m1, 2 * l2, 2 * m2, 2 * l3, 2 * M) *
                                      clebsch_gordan(2 * l3, 2 * M, 2 * l3, -2 * M, 0, 0);
-                    if (c != 0.0) {
+                    // (-m1, -m2, M) gives the conjugate of the (m1, m2, -M) product with the same
+                    // coefficient (l1 + l2 + l3 even, A_{l,-m} = (-1)^m conj(A_{l,m}), A_{l,0} real):
+                    // keep M > 0, or M = 0 and m1 > 0, at twice the weight, and the all-zero term once
+                    const bool upper = M > 0 || (M == 0 && m1 > 0);
+                    if (c != 0.0 && (upper || (m1 == 0 && m2 == 0))) {
+                        const double cw = upper ? 2.0 * c : c;
                         const uint32_t idx = (uint32_t)lm_full(l1, m1) | (uint32_t)lm_full(l2, m2) << 10 |
                                              (uint32_t)lm_full(l3, -M) << 20;
-                        cf.push_back(AceCoef{c, (float)c, idx});
+                        cf.push_back(AceCoef{cw, (float)cw, idx});
                     }
                 }
             lists[2 * key + 1] = (int)cf.size() - lists[2 * key];
