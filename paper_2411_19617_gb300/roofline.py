@@ -181,19 +181,27 @@ def force_flops_per_pair(twojmax: int) -> int:
     return f
 
 
-def ace_flops(ap, pairs: int, points: int) -> int:
+def ace_flops(ap, pairs: int, points: int, folded: bool = False) -> int:
     """Algorithmic FLOP of the ACE descriptors: per neighbour pair the spherical
     harmonics (8 per (l, m >= 0)), the Chebyshev radial functions (3 per n) and the
     grid-basis accumulation (4 per (n, l, m >= 0): real R times complex Y, added);
     per point the invariants (N = 2: 4 per m; N = 3: 10 per (m1, m2) term with a nonzero
-    Clebsch-Gordan factor)."""
+    Clebsch-Gordan factor).  folded: count the invariant terms a kernel evaluates after the
+    conjugate symmetry A_{l,-m} = (-1)^m conj(A_{l,m}) pairs them (N = 2: m >= 0 only;
+    N = 3: M > 0, or M = 0 and m1 >= 0 with m1 = 0 only for the all-zero term)."""
     nmax = max(ap.nmax1, ap.nmax2, ap.nmax3)
     lmax = max(ap.lmax2, ap.lmax3)
     nlm = (lmax + 1) * (lmax + 2) // 2
     per_pair = 8 * nlm + 3 * nmax + 4 * nmax * nlm
     ns = ap.n_species
     n2ch = ns * ap.nmax2
-    per_point = (n2ch * (n2ch + 1) // 2) * sum(4 * (2 * l + 1) for l in range(ap.lmax2 + 1))
+    per_m2 = [(l + 1) if folded else (2 * l + 1) for l in range(ap.lmax2 + 1)]
+    per_point = (n2ch * (n2ch + 1) // 2) * sum(4 * k for k in per_m2)
+
+    def kept(m1, m2):
+        M = m1 + m2
+        return not folded or M > 0 or (M == 0 and m1 >= 0)
+
     ch3 = [(mu, n, l) for mu in range(ns) for n in range(ap.nmax3) for l in range(ap.lmax3 + 1)]
     terms = {}
     for i in range(len(ch3)):
@@ -204,7 +212,7 @@ def ace_flops(ap, pairs: int, points: int) -> int:
                     key = (l1, l2, l3)
                     if key not in terms:
                         terms[key] = sum(1 for m1 in range(-l1, l1 + 1) for m2 in range(-l2, l2 + 1)
-                                         if abs(m1 + m2) <= l3
+                                         if abs(m1 + m2) <= l3 and kept(m1, m2)
                                          and cg_nonzero(2 * l1, 2 * m1, 2 * l2, 2 * m2, 2 * l3, 2 * (m1 + m2)))
                     per_point += 10 * terms[key]
     return per_pair * pairs + per_point * points
