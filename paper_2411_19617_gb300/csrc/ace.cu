@@ -10,7 +10,8 @@
 //   Ptilde_m^m = (-1)^m (2m-1)!!,  Ptilde_{m+1}^m = (2m+1) z Ptilde_m^m,
 //   (l - m) Ptilde_l^m = (2l-1) z Ptilde_{l-1}^m - (l+m-1) Ptilde_{l-2}^m,
 // a polynomial form that needs no angle and no division at the poles; only
-// m >= 0 is stored (A_{l,-m} = (-1)^m conj(A_{l,m}) for a real density).
+// m >= 0 is summed over the neighbours (A_{l,-m} = (-1)^m conj(A_{l,m}) for a
+// real density fills the rest).
 // Invariants: N = 1: A_{mu n 0 0}; N = 2: sum_m <l m l -m|0 0> A_{c1 l m} A_{c2 l -m};
 // N = 3: sum <l1 m1 l2 m2|l3 M><l3 M l3 -M|0 0> A_{c1 l1 m1} A_{c2 l2 m2} A_{c3 l3 -M}.
 //
@@ -18,8 +19,12 @@
 // lane evaluates R_n and Y_l^m of its neighbour, and for every (species, n) a
 // reduce-scatter over the warp (fixed order: deterministic) leaves lane l with
 // the batch's sum of value l of a chunk of 16 (l, m) elements (re, im), which
-// it adds into the warp's shared-memory copy of A.  The lanes then take descriptor columns and contract
-// A with host-built coefficient lists; each row is written coalesced.
+// it adds into the warp's shared-memory copy of A; the m < 0 elements are then
+// filled by the symmetry.  The lanes then take descriptor columns, in descending
+// order of cost so that the 32 columns taken together cost about the same, and
+// contract A with host-built coefficient lists (N = 2 over m >= 0 and N = 3 over
+// half of the (m1, m2) plane: the other half gives the complex conjugates), each
+// column written to its place in the row.
 #include <cuda_runtime.h>
 
 #include <algorithm>
