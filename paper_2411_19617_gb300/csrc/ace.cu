@@ -129,8 +129,11 @@ __device__ __forceinline__ void reduce_scatter(T (&v)[N], int lane) {
 
 // LMX: the largest l the kernel evaluates (4, 6 or 8, at least lmax); STAGE: the column and
 // coefficient tables are copied into shared memory (else read from global memory)
+// (FP32 up to l = 6: four CTAs per SM, 128 registers without spills, 16 warps to hide the shuffle
+// and shared-load latencies; l = 8 and FP64 need more registers and keep three)
 template <class T, int LMX, bool STAGE>
-__global__ void __launch_bounds__(kAceWarps * 32, 3) k_ace(AceArgs g, T* __restrict__ out) {
+__global__ void __launch_bounds__(kAceWarps * 32, (sizeof(T) == 4 && LMX <= 6) ? 4 : 3)
+    k_ace(AceArgs g, T* __restrict__ out) {
     constexpr int NLM = (LMX + 1) * (LMX + 2) / 2;
     using C = typename Cx<T>::type;
     extern __shared__ __align__(16) unsigned char smem_ace[];
