@@ -167,9 +167,12 @@ __global__ void __launch_bounds__(kAceWarps * 32, (sizeof(T) == 4 && LMX <= 6) ?
         }
         __syncwarp();
         const int n = min(g.cnt[p], g.cap);
-        const int ix = (int)(p % g.grid[0]);
-        const int iy = (int)((p / g.grid[0]) % g.grid[1]);
-        const int iz = (int)(p / ((int64_t)g.grid[0] * g.grid[1]));
+        // grid index in 32 bits (P < 2^32, checked on the host)
+        const uint32_t pu = (uint32_t)p, gx = (uint32_t)g.grid[0], gy = (uint32_t)g.grid[1];
+        const uint32_t pyz = pu / gx;
+        const int ix = (int)(pu - pyz * gx);
+        const int iy = (int)(pyz % gy);
+        const int iz = (int)(pyz / gy);
         const double rx = g.gcoord[ix], ry = g.gcoord[g.grid[0] + iy], rz = g.gcoord[g.grid[0] + g.grid[1] + iz];
         for (int k0 = 0; k0 < n; k0 += 32) {
             const int k = k0 + lane;
@@ -324,24 +327,32 @@ __global__ void __launch_bounds__(kAceWarps * 32, (sizeof(T) == 4 && LMX <= 6) ?
 
 }  // namespace
 
-// the kernel with the table path the arguments ask for
+// the kernel with the table path the arguments ask for, as one wave of the CTAs the SMs hold at once
+// (the warps stride over the points, so a second wave would only add a partly idle tail)
+template <class T, int LMX, bool STAGE>
+static void launch_ace_k(int64_t want, int sms, size_t smem, const AceArgs& g, T* out, cudaStream_t st) {
+    cudaFuncSetAttribute(k_ace<T, LMX, STAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ace<T, LMX, STAGE>, kAceWarps * 32, smem) !=
+            cudaSuccess ||
+        per_sm < 1)
+        per_sm = 1;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms * per_sm));
+    k_ace<T, LMX, STAGE><<<grid, kAceWarps * 32, smem, st>>>(g, out);
+}
+
 template <class T, int LMX>
-static void launch_ace_l(int grid, size_t smem, const AceArgs& g, T* out, cudaStream_t st) {
-    if (g.stage) {
-        cudaFuncSetAttribute(k_ace<T, LMX, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_ace<T, LMX, true><<<grid, kAceWarps * 32, smem, st>>>(g, out);
-    } else {
-        cudaFuncSetAttribute(k_ace<T, LMX, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_ace<T, LMX, false><<<grid, kAceWarps * 32, smem, st>>>(g, out);
-    }
+static void launch_ace_l(int64_t want, int sms, size_t smem, const AceArgs& g, T* out, cudaStream_t st) {
+    if (g.stage) launch_ace_k<T, LMX, true>(want, sms, smem, g, out, st);
+    else launch_ace_k<T, LMX, false>(want, sms, smem, g, out, st);
 }
 
 // the kernel compiled for the smallest supported l range that covers lmax
 template <class T>
-static void launch_ace(int lmax, int grid, size_t smem, const AceArgs& g, T* out, cudaStream_t st) {
-    if (lmax <= 4) launch_ace_l<T, 4>(grid, smem, g, out, st);
-    else if (lmax <= 6) launch_ace_l<T, 6>(grid, smem, g, out, st);
-    else launch_ace_l<T, kAceLMax>(grid, smem, g, out, st);
+static void launch_ace(int lmax, int64_t want, int sms, size_t smem, const AceArgs& g, T* out, cudaStream_t st) {
+    if (lmax <= 4) launch_ace_l<T, 4>(want, sms, smem, g, out, st);
+    else if (lmax <= 6) launch_ace_l<T, 6>(want, sms, smem, g, out, st);
+    else launch_ace_l<T, kAceLMax>(want, sms, smem, g, out, st);
 }
 
 // columns in the order of the documented enumeration; returns the count
@@ -434,6 +445,8 @@ int check_ace_params(const mala_ace_params* ap) {
 // ACE descriptors of one snapshot from its staged atoms and complete neighbour lists
 int ace_from_lists(Ctx* c, const SnapDev& sd, const mala_snapshot* snap, const mala_ace_params* ap,
                    const NbrOut& nl, void* out, mala_precision prec, cudaStream_t st) {
+    if (sd.g.P >= ((int64_t)1 << 32))  // the kernel's grid-index arithmetic is 32-bit
+        return fail(MALA_ERR_UNSUPPORTED, "ACE descriptors need fewer than 2^32 grid points");
     std::vector<AceCol> cols;
     std::vector<AceCoef> coefs;
     const int nd = ace_columns(ap, &cols, &coefs);
@@ -501,14 +514,14 @@ int ace_from_lists(Ctx* c, const SnapDev& sd, const mala_snapshot* snap, const m
     g.stage = ace_table_bytes(nd, g.n_coef) <= (size_t)96 * 1024 ? 1 : 0;
     if (g.P > 0 && nd > 0) {
         const int64_t want = (g.P + kAceWarps - 1) / kAceWarps;
-        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)c->num_sms * 8));
+        const int sms = std::max(1, c->num_sms);
         const size_t tb = g.stage ? ace_table_bytes(nd, g.n_coef) : 0;
         if (prec == MALA_MIXED) {
             const size_t smem = tb + sizeof(float2) * (size_t)g.nA * kAceWarps;
-            MALA_PROF(c, "k_ace", st, (launch_ace<float>(lmax, grid, smem, g, static_cast<float*>(out), st)));
+            MALA_PROF(c, "k_ace", st, (launch_ace<float>(lmax, want, sms, smem, g, static_cast<float*>(out), st)));
         } else {
             const size_t smem = tb + sizeof(double2) * (size_t)g.nA * kAceWarps;
-            MALA_PROF(c, "k_ace", st, (launch_ace<double>(lmax, grid, smem, g, static_cast<double*>(out), st)));
+            MALA_PROF(c, "k_ace", st, (launch_ace<double>(lmax, want, sms, smem, g, static_cast<double*>(out), st)));
         }
         MALA_CUDA_TRY(cudaGetLastError());
     }
