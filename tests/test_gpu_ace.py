@@ -65,3 +65,23 @@ def test_ace_full_al_workload_sampled():
     got = D[torch.as_tensor(pts, device=D.device)].double().cpu().numpy()
     ref = ace.ace_grid(s, ap, points=pts)
     assert descriptor_error(got, ref) < 2e-5
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_ace_tables_in_global_memory(precision):
+    """A column set whose tables exceed what the kernel stages in shared memory (96 KB): 2,501
+    columns, whose column table alone takes 97.7 KB at 40 bytes a column, so the kernel reads the
+    column and coefficient tables from global memory; sampled points against the oracle."""
+    torch = need_gpu()
+    from paper_2411_19617_gb300 import api
+    c = ctx()
+    snap = wl.al_fcc(2, 0.2, 6, seed=12)
+    ap = ace.AceParams(rcut=4.676, nmax1=2, nmax2=2, lmax2=2, nmax3=5, lmax3=6)
+    assert api.ace_count(ap) * 40 > 96 * 1024
+    prec = api.MIXED if precision == "mixed" else api.FP64_PLAIN
+    D = c.ace_descriptors(snap, ap, prec)
+    pts = wl.sample_points(snap.n_points, 6, seed=4)
+    got = D[torch.as_tensor(pts, device=D.device)].double().cpu().numpy()
+    ref = ace.ace_grid(snap, ap, points=pts)
+    err = descriptor_error(got, ref)
+    assert err < (1e-10 if precision == "fp64" else 2e-5), err
